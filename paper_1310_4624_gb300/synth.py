@@ -1,0 +1,165 @@
+"""Seeded synthetic inputs: workload presets and spot-tracking image sequences.
+
+This module is the one piece shared by the CUDA path's tests/benchmark and the
+CPU oracle.  It holds no filter arithmetic: it renders frames and ground truth
+and names the parameter sets.  The paper's own ten 512x512 sequences are not
+available; these stand in for them with the appearance model the paper
+describes (Sec. V, Fig. 1): a small isotropic Gaussian spot of amplitude A on
+background b, Poisson noise, moving under constant velocity.
+
+Recipe (all draws from ``numpy.random.default_rng(data_seed)``):
+  * start position uniform in the central region [H/4, 3H/4) x [W/4, 3W/4)
+    (64x64 frames: [16, 48)^2, the central 32x32);
+  * velocity uniform in [-vmax, vmax]^2, redrawn until the whole track stays at
+    least ``margin`` px inside the frame;
+  * frame k: z(u, v) ~ Poisson(b + A exp(-((u - x_k)^2 + (v - y_k)^2) / (2 s^2)))
+    as float32, pixel (u, v) = (column, row) centred at integer coordinates.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Tuple
+
+import numpy as np
+
+RNA, ARNA = 0, 1
+INIT_POINT, INIT_UNIFORM, INIT_SHARING = 0, 1, 2
+
+
+@dataclasses.dataclass
+class Workload:
+    """Parameters of one tracking workload (one track)."""
+    name: str
+    G: int
+    Np: int
+    H: int
+    W: int
+    T: int
+    mode: int = RNA
+    sigma_psf: float = 1.5
+    amplitude: float = 10.0
+    background: float = 1.0
+    sigma_obs: float = 1.0
+    sigma_pos: float = 0.5
+    sigma_v: float = 0.1
+    sigma_I: float = 0.5
+    ex_ratio: float = 0.10
+    pe_eff_cutoff: float = 0.99
+    patch_radius: int = 5
+    seed: int = 0          # Philox key of the filter
+    data_seed: int = 0     # numpy seed of the sequence
+    init: int = INIT_POINT
+    vmax: float = 1.0
+    margin: float = 6.0
+    share_radius: float = 2.0     # information-sharing init: disc radius of group 0
+    share_vmax: float = 2.0       # other groups: velocity range
+    share_I: Tuple[float, float] = (1.0, 20.0)
+
+    @property
+    def N(self) -> int:
+        return self.G * self.Np
+
+    def replace(self, **kw) -> "Workload":
+        return dataclasses.replace(self, **kw)
+
+
+def small_rna(**kw) -> Workload:
+    """One 20-frame 64x64 track, G=4 x 1024, RNA 10% on the fixed ring."""
+    return Workload(name="small_rna_64x64_G4x1024", G=4, Np=1024, H=64, W=64, T=20, mode=RNA).replace(**kw)
+
+
+def tracking(mode: int = ARNA, **kw) -> Workload:
+    """100 frames 512x512, G=64 x 16384 (1,048,576 particles), init at the truth."""
+    name = "tracking_512x512_G64x16384_" + ("arna" if mode == ARNA else "rna10")
+    return Workload(name=name, G=64, Np=16384, H=512, W=512, T=100, mode=mode).replace(**kw)
+
+
+def sharing(mode: int = ARNA, **kw) -> Workload:
+    """100 frames 512x512, G=256 x 4096; group 0 near the truth, the rest uniform."""
+    name = "sharing_512x512_G256x4096_" + ("arna" if mode == ARNA else "rna10")
+    return Workload(name=name, G=256, Np=4096, H=512, W=512, T=100, mode=mode,
+                    init=INIT_SHARING).replace(**kw)
+
+
+def differentiable(**kw) -> Workload:
+    """50 frames 512x512, G=16 x 65536, ARNA."""
+    return Workload(name="grad_512x512_G16x65536", G=16, Np=65536, H=512, W=512, T=50,
+                    mode=ARNA).replace(**kw)
+
+
+def batched_tracks(n_tracks: int = 512, seed: int = 0, H: int = 256, W: int = 256, T: int = 50,
+                   n_range=(4096, 262144), g_range=(4, 128)) -> List[Workload]:
+    """Independent tracks with log-uniform particle and group counts; N_t is
+    rounded down to a multiple of G_t."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for t in range(n_tracks):
+        n = int(round(math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))))
+        g = int(round(math.exp(rng.uniform(math.log(g_range[0]), math.log(g_range[1])))))
+        amp = float(rng.uniform(5.0, 20.0))
+        spsf = float(rng.uniform(1.2, 2.0))
+        out.append(Workload(name="batched_%d" % t, G=g, Np=max(1, n // g), H=H, W=W, T=T, mode=ARNA,
+                            sigma_psf=spsf, amplitude=amp, seed=seed, data_seed=1000 + t))
+    return out
+
+
+def truth_track(wl: Workload) -> np.ndarray:
+    """Ground truth (T, 5): x, y, vx, vy, I with constant velocity."""
+    rng = np.random.default_rng(wl.data_seed)
+    H, W, T = wl.H, wl.W, wl.T
+    x0 = rng.uniform(W / 4, 3 * W / 4)
+    y0 = rng.uniform(H / 4, 3 * H / 4)
+    for _ in range(10000):
+        vx, vy = rng.uniform(-wl.vmax, wl.vmax, size=2)
+        xs = x0 + vx * np.arange(T)
+        ys = y0 + vy * np.arange(T)
+        if (xs.min() >= wl.margin and xs.max() <= W - 1 - wl.margin and
+                ys.min() >= wl.margin and ys.max() <= H - 1 - wl.margin):
+            break
+    else:  # pragma: no cover - the central start always admits small velocities
+        vx = vy = 0.0
+        xs = np.full(T, x0)
+        ys = np.full(T, y0)
+    tr = np.zeros((T, 5))
+    tr[:, 0], tr[:, 1], tr[:, 2], tr[:, 3], tr[:, 4] = xs, ys, vx, vy, wl.amplitude
+    return tr
+
+
+def render(wl: Workload, truth: np.ndarray, rng: np.random.Generator, noise: bool = True) -> np.ndarray:
+    """Frames (T, H, W) float32 of the spot along ``truth``."""
+    T = truth.shape[0]
+    u = np.arange(wl.W, dtype=np.float64)
+    v = np.arange(wl.H, dtype=np.float64)
+    frames = np.empty((T, wl.H, wl.W), np.float32)
+    s2 = 2.0 * wl.sigma_psf ** 2
+    for k in range(T):
+        gx = np.exp(-(u - truth[k, 0]) ** 2 / s2)
+        gy = np.exp(-(v - truth[k, 1]) ** 2 / s2)
+        lam = wl.background + truth[k, 4] * np.outer(gy, gx)
+        frames[k] = rng.poisson(lam).astype(np.float32) if noise else lam.astype(np.float32)
+    return frames
+
+
+def make_sequence(wl: Workload, noise: bool = True, T: Optional[int] = None):
+    """(frames (T, H, W) float32, truth (T, 5) float64) for a workload."""
+    if T is not None:
+        wl = wl.replace(T=T)
+    truth = truth_track(wl)
+    rng = np.random.default_rng([wl.data_seed, 1])
+    return render(wl, truth, rng, noise=noise), truth
+
+
+def init_arrays(wl: Workload, truth0: np.ndarray):
+    """(kind, x0[5], lo[5], hi[5], radius) of the initial population.
+
+    POINT: every particle at the truth (tracking mode, Sec. V).  SHARING:
+    group 0 in a disc of ``share_radius`` around the truth with the true
+    velocity and intensity; the other groups uniform over the image, with
+    velocity in [-share_vmax, share_vmax]^2 and intensity in ``share_I``
+    (information-sharing mode, Sec. V).
+    """
+    x0 = np.array(truth0, np.float64)
+    lo = np.array([0.0, 0.0, -wl.share_vmax, -wl.share_vmax, wl.share_I[0]])
+    hi = np.array([wl.W - 1.0, wl.H - 1.0, wl.share_vmax, wl.share_vmax, wl.share_I[1]])
+    return wl.init, x0, lo, hi, wl.share_radius
