@@ -1,0 +1,327 @@
+"""Benchmark: particle-steps/s of the RNA / ARNA filter step on GB300.
+
+Workload (the tracking scenario): one 512x512 spot-tracking sequence, G = 64
+groups x 16384 particles (1,048,576), particles initialised at the truth,
+ARNA (adaptive exchange share, random ring each step); the RNA 10% fixed-ring
+run on the same Philox streams is reported beside it.  Synthetic frames
+(see paper_1310_4624_gb300/synth.py).
+
+One timed step = one pf_step over all particles: frame preparation,
+exchange + propagation + likelihood, per-group resampling and the global
+reduction / next-step ring and ratio.  L2 is flushed (a 256 MB write)
+between timed steps, outside the timed interval; each step is timed with
+CUDA events on the launch stream.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica (its own seed and
+sequence): the path does not shard across GPUs, so N > 1 is weak scaling.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (propagate+weight+ARNA)"
+UNIT = "particle-steps/s"
+
+# Algorithmic work of the dominant kernel (propagate_weight) per particle and
+# step; derivation in DESIGN.md ("Roofline").
+ALG_LANE_OPS = 540      # FP32 + INT32 lane operations
+ALG_SFU_OPS = 35        # MUFU operations
+ALG_BYTES = 48          # HBM bytes of the whole step per particle
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(n)
+        out.update(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=sorted(reasons), samples=len(rows))
+        return out
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(x: float, ws: int, dev) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def time_filter(pf, fr, first: int, K: int, flush, profile: bool):
+    """Device time (ms) of K steps, L2 flushed before each."""
+    import torch
+    stream = pf.stream
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    if profile:
+        pf.profile(True)
+    for i in range(K):
+        flush.zero_()
+        evs[i][0].record(stream)
+        pf.step(fr[first + i])
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    if profile:
+        pf.profile(False)
+    return sum(a.elapsed_time(b) for a, b in evs)
+
+
+def cpu_baseline(wl, frames, truth, steps: int = 2):
+    """The FP64 oracle as it stands, single-threaded, on the full workload
+    population for `steps` steps after an untimed step 0."""
+    import oracle as ora
+    ocfg = ora.cfg_from_workload(wl)
+    pop = ora.init_population(ocfg, ora.INIT_POINT, np.float32(truth[0]).astype(np.float64))
+    r = ora.step(ocfg, 0, frames[0], pop)
+    t0 = time.perf_counter()
+    for k in range(1, steps + 1):
+        r = ora.step(ocfg, k, frames[k], r.pop_out, r.Lambda)
+    dt = time.perf_counter() - t0
+    return {"value": wl.N * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d oracle steps (k=1..%d) of the full %d-particle workload, FP64, 1 thread, %.1f s"
+                      % (steps, steps, wl.N, dt)}
+
+
+def run_reference(args, ws, rank):
+    """The reference arm: the CPU oracle, timed as it stands, on a bounded
+    sample of the same workload (all 64 groups, 1024 particles each)."""
+    if rank != 0:
+        return
+    import oracle as ora
+    from paper_1310_4624_gb300 import synth
+    K, W = args.steps, args.warmup
+    full = synth.tracking(mode=synth.ARNA, T=max(K + W + 1, 8))
+    wl = full.replace(Np=1024)
+    frames, truth = synth.make_sequence(wl)
+    ocfg = ora.cfg_from_workload(wl)
+    pop = ora.init_population(ocfg, ora.INIT_POINT, np.float32(truth[0]).astype(np.float64))
+    lam = None
+    for k in range(W):
+        r = ora.step(ocfg, k, frames[k], pop, lam)
+        pop, lam = r.pop_out, r.Lambda
+    t0 = time.perf_counter()
+    for k in range(W, W + K):
+        r = ora.step(ocfg, k, frames[k], pop, lam)
+        pop, lam = r.pop_out, r.Lambda
+    dt = time.perf_counter() - t0
+    value = wl.N * K / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
+            "warmup": W, "ms_per_step": dt / K * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": full.name, "particles": full.N, "G": full.G, "Np": full.Np,
+                       "frame": "%dx%d" % (full.H, full.W), "mode": "ARNA",
+                       "sample": "G=64 x 1024 particles per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "each step: all 64 groups x 1024 particles of the workload, FP64 oracle, "
+                                       "1 thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_setup()
+    K, W = args.steps, max(3, args.warmup)
+
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1310_4624_gb300 import synth
+    from paper_1310_4624_gb300.filter import ParticleFilter, config_from_workload
+
+    T = W + K + 1
+    res = {}
+    for mode in (synth.ARNA, synth.RNA):
+        wl = synth.tracking(mode=mode, T=T, seed=rank, data_seed=rank)
+        frames, truth = synth.make_sequence(wl)
+        fr = torch.from_numpy(frames).to(dev)
+        pf = ParticleFilter([config_from_workload(wl, truth[0], track_id=0)], history=T + 1, device=dev)
+        for k in range(W):
+            pf.step(fr[k])
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local) if mode == synth.ARNA else None
+        barrier(ws)
+        if sampler:
+            sampler.start()
+        ms = time_filter(pf, fr, W, K, flush, profile=True)
+        clocks = sampler.stop() if sampler else None
+        barrier(ws)
+        prof = pf.profile_read()
+        hs = pf.history_stats(0, W + K)
+        rmse = math.sqrt(np.mean([np.sum((h["xhat"][:2] - truth[h["step"], :2]) ** 2) for h in hs]))
+        res[mode] = dict(wl=wl, ms=reduce_max(ms, ws, dev), prof=prof, clocks=clocks, rmse=rmse,
+                         n_ex=[h["n_ex"] for h in hs], frames=frames, truth=truth)
+        pf.close()
+        del flush
+
+    # end to end through the public API: pinned host frame -> device, step,
+    # estimate read back to the host, every step
+    wl = res[synth.ARNA]["wl"]
+    frames = res[synth.ARNA]["frames"]
+    truth = res[synth.ARNA]["truth"]
+    host = torch.from_numpy(frames).pin_memory()
+    dbuf = torch.empty((2, wl.H, wl.W), dtype=torch.float32, device=dev)
+    pf = ParticleFilter([config_from_workload(wl, truth[0])], history=T + 1, device=dev)
+    for k in range(W):
+        dbuf[k & 1].copy_(host[k], non_blocking=True)
+        pf.step(dbuf[k & 1])
+        pf.estimate()
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for k in range(W, W + K):
+        dbuf[k & 1].copy_(host[k], non_blocking=True)
+        pf.step(dbuf[k & 1])
+        pf.estimate()
+    t1 = time.perf_counter()
+    e2e_s = reduce_max(t1 - t0, ws, dev)
+    pf.close()
+
+    a = res[synth.ARNA]
+    n_all = wl.N * ws
+    value = n_all * K / (a["ms"] / 1e3)
+    peaks, src = _peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    lane_peak = sms * 128 * f_max
+    k1_launches, k1_ms = a["prof"]["propagate_weight"]
+    k1_avg_s = k1_ms / 1e3 / max(1, k1_launches)
+    achieved = ALG_LANE_OPS * wl.N / k1_avg_s
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": lane_peak / 1e12, "unit": "Tops/s",
+                "frac": achieved / lane_peak, "traffic": None,
+                "kernel": "k_propagate_weight", "peak_source": "%d SMs x 128 lanes x %.0f MHz (%s sm_max_mhz)"
+                % (sms, f_max / 1e6, src),
+                "kernel_ms": k1_avg_s * 1e3,
+                "hbm_frac": ALG_BYTES * wl.N / k1_avg_s / (float(peaks["hbm_gbs"]) * 1e9),
+                "sfu_frac": ALG_SFU_OPS * wl.N / k1_avg_s / (sms * 16 * f_max)}
+    kernels = {n: {"launches": c, "ms_per_step": ms / max(1, c), "share": ms / max(1e-12, sum(
+        v[1] for v in a["prof"].values()))} for n, (c, ms) in a["prof"].items()}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+            "ms_per_step": a["ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": a["wl"].name, "particles": wl.N, "G": wl.G, "Np": wl.Np,
+                       "frame": "%dx%d" % (wl.H, wl.W), "mode": "ARNA", "init": "all particles at the truth",
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "flushed (256 MB write) before every timed step, outside the timed interval"},
+            "e2e": {"value": n_all * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": wl.H * wl.W * 4,
+                    "d2h_bytes_per_step": 5 * 4 + 8},
+            "gpu_launches": K * 4,
+            "roofline": roofline,
+            "kernels": kernels,
+            "clocks": a["clocks"],
+            "rmse_px": a["rmse"],
+            "rna10": {"value": n_all * K / (res[synth.RNA]["ms"] / 1e3), "ms_per_step": res[synth.RNA]["ms"] / K,
+                      "rmse_px": res[synth.RNA]["rmse"]},
+            "arna_n_ex": a["n_ex"][:12]}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, frames, truth)
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,236 @@
+/*
+ * pfarna.h -- C ABI of libpfarna, a GB300 (sm_103a) particle filter with
+ * distributed resampling by non-proportional allocation, RNA and adaptive
+ * RNA (ARNA), after Demirel, Smal, Niessen, Meijering, Sbalzarini, "An
+ * Adaptive Distributed Resampling Algorithm with Non-Proportional
+ * Allocation" (arXiv:1310.4624).
+ *
+ * One call of pf_step advances every track of a handle by one time step of
+ * the paper's Alg. 3 (ARNA) or Alg. 2 (RNA): ring order (Sec. IV-B), exchange
+ * count (Eq. 3, Eq. 4), ring exchange with fixed group sizes (Sec. III-A),
+ * renormalisation, propagation and likelihood weighting (Alg. 1 steps P and
+ * U), group estimate and weight, per-group systematic resampling, and the
+ * global reduction the paper assigns to a master PE.  The paper's M
+ * processing elements are G groups of N_p particles inside one GPU.
+ *
+ * Conventions for every function below:
+ *   - Pointers named *_dev are device pointers, *_host are host pointers.
+ *   - Particle slot i = g * Np + j (group g, slot j) inside a track; arrays
+ *     that span several tracks concatenate the tracks in handle order.
+ *   - State vectors are (x, y, vx, vy, I): position in pixels (x = column,
+ *     y = row, pixel centres at integer coordinates), velocity in pixels per
+ *     frame, spot amplitude.  Device state arrays passed across this ABI are
+ *     structure-of-arrays float32, component-major: 5 rows of N floats.
+ *   - Frames are H x W float32, row-major, device-resident.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  Calls enqueue work and return without synchronising,
+ *     except pf_estimate, pf_exchange_stats and pf_history, which copy to the
+ *     host and wait for the handle's last stream.
+ *   - Every call returns a pf_status; nothing is thrown across the ABI.  On
+ *     failure the text of the error is available from pf_last_error.
+ *   - The caller owns all device memory (workspace, frames, outputs); the
+ *     handle owns only host-side metadata and is freed by pf_destroy.
+ *   - Device faults detected by the kernels (bad index, bounded wait
+ *     exhausted, internal invariant) set a device error word; it is read and
+ *     reported (PF_ERR_DEVICE / PF_ERR_TIMEOUT) by the next call that
+ *     synchronises.
+ */
+#ifndef PFARNA_H
+#define PFARNA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PF_ABI_VERSION 1
+
+typedef enum pf_status {
+  PF_OK = 0,
+  PF_ERR_ARG = 1,        /* invalid argument (sizes, NULL, unsupported config) */
+  PF_ERR_STATE = 2,      /* call out of order (e.g. stats for a step not run) */
+  PF_ERR_CUDA = 3,       /* a CUDA runtime call failed */
+  PF_ERR_WORKSPACE = 4,  /* workspace too small or misaligned */
+  PF_ERR_DEGENERATE = 5, /* every group of a track lost all weight */
+  PF_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up */
+  PF_ERR_DEVICE = 7      /* a kernel reported an internal error */
+} pf_status;
+
+/* Exchange schedule (Sec. III-B, Sec. IV). */
+enum { PF_RNA = 0, PF_ARNA = 1 };
+
+/* Initial population (Sec. V, "tracking" and "information sharing"). */
+enum {
+  PF_INIT_POINT = 0,   /* every particle at init_state */
+  PF_INIT_UNIFORM = 1, /* component d uniform in [init_lo[d], init_hi[d]] */
+  PF_INIT_SHARING = 2, /* group 0: position uniform in the disc of radius
+                          init_radius around init_state, other components of
+                          init_state; groups >= 1: as PF_INIT_UNIFORM */
+  PF_INIT_USER = 3     /* copied from pf_init's user_state_dev */
+};
+
+/* One track's filter.  Observation model (Sec. V, Fig. 1): a Gaussian spot
+ * of width sigma_psf and amplitude I on background `background`; the
+ * log-likelihood of a particle is -sum (z - background - I gx gy)^2 /
+ * (2 sigma_obs^2) over the (2 patch_radius + 1)^2 pixels around its nearest
+ * pixel, pixels outside the frame counting as background.  Dynamics: nearly
+ * constant velocity with unit frame interval and independent Gaussian noise
+ * sigma_pos (position), sigma_v (velocity), sigma_I (intensity). */
+typedef struct pf_track_config {
+  int32_t G;            /* groups (the paper's M PEs), 1 .. 4096 */
+  int32_t Np;           /* particles per group (N_p = N / M), 1 .. 2^24 / G */
+  int32_t H, W;         /* frame size, 1 .. 16384 each */
+  int32_t patch_radius; /* 1 .. 7; the paper's workloads use 5 (11 x 11) */
+  int32_t mode;         /* PF_RNA or PF_ARNA */
+  float sigma_psf, background, sigma_obs;
+  float sigma_pos, sigma_v, sigma_I;
+  float ex_ratio;       /* PF_RNA: N_ex = floor(ex_ratio * Np), ex_ratio in [0, 1] */
+  float pe_eff_cutoff;  /* PF_ARNA: no exchange once PE_eff >= cutoff * G (0.99) */
+  int32_t init_kind;    /* PF_INIT_* */
+  float init_state[5];
+  float init_lo[5];
+  float init_hi[5];
+  float init_radius;
+  int32_t reserved0;    /* must be 0 */
+  uint64_t seed;        /* Philox4x32-10 key */
+  uint32_t track_id;    /* Philox stream id of this track, < 2^24 */
+  int32_t record_ancestors; /* 1: keep per-step ancestry for pf_backward */
+} pf_track_config;
+
+/* Statistics of one completed step of one track. */
+typedef struct pf_step_stats {
+  int32_t step;              /* k, 0-based */
+  int32_t n_ex;              /* particles each group sent at step k */
+  double pe_eff;             /* Eq. 4 PE_eff of the weights carried into step k, in [1, G] */
+  double log_c;              /* log of the step's incremental likelihood estimate */
+  double log_Z;              /* sum of log_c over steps 0 .. k */
+  float xhat[5];             /* global estimate x^_k (Alg. 3 step 10) */
+  int32_t degenerate_groups; /* groups whose weights were all zero / NaN */
+} pf_step_stats;
+
+typedef struct pf_handle pf_handle;
+
+/* ABI version of the loaded library (PF_ABI_VERSION it was built with). */
+int32_t pf_abi_version(void);
+
+/* Workspace bytes needed by pf_init for `n_tracks` configs (cfg[0..n-1])
+ * keeping `history` steps of statistics (>= 1; the last `history` steps stay
+ * readable through pf_exchange_stats / pf_history).  With record_ancestors
+ * set, `history` is also the longest sequence pf_backward can differentiate.
+ * Errors: PF_ERR_ARG for invalid configs or NULL pointers. */
+pf_status pf_query_workspace(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
+                             size_t* bytes);
+
+/* Create a filter over `n_tracks` tracks in the caller's device workspace
+ * (`bytes` >= pf_query_workspace's answer, 256-byte aligned) and enqueue the
+ * draw of the initial population on `stream`.  user_state_dev: for tracks
+ * with init_kind == PF_INIT_USER, the initial states as 5 x N_total float32
+ * SoA (N_total = sum of G * Np over all tracks; other tracks' columns are
+ * ignored), else may be NULL; it is read before pf_init's work completes on
+ * the stream.  All tracks of one handle must share patch_radius.  The
+ * workspace must stay allocated and untouched until pf_destroy.
+ * Errors: PF_ERR_ARG, PF_ERR_WORKSPACE, PF_ERR_CUDA. */
+pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history, void* workspace_dev,
+                  size_t bytes, const float* user_state_dev, void* stream, pf_handle** out);
+
+/* Enqueue one time step k (Alg. 3, or Alg. 2 for PF_RNA) for every track.
+ * frames_host: host array of n_tracks device pointers, frame k of each
+ * track (H x W float32); the frames must stay valid until the step has run
+ * on `stream`.  At k = 0 there is no propagation and no exchange: the
+ * initial population is weighted by frame 0.
+ * Errors: PF_ERR_ARG (NULL frame), PF_ERR_STATE (handle failed before),
+ * PF_ERR_CUDA. */
+pf_status pf_step(pf_handle* h, const float* const* frames_host, void* stream);
+
+/* Wait for the handle's last stream and copy the latest global estimate
+ * (n_tracks x 5 floats, may be NULL) and log marginal-likelihood estimate
+ * log Z = sum_k log c_k (n_tracks doubles, may be NULL) to the host.
+ * Errors: PF_ERR_STATE (no step run), PF_ERR_DEGENERATE (some track lost all
+ * weight: its values are NaN / -inf), PF_ERR_DEVICE / PF_ERR_TIMEOUT (the
+ * kernels reported an error), PF_ERR_CUDA. */
+pf_status pf_estimate(pf_handle* h, float* xhat_host, double* log_Z_host);
+
+/* Statistics of step `step` (< steps run, and among the last `history`) of
+ * track `track`; optional per-group arrays (length G, may be NULL):
+ * ring_host[p] = group at ring position p (group ring[p] sends to
+ * ring[(p+1) mod G]) used at that step; group_logW_host = log W^(m) after
+ * the step; group_xhat_host = group estimates x^^m, 5 x G SoA;
+ * group_ess_host = 1 / sum w^2 within each group.  Waits for the stream.
+ * Errors: PF_ERR_ARG, PF_ERR_STATE, PF_ERR_CUDA. */
+pf_status pf_exchange_stats(pf_handle* h, int32_t track, int32_t step, pf_step_stats* out,
+                            int32_t* ring_host, double* group_logW_host, float* group_xhat_host,
+                            float* group_ess_host);
+
+/* Statistics of `count` consecutive steps first .. first+count-1 of one
+ * track (each among the last `history`).  Waits for the stream.
+ * Errors: PF_ERR_ARG, PF_ERR_STATE, PF_ERR_CUDA. */
+pf_status pf_history(pf_handle* h, int32_t track, int32_t first, int32_t count, pf_step_stats* out);
+
+/* Device-to-device copies, enqueued on `stream`, of the latest step's
+ * particles of track `track` (each pointer may be NULL):
+ *   states_dev: the propagated states X_k before resampling, 5 x N SoA;
+ *   anc_dev:    resampling ancestors, anc[g*Np + j] = slot (within the
+ *               track, g*Np + a) whose state slot j of group g copies;
+ *   logw_dev:   log w~_k = log of the renormalised prior weight plus the
+ *               log-likelihood, the input of the resampler;
+ *   parent_dev: the slot of X_{k-1} that each slot was propagated from
+ *               (the exchange composed with the previous resampling).
+ * Errors: PF_ERR_ARG, PF_ERR_STATE, PF_ERR_CUDA. */
+pf_status pf_particles(pf_handle* h, int32_t track, float* states_dev, uint32_t* anc_dev,
+                       float* logw_dev, uint32_t* parent_dev, void* stream);
+
+/* Workspace bytes for pf_resample on G groups of Np particles. */
+pf_status pf_resample_workspace(int32_t G, int32_t Np, size_t* bytes);
+
+/* Per-group systematic resampling (Alg. 1 step 6) of G groups of Np
+ * particles, on the GPU kernel pf_step uses, exposed for verification.
+ * logw_dev: G*Np float32 log-weights, group-major; u_dev: G uint32 uniform
+ * words (the offset is u / 2^32); anc_dev: G*Np uint32 outputs, anc[g*Np+j]
+ * = ancestor slot within the group (0 .. Np-1); q_dev: optional G*Np uint64
+ * outputs, the fixed-point weight codes the resampler used (may be NULL).
+ * Weight codes: with M the group maximum, q = trunc(p 2^(n+40)) where
+ * z = fl(fl(lw - M) * fl32(log2 e)), n = rint(z), p = the degree-7 Taylor
+ * polynomial of 2^(z-n) in FP32 Horner form; q = 0 when z < -40 or NaN.
+ * Output j takes the particle i with S_i <= (j + u/2^32) Q / Np < S_{i+1},
+ * S the prefix sums of q and Q their total, compared exactly in 128-bit
+ * integers; a group with Q = 0 resamples as the identity.
+ * Errors: PF_ERR_ARG, PF_ERR_WORKSPACE, PF_ERR_CUDA. */
+pf_status pf_resample(const float* logw_dev, const uint32_t* u_dev, int32_t G, int32_t Np,
+                      uint32_t* anc_dev, uint64_t* q_dev, void* workspace_dev, size_t bytes,
+                      void* stream);
+
+/* Kernel timing.  With enable = 1, every later pf_step records a pair of
+ * CUDA events around each of its kernels, on the stream it launches them
+ * on; enable = 0 stops recording.  Recording adds no synchronisation.
+ * Errors: PF_ERR_ARG, PF_ERR_CUDA. */
+pf_status pf_profile_enable(pf_handle* h, int32_t enable);
+
+/* Kernels of one step, in launch order, as indexed by pf_profile_read. */
+enum {
+  PF_KERNEL_FRAME_PREP = 0,
+  PF_KERNEL_PROPAGATE_WEIGHT = 1,
+  PF_KERNEL_RESAMPLE = 2,
+  PF_KERNEL_GLOBAL = 3,
+  PF_KERNEL_COUNT = 4
+};
+
+/* Wait for the recorded work, then write, for each of the first n (<=
+ * PF_KERNEL_COUNT) kernels, the number of recorded launches and their
+ * summed device duration in milliseconds; the records are then cleared.
+ * Either array may be NULL.  Errors: PF_ERR_ARG, PF_ERR_CUDA. */
+pf_status pf_profile_read(pf_handle* h, int32_t n, int64_t* launches, double* total_ms);
+
+/* Release the handle's host metadata (the workspace stays the caller's). */
+void pf_destroy(pf_handle* h);
+
+/* Text of the last error of `h`, or of the calling thread's last failed
+ * handle-less call when h is NULL.  Never NULL; valid until the next call. */
+const char* pf_last_error(const pf_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PFARNA_H */

@@ -73,6 +73,7 @@ def lib():
         L.ora_propagate.argtypes = [C.POINTER(Cfg), C.c_uint32, _P, _P]
         L.ora_loglik_image.argtypes = [C.POINTER(Cfg), _P, C.c_double, C.c_double, C.c_double]
         L.ora_loglik_image.restype = C.c_double
+        L.ora_loglik_image_batch.argtypes = [C.POINTER(Cfg), _P, _P, C.c_int64, _P]
         L.ora_exp2_coeffs.argtypes = [_P]
         L.ora_quantize.argtypes = [_P, C.c_int32, _P]
         L.ora_resample.argtypes = [_P, C.c_int32, C.c_uint32, _P]
@@ -104,11 +105,15 @@ def make_cfg(G, Np, H=64, W=64, R=5, mode=RNA, obs_kind=OBS_IMAGE, sigma_psf=1.5
 
 
 def cfg_from_workload(wl, track: int = 0) -> Cfg:
-    """Oracle configuration from a ``synth.Workload`` (plain parameters)."""
+    """Oracle configuration from a ``synth.Workload`` (plain parameters).
+
+    Real parameters are rounded to FP32 first: the GPU library receives them
+    as FP32, and both sides must work from the same numbers."""
+    f = lambda v: float(np.float32(v))  # noqa: E731
     return make_cfg(G=wl.G, Np=wl.Np, H=wl.H, W=wl.W, R=wl.patch_radius, mode=wl.mode,
-                    sigma_psf=wl.sigma_psf, background=wl.background, sigma_obs=wl.sigma_obs,
-                    sigma_pos=wl.sigma_pos, sigma_v=wl.sigma_v, sigma_I=wl.sigma_I,
-                    ex_ratio=wl.ex_ratio, cutoff=wl.pe_eff_cutoff, seed=wl.seed, track=track)
+                    sigma_psf=f(wl.sigma_psf), background=f(wl.background), sigma_obs=f(wl.sigma_obs),
+                    sigma_pos=f(wl.sigma_pos), sigma_v=f(wl.sigma_v), sigma_I=f(wl.sigma_I),
+                    ex_ratio=f(wl.ex_ratio), cutoff=f(wl.pe_eff_cutoff), seed=wl.seed, track=track)
 
 
 # ---------------------------------------------------------------- primitives
@@ -200,12 +205,13 @@ def loglik_image(cfg: Cfg, frame, x: float, y: float, I: float) -> float:
 
 
 def loglik_image_many(cfg: Cfg, frame, states) -> np.ndarray:
-    """l for each column of a (5, n) state array (a plain loop over the C routine)."""
+    """l for each column of a (5, n) state array."""
     f = _c(frame, np.float32)
-    st = np.asarray(states, np.float64)
-    L = lib()
-    return np.array([L.ora_loglik_image(C.byref(cfg), _ptr(f), float(st[0, i]), float(st[1, i]),
-                                        float(st[4, i])) for i in range(st.shape[1])])
+    st = _c(states, np.float64)
+    n = st.shape[1]
+    out = np.zeros(n)
+    lib().ora_loglik_image_batch(C.byref(cfg), _ptr(f), _ptr(st), n, _ptr(out))
+    return out
 
 
 def exp2_coeffs() -> np.ndarray:

@@ -329,6 +329,11 @@ double ora_loglik_image(const ora_cfg* c, const float* frame, double x, double y
   return -acc / (2.0 * c->sigma_obs * c->sigma_obs);
 }
 
+/* ora_loglik_image for each column of a 5 x n state array. */
+void ora_loglik_image_batch(const ora_cfg* c, const float* frame, const double* states, int64_t n, double* out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = ora_loglik_image(c, frame, states[i], states[n + i], states[4 * n + i]);
+}
+
 /* Linear-Gaussian observation of the position (z = (x, y) + noise), used
  * only to pin the filter against the Kalman filter. */
 double ora_loglik_point(const ora_cfg* c, const float* obs, double x, double y) {
@@ -492,10 +497,10 @@ static double lse(const double* v, int64_t n) {
  * particle of group m carrying weight W_m / Np with W_m = exp(Lambda_in[m])
  * (Alg. 3 step 8).  At k = 0 pop_in is the initial sample and Lambda_in is
  * ignored (all groups equal).  obs: the frame (H x W, row-major) or, for
- * ORA_OBS_POINT, two floats.  lw_override: if not NULL, the resampler
- * quantizes these FP32 log-weights instead of the oracle's own (used to feed
- * both sides identical weights).  Returns 0, or 1 if every group is
- * degenerate. */
+ * ORA_OBS_POINT, two floats.  lw_override: if not NULL, steps S7-S9 (group
+ * weights, estimates, resampling) use these FP32 log-weights instead of the
+ * oracle's own (so both sides can be fed identical weights); o->lw still
+ * receives the oracle's own.  Returns 0, or 1 if every group is degenerate. */
 int ora_step(const ora_cfg* c, uint32_t k, const float* obs, const double* pop_in,
              const double* Lambda_in, const float* lw_override, ora_step_out* o) {
   int32_t G = c->G, Np = c->Np;
@@ -527,10 +532,20 @@ int ora_step(const ora_cfg* c, uint32_t k, const float* obs, const double* pop_i
     o->lw[i] = Lam[o->origin[i]] - log((double)Np) - lse_lam + l;
   }
 
+  /* With lw_override the remaining steps (S7-S9) use those log-weights, so
+   * that both sides can be fed identical weights. */
+  double* lwe = o->lw;
+  double* lwbuf = NULL;
+  if (lw_override) {
+    lwbuf = (double*)malloc(sizeof(double) * (size_t)N);
+    for (int64_t i = 0; i < N; ++i) lwbuf[i] = (double)lw_override[i];
+    lwe = lwbuf;
+  }
+
   /* S7 (Alg. 3 step 6): group estimate and group weight, FP64 */
   int32_t degen = 0;
   for (int32_t m = 0; m < G; ++m) {
-    const double* lwm = o->lw + (int64_t)m * Np;
+    const double* lwm = lwe + (int64_t)m * Np;
     double mx = -INFINITY;
     for (int32_t j = 0; j < Np; ++j)
       if (lwm[j] > mx) mx = lwm[j];
@@ -574,6 +589,7 @@ int ora_step(const ora_cfg* c, uint32_t k, const float* obs, const double* pop_i
     ora_resample(qm, Np, ora_resample_uniform(c, (uint32_t)m, k), o->anc + (int64_t)m * Np);
   }
   free(lwf);
+  free(lwbuf);
 
   /* S10 (Alg. 3 step 8): the resampled population; group weights carried */
   for (int d = 0; d < 5; ++d)

@@ -1,0 +1,586 @@
+// pf_api.cu -- the C ABI declared in include/pfarna.h: validation, workspace
+// layout, launch sequence of one filter step, and read-back.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pfarna.h"
+#include "pf_device.cuh"
+#include "pf_launch.h"
+
+using namespace pf;
+
+struct pf_handle {
+  int n_tracks = 0, history = 0, R = 5;
+  std::vector<pf_track_config> cfg;
+  std::vector<TrackParams> tp;
+  long long N_total = 0;
+  int G_total = 0, n_tiles = 0;
+  int k1_grid = 1, rs_cluster = 1;
+  int steps_run = 0;
+  int failed = 0;
+  cudaStream_t last_stream = nullptr;
+  std::string err;
+  QuantCoeffs qc{};
+  // device pointers into the caller's workspace
+  TrackParams* trk = nullptr;
+  TrackState* ts = nullptr;
+  GroupState* gs = nullptr;
+  GroupDesc* gd = nullptr;
+  int4* tiles = nullptr;
+  float4* pv[2] = {nullptr, nullptr};
+  float* In[2] = {nullptr, nullptr};
+  uint32_t* anc = nullptr;
+  float* lw = nullptr;
+  float* tile_part = nullptr;
+  float* ypad = nullptr;
+  HistRec* hist = nullptr;
+  GroupHist* ghist = nullptr;
+  int* ring = nullptr;
+  uint32_t* parent = nullptr;
+  DevState* ds = nullptr;
+  // kernel timing (pf_profile_enable / pf_profile_read)
+  int prof = 0;
+  std::vector<cudaEvent_t> ev[PF_KERNEL_COUNT];  // start, stop, start, stop, ...
+  ~pf_handle() {
+    for (auto& v : ev)
+      for (cudaEvent_t e : v) cudaEventDestroy(e);
+  }
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+pf_status fail(pf_handle* h, pf_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_err = msg;
+  return st;
+}
+
+pf_status cuda_fail(pf_handle* h, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  if (h) h->failed = 1;
+  return fail(h, PF_ERR_CUDA, m);
+}
+
+constexpr size_t ALIGN = 256;
+size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+// Coefficients of the weight code: c_0 = 1, c_d = c_{d-1} ln2 / d in FP64,
+// each rounded once to FP32; log2(e) rounded once to FP32.
+QuantCoeffs make_qc() {
+  QuantCoeffs q{};
+  const double LN2 = 0.69314718055994530942;
+  double d = 1.0;
+  q.c[0] = 1.0f;
+  for (int k = 1; k < 8; ++k) {
+    d = d * LN2 / (double)k;
+    q.c[k] = (float)d;
+  }
+  q.l2e = (float)1.4426950408889634;
+  return q;
+}
+
+struct Layout {
+  size_t trk, ts, gs, gd, tiles, pv0, pv1, I0, I1, anc, lw, tp, ypad, hist, ghist, ring, parent, ds, total;
+  long long N_total = 0, ypad_total = 0, parent_total = 0, ghist_total = 0;
+  int G_total = 0, n_tiles = 0, hist_total = 0;
+  int R = 5;
+};
+
+bool finite_nonneg(float v) { return std::isfinite(v) && v >= 0.0f; }
+
+std::string validate(const pf_track_config* c, int n, int history) {
+  if (!c) return "cfg is NULL";
+  if (n < 1) return "n_tracks must be >= 1";
+  if (history < 1) return "history must be >= 1";
+  long long total = 0;
+  for (int t = 0; t < n; ++t) {
+    const pf_track_config& x = c[t];
+    char b[160];
+    auto bad = [&](const char* what) {
+      std::snprintf(b, sizeof b, "track %d: %s", t, what);
+      return std::string(b);
+    };
+    if (x.G < 1 || x.G > MAX_G) return bad("G must be in [1, 4096]");
+    if (x.Np < 1 || (long long)x.G * x.Np > (1ll << 24) * 16) return bad("Np must be >= 1 and G*Np <= 2^28");
+    if (x.H < 1 || x.W < 1 || x.H > 16384 || x.W > 16384) return bad("H and W must be in [1, 16384]");
+    if (x.patch_radius < 1 || x.patch_radius > 7) return bad("patch_radius must be in [1, 7]");
+    if (x.patch_radius != c[0].patch_radius) return bad("all tracks must share patch_radius");
+    if (x.mode != PF_RNA && x.mode != PF_ARNA) return bad("mode must be PF_RNA or PF_ARNA");
+    if (x.init_kind < PF_INIT_POINT || x.init_kind > PF_INIT_USER) return bad("unknown init_kind");
+    if (!(std::isfinite(x.sigma_psf) && x.sigma_psf > 0.0f)) return bad("sigma_psf must be > 0");
+    if (!(std::isfinite(x.sigma_obs) && x.sigma_obs > 0.0f)) return bad("sigma_obs must be > 0");
+    if (!std::isfinite(x.background)) return bad("background must be finite");
+    if (!finite_nonneg(x.sigma_pos) || !finite_nonneg(x.sigma_v) || !finite_nonneg(x.sigma_I))
+      return bad("process noise must be finite and >= 0");
+    if (!(x.ex_ratio >= 0.0f && x.ex_ratio <= 1.0f)) return bad("ex_ratio must be in [0, 1]");
+    if (!std::isfinite(x.pe_eff_cutoff)) return bad("pe_eff_cutoff must be finite");
+    if (x.track_id >= (1u << 24)) return bad("track_id must be < 2^24");
+    if (x.reserved0 != 0) return bad("reserved0 must be 0");
+    for (int d = 0; d < 5; ++d)
+      if (!std::isfinite(x.init_state[d]) || !std::isfinite(x.init_lo[d]) || !std::isfinite(x.init_hi[d]))
+        return bad("init_state / init_lo / init_hi must be finite");
+    if (!finite_nonneg(x.init_radius)) return bad("init_radius must be finite and >= 0");
+    total += (long long)x.G * x.Np;
+  }
+  if (total >= (1ll << 31)) return "total particles must be < 2^31";
+  return "";
+}
+
+Layout plan(const pf_track_config* c, int n, int history) {
+  Layout L{};
+  L.R = c[0].patch_radius;
+  const int pad = 2 * L.R + 1;
+  for (int t = 0; t < n; ++t) {
+    const long long Nt = (long long)c[t].G * c[t].Np;
+    L.N_total += Nt;
+    L.G_total += c[t].G;
+    L.n_tiles += c[t].G * ((c[t].Np + K1_THREADS - 1) / K1_THREADS);
+    const long long pitch = ((long long)c[t].W + 2 * pad + 3) / 4 * 4;
+    L.ypad_total += pitch * ((long long)c[t].H + 2 * pad);
+    if (c[t].record_ancestors) L.parent_total += Nt * history;
+    L.hist_total += history;
+    L.ghist_total += (long long)history * c[t].G;
+  }
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align_up(o + bytes);
+    return at;
+  };
+  L.ds = take(sizeof(DevState));
+  L.trk = take(sizeof(TrackParams) * n);
+  L.ts = take(sizeof(TrackState) * n);
+  L.gs = take(sizeof(GroupState) * L.G_total);
+  L.gd = take(sizeof(GroupDesc) * L.G_total);
+  L.ring = take(sizeof(int) * L.G_total);
+  L.tiles = take(sizeof(int4) * L.n_tiles);
+  L.pv0 = take(sizeof(float4) * L.N_total);
+  L.pv1 = take(sizeof(float4) * L.N_total);
+  L.I0 = take(sizeof(float) * L.N_total);
+  L.I1 = take(sizeof(float) * L.N_total);
+  L.anc = take(sizeof(uint32_t) * L.N_total);
+  L.lw = take(sizeof(float) * L.N_total);
+  L.tp = take(sizeof(float) * 8 * (size_t)L.n_tiles);
+  L.ypad = take(sizeof(float) * (size_t)L.ypad_total);
+  L.hist = take(sizeof(HistRec) * (size_t)L.hist_total);
+  L.ghist = take(sizeof(GroupHist) * (size_t)L.ghist_total);
+  L.parent = take(sizeof(uint32_t) * (size_t)(L.parent_total > 0 ? L.parent_total : 1));
+  L.total = o;
+  return L;
+}
+
+int num_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+  return sms > 0 ? sms : 1;
+}
+
+int resample_cluster(int Np, bool single_track) {
+  if (!single_track) return 1;
+  int c = (Np + RS_SUB - 1) / RS_SUB;
+  return c < 1 ? 1 : (c > 8 ? 8 : c);
+}
+
+pf_status check_device(pf_handle* h) {
+  DevState ds{};
+  cudaError_t e = cudaMemcpy(&ds, h->ds, sizeof ds, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "reading the device error word");
+  if (ds.err) {
+    char b[200];
+    std::snprintf(b, sizeof b, "kernel reported error bits 0x%x (info %u %u %u)", ds.err, ds.err_info[0],
+                  ds.err_info[1], ds.err_info[2]);
+    h->failed = 1;
+    return fail(h, (ds.err & ERR_TIMEOUT) ? PF_ERR_TIMEOUT : PF_ERR_DEVICE, b);
+  }
+  return PF_OK;
+}
+
+// Records an event before (begin = true) or after a kernel when profiling.
+cudaError_t mark(pf_handle* h, int kernel, cudaStream_t s) {
+  if (!h->prof) return cudaSuccess;
+  cudaEvent_t e;
+  cudaError_t r = cudaEventCreate(&e);
+  if (r != cudaSuccess) return r;
+  h->ev[kernel].push_back(e);
+  return cudaEventRecord(e, s);
+}
+
+pf_status sync(pf_handle* h) {
+  cudaError_t e = cudaStreamSynchronize(h->last_stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+  return check_device(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t pf_abi_version(void) { return PF_ABI_VERSION; }
+
+pf_status pf_query_workspace(const pf_track_config* cfg, int32_t n_tracks, int32_t history, size_t* bytes) {
+  if (!bytes) return fail(nullptr, PF_ERR_ARG, "bytes is NULL");
+  const std::string v = validate(cfg, n_tracks, history);
+  if (!v.empty()) return fail(nullptr, PF_ERR_ARG, v);
+  *bytes = plan(cfg, n_tracks, history).total;
+  return PF_OK;
+}
+
+pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history, void* workspace, size_t bytes,
+                  const float* user_state, void* stream, pf_handle** out) {
+  if (!out) return fail(nullptr, PF_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  const std::string v = validate(cfg, n_tracks, history);
+  if (!v.empty()) return fail(nullptr, PF_ERR_ARG, v);
+  if (!workspace) return fail(nullptr, PF_ERR_ARG, "workspace is NULL");
+  if ((uintptr_t)workspace % ALIGN) return fail(nullptr, PF_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  const Layout L = plan(cfg, n_tracks, history);
+  if (bytes < L.total) return fail(nullptr, PF_ERR_WORKSPACE, "workspace too small");
+  bool need_user = false;
+  for (int t = 0; t < n_tracks; ++t) need_user |= cfg[t].init_kind == PF_INIT_USER;
+  if (need_user && !user_state) return fail(nullptr, PF_ERR_ARG, "PF_INIT_USER needs user_state_dev");
+
+  pf_handle* h = new pf_handle();
+  h->n_tracks = n_tracks;
+  h->history = history;
+  h->R = L.R;
+  h->cfg.assign(cfg, cfg + n_tracks);
+  h->N_total = L.N_total;
+  h->G_total = L.G_total;
+  h->n_tiles = L.n_tiles;
+  h->qc = make_qc();
+  h->last_stream = (cudaStream_t)stream;
+  char* w = (char*)workspace;
+  h->ds = (DevState*)(w + L.ds);
+  h->trk = (TrackParams*)(w + L.trk);
+  h->ts = (TrackState*)(w + L.ts);
+  h->gs = (GroupState*)(w + L.gs);
+  h->gd = (GroupDesc*)(w + L.gd);
+  h->ring = (int*)(w + L.ring);
+  h->tiles = (int4*)(w + L.tiles);
+  h->pv[0] = (float4*)(w + L.pv0);
+  h->pv[1] = (float4*)(w + L.pv1);
+  h->In[0] = (float*)(w + L.I0);
+  h->In[1] = (float*)(w + L.I1);
+  h->anc = (uint32_t*)(w + L.anc);
+  h->lw = (float*)(w + L.lw);
+  h->tile_part = (float*)(w + L.tp);
+  h->ypad = (float*)(w + L.ypad);
+  h->hist = (HistRec*)(w + L.hist);
+  h->ghist = (GroupHist*)(w + L.ghist);
+  h->parent = (uint32_t*)(w + L.parent);
+
+  // host tables
+  const int pad = 2 * L.R + 1;
+  std::vector<TrackParams> tp(n_tracks);
+  std::vector<GroupDesc> gd;
+  std::vector<int4> tiles;
+  gd.reserve(L.G_total);
+  tiles.reserve(L.n_tiles);
+  long long part = 0, ypo = 0, paro = 0, gho = 0;
+  int gro = 0, tio = 0, ho = 0;
+  for (int t = 0; t < n_tracks; ++t) {
+    const pf_track_config& c = cfg[t];
+    TrackParams& P = tp[t];
+    std::memset(&P, 0, sizeof P);
+    P.G = c.G; P.Np = c.Np; P.H = c.H; P.W = c.W;
+    P.mode = c.mode; P.init_kind = c.init_kind;
+    P.spsf = c.sigma_psf; P.bg = c.background; P.sobs = c.sigma_obs;
+    P.spos = c.sigma_pos; P.sv = c.sigma_v; P.sI = c.sigma_I;
+    P.ex_ratio = c.ex_ratio; P.cutoff = c.pe_eff_cutoff;
+    P.c_psf = (float)(1.4426950408889634 / (2.0 * (double)c.sigma_psf * (double)c.sigma_psf));
+    P.inv2so2 = (float)(1.0 / (2.0 * (double)c.sigma_obs * (double)c.sigma_obs));
+    P.key0 = (uint32_t)c.seed;
+    P.key1 = (uint32_t)(c.seed >> 32);
+    P.tag = c.track_id << 8;
+    P.record = c.record_ancestors ? 1 : 0;
+    P.part_off = part;
+    P.group_off = gro;
+    P.tile_off = tio;
+    P.tiles_per_group = (c.Np + K1_THREADS - 1) / K1_THREADS;
+    P.pitch = (int)(((long long)c.W + 2 * pad + 3) / 4 * 4);
+    P.ypad_off = ypo;
+    P.hist_off = ho;
+    P.ghist_off = gho;
+    P.parent_off = paro;
+    for (int d = 0; d < 5; ++d) {
+      P.init_state[d] = c.init_state[d];
+      P.init_lo[d] = c.init_lo[d];
+      P.init_hi[d] = c.init_hi[d];
+    }
+    P.init_radius = c.init_radius;
+    for (int g = 0; g < c.G; ++g) {
+      GroupDesc D{};
+      D.base = part + (long long)g * c.Np;
+      D.Np = c.Np;
+      D.track = t;
+      D.g = g;
+      D.tile_begin = (int)tiles.size();
+      for (int j0 = 0; j0 < c.Np; j0 += K1_THREADS)
+        tiles.push_back(make_int4(t, g, j0, c.Np - j0 < K1_THREADS ? c.Np - j0 : K1_THREADS));
+      D.tile_count = (int)tiles.size() - D.tile_begin;
+      gd.push_back(D);
+    }
+    const long long Nt = (long long)c.G * c.Np;
+    part += Nt;
+    gro += c.G;
+    tio += c.G * P.tiles_per_group;
+    ypo += (long long)P.pitch * (c.H + 2 * pad);
+    ho += history;
+    gho += (long long)history * c.G;
+    if (c.record_ancestors) paro += Nt * history;
+  }
+  h->tp = tp;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(w, 0, L.total, s)) != cudaSuccess) { pf_destroy(h); return cuda_fail(nullptr, e, "cudaMemsetAsync"); }
+  if ((e = cudaMemcpyAsync(h->trk, tp.data(), sizeof(TrackParams) * n_tracks, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(h->gd, gd.data(), sizeof(GroupDesc) * gd.size(), cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(h->tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s))) {
+    pf_destroy(h);
+    return cuda_fail(nullptr, e, "uploading track tables");
+  }
+  // the staging copies above read pageable host memory, so they complete
+  // (from the host's point of view) before returning; the vectors may go.
+
+  const int sms = num_sms();
+  int occ = 1;
+  if ((e = k1_occupancy(h->R, &occ)) != cudaSuccess) { pf_destroy(h); return cuda_fail(nullptr, e, "occupancy"); }
+  const long long want = (long long)sms * (occ > 0 ? occ : 1);
+  h->k1_grid = (int)(h->n_tiles < want ? h->n_tiles : want);
+  h->rs_cluster = resample_cluster(cfg[0].Np, n_tracks == 1);
+
+  InitArgs ia{h->trk, h->tiles, h->n_tiles, h->N_total, user_state, h->pv[1], h->In[1]};
+  if ((e = launch_init(ia, h->k1_grid, s)) != cudaSuccess) { pf_destroy(h); return cuda_fail(nullptr, e, "k_init"); }
+  GlobalArgs ga{h->trk, h->ts, h->gs, h->ring, h->hist, h->ghist, h->history, 0, h->ds};
+  if ((e = launch_global(ga, n_tracks, s)) != cudaSuccess) { pf_destroy(h); return cuda_fail(nullptr, e, "k_global"); }
+  *out = h;
+  return PF_OK;
+}
+
+pf_status pf_step(pf_handle* h, const float* const* frames, void* stream) {
+  if (!h) return fail(nullptr, PF_ERR_ARG, "handle is NULL");
+  if (h->failed) return fail(h, PF_ERR_STATE, "handle failed earlier: " + h->err);
+  if (!frames) return fail(h, PF_ERR_ARG, "frames is NULL");
+  for (int t = 0; t < h->n_tracks; ++t)
+    if (!frames[t]) return fail(h, PF_ERR_ARG, "frame pointer of track " + std::to_string(t) + " is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  // frame preparation, up to MAX_FRAMES_PER_LAUNCH tracks per launch
+  if ((e = mark(h, PF_KERNEL_FRAME_PREP, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
+  for (int t0 = 0; t0 < h->n_tracks; t0 += MAX_FRAMES_PER_LAUNCH) {
+    const int nt = h->n_tracks - t0 < MAX_FRAMES_PER_LAUNCH ? h->n_tracks - t0 : MAX_FRAMES_PER_LAUNCH;
+    FrameArgs a;
+    a.trk = h->trk;
+    a.ypad = h->ypad;
+    a.t0 = t0;
+    a.R = h->R;
+    long long maxpix = 1;
+    for (int i = 0; i < nt; ++i) {
+      a.frames[i] = frames[t0 + i];
+      const long long px = (long long)h->cfg[t0 + i].H * h->cfg[t0 + i].W;
+      if (px > maxpix) maxpix = px;
+    }
+    const long long bx = (maxpix + 255) / 256;
+    if ((e = launch_frame_prep(a, nt, (int)(bx > 1024 ? 1024 : bx), s)) != cudaSuccess)
+      return cuda_fail(h, e, "k_frame_prep");
+  }
+  if ((e = mark(h, PF_KERNEL_FRAME_PREP, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
+  K1Args k1{h->trk, h->tiles, h->n_tiles, h->gs, h->ts, h->ds, h->pv[0], h->pv[1], h->In[0], h->In[1],
+            h->anc, h->parent, h->history, h->lw, h->tile_part, h->ypad};
+  if ((e = mark(h, PF_KERNEL_PROPAGATE_WEIGHT, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
+  if ((e = launch_propagate(k1, h->R, h->k1_grid, s)) != cudaSuccess) return cuda_fail(h, e, "k_propagate_weight");
+  if ((e = mark(h, PF_KERNEL_PROPAGATE_WEIGHT, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
+  ResampleArgs ra{h->gd, h->gs, h->tile_part, h->lw, h->anc, nullptr, nullptr, 0, h->qc, h->ds};
+  if ((e = mark(h, PF_KERNEL_RESAMPLE, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
+  if ((e = launch_resample(ra, h->G_total, h->rs_cluster, s)) != cudaSuccess) return cuda_fail(h, e, "k_resample");
+  if ((e = mark(h, PF_KERNEL_RESAMPLE, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
+  GlobalArgs ga{h->trk, h->ts, h->gs, h->ring, h->hist, h->ghist, h->history, 1, h->ds};
+  if ((e = mark(h, PF_KERNEL_GLOBAL, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
+  if ((e = launch_global(ga, h->n_tracks, s)) != cudaSuccess) return cuda_fail(h, e, "k_global");
+  if ((e = mark(h, PF_KERNEL_GLOBAL, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
+  h->steps_run += 1;
+  h->last_stream = s;
+  return PF_OK;
+}
+
+pf_status pf_estimate(pf_handle* h, float* xhat, double* logZ) {
+  if (!h) return fail(nullptr, PF_ERR_ARG, "handle is NULL");
+  if (h->steps_run == 0) return fail(h, PF_ERR_STATE, "no step has run");
+  pf_status st = sync(h);
+  if (st != PF_OK) return st;
+  std::vector<TrackState> ts(h->n_tracks);
+  cudaError_t e = cudaMemcpy(ts.data(), h->ts, sizeof(TrackState) * h->n_tracks, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "reading track state");
+  bool degen = false;
+  for (int t = 0; t < h->n_tracks; ++t) {
+    if (xhat)
+      for (int d = 0; d < 5; ++d) xhat[t * 5 + d] = ts[t].xhat[d];
+    if (logZ) logZ[t] = ts[t].log_Z;
+    degen |= (ts[t].flags & 1) != 0;
+  }
+  if (degen) return fail(h, PF_ERR_DEGENERATE, "a track lost all particle weight");
+  return PF_OK;
+}
+
+static pf_status check_step(pf_handle* h, int track, int step) {
+  if (track < 0 || track >= h->n_tracks) return fail(h, PF_ERR_ARG, "track out of range");
+  if (step < 0 || step >= h->steps_run) return fail(h, PF_ERR_STATE, "step has not run");
+  if (step < h->steps_run - h->history) return fail(h, PF_ERR_STATE, "step is older than the kept history");
+  return PF_OK;
+}
+
+pf_status pf_exchange_stats(pf_handle* h, int32_t track, int32_t step, pf_step_stats* out, int32_t* ring_host,
+                            double* logW_host, float* xhat_host, float* ess_host) {
+  if (!h) return fail(nullptr, PF_ERR_ARG, "handle is NULL");
+  pf_status st = check_step(h, track, step);
+  if (st != PF_OK) return st;
+  if ((st = sync(h)) != PF_OK) return st;
+  const TrackParams& P = h->tp[track];
+  const int slot = step % h->history;
+  HistRec r{};
+  cudaError_t e = cudaMemcpy(&r, h->hist + P.hist_off + slot, sizeof r, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "reading history");
+  if (r.step != step) return fail(h, PF_ERR_STATE, "history slot holds another step");
+  if (out) {
+    out->step = r.step;
+    out->n_ex = r.n_ex;
+    out->pe_eff = r.pe_eff;
+    out->log_c = r.log_c;
+    out->log_Z = r.log_Z;
+    for (int d = 0; d < 5; ++d) out->xhat[d] = r.xhat[d];
+    out->degenerate_groups = r.degenerate;
+  }
+  if (ring_host || logW_host || xhat_host || ess_host) {
+    std::vector<GroupHist> gh(P.G);
+    e = cudaMemcpy(gh.data(), h->ghist + P.ghist_off + (long long)slot * P.G, sizeof(GroupHist) * P.G,
+                   cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "reading group history");
+    for (int m = 0; m < P.G; ++m) {
+      if (ring_host) ring_host[m] = gh[m].ring;
+      if (logW_host) logW_host[m] = gh[m].logW;
+      if (xhat_host)
+        for (int d = 0; d < 5; ++d) xhat_host[d * P.G + m] = gh[m].xs[d];
+      if (ess_host) ess_host[m] = gh[m].ess;
+    }
+  }
+  return PF_OK;
+}
+
+pf_status pf_history(pf_handle* h, int32_t track, int32_t first, int32_t count, pf_step_stats* out) {
+  if (!h) return fail(nullptr, PF_ERR_ARG, "handle is NULL");
+  if (!out || count < 0) return fail(h, PF_ERR_ARG, "bad output");
+  for (int i = 0; i < count; ++i) {
+    pf_status st = pf_exchange_stats(h, track, first + i, out + i, nullptr, nullptr, nullptr, nullptr);
+    if (st != PF_OK) return st;
+  }
+  return PF_OK;
+}
+
+pf_status pf_particles(pf_handle* h, int32_t track, float* states, uint32_t* anc, float* logw, uint32_t* parent,
+                       void* stream) {
+  if (!h) return fail(nullptr, PF_ERR_ARG, "handle is NULL");
+  if (track < 0 || track >= h->n_tracks) return fail(h, PF_ERR_ARG, "track out of range");
+  if (h->steps_run == 0) return fail(h, PF_ERR_STATE, "no step has run");
+  const TrackParams& P = h->tp[track];
+  if (parent && !P.record) return fail(h, PF_ERR_STATE, "parents are kept only with record_ancestors");
+  const int k = h->steps_run - 1;
+  const long long Nt = (long long)P.G * P.Np;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (states && (e = launch_export_states(h->pv[k & 1] + P.part_off, h->In[k & 1] + P.part_off, Nt, states, s)))
+    return cuda_fail(h, e, "export states");
+  if (anc && (e = cudaMemcpyAsync(anc, h->anc + P.part_off, sizeof(uint32_t) * Nt, cudaMemcpyDeviceToDevice, s)))
+    return cuda_fail(h, e, "copy ancestors");
+  if (logw && (e = cudaMemcpyAsync(logw, h->lw + P.part_off, sizeof(float) * Nt, cudaMemcpyDeviceToDevice, s)))
+    return cuda_fail(h, e, "copy log-weights");
+  if (parent &&
+      (e = cudaMemcpyAsync(parent, h->parent + P.parent_off + (long long)(k % h->history) * Nt, sizeof(uint32_t) * Nt,
+                           cudaMemcpyDeviceToDevice, s)))
+    return cuda_fail(h, e, "copy parents");
+  return PF_OK;
+}
+
+// Standalone resampler: workspace = DevState | GroupDesc[G] | GroupState[G].
+static size_t resample_ws(int G) {
+  return align_up(sizeof(DevState)) + align_up(sizeof(GroupDesc) * G) + align_up(sizeof(GroupState) * G);
+}
+
+pf_status pf_resample_workspace(int32_t G, int32_t Np, size_t* bytes) {
+  if (!bytes) return fail(nullptr, PF_ERR_ARG, "bytes is NULL");
+  if (G < 1 || Np < 1 || (long long)G * Np >= (1ll << 31)) return fail(nullptr, PF_ERR_ARG, "bad G or Np");
+  *bytes = resample_ws(G);
+  return PF_OK;
+}
+
+pf_status pf_resample(const float* logw, const uint32_t* u, int32_t G, int32_t Np, uint32_t* anc, uint64_t* q,
+                      void* workspace, size_t bytes, void* stream) {
+  if (!logw || !u || !anc || !workspace) return fail(nullptr, PF_ERR_ARG, "NULL pointer");
+  if (G < 1 || Np < 1 || (long long)G * Np >= (1ll << 31)) return fail(nullptr, PF_ERR_ARG, "bad G or Np");
+  if ((uintptr_t)workspace % ALIGN) return fail(nullptr, PF_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  if (bytes < resample_ws(G)) return fail(nullptr, PF_ERR_WORKSPACE, "workspace too small");
+  char* w = (char*)workspace;
+  DevState* ds = (DevState*)w;
+  GroupDesc* gd = (GroupDesc*)(w + align_up(sizeof(DevState)));
+  GroupState* gs = (GroupState*)(w + align_up(sizeof(DevState)) + align_up(sizeof(GroupDesc) * G));
+  std::vector<GroupDesc> h(G);
+  for (int g = 0; g < G; ++g) {
+    h[g] = GroupDesc{};
+    h[g].base = (long long)g * Np;
+    h[g].Np = Np;
+    h[g].g = g;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(ds, 0, sizeof(DevState), s)) ||
+      (e = cudaMemcpyAsync(gd, h.data(), sizeof(GroupDesc) * G, cudaMemcpyHostToDevice, s)))
+    return cuda_fail(nullptr, e, "pf_resample setup");
+  ResampleArgs ra{gd, gs, nullptr, logw, anc, (unsigned long long*)q, u, 1, make_qc(), ds};
+  if ((e = launch_resample(ra, G, resample_cluster(Np, true), s)) != cudaSuccess)
+    return cuda_fail(nullptr, e, "k_resample");
+  return PF_OK;
+}
+
+pf_status pf_profile_enable(pf_handle* h, int32_t enable) {
+  if (!h) return fail(nullptr, PF_ERR_ARG, "handle is NULL");
+  h->prof = enable ? 1 : 0;
+  return PF_OK;
+}
+
+pf_status pf_profile_read(pf_handle* h, int32_t n, int64_t* launches, double* total_ms) {
+  if (!h) return fail(nullptr, PF_ERR_ARG, "handle is NULL");
+  if (n < 0 || n > PF_KERNEL_COUNT) return fail(h, PF_ERR_ARG, "n out of range");
+  for (int i = 0; i < PF_KERNEL_COUNT; ++i) {
+    const std::vector<cudaEvent_t>& v = h->ev[i];
+    double ms = 0.0;
+    for (size_t j = 0; j + 1 < v.size(); j += 2) {
+      cudaError_t e = cudaEventSynchronize(v[j + 1]);
+      if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
+      float t = 0.0f;
+      if ((e = cudaEventElapsedTime(&t, v[j], v[j + 1])) != cudaSuccess) return cuda_fail(h, e, "elapsed time");
+      ms += t;
+    }
+    if (i < n) {
+      if (launches) launches[i] = (int64_t)(v.size() / 2);
+      if (total_ms) total_ms[i] = ms;
+    }
+  }
+  for (auto& v : h->ev) {
+    for (cudaEvent_t e : v) cudaEventDestroy(e);
+    v.clear();
+  }
+  return PF_OK;
+}
+
+void pf_destroy(pf_handle* h) { delete h; }
+
+const char* pf_last_error(const pf_handle* h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,224 @@
+// pf_device.cuh -- device-side data layout and helpers of libpfarna.
+//
+// Paper: Demirel et al., "An Adaptive Distributed Resampling Algorithm with
+// Non-Proportional Allocation" (arXiv:1310.4624).  The paper's M processing
+// elements are G groups of Np particles; one track = one filter.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pf {
+
+// ---------------------------------------------------------------- constants
+constexpr int K1_THREADS = 128;       // particles per propagate/weight tile
+constexpr int RS_THREADS = 512;       // resampler CTA
+constexpr int RS_ITEMS = 8;           // items per thread per resampler sub-chunk
+constexpr int RS_SUB = RS_THREADS * RS_ITEMS;
+constexpr int GL_THREADS = 256;       // per-track global-step CTA
+constexpr int MAX_G = 4096;           // groups per track
+constexpr int MAX_FRAMES_PER_LAUNCH = 1024;
+
+// Philox stream ids (counter word 3 = track << 8 | stream << 4 | call).
+constexpr uint32_t ST_INIT = 0, ST_PROP = 1, ST_RESAMPLE = 2, ST_RING = 3, ST_EXCH = 4;
+
+// Device error word bits.
+constexpr uint32_t ERR_INDEX = 1u, ERR_TIMEOUT = 2u, ERR_INVARIANT = 4u, ERR_DRAW = 8u;
+
+enum : int { MODE_RNA = 0, MODE_ARNA = 1 };
+enum : int { INIT_POINT = 0, INIT_UNIFORM = 1, INIT_SHARING = 2, INIT_USER = 3 };
+
+// ------------------------------------------------------------- data layout
+// Read-only per-track parameters, built on the host at init.
+struct TrackParams {
+  int G, Np, H, W;
+  int mode, init_kind;
+  float spsf, bg, sobs, spos, sv, sI;
+  float ex_ratio, cutoff;
+  float c_psf;      // log2(e) / (2 sigma_psf^2): gx(u) = 2^(-c_psf (u-x)^2)
+  float inv2so2;    // 1 / (2 sigma_obs^2)
+  uint32_t key0, key1, tag;   // Philox key; tag = track_id << 8
+  int record;
+  long long part_off;         // first particle of the track (global slot)
+  int group_off;              // first group of the track (global group)
+  int tile_off;               // first propagate tile of the track
+  int tiles_per_group;
+  int pitch;                  // padded frame row pitch (floats)
+  long long ypad_off;         // padded frame offset (floats)
+  int hist_off;               // first history record of the track
+  long long ghist_off;        // first per-group history entry of the track
+  long long parent_off;       // first ancestry record (slots) of the track
+  float init_state[5], init_lo[5], init_hi[5], init_radius;
+};
+
+// Mutable per-track state.
+struct TrackState {
+  int k;             // step to run next
+  int n_ex;          // particles each group sends at step k
+  int degenerate;    // groups with no weight at the last step
+  int flags;         // bit 0: every group degenerate at some step
+  double pe_eff;     // PE_eff used for step k
+  double log_c;      // last step's log c
+  double log_Z;      // sum of log c
+  float xhat[5];
+  int steps_done;
+};
+
+// Per-group state (global group index).
+struct GroupState {
+  double lambda;        // carried log group weight log W^(m)
+  float off;            // log w offset of particles originating here at step k
+  int pred;             // group (track-local) that sends to this one at step k
+  uint32_t exo;         // exchange offset o_g of step k
+  uint32_t u;           // resampling uniform word of step k
+  float M;              // group max log-weight (step k)
+  int pad0;
+  unsigned long long Q; // group total weight code (step k)
+  float xs[5];          // group estimate x^^m (step k)
+  float ess;            // group ESS (step k)
+};
+
+// Static description of a group.
+struct GroupDesc {
+  long long base;   // global slot of its slot 0
+  int Np;
+  int track;
+  int g;            // track-local group index
+  int tile_begin;   // first propagate tile
+  int tile_count;
+  int pad;
+};
+
+// One history record per (track, step).
+struct HistRec {
+  int step, n_ex;
+  double pe_eff, log_c, log_Z;
+  float xhat[5];
+  int degenerate;
+};
+
+// Per-group history entry.
+struct GroupHist {
+  double logW;      // log W^(m) after the step
+  int ring;         // group at ring position p used at the step
+  float xs[5];
+  float ess;
+};
+
+struct DevState {
+  unsigned int err;
+  unsigned int err_info[3];
+};
+
+// ------------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds, each two 32x32 -> 64
+// multiplies and a Weyl bump of the key.
+__device__ __forceinline__ uint4 philox(uint32_t k0, uint32_t k1, uint4 c) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t a = c.x, b = c.z;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, a), lo0 = 0xD2511F53u * a;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, b), lo1 = 0xCD9E8D57u * b;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Uniform in (0,1): ((w >> 9) + 1/2) 2^-23, exact in FP32.
+__device__ __forceinline__ float u01(uint32_t w) {
+  return __fmul_rn(__fadd_rn((float)(w >> 9), 0.5f), 1.1920928955078125e-7f);
+}
+
+// Box-Muller pair from two words: rho (cos, sin) of 2 pi u_b.  The angle is
+// evaluated as 2 pi u_b - pi (the sign folded into rho) so the fast sine and
+// cosine stay within [-pi, pi].
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& e0, float& e1) {
+  const float rho = sqrtf(-2.0f * logf(u01(wa)));
+  float s, c;
+  __sincosf(fmaf(u01(wb), 6.28318530717958647f, -3.14159265358979323f), &s, &c);
+  e0 = -rho * c;
+  e1 = -rho * s;
+}
+
+// Lemire bounded integer in [0, s) (multiply-shift with rejection, ACM
+// TOMACS 2019); returns false when the word must be redrawn.
+__device__ __forceinline__ bool bounded(uint32_t w, uint32_t s, uint32_t& out) {
+  const unsigned long long m = (unsigned long long)w * s;
+  const uint32_t l = (uint32_t)m;
+  if (l < s) {
+    const uint32_t t = (0u - s) % s;
+    if (l < t) return false;
+  }
+  out = (uint32_t)(m >> 32);
+  return true;
+}
+
+// Attempt a of stream `stream`, index c0, step k, word 0.  Returns false if
+// 64 attempts were rejected (probability < 2^-64 per call for s < 2^31).
+__device__ __forceinline__ bool draw_bounded(uint32_t k0, uint32_t k1, uint32_t tag, uint32_t stream,
+                                             uint32_t c0, uint32_t k, uint32_t s, uint32_t& out) {
+  for (uint32_t a = 0; a < 64; ++a) {
+    const uint4 w = philox(k0, k1, make_uint4(c0, a, k, tag | (stream << 4)));
+    if (bounded(w.x, s, out)) return true;
+  }
+  out = 0;
+  return false;
+}
+
+// ------------------------------------------------------- fixed-point weights
+// q = trunc(p 2^(n+40)), z = fl(fl(lw - M) * L2E), n = rint(z), f = z - n,
+// p = sum_{d<=7} c_d f^d by FP32 Horner; 0 when z < -40 or NaN.  All
+// operations are single IEEE roundings (no contraction), so the code is
+// reproducible on any IEEE machine.
+struct QuantCoeffs {
+  float c[8];
+  float l2e;
+};
+
+__device__ __forceinline__ unsigned long long quantize(float lw, float M, const QuantCoeffs& qc) {
+  const float t = __fsub_rn(lw, M);
+  const float z = __fmul_rn(t, qc.l2e);
+  if (!(z >= -40.0f)) return 0ull;
+  const float n = rintf(z);
+  const float f = __fsub_rn(z, n);
+  float p = qc.c[7];
+#pragma unroll
+  for (int d = 6; d >= 0; --d) p = __fmaf_rn(p, f, qc.c[d]);
+  const float scale = __int_as_float(((int)n + 40 + 127) << 23);  // 2^(n+40), n in [-40, 0]
+  return (unsigned long long)__fmul_rn(p, scale);
+}
+
+// ------------------------------------------------------- 128-bit compares
+struct U128 {
+  unsigned long long lo, hi;
+};
+__device__ __forceinline__ U128 mul64(unsigned long long a, unsigned long long b) {
+  return U128{a * b, __umul64hi(a, b)};
+}
+__device__ __forceinline__ bool lt128(U128 a, U128 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ U128 shl32(U128 a) { return U128{a.lo << 32, (a.hi << 32) | (a.lo >> 32)}; }
+
+// Output j of a group with total Q, Np outputs and uniform word u lies
+// strictly below the prefix S: (j 2^32 + u) Q < S Np 2^32.
+struct ThetaCmp {
+  unsigned long long Q;
+  unsigned long long Np;
+  uint32_t u;
+  __device__ __forceinline__ bool below(long long j, unsigned long long S) const {
+    const U128 lhs = mul64(((unsigned long long)j << 32) | u, Q);
+    const U128 rhs = shl32(mul64(S, Np));
+    return lt128(lhs, rhs);
+  }
+};
+
+__device__ __forceinline__ void set_error(DevState* ds, uint32_t bit, uint32_t a, uint32_t b, uint32_t c) {
+  if (atomicOr(&ds->err, bit) == 0) {
+    ds->err_info[0] = a;
+    ds->err_info[1] = b;
+    ds->err_info[2] = c;
+  }
+}
+
+}  // namespace pf

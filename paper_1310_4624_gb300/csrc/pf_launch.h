@@ -1,0 +1,82 @@
+// pf_launch.h -- kernel argument blocks and launchers shared by the C-ABI
+// layer (pf_api.cu) and the kernels (pf_kernels.cu).  Internal to libpfarna.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "pf_device.cuh"
+
+namespace pf {
+
+struct InitArgs {
+  const TrackParams* trk;
+  const int4* tiles;   // (track, group, first slot, count) per tile
+  int n_tiles;
+  long long n_total;
+  const float* user;   // 5 x n_total SoA or nullptr
+  float4* pv;          // buffer read by step 0
+  float* In;
+};
+
+struct FrameArgs {
+  const TrackParams* trk;
+  float* ypad;
+  int t0;              // first track of this launch
+  int R;
+  const float* frames[MAX_FRAMES_PER_LAUNCH];
+};
+
+struct K1Args {
+  const TrackParams* trk;
+  const int4* tiles;
+  int n_tiles;
+  GroupState* grp;
+  const TrackState* ts;
+  DevState* ds;
+  float4* pv0;
+  float4* pv1;
+  float* I0;
+  float* I1;
+  const uint32_t* anc;  // previous step's ancestors (track-local slots)
+  uint32_t* parent;     // ancestry records or nullptr
+  int history;
+  float* lw;
+  float* tile_part;     // 8 floats per tile
+  const float* ypad;
+};
+
+struct ResampleArgs {
+  const GroupDesc* gd;
+  GroupState* gs;
+  const float* tile_part;      // nullptr: no group estimate
+  const float* lw;
+  uint32_t* anc;
+  unsigned long long* q_out;   // nullptr: not stored
+  const uint32_t* u_arr;       // nullptr: GroupState::u
+  int local_idx;               // 1: ancestors within the group
+  QuantCoeffs qc;
+  DevState* ds;
+};
+
+struct GlobalArgs {
+  const TrackParams* trk;
+  TrackState* ts;
+  GroupState* gs;
+  int* ring;
+  HistRec* hist;
+  GroupHist* ghist;
+  int history;
+  int finalize;  // 0: prepare step 0 only
+  DevState* ds;
+};
+
+cudaError_t launch_init(const InitArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_frame_prep(const FrameArgs& a, int nt, int blocks_x, cudaStream_t s);
+cudaError_t launch_propagate(const K1Args& a, int R, int grid, cudaStream_t s);
+cudaError_t launch_resample(const ResampleArgs& a, int n_groups, int cluster, cudaStream_t s);
+cudaError_t launch_global(const GlobalArgs& a, int n_tracks, cudaStream_t s);
+cudaError_t launch_export_states(const float4* pv, const float* In, long long n, float* out, cudaStream_t s);
+cudaError_t k1_occupancy(int R, int* blocks_per_sm);
+const void* propagate_kernel(int R);
+
+}  // namespace pf

@@ -1,0 +1,156 @@
+"""ParticleFilter: a PyTorch-facing handle on libpfarna.
+
+PyTorch supplies device memory (the workspace, frames, outputs) and the CUDA
+stream; every step of the filter runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import binding as B
+from .synth import INIT_POINT, INIT_SHARING, INIT_UNIFORM, Workload
+
+
+def config_from_workload(wl: Workload, truth0=None, track_id: int = 0, record_ancestors: bool = False,
+                         init_kind: Optional[int] = None) -> B.pf_track_config:
+    """The C config of a workload; the initial population is centred on truth0."""
+    c = B.pf_track_config()
+    c.G, c.Np, c.H, c.W = wl.G, wl.Np, wl.H, wl.W
+    c.patch_radius = wl.patch_radius
+    c.mode = wl.mode
+    c.sigma_psf, c.background, c.sigma_obs = wl.sigma_psf, wl.background, wl.sigma_obs
+    c.sigma_pos, c.sigma_v, c.sigma_I = wl.sigma_pos, wl.sigma_v, wl.sigma_I
+    c.ex_ratio, c.pe_eff_cutoff = wl.ex_ratio, wl.pe_eff_cutoff
+    c.init_kind = wl.init if init_kind is None else init_kind
+    x0 = np.zeros(5) if truth0 is None else np.asarray(truth0, np.float64)
+    lo = [0.0, 0.0, -wl.share_vmax, -wl.share_vmax, wl.share_I[0]]
+    hi = [wl.W - 1.0, wl.H - 1.0, wl.share_vmax, wl.share_vmax, wl.share_I[1]]
+    for d in range(5):
+        c.init_state[d] = float(x0[d])
+        c.init_lo[d] = lo[d]
+        c.init_hi[d] = hi[d]
+    c.init_radius = wl.share_radius
+    c.reserved0 = 0
+    c.seed = wl.seed
+    c.track_id = track_id
+    c.record_ancestors = 1 if record_ancestors else 0
+    return c
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class ParticleFilter:
+    """One handle over one or more tracks, in a workspace PyTorch allocates."""
+
+    def __init__(self, configs: Sequence[B.pf_track_config], history: int = 128,
+                 user_state: Optional[torch.Tensor] = None, device="cuda:0", stream: Optional[torch.cuda.Stream] = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("ParticleFilter needs a CUDA device; there is no CPU path")
+        self.device = torch.device(device)
+        self.configs = list(configs)
+        self.n_tracks = len(self.configs)
+        self.history = history
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.N = [c.G * c.Np for c in self.configs]
+        nbytes = B.pf_query_workspace(self.configs, history)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        self._ws_bytes = nbytes
+        self._user = user_state
+        self.handle = B.pf_init(self.configs, history, self._ws_ptr, nbytes, _ptr(user_state),
+                                C.c_void_p(self.stream.cuda_stream))
+        self.steps = 0
+
+    def close(self):
+        if getattr(self, "handle", None):
+            B.pf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, frames) -> None:
+        """Advance every track by one step; frames: one (H, W) float32 CUDA tensor per track."""
+        if isinstance(frames, torch.Tensor) and frames.dim() == 2:
+            frames = [frames]
+        ptrs = []
+        for f in frames:
+            if f.dtype != torch.float32 or not f.is_cuda or not f.is_contiguous():
+                raise ValueError("frames must be contiguous float32 CUDA tensors")
+            ptrs.append(f.data_ptr())
+        B.pf_step(self.handle, ptrs, C.c_void_p(self.stream.cuda_stream))
+        self.steps += 1
+
+    def profile(self, enable: bool = True) -> None:
+        """Record CUDA events around each kernel of the following steps."""
+        B.pf_profile_enable(self.handle, enable)
+
+    def profile_read(self) -> dict:
+        """{kernel: (launches, total ms)} since profiling was enabled / last read."""
+        return B.pf_profile_read(self.handle)
+
+    def estimate(self):
+        """(xhat (n_tracks, 5) float32, log_Z (n_tracks,) float64, status)."""
+        x = np.zeros((self.n_tracks, 5), np.float32)
+        z = np.zeros(self.n_tracks, np.float64)
+        st = B.pf_estimate(self.handle, x.ctypes.data_as(C.c_void_p), z.ctypes.data_as(C.c_void_p))
+        return x, z, st
+
+    def stats(self, step: int, track: int = 0) -> dict:
+        G = self.configs[track].G
+        ring = np.zeros(G, np.int32)
+        logW = np.zeros(G, np.float64)
+        gx = np.zeros((5, G), np.float32)
+        ess = np.zeros(G, np.float32)
+        s = B.pf_exchange_stats(self.handle, track, step, ring.ctypes.data_as(C.c_void_p),
+                                logW.ctypes.data_as(C.c_void_p), gx.ctypes.data_as(C.c_void_p),
+                                ess.ctypes.data_as(C.c_void_p))
+        return dict(step=s.step, n_ex=s.n_ex, pe_eff=s.pe_eff, log_c=s.log_c, log_Z=s.log_Z,
+                    xhat=np.array(s.xhat[:]), degenerate=s.degenerate_groups, ring=ring, logW=logW,
+                    group_xhat=gx, group_ess=ess)
+
+    def history_stats(self, first: int, count: int, track: int = 0) -> List[dict]:
+        out = B.pf_history(self.handle, track, first, count)
+        return [dict(step=s.step, n_ex=s.n_ex, pe_eff=s.pe_eff, log_c=s.log_c, log_Z=s.log_Z,
+                     xhat=np.array(s.xhat[:]), degenerate=s.degenerate_groups) for s in out]
+
+    def particles(self, track: int = 0, parents: bool = False) -> dict:
+        """Latest step's X_k (5, N), ancestors, log-weights (and parents)."""
+        n = self.N[track]
+        st = torch.empty((5, n), dtype=torch.float32, device=self.device)
+        anc = torch.empty(n, dtype=torch.int32, device=self.device)
+        lw = torch.empty(n, dtype=torch.float32, device=self.device)
+        par = torch.empty(n, dtype=torch.int32, device=self.device) if parents else None
+        B.pf_particles(self.handle, track, _ptr(st), _ptr(anc), _ptr(lw), _ptr(par),
+                       C.c_void_p(self.stream.cuda_stream))
+        self.stream.synchronize()
+        out = dict(states=st, anc=anc, logw=lw)
+        if parents:
+            out["parent"] = par
+        return out
+
+
+def resample(logw: torch.Tensor, u: torch.Tensor, G: int, Np: int, want_q: bool = False):
+    """GPU per-group systematic resampling (pf_resample) of G*Np log-weights."""
+    assert logw.dtype == torch.float32 and logw.is_cuda and logw.numel() == G * Np
+    assert u.dtype == torch.int32 and u.numel() == G
+    dev = logw.device
+    anc = torch.empty(G * Np, dtype=torch.int32, device=dev)
+    q = torch.empty(G * Np, dtype=torch.int64, device=dev) if want_q else None
+    nb = B.pf_resample_workspace(G, Np)
+    ws = torch.empty(nb + 256, dtype=torch.uint8, device=dev)
+    wp = (ws.data_ptr() + 255) // 256 * 256
+    s = torch.cuda.current_stream(dev)
+    B.pf_resample(_ptr(logw), _ptr(u), G, Np, _ptr(anc), _ptr(q), C.c_void_p(wp), nb, C.c_void_p(s.cuda_stream))
+    s.synchronize()
+    return (anc, q) if want_q else anc

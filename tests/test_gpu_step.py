@@ -1,0 +1,64 @@
+"""The whole GPU filter step (pf_step through the C ABI) against the CPU
+oracle, step by step: ring order, exchange count, ancestry and resampling
+bit-exact; states, log-weights and group / global statistics within 1e-5
+relative + 1e-4 absolute."""
+import numpy as np
+import pytest
+
+from paper_1310_4624_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dev():
+    import __graft_entry__ as ge
+    ge.build()
+    return torch.device("cuda:0")
+
+
+def _run(dev, wl, steps):
+    from parity_util import run_and_compare
+    from paper_1310_4624_gb300.filter import ParticleFilter, config_from_workload
+    frames, truth = synth.make_sequence(wl, T=steps)
+    cfg = config_from_workload(wl, truth[0], record_ancestors=True)
+    pf = ParticleFilter([cfg], history=max(4, steps), device=dev)
+    fr = torch.from_numpy(frames).to(dev)
+    rep = run_and_compare(pf, wl, frames, truth[0], steps, fr)
+    pf.close()
+    return rep
+
+
+SMALL = [
+    ("cfg1_rna", synth.small_rna()),                                                        # G=4 x 1024, 64x64
+    ("arna_ragged", synth.small_rna(G=5, Np=300, H=40, W=40, mode=synth.ARNA)),
+    ("rna50_nonsquare", synth.small_rna(G=3, Np=257, H=48, W=56, ex_ratio=0.5, seed=5, data_seed=3)),
+    ("single_group", synth.small_rna(G=1, Np=500, mode=synth.ARNA)),
+    ("two_groups_multi_tile", synth.small_rna(G=2, Np=4096 + 33, mode=synth.ARNA, seed=9)),
+    ("sharing_init", synth.sharing(G=8, Np=512, H=64, W=64, mode=synth.ARNA)),
+    ("sharing_rna", synth.sharing(G=6, Np=200, H=64, W=64, mode=synth.RNA)),
+    ("full_ratio", synth.small_rna(G=3, Np=64, ex_ratio=1.0)),
+    ("patch_r3", synth.small_rna(G=2, Np=128, patch_radius=3)),
+]
+
+
+@pytest.mark.parametrize("name,wl", SMALL, ids=[n for n, _ in SMALL])
+def test_small_configs_match_oracle(dev, name, wl):
+    rep = _run(dev, wl, 6)
+    assert len(rep) == 6
+
+
+@pytest.mark.parametrize("mode", [synth.RNA, synth.ARNA])
+def test_tracking_scale_matches_oracle(dev, mode):
+    """The benchmark's tracking workload shape: 512x512, G=64 x 16384."""
+    rep = _run(dev, synth.tracking(mode=mode), 3)
+    if mode == synth.RNA:
+        assert [r["n_ex"] for r in rep] == [0, 1638, 1638]
+
+
+def test_sharing_scale_matches_oracle(dev):
+    """Information-sharing workload shape: 512x512, G=256 x 4096, ARNA."""
+    rep = _run(dev, synth.sharing(mode=synth.ARNA), 3)
+    assert rep[1]["n_ex"] > 0
