@@ -79,8 +79,8 @@ enum {
  * constant velocity with unit frame interval and independent Gaussian noise
  * sigma_pos (position), sigma_v (velocity), sigma_I (intensity). */
 typedef struct pf_track_config {
-  int32_t G;            /* groups (the paper's M PEs), 1 .. 4096 */
-  int32_t Np;           /* particles per group (N_p = N / M), 1 .. 2^24 / G */
+  int32_t G;            /* groups (the paper's M PEs), 1 .. 1024 */
+  int32_t Np;           /* particles per group (N_p = N / M), 1 .. 2^20; G*Np < 2^31 */
   int32_t H, W;         /* frame size, 1 .. 16384 each */
   int32_t patch_radius; /* 1 .. 7; the paper's workloads use 5 (11 x 11) */
   int32_t mode;         /* PF_RNA or PF_ARNA */
@@ -196,6 +196,7 @@ pf_status pf_resample_workspace(int32_t G, int32_t Np, size_t* bytes);
  * Output j takes the particle i with S_i <= (j + u/2^32) Q / Np < S_{i+1},
  * S the prefix sums of q and Q their total, compared exactly in 128-bit
  * integers; a group with Q = 0 resamples as the identity.
+ * G >= 1, 1 <= Np <= 2^20, G*Np < 2^31.
  * Errors: PF_ERR_ARG, PF_ERR_WORKSPACE, PF_ERR_CUDA. */
 pf_status pf_resample(const float* logw_dev, const uint32_t* u_dev, int32_t G, int32_t Np,
                       uint32_t* anc_dev, uint64_t* q_dev, void* workspace_dev, size_t bytes,

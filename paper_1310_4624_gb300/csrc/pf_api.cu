@@ -1,6 +1,8 @@
 // pf_api.cu -- the C ABI declared in include/pfarna.h: validation, workspace
 // layout, launch sequence of one filter step, and read-back.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <cmath>
 #include <cstdio>
@@ -41,8 +43,12 @@ struct pf_handle {
   HistRec* hist = nullptr;
   GroupHist* ghist = nullptr;
   int* ring = nullptr;
+  int* ring_next = nullptr;
+  int n_ring_blocks = 0;
+  int max_G = 1;
   uint32_t* parent = nullptr;
   DevState* ds = nullptr;
+  CUtensorMap* tmaps = nullptr;  // nullptr: frames read through L1 only
   // kernel timing (pf_profile_enable / pf_profile_read)
   int prof = 0;
   std::vector<cudaEvent_t> ev[PF_KERNEL_COUNT];  // start, stop, start, stop, ...
@@ -87,11 +93,22 @@ QuantCoeffs make_qc() {
 }
 
 struct Layout {
-  size_t trk, ts, gs, gd, tiles, pv0, pv1, I0, I1, anc, lw, tp, ypad, hist, ghist, ring, parent, ds, total;
+  size_t trk, ts, gs, gd, tiles, pv0, pv1, I0, I1, anc, lw, tp, ypad, hist, ghist, ring, ring_next, parent, ds, tmap, total;
   long long N_total = 0, ypad_total = 0, parent_total = 0, ghist_total = 0;
   int G_total = 0, n_tiles = 0, hist_total = 0;
   int R = 5;
 };
+
+// Padded frame geometry: a border of 2R+1 zero pixels, rows 16-byte
+// aligned, and at least one TMA box in each dimension.
+long long pad_pitch(int W, int R) {
+  const long long p = ((long long)W + 2 * (2 * R + 1) + 3) / 4 * 4;
+  return p < ROI_W ? ROI_W : p;
+}
+long long pad_rows(int H, int R) {
+  const long long r = (long long)H + 2 * (2 * R + 1);
+  return r < ROI_BOX_H ? ROI_BOX_H : r;
+}
 
 bool finite_nonneg(float v) { return std::isfinite(v) && v >= 0.0f; }
 
@@ -107,8 +124,8 @@ std::string validate(const pf_track_config* c, int n, int history) {
       std::snprintf(b, sizeof b, "track %d: %s", t, what);
       return std::string(b);
     };
-    if (x.G < 1 || x.G > MAX_G) return bad("G must be in [1, 4096]");
-    if (x.Np < 1 || (long long)x.G * x.Np > (1ll << 24) * 16) return bad("Np must be >= 1 and G*Np <= 2^28");
+    if (x.G < 1 || x.G > MAX_G) return bad("G must be in [1, 1024]");
+    if (x.Np < 1 || x.Np > (1 << 20)) return bad("Np must be in [1, 2^20]");
     if (x.H < 1 || x.W < 1 || x.H > 16384 || x.W > 16384) return bad("H and W must be in [1, 16384]");
     if (x.patch_radius < 1 || x.patch_radius > 7) return bad("patch_radius must be in [1, 7]");
     if (x.patch_radius != c[0].patch_radius) return bad("all tracks must share patch_radius");
@@ -136,14 +153,12 @@ std::string validate(const pf_track_config* c, int n, int history) {
 Layout plan(const pf_track_config* c, int n, int history) {
   Layout L{};
   L.R = c[0].patch_radius;
-  const int pad = 2 * L.R + 1;
   for (int t = 0; t < n; ++t) {
     const long long Nt = (long long)c[t].G * c[t].Np;
     L.N_total += Nt;
     L.G_total += c[t].G;
-    L.n_tiles += c[t].G * ((c[t].Np + K1_THREADS - 1) / K1_THREADS);
-    const long long pitch = ((long long)c[t].W + 2 * pad + 3) / 4 * 4;
-    L.ypad_total += pitch * ((long long)c[t].H + 2 * pad);
+    L.n_tiles += c[t].G * ((c[t].Np + K1_TILE - 1) / K1_TILE);
+    L.ypad_total += pad_pitch(c[t].W, L.R) * pad_rows(c[t].H, L.R);
     if (c[t].record_ancestors) L.parent_total += Nt * history;
     L.hist_total += history;
     L.ghist_total += (long long)history * c[t].G;
@@ -155,11 +170,13 @@ Layout plan(const pf_track_config* c, int n, int history) {
     return at;
   };
   L.ds = take(sizeof(DevState));
+  L.tmap = take(sizeof(CUtensorMap) * n);
   L.trk = take(sizeof(TrackParams) * n);
   L.ts = take(sizeof(TrackState) * n);
   L.gs = take(sizeof(GroupState) * L.G_total);
   L.gd = take(sizeof(GroupDesc) * L.G_total);
   L.ring = take(sizeof(int) * L.G_total);
+  L.ring_next = take(sizeof(int) * L.G_total);
   L.tiles = take(sizeof(int4) * L.n_tiles);
   L.pv0 = take(sizeof(float4) * L.N_total);
   L.pv1 = take(sizeof(float4) * L.N_total);
@@ -264,6 +281,7 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
   h->gs = (GroupState*)(w + L.gs);
   h->gd = (GroupDesc*)(w + L.gd);
   h->ring = (int*)(w + L.ring);
+  h->ring_next = (int*)(w + L.ring_next);
   h->tiles = (int4*)(w + L.tiles);
   h->pv[0] = (float4*)(w + L.pv0);
   h->pv[1] = (float4*)(w + L.pv1);
@@ -276,9 +294,9 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
   h->hist = (HistRec*)(w + L.hist);
   h->ghist = (GroupHist*)(w + L.ghist);
   h->parent = (uint32_t*)(w + L.parent);
+  h->tmaps = (CUtensorMap*)(w + L.tmap);
 
   // host tables
-  const int pad = 2 * L.R + 1;
   std::vector<TrackParams> tp(n_tracks);
   std::vector<GroupDesc> gd;
   std::vector<int4> tiles;
@@ -297,6 +315,7 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
     P.ex_ratio = c.ex_ratio; P.cutoff = c.pe_eff_cutoff;
     P.c_psf = (float)(1.4426950408889634 / (2.0 * (double)c.sigma_psf * (double)c.sigma_psf));
     P.inv2so2 = (float)(1.0 / (2.0 * (double)c.sigma_obs * (double)c.sigma_obs));
+    P.kappa = (float)std::exp2(-2.0 * (double)P.c_psf);
     P.key0 = (uint32_t)c.seed;
     P.key1 = (uint32_t)(c.seed >> 32);
     P.tag = c.track_id << 8;
@@ -304,8 +323,9 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
     P.part_off = part;
     P.group_off = gro;
     P.tile_off = tio;
-    P.tiles_per_group = (c.Np + K1_THREADS - 1) / K1_THREADS;
-    P.pitch = (int)(((long long)c.W + 2 * pad + 3) / 4 * 4);
+    P.tiles_per_group = (c.Np + K1_TILE - 1) / K1_TILE;
+    P.m_Np = fastdiv_magic((uint32_t)c.Np);
+    P.pitch = (int)pad_pitch(c.W, L.R);
     P.ypad_off = ypo;
     P.hist_off = ho;
     P.ghist_off = gho;
@@ -323,8 +343,8 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
       D.track = t;
       D.g = g;
       D.tile_begin = (int)tiles.size();
-      for (int j0 = 0; j0 < c.Np; j0 += K1_THREADS)
-        tiles.push_back(make_int4(t, g, j0, c.Np - j0 < K1_THREADS ? c.Np - j0 : K1_THREADS));
+      for (int j0 = 0; j0 < c.Np; j0 += K1_TILE)
+        tiles.push_back(make_int4(t, g, j0, c.Np - j0 < K1_TILE ? c.Np - j0 : K1_TILE));
       D.tile_count = (int)tiles.size() - D.tile_begin;
       gd.push_back(D);
     }
@@ -332,18 +352,44 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
     part += Nt;
     gro += c.G;
     tio += c.G * P.tiles_per_group;
-    ypo += (long long)P.pitch * (c.H + 2 * pad);
+    ypo += (long long)P.pitch * pad_rows(c.H, L.R);
     ho += history;
     gho += (long long)history * c.G;
     if (c.record_ancestors) paro += Nt * history;
   }
   h->tp = tp;
   cudaStream_t s = (cudaStream_t)stream;
+
+  // One TMA descriptor per track over its padded frame (boxes of ROI_W x
+  // ROI_BOX_H floats).  If the driver cannot encode them, the propagate
+  // kernel reads every frame through L1 instead.
+  std::vector<CUtensorMap> maps(n_tracks);
+  {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    bool ok = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                  cudaSuccess && q == cudaDriverEntryPointSuccess && fn != nullptr;
+    for (int t = 0; ok && t < n_tracks; ++t) {
+      const TrackParams& P = tp[t];
+      cuuint64_t dims[2] = {(cuuint64_t)P.pitch, (cuuint64_t)pad_rows(P.H, L.R)};
+      cuuint64_t strides[1] = {(cuuint64_t)P.pitch * sizeof(float)};
+      cuuint32_t box[2] = {(cuuint32_t)ROI_W, (cuuint32_t)ROI_BOX_H};
+      cuuint32_t estr[2] = {1, 1};
+      CUresult r = ((PFN_cuTensorMapEncodeTiled_v12000)fn)(
+          &maps[t], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)(h->ypad + P.ypad_off), dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      ok = (r == CUDA_SUCCESS);
+    }
+    if (!ok) h->tmaps = nullptr;
+  }
   cudaError_t e;
   if ((e = cudaMemsetAsync(w, 0, L.total, s)) != cudaSuccess) { pf_destroy(h); return cuda_fail(nullptr, e, "cudaMemsetAsync"); }
   if ((e = cudaMemcpyAsync(h->trk, tp.data(), sizeof(TrackParams) * n_tracks, cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemcpyAsync(h->gd, gd.data(), sizeof(GroupDesc) * gd.size(), cudaMemcpyHostToDevice, s)) ||
-      (e = cudaMemcpyAsync(h->tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s))) {
+      (e = cudaMemcpyAsync(h->tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s)) ||
+      (h->tmaps && (e = cudaMemcpyAsync(h->tmaps, maps.data(), sizeof(CUtensorMap) * n_tracks,
+                                        cudaMemcpyHostToDevice, s)))) {
     pf_destroy(h);
     return cuda_fail(nullptr, e, "uploading track tables");
   }
@@ -355,12 +401,16 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
   if ((e = k1_occupancy(h->R, &occ)) != cudaSuccess) { pf_destroy(h); return cuda_fail(nullptr, e, "occupancy"); }
   const long long want = (long long)sms * (occ > 0 ? occ : 1);
   h->k1_grid = (int)(h->n_tiles < want ? h->n_tiles : want);
+  int n_arna = 0;
+  for (int t = 0; t < n_tracks; ++t) n_arna += (cfg[t].mode == PF_ARNA && cfg[t].G > 1 && cfg[t].G <= RING_SMEM_G);
+  h->n_ring_blocks = n_arna == 0 ? 0 : (n_arna < 16 ? n_arna : 16);
+  for (int t = 0; t < n_tracks; ++t) h->max_G = cfg[t].G > h->max_G ? cfg[t].G : h->max_G;
   h->rs_cluster = resample_cluster(cfg[0].Np, n_tracks == 1);
 
   InitArgs ia{h->trk, h->tiles, h->n_tiles, h->N_total, user_state, h->pv[1], h->In[1]};
   if ((e = launch_init(ia, h->k1_grid, s)) != cudaSuccess) { pf_destroy(h); return cuda_fail(nullptr, e, "k_init"); }
-  GlobalArgs ga{h->trk, h->ts, h->gs, h->ring, h->hist, h->ghist, h->history, 0, h->ds};
-  if ((e = launch_global(ga, n_tracks, s)) != cudaSuccess) { pf_destroy(h); return cuda_fail(nullptr, e, "k_global"); }
+  GlobalArgs ga{h->trk, h->ts, h->gs, h->ring, h->ring_next, h->hist, h->ghist, h->history, 0, h->ds};
+  if ((e = launch_global(ga, n_tracks, h->max_G, s)) != cudaSuccess) { pf_destroy(h); return cuda_fail(nullptr, e, "k_global"); }
   *out = h;
   return PF_OK;
 }
@@ -382,29 +432,29 @@ pf_status pf_step(pf_handle* h, const float* const* frames, void* stream) {
     a.ypad = h->ypad;
     a.t0 = t0;
     a.R = h->R;
-    long long maxpix = 1;
+    int maxH = 1;
     for (int i = 0; i < nt; ++i) {
       a.frames[i] = frames[t0 + i];
-      const long long px = (long long)h->cfg[t0 + i].H * h->cfg[t0 + i].W;
-      if (px > maxpix) maxpix = px;
+      if (h->cfg[t0 + i].H > maxH) maxH = h->cfg[t0 + i].H;
     }
-    const long long bx = (maxpix + 255) / 256;
-    if ((e = launch_frame_prep(a, nt, (int)(bx > 1024 ? 1024 : bx), s)) != cudaSuccess)
+    if ((e = launch_frame_prep(a, nt, maxH > 4096 ? 4096 : maxH, s)) != cudaSuccess)
       return cuda_fail(h, e, "k_frame_prep");
   }
   if ((e = mark(h, PF_KERNEL_FRAME_PREP, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
   K1Args k1{h->trk, h->tiles, h->n_tiles, h->gs, h->ts, h->ds, h->pv[0], h->pv[1], h->In[0], h->In[1],
-            h->anc, h->parent, h->history, h->lw, h->tile_part, h->ypad};
+            h->anc, h->parent, h->history, h->lw, h->tile_part, h->ypad, h->tmaps, h->ring_next,
+            h->n_ring_blocks, h->n_tracks};
   if ((e = mark(h, PF_KERNEL_PROPAGATE_WEIGHT, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
-  if ((e = launch_propagate(k1, h->R, h->k1_grid, s)) != cudaSuccess) return cuda_fail(h, e, "k_propagate_weight");
+  if ((e = launch_propagate(k1, h->R, h->k1_grid + h->n_ring_blocks, s)) != cudaSuccess)
+    return cuda_fail(h, e, "k_propagate_weight");
   if ((e = mark(h, PF_KERNEL_PROPAGATE_WEIGHT, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
   ResampleArgs ra{h->gd, h->gs, h->tile_part, h->lw, h->anc, nullptr, nullptr, 0, h->qc, h->ds};
   if ((e = mark(h, PF_KERNEL_RESAMPLE, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
   if ((e = launch_resample(ra, h->G_total, h->rs_cluster, s)) != cudaSuccess) return cuda_fail(h, e, "k_resample");
   if ((e = mark(h, PF_KERNEL_RESAMPLE, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
-  GlobalArgs ga{h->trk, h->ts, h->gs, h->ring, h->hist, h->ghist, h->history, 1, h->ds};
+  GlobalArgs ga{h->trk, h->ts, h->gs, h->ring, h->ring_next, h->hist, h->ghist, h->history, 1, h->ds};
   if ((e = mark(h, PF_KERNEL_GLOBAL, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
-  if ((e = launch_global(ga, h->n_tracks, s)) != cudaSuccess) return cuda_fail(h, e, "k_global");
+  if ((e = launch_global(ga, h->n_tracks, h->max_G, s)) != cudaSuccess) return cuda_fail(h, e, "k_global");
   if ((e = mark(h, PF_KERNEL_GLOBAL, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
   h->steps_run += 1;
   h->last_stream = s;
@@ -515,7 +565,8 @@ static size_t resample_ws(int G) {
 
 pf_status pf_resample_workspace(int32_t G, int32_t Np, size_t* bytes) {
   if (!bytes) return fail(nullptr, PF_ERR_ARG, "bytes is NULL");
-  if (G < 1 || Np < 1 || (long long)G * Np >= (1ll << 31)) return fail(nullptr, PF_ERR_ARG, "bad G or Np");
+  if (G < 1 || Np < 1 || Np > (1 << 20) || (long long)G * Np >= (1ll << 31))
+    return fail(nullptr, PF_ERR_ARG, "bad G or Np");
   *bytes = resample_ws(G);
   return PF_OK;
 }
@@ -523,7 +574,8 @@ pf_status pf_resample_workspace(int32_t G, int32_t Np, size_t* bytes) {
 pf_status pf_resample(const float* logw, const uint32_t* u, int32_t G, int32_t Np, uint32_t* anc, uint64_t* q,
                       void* workspace, size_t bytes, void* stream) {
   if (!logw || !u || !anc || !workspace) return fail(nullptr, PF_ERR_ARG, "NULL pointer");
-  if (G < 1 || Np < 1 || (long long)G * Np >= (1ll << 31)) return fail(nullptr, PF_ERR_ARG, "bad G or Np");
+  if (G < 1 || Np < 1 || Np > (1 << 20) || (long long)G * Np >= (1ll << 31))
+    return fail(nullptr, PF_ERR_ARG, "bad G or Np");
   if ((uintptr_t)workspace % ALIGN) return fail(nullptr, PF_ERR_WORKSPACE, "workspace must be 256-byte aligned");
   if (bytes < resample_ws(G)) return fail(nullptr, PF_ERR_WORKSPACE, "workspace too small");
   char* w = (char*)workspace;

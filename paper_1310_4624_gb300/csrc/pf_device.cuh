@@ -6,17 +6,32 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace pf {
 
 // ---------------------------------------------------------------- constants
-constexpr int K1_THREADS = 128;       // particles per propagate/weight tile
+constexpr int K1_THREADS = 256;       // threads of the propagate/weight kernel
+#ifndef PF_K1_PPT
+#define PF_K1_PPT 2
+#endif
+constexpr int K1_PPT = PF_K1_PPT;     // particles per thread
+constexpr int K1_TILE = K1_THREADS * K1_PPT;  // slots per tile (one group)
+#ifndef PF_K1_MIN_BLOCKS
+#define PF_K1_MIN_BLOCKS 4
+#endif
+constexpr int K1_MIN_BLOCKS = PF_K1_MIN_BLOCKS;  // resident propagate CTAs per SM the register budget targets
+constexpr int ROI_W = 40;             // staged frame box width = smem row pitch (floats, = 8 mod 32 banks)
+constexpr int ROI_BOX_H = 8;          // rows per TMA box
+constexpr int ROI_MAX_BOXES = 8;      // staged rows <= 64
+constexpr int ROI_FLOATS = ROI_W * ROI_BOX_H * ROI_MAX_BOXES;
+constexpr int RING_SMEM_G = ROI_FLOATS / 2;  // ring orders drawn ahead up to this G
 constexpr int RS_THREADS = 512;       // resampler CTA
 constexpr int RS_ITEMS = 8;           // items per thread per resampler sub-chunk
 constexpr int RS_SUB = RS_THREADS * RS_ITEMS;
-constexpr int GL_THREADS = 256;       // per-track global-step CTA
-constexpr int MAX_G = 4096;           // groups per track
+constexpr int GL_THREADS = 1024;      // per-track global-step CTA, one thread per group
+constexpr int MAX_G = GL_THREADS;      // groups per track
 constexpr int MAX_FRAMES_PER_LAUNCH = 1024;
 
 // Philox stream ids (counter word 3 = track << 8 | stream << 4 | call).
@@ -37,6 +52,8 @@ struct TrackParams {
   float ex_ratio, cutoff;
   float c_psf;      // log2(e) / (2 sigma_psf^2): gx(u) = 2^(-c_psf (u-x)^2)
   float inv2so2;    // 1 / (2 sigma_obs^2)
+  float kappa;      // 2^(-2 c_psf): ratio of successive Gaussian ratios
+  unsigned long long m_Np;  // fast-division reciprocal of Np
   uint32_t key0, key1, tag;   // Philox key; tag = track_id << 8
   int record;
   long long part_off;         // first particle of the track (global slot)
@@ -62,11 +79,12 @@ struct TrackState {
   double log_Z;      // sum of log c
   float xhat[5];
   int steps_done;
+  unsigned long long m_nex;  // fast-division reciprocal of n_ex (see fastdiv)
 };
 
 // Per-group state (global group index).
 struct GroupState {
-  double lambda;        // carried log group weight log W^(m)
+  double lambda;        // carried log group weight log W^(m) (an FP32 value)
   float off;            // log w offset of particles originating here at step k
   int pred;             // group (track-local) that sends to this one at step k
   uint32_t exo;         // exchange offset o_g of step k
@@ -167,6 +185,18 @@ __device__ __forceinline__ bool draw_bounded(uint32_t k0, uint32_t k1, uint32_t 
   return false;
 }
 
+// ------------------------------------------------------- fast division
+// floor(n / d) for n < 2^32 and 1 <= d < 2^32 as the high word of n * M,
+// M = ceil(2^64 / d) (Lemire, Kaser, Kurz, "Faster remainder by direct
+// computation", 2019: exact when 64 >= 32 + log2 d); d = 1 is passed as
+// M = 0 and returns n.
+__host__ __device__ inline unsigned long long fastdiv_magic(uint32_t d) {
+  return d <= 1 ? 0ull : (~0ull) / d + 1ull;
+}
+__device__ __forceinline__ uint32_t fastdiv(uint32_t n, unsigned long long M) {
+  return M == 0ull ? n : (uint32_t)__umul64hi((unsigned long long)n, M);
+}
+
 // ------------------------------------------------------- fixed-point weights
 // q = trunc(p 2^(n+40)), z = fl(fl(lw - M) * L2E), n = rint(z), f = z - n,
 // p = sum_{d<=7} c_d f^d by FP32 Horner; 0 when z < -40 or NaN.  All
@@ -186,30 +216,44 @@ __device__ __forceinline__ unsigned long long quantize(float lw, float M, const 
   float p = qc.c[7];
 #pragma unroll
   for (int d = 6; d >= 0; --d) p = __fmaf_rn(p, f, qc.c[d]);
-  const float scale = __int_as_float(((int)n + 40 + 127) << 23);  // 2^(n+40), n in [-40, 0]
-  return (unsigned long long)__fmul_rn(p, scale);
+  // trunc(p 2^(n+40)) with integer shifts of p's significand (p > 0 normal):
+  // p = mant 2^(ex - 23), so the code is mant shifted by ex - 23 + n + 40.
+  const uint32_t bits = __float_as_uint(p);
+  const unsigned long long mant = (bits & 0x7fffffu) | 0x800000u;
+  const int sh = (int)((bits >> 23) & 0xffu) - 127 - 23 + (int)n + 40;
+  return sh >= 0 ? (mant << sh) : (mant >> (-sh));
 }
 
-// ------------------------------------------------------- 128-bit compares
-struct U128 {
-  unsigned long long lo, hi;
-};
-__device__ __forceinline__ U128 mul64(unsigned long long a, unsigned long long b) {
-  return U128{a * b, __umul64hi(a, b)};
+// FP32 approximation of a 64-bit unsigned value from its two 32-bit halves
+// (32-bit conversions only; relative error < 2^-23).
+__device__ __forceinline__ float u64_to_float_approx(unsigned long long v) {
+  return __fmaf_rn((float)(uint32_t)(v >> 32), 4294967296.0f, (float)(uint32_t)v);
 }
-__device__ __forceinline__ bool lt128(U128 a, U128 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
-__device__ __forceinline__ U128 shl32(U128 a) { return U128{a.lo << 32, (a.hi << 32) | (a.lo >> 32)}; }
 
-// Output j of a group with total Q, Np outputs and uniform word u lies
-// strictly below the prefix S: (j 2^32 + u) Q < S Np 2^32.
-struct ThetaCmp {
-  unsigned long long Q;
-  unsigned long long Np;
-  uint32_t u;
-  __device__ __forceinline__ bool below(long long j, unsigned long long S) const {
-    const U128 lhs = mul64(((unsigned long long)j << 32) | u, Q);
-    const U128 rhs = shl32(mul64(S, Np));
-    return lt128(lhs, rhs);
+// ------------------------------------------------- resampling thresholds
+// Output j of a group with total weight code Q, Np outputs and uniform word
+// u sits at theta_j = (j 2^32 + u) Q / (Np 2^32) on the prefix-sum axis.
+// Prefix sums S are integers, so theta_j < S exactly when T_j < S with
+// T_j = floor(theta_j) = j A + F1 + floor((j B + F0) / Np), where
+// A = Q div Np, B = Q mod Np, F = floor(u Q / 2^32), F1 = F div Np,
+// F0 = F mod Np.  With Np <= 2^20, j B + F0 < 2^41, and the division is the
+// high word of a product with ceil(2^64 / Np) (exact: 64 >= 41 + 20).
+struct Thresholds {
+  unsigned long long A, F1, M;
+  uint32_t B, F0, Np;
+
+  __device__ __forceinline__ void init(unsigned long long Q, uint32_t np, uint32_t u) {
+    Np = np;
+    A = Q / np;
+    B = (uint32_t)(Q - A * np);
+    const unsigned long long F = (unsigned long long)u * (Q >> 32) + (((unsigned long long)u * (uint32_t)Q) >> 32);
+    F1 = F / np;
+    F0 = (uint32_t)(F - F1 * np);
+    M = np > 1 ? (~0ull) / np + 1ull : 0ull;
+  }
+  __device__ __forceinline__ unsigned long long T(uint32_t j) const {
+    const unsigned long long n = (unsigned long long)j * B + F0;
+    return (unsigned long long)j * A + F1 + (Np > 1 ? __umul64hi(n, M) : n);
   }
 };
 

@@ -20,7 +20,10 @@
 // The step index lives on the device, so the same launch sequence serves
 // every step.
 #include <cooperative_groups.h>
+#include <cuda.h>
 #include <cuda_runtime.h>
+
+#include <climits>
 
 #include <cmath>
 #include <cstdint>
@@ -115,11 +118,13 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
 // Initial population (Sec. V tracking / information-sharing modes), drawn
 // from Philox stream INIT into the buffer step 0 reads.
 __global__ void __launch_bounds__(K1_THREADS) k_init(InitArgs a) {
-  for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
-    const int4 td = a.tiles[tile];
-    if ((int)threadIdx.x >= td.w) continue;
+  for (int e = blockIdx.x * K1_PPT; e < a.n_tiles * K1_PPT; e += gridDim.x * K1_PPT) {
+   for (int q = 0; q < K1_PPT; ++q) {
+    const int4 td = a.tiles[(e + q) / K1_PPT];
+    const int jj = threadIdx.x + ((e + q) % K1_PPT) * K1_THREADS;
+    if (jj >= td.w) continue;
     const TrackParams& P = a.trk[td.x];
-    const int g = td.y, j = td.z + threadIdx.x;
+    const int g = td.y, j = td.z + jj;
     const long long i = P.part_off + (long long)g * P.Np + j;
     float s[5];
     if (P.init_kind == INIT_USER) {
@@ -147,6 +152,7 @@ __global__ void __launch_bounds__(K1_THREADS) k_init(InitArgs a) {
     }
     a.pv[i] = make_float4(s[0], s[1], s[2], s[3]);
     a.In[i] = s[4];
+   }
   }
 }
 
@@ -160,138 +166,443 @@ __global__ void k_frame_prep(FrameArgs a) {
   const float* __restrict__ z = a.frames[tt];
   float* __restrict__ yp = a.ypad + P.ypad_off;
   const int pad = 2 * a.R + 1;
-  const long long n = (long long)P.H * P.W;
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-    const int v = (int)(p / P.W), u = (int)(p - (long long)v * P.W);
-    yp[(long long)(v + pad) * P.pitch + (u + pad)] = __fsub_rn(__ldg(z + p), P.bg);
+  const float bg = P.bg;
+  for (int v = blockIdx.x; v < P.H; v += gridDim.x) {
+    const float* __restrict__ zr = z + (long long)v * P.W;
+    float* __restrict__ yr = yp + (long long)(v + pad) * P.pitch + pad;
+    for (int u = threadIdx.x; u < P.W; u += blockDim.x) yr[u] = __fsub_rn(__ldg(zr + u), bg);
   }
 }
 
 // ===================================================================== K1
-// Log-likelihood of one particle (Sec. V appearance model):
-//   -sum_{(2R+1)^2 patch} (y - I gx(u) gy(v))^2 / (2 sigma_obs^2),
-// patch centred on the nearest pixel, y = z - b, y = 0 outside the frame.
-// Reads the padded frame; the centre is clamped so that a patch entirely
-// off the frame reads padding, while the model terms use the true centre.
+// Gaussian profile values 2^(-c (u - x)^2) on the D = 2R+1 patch columns
+// u = cf - R .. cf + R, by a ratio recurrence from the centre column
+// outwards: g(u+1) = g(u) r(u), r(u+1) = r(u) 2^(-2c).  Three MUFU ex2 per
+// axis instead of D; relative error <= 2R FP32 roundings.
 template <int R>
-__device__ __forceinline__ float loglik(const float* __restrict__ yp, int pitch, int H, int W, float x, float y,
-                                        float I, float c_psf, float inv2so2) {
-  constexpr int D = 2 * R + 1;
-  constexpr int PAD = 2 * R + 1;
-  const float cxf = floorf(x + 0.5f), cyf = floorf(y + 0.5f);
-  const int cx = (int)fminf(fmaxf(cxf, -(float)(R + 1)), (float)(W + R));
-  const int cy = (int)fminf(fmaxf(cyf, -(float)(R + 1)), (float)(H + R));
-  const float* __restrict__ row = yp + (long long)(cy - R + PAD) * pitch + (cx - R + PAD);
-  float gxI[D];
+__device__ __forceinline__ void gauss_row(float cf, float x, float c, float kappa, float (&g)[2 * R + 1]) {
+  const float d = cf - x;                        // centre offset, |d| <= 1/2
+  g[R] = ex2(-c * d * d);
+  float up = ex2(-c * fmaf(2.0f, d, 1.0f));      // g(R+1) / g(R)
+  float dn = ex2(c * fmaf(2.0f, d, -1.0f));      // g(R-1) / g(R)
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
-    const float d = (cxf + (float)(a - R)) - x;
-    gxI[a] = I * ex2(-c_psf * d * d);
+  for (int a = 1; a <= R; ++a) {
+    g[R + a] = g[R + a - 1] * up;
+    g[R - a] = g[R - a + 1] * dn;
+    up *= kappa;
+    dn *= kappa;
   }
-  float acc = 0.0f;
+}
+
+// One patch row: acc + sum_a (y_a - gxI[a] gy)^2, rows of shared memory
+// (compile-time pitch) or of global memory read through L1.
+template <int R>
+__device__ __forceinline__ float row_ss_smem(const float* __restrict__ rp, const float (&gxI)[2 * R + 1], float gy,
+                                             float acc) {
 #pragma unroll
-  for (int b = 0; b < D; ++b) {
-    const float d = (cyf + (float)(b - R)) - y;
-    const float gy = ex2(-c_psf * d * d);
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const float r = fmaf(-gxI[a], gy, __ldg(row + a));
-      acc = fmaf(r, r, acc);
-    }
-    row += pitch;
+  for (int a = 0; a < 2 * R + 1; ++a) {
+    const float r = fmaf(-gxI[a], gy, rp[a]);
+    acc = fmaf(r, r, acc);
   }
-  return -acc * inv2so2;
+  return acc;
+}
+template <int R>
+__device__ __forceinline__ float row_ss_global(const float* __restrict__ rp, const float (&gxI)[2 * R + 1], float gy,
+                                               float acc) {
+#pragma unroll
+  for (int a = 0; a < 2 * R + 1; ++a) {
+    const float r = fmaf(-gxI[a], gy, __ldg(rp + a));
+    acc = fmaf(r, r, acc);
+  }
+  return acc;
+}
+
+// Sum over the patch of (y - I gx gy)^2; `row(b)` is the address of patch
+// row b (0 .. 2R).  Rows are visited centre-out so that gy follows the same
+// ratio recurrence as gauss_row with four live registers; dy = cyf - y.
+template <int R, bool SMEM>
+__device__ __forceinline__ float patch_ss(const float* __restrict__ base, int pitch, const float (&gxI)[2 * R + 1],
+                                          float dy, float c, float kappa) {
+  auto row = [&](int b, float gy, float acc) {
+    if constexpr (SMEM)
+      return row_ss_smem<R>(base + b * ROI_W, gxI, gy, acc);
+    else
+      return row_ss_global<R>(base + (long long)b * pitch, gxI, gy, acc);
+  };
+  const float g = ex2(-c * dy * dy);
+  float up = ex2(-c * fmaf(2.0f, dy, 1.0f));
+  float dn = ex2(c * fmaf(2.0f, dy, -1.0f));
+  float acc = row(R, g, 0.0f);
+  float gu = g, gd = g;
+#pragma unroll
+  for (int a = 1; a <= R; ++a) {
+    gu *= up;
+    gd *= dn;
+    up *= kappa;
+    dn *= kappa;
+    acc = row(R + a, gu, acc);
+    acc = row(R - a, gd, acc);
+  }
+  return acc;
+}
+
+// Natural log of a uniform u = ((w >> 9) + 1/2) 2^-23: MUFU log2 where its
+// absolute error (2^-22 on [1/2, 2]) is small against |ln u|, and the series
+// -(t + t^2/2 + t^3/3), t = 1 - u, for the top 2^-10 of the interval.
+__device__ __forceinline__ float log_u01(float u) {
+  const float t = 1.0f - u;  // exact
+  const float series = -t * fmaf(t, fmaf(t, 0.333333343f, 0.5f), 1.0f);
+  return t < 9.765625e-4f ? series : __log2f(u) * 0.693147182f;
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Box-Muller pair (see box_muller in pf_device.cuh for the definition).
+__device__ __forceinline__ void box_muller_fast(uint32_t wa, uint32_t wb, float& e0, float& e1) {
+  const float rho = sqrt_approx(-2.0f * log_u01(u01(wa)));
+  float s, c;
+  __sincosf(fmaf(u01(wb), 6.28318530717958647f, -3.14159265358979323f), &s, &c);
+  e0 = -rho * c;
+  e1 = -rho * s;
 }
 
 // Slot i = (group g, slot j) of step k takes the particle of slot src of the
 // exchanged population (Sec. III-A/C): group g's send set is the systematic
 // slot subsample s_{g,t} = floor((t Np + o_g) / N_ex); slot s_{r,t} of the
 // receiver r gets sender pred(r)'s slot s_{pred(r),t} with its origin
-// weight.  Returns the origin group.
+// weight.  Returns the origin group.  Np (N_ex + 1) < 2^32 uses 32-bit
+// arithmetic with precomputed reciprocals; larger products use 64 bits.
 __device__ __forceinline__ int exchange_source(const GroupState* __restrict__ gs, int g, int j, int Np, int nex,
-                                               long long& src_local) {
+                                               unsigned long long mNp, unsigned long long mnex, long long& src_local) {
   src_local = (long long)g * Np + j;
   if (nex <= 0) return g;
-  const long long o_r = gs[g].exo;
+  const uint32_t o_r = gs[g].exo;
+  if ((unsigned long long)Np * (unsigned long long)(nex + 1) < (1ull << 32)) {
+    const uint32_t jn = (uint32_t)j * (uint32_t)nex;
+    const uint32_t t = jn <= o_r ? 0u : fastdiv(jn - o_r + (uint32_t)Np - 1u, mNp);
+    if (t < (uint32_t)nex && t * (uint32_t)Np + o_r < jn + (uint32_t)nex) {
+      const int sg = gs[g].pred;
+      src_local = (long long)sg * Np + fastdiv(t * (uint32_t)Np + gs[sg].exo, mnex);
+      return sg;
+    }
+    return g;
+  }
   const long long num = (long long)j * nex - o_r;
   const long long t = num <= 0 ? 0 : (num + Np - 1) / Np;
   if (t < nex && t * Np + o_r < (long long)(j + 1) * nex) {
     const int sg = gs[g].pred;
-    const long long o_s = gs[sg].exo;
-    src_local = (long long)sg * Np + (t * Np + o_s) / nex;
+    src_local = (long long)sg * Np + (t * Np + gs[sg].exo) / nex;
     return sg;
   }
   return g;
 }
 
+// Two Philox4x32-10 blocks of the same key in lockstep (shared key schedule).
+__device__ __forceinline__ void philox2(uint32_t k0, uint32_t k1, uint4& c, uint4& d) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x, p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    const unsigned long long q0 = (unsigned long long)0xD2511F53u * d.x, q1 = (unsigned long long)0xCD9E8D57u * d.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
+    d = make_uint4((uint32_t)(q1 >> 32) ^ d.y ^ k0, (uint32_t)q1, (uint32_t)(q0 >> 32) ^ d.w ^ k1, (uint32_t)q0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+// Sum of 8 values over a warp by recursive halving (reduce-scatter): after
+// it, lane l holds the total of value ((l >> 2) & 7) (bit-reversed order
+// handled by the caller through `slot`).
+__device__ __forceinline__ float warp_reduce8(float (&v)[8], int lane, int& slot) {
+  float w4[4], w2[2];
+  const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float send = b16 ? v[i] : v[i + 4];
+    const float keep = b16 ? v[i + 4] : v[i];
+    w4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float send = b8 ? w4[i] : w4[i + 2];
+    const float keep = b8 ? w4[i + 2] : w4[i];
+    w2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  const float send = b4 ? w2[0] : w2[1];
+  const float keep = b4 ? w2[1] : w2[0];
+  float x = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  x += __shfl_xor_sync(0xffffffffu, x, 2);
+  x += __shfl_xor_sync(0xffffffffu, x, 1);
+  slot = (b16 ? 4 : 0) + (b8 ? 2 : 0) + (b4 ? 1 : 0);
+  return x;
+}
+
+// Order-preserving map of a float to an int (for warp max through redux).
+__device__ __forceinline__ int float_key(float f) {
+  const int i = __float_as_int(f);
+  return i ^ ((i >> 31) & 0x7fffffff);
+}
+__device__ __forceinline__ float key_float(int i) { return __int_as_float(i ^ ((i >> 31) & 0x7fffffff)); }
+
+// Fisher-Yates ring order of step k (Sec. IV-B, Alg. 3 step 1) for one
+// track, by one warp: the bounded draws r_j in [0, j] in parallel, the
+// descending swaps by lane 0 in shared memory.
+__device__ void ring_for_step(const TrackParams& P, int track, uint32_t k, int* __restrict__ out, int* __restrict__ sh,
+                              DevState* ds) {
+  const int lane = threadIdx.x & 31;
+  const int G = P.G;
+  for (int p = lane; p < G; p += 32) {
+    uint32_t r = 0;
+    if (p >= 1 && !draw_bounded(P.key0, P.key1, P.tag, ST_RING, (uint32_t)p, k, (uint32_t)p + 1u, r))
+      set_error(ds, ERR_DRAW, 1u, (uint32_t)track, (uint32_t)p);
+    sh[p] = (int)r;           // r_j, turned into the permutation below
+    out[p] = p;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    for (int j = G - 1; j >= 1; --j) {
+      const int r = sh[j];
+      const int tmp = out[j];
+      out[j] = out[r];
+      out[r] = tmp;
+    }
+  }
+  __syncwarp();
+}
+
+// ---- TMA / mbarrier helpers (inline PTX) ---------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase `parity`; false if it did not complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tma_load_2d(float* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Propagate + weight: tiles of K1_TILE = K1_PPT x K1_THREADS slots of one
+// group, K1_PPT particles per thread.  Each tile stages the bounding box of
+// its particles' patches (padded frame coordinates) into shared memory with
+// TMA when it fits ROI_W x ROI_BOX_H*ROI_MAX_BOXES floats, else reads the
+// frame through L1.  Leading blocks draw the next step's ARNA rings.
 template <int R>
-__global__ void __launch_bounds__(K1_THREADS) k_propagate_weight(K1Args a) {
+__global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(K1Args a) {
+  constexpr int D = 2 * R + 1;
+  constexpr int PAD = 2 * R + 1;
+  constexpr int NW = K1_THREADS / 32;
   const int k = a.ts[0].k;
   const float4* __restrict__ pv_prev = (k & 1) ? a.pv0 : a.pv1;
   const float* __restrict__ I_prev = (k & 1) ? a.I0 : a.I1;
   float4* __restrict__ pv_cur = (k & 1) ? a.pv1 : a.pv0;
   float* __restrict__ I_cur = (k & 1) ? a.I1 : a.I0;
-  __shared__ float s_red[K1_THREADS / 32][8];
+  __shared__ __align__(128) float s_roi[1][ROI_FLOATS];  // the staged box (TMA target)
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ float s_red[NW][8];
+  __shared__ int s_box[NW][4];
+  __shared__ int s_key[NW];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if ((int)blockIdx.x < a.n_ring_blocks) {
+    // Leading blocks: the next step's ARNA ring orders, off the critical
+    // path (they depend only on the seed and the step index).
+    if (warp == 0) {
+      int* perm = reinterpret_cast<int*>(&s_roi[0][0]);
+      int* rr = perm + RING_SMEM_G;
+      for (int t = blockIdx.x; t < a.n_tracks; t += a.n_ring_blocks) {
+        const TrackParams& P = a.trk[t];
+        if (P.mode != MODE_ARNA || P.G <= 1 || P.G > RING_SMEM_G) continue;
+        ring_for_step(P, t, (uint32_t)(k + 1), perm, rr, a.ds);
+        for (int p = lane; p < P.G; p += 32) a.ring_next[P.group_off + p] = perm[p];
+        __syncwarp();
+      }
+    }
+    return;
+  }
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar, 1);
+    fence_proxy_async();
+  }
+  __syncthreads();
+  uint32_t phase = 0;
 
-  for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+  for (int tile = blockIdx.x - a.n_ring_blocks; tile < a.n_tiles; tile += gridDim.x - a.n_ring_blocks) {
     const int4 td = a.tiles[tile];
     const TrackParams& P = a.trk[td.x];
-    const bool active = (int)threadIdx.x < td.w;
-    float lw = -INFINITY, I = 0.0f;
-    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (active) {
-      const int g = td.y, j = td.z + threadIdx.x, Np = P.Np;
+    const int g = td.y, Np = P.Np;
+    const GroupState* __restrict__ gs = a.grp + P.group_off;
+    const int nex = k > 0 ? a.ts[td.x].n_ex : 0;
+    const unsigned long long mnex = a.ts[td.x].m_nex;
+    float4 s[K1_PPT];
+    float I[K1_PPT];
+    int og[K1_PPT], pu[K1_PPT], pv[K1_PPT];
+    int umin = INT_MAX, umax = INT_MIN, vmin = INT_MAX, vmax = INT_MIN;
+#pragma unroll
+    for (int q = 0; q < K1_PPT; ++q) {
+      const int jj = threadIdx.x + q * K1_THREADS;
+      const bool active = jj < td.w;
+      const int j = td.z + jj;
       const long long il = (long long)g * Np + j;
-      const GroupState* __restrict__ gs = a.grp + P.group_off;
-      long long src;
-      const int og = (k == 0) ? g : exchange_source(gs, g, j, Np, a.ts[td.x].n_ex, src);
-      if (k == 0) src = il;
-      const long long par = (k == 0) ? src : (long long)a.anc[P.part_off + src];
-      if (par < 0 || par >= (long long)P.G * Np) {
-        set_error(a.ds, ERR_INDEX, 1u, (uint32_t)tile, (uint32_t)par);
-      } else {
-        s = pv_prev[P.part_off + par];
-        I = I_prev[P.part_off + par];
+      s[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      I[q] = 0.0f;
+      og[q] = g;
+      if (active) {
+        long long src = il;
+        og[q] = exchange_source(gs, g, j, Np, nex, P.m_Np, mnex, src);
+        const long long par = (k == 0) ? src : (long long)a.anc[P.part_off + src];
+        if (par < 0 || par >= (long long)P.G * Np) {
+          set_error(a.ds, ERR_INDEX, 1u, (uint32_t)tile, (uint32_t)par);
+        } else {
+          s[q] = pv_prev[P.part_off + par];
+          I[q] = I_prev[P.part_off + par];
+        }
+        if (k > 0) {
+          // Alg. 1 step P: nearly constant velocity, unit frame interval
+          uint4 w0 = make_uint4(j, g, k, P.tag | (ST_PROP << 4) | 0u);
+          uint4 w1 = make_uint4(j, g, k, P.tag | (ST_PROP << 4) | 1u);
+          philox2(P.key0, P.key1, w0, w1);
+          float e0, e1, e2, e3, e4, e5;
+          box_muller_fast(w0.x, w0.y, e0, e1);
+          box_muller_fast(w0.z, w0.w, e2, e3);
+          box_muller_fast(w1.x, w1.y, e4, e5);
+          s[q].x = fmaf(P.spos, e0, s[q].x + s[q].z);
+          s[q].y = fmaf(P.spos, e1, s[q].y + s[q].w);
+          s[q].z = fmaf(P.sv, e2, s[q].z);
+          s[q].w = fmaf(P.sv, e3, s[q].w);
+          I[q] = fmaf(P.sI, e4, I[q]);
+        }
+        pv_cur[P.part_off + il] = s[q];
+        I_cur[P.part_off + il] = I[q];
+        if (P.record)
+          a.parent[P.parent_off + (long long)(k % a.history) * ((long long)P.G * Np) + il] = (uint32_t)par;
+        // patch corner in padded-frame coordinates (centre clamped so that a
+        // patch wholly off the frame reads the zero border)
+        pu[q] = (int)fminf(fmaxf(floorf(s[q].x + 0.5f), -(float)(R + 1)), (float)(P.W + R)) - R + PAD;
+        pv[q] = (int)fminf(fmaxf(floorf(s[q].y + 0.5f), -(float)(R + 1)), (float)(P.H + R)) - R + PAD;
+        umin = min(umin, pu[q]);
+        umax = max(umax, pu[q]);
+        vmin = min(vmin, pv[q]);
+        vmax = max(vmax, pv[q]);
       }
-      if (k > 0) {
-        // Alg. 1 step P: nearly constant velocity, unit frame interval
-        const uint4 w0 = philox(P.key0, P.key1, make_uint4(j, g, k, P.tag | (ST_PROP << 4) | 0u));
-        const uint4 w1 = philox(P.key0, P.key1, make_uint4(j, g, k, P.tag | (ST_PROP << 4) | 1u));
-        float e0, e1, e2, e3, e4, e5;
-        box_muller(w0.x, w0.y, e0, e1);
-        box_muller(w0.z, w0.w, e2, e3);
-        box_muller(w1.x, w1.y, e4, e5);
-        s.x = fmaf(P.spos, e0, s.x + s.z);
-        s.y = fmaf(P.spos, e1, s.y + s.w);
-        s.z = fmaf(P.sv, e2, s.z);
-        s.w = fmaf(P.sv, e3, s.w);
-        I = fmaf(P.sI, e4, I);
-      }
-      const long long i = P.part_off + il;
-      pv_cur[i] = s;
-      I_cur[i] = I;
-      if (P.record) a.parent[P.parent_off + (long long)(k % a.history) * ((long long)P.G * Np) + il] = (uint32_t)par;
-      // Alg. 1 step U with the renormalised carried weight (Alg. 3 step 4)
-      lw = gs[og].off + loglik<R>(a.ypad + P.ypad_off, P.pitch, P.H, P.W, s.x, s.y, I, P.c_psf, P.inv2so2);
-      a.lw[i] = lw;
     }
-    // Per-tile partial sums for the group estimate, relative to the tile max.
-    float m = warp_max(active ? lw : -INFINITY);
-    if (lane == 0) s_red[warp][0] = m;
-    __syncthreads();
-    float Mt = s_red[0][0];
-#pragma unroll
-    for (int w = 1; w < K1_THREADS / 32; ++w) Mt = fmaxf(Mt, s_red[w][0]);
-    __syncthreads();
-    const float e = (active && lw - Mt >= -87.0f) ? __expf(lw - Mt) : 0.0f;
-    float v[7] = {e, e * s.x, e * s.y, e * s.z, e * s.w, e * I, e * e};
-#pragma unroll
-    for (int q = 0; q < 7; ++q) v[q] = warp_sum(v[q]);
+
+    // tile bounding box of the patches
+    umin = __reduce_min_sync(0xffffffffu, umin);
+    umax = __reduce_max_sync(0xffffffffu, umax);
+    vmin = __reduce_min_sync(0xffffffffu, vmin);
+    vmax = __reduce_max_sync(0xffffffffu, vmax);
     if (lane == 0) {
-#pragma unroll
-      for (int q = 0; q < 7; ++q) s_red[warp][q + 1] = v[q];
+      s_box[warp][0] = umin;
+      s_box[warp][1] = umax;
+      s_box[warp][2] = vmin;
+      s_box[warp][3] = vmax;
     }
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      umin = min(umin, s_box[w][0]);
+      umax = max(umax, s_box[w][1]);
+      vmin = min(vmin, s_box[w][2]);
+      vmax = max(vmax, s_box[w][3]);
+    }
+    const int u0 = umin & ~3;
+    const int nbox = (vmax + D - vmin + ROI_BOX_H - 1) / ROI_BOX_H;
+    const bool staged = a.tmaps != nullptr && (umax + D - u0) <= ROI_W && nbox <= ROI_MAX_BOXES;
+
+    if (staged) {
+      if (threadIdx.x == 0) {
+        fence_proxy_async();  // earlier generic reads of s_roi before the async-proxy writes
+        mbar_expect_tx(&s_bar, (uint32_t)(nbox * ROI_W * ROI_BOX_H * sizeof(float)));
+        for (int b = 0; b < nbox; ++b)
+          tma_load_2d(&s_roi[0][b * ROI_W * ROI_BOX_H], a.tmaps + td.x, u0, vmin + b * ROI_BOX_H, &s_bar);
+      }
+      const bool ok = mbar_wait(&s_bar, phase);
+      if (__syncthreads_or(!ok)) {
+        // the copy did not land within the bound: report and stop this CTA
+        // after a second bounded wait, so no copy is left in flight
+        if (threadIdx.x == 0) {
+          set_error(a.ds, ERR_TIMEOUT, 4u, (uint32_t)tile, 0u);
+          mbar_wait(&s_bar, phase);
+        }
+        return;
+      }
+      phase ^= 1u;
+    }
+
+    // Alg. 1 step U with the renormalised carried weight (Alg. 3 step 4)
+    float lw[K1_PPT];
+#pragma unroll
+    for (int q = 0; q < K1_PPT; ++q) {
+      const int jj = threadIdx.x + q * K1_THREADS;
+      lw[q] = -INFINITY;
+      if (jj < td.w) {
+        float gxI[D];
+        gauss_row<R>(floorf(s[q].x + 0.5f), s[q].x, P.c_psf, P.kappa, gxI);
+#pragma unroll
+        for (int c = 0; c < D; ++c) gxI[c] *= I[q];
+        const float dy = floorf(s[q].y + 0.5f) - s[q].y;
+        float ss;
+        if (staged) {
+          ss = patch_ss<R, true>(&s_roi[0][(pv[q] - vmin) * ROI_W + (pu[q] - u0)], 0, gxI, dy, P.c_psf, P.kappa);
+        } else {
+          ss = patch_ss<R, false>(a.ypad + P.ypad_off + (long long)pv[q] * P.pitch + pu[q], P.pitch, gxI, dy,
+                                  P.c_psf, P.kappa);
+        }
+        lw[q] = gs[og[q]].off - ss * P.inv2so2;
+        a.lw[P.part_off + (long long)g * Np + td.z + jj] = lw[q];
+      }
+    }
+
+    // Per-tile partial sums for the group estimate, relative to the tile max.
+    int key = INT_MIN;
+#pragma unroll
+    for (int q = 0; q < K1_PPT; ++q)
+      if (lw[q] == lw[q]) key = max(key, float_key(lw[q]));  // NaN does not count
+    key = __reduce_max_sync(0xffffffffu, key);
+    if (lane == 0) s_key[warp] = key;
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < NW; ++w) key = max(key, s_key[w]);
+    const float Mt = key_float(key);
+    float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int q = 0; q < K1_PPT; ++q) {
+      const float e = (lw[q] - Mt >= -87.0f) ? __expf(lw[q] - Mt) : 0.0f;
+      v[0] += e;
+      v[1] = fmaf(e, s[q].x, v[1]);
+      v[2] = fmaf(e, s[q].y, v[2]);
+      v[3] = fmaf(e, s[q].z, v[3]);
+      v[4] = fmaf(e, s[q].w, v[4]);
+      v[5] = fmaf(e, I[q], v[5]);
+      v[6] = fmaf(e, e, v[6]);
+    }
+    int slot;
+    const float x = warp_reduce8(v, lane, slot);
+    if ((lane & 3) == 0) s_red[warp][slot] = x;
     __syncthreads();
     if (threadIdx.x < 8) {
       float r;
@@ -300,7 +611,7 @@ __global__ void __launch_bounds__(K1_THREADS) k_propagate_weight(K1Args a) {
       } else {
         r = 0.0f;
 #pragma unroll
-        for (int w = 0; w < K1_THREADS / 32; ++w) r += s_red[w][threadIdx.x];
+        for (int w = 0; w < NW; ++w) r += s_red[w][threadIdx.x - 1];
       }
       a.tile_part[(long long)tile * 8 + threadIdx.x] = r;
     }
@@ -311,39 +622,66 @@ __global__ void __launch_bounds__(K1_THREADS) k_propagate_weight(K1Args a) {
 // ===================================================================== K3
 // Number of outputs j in [0, Np) with (j 2^32 + u) Q < S Np 2^32: an FP32
 // estimate, then exact 128-bit corrections (the estimate is within 1).
-__device__ __forceinline__ long long count_below(const ThetaCmp& th, unsigned long long S, int Np, DevState* ds) {
+// #{j in [0, Np) : T_j < S}: an FP32 estimate, then exact corrections.
+__device__ __forceinline__ int count_below(const Thresholds& th, unsigned long long S, float inv_Q, int Np,
+                                           uint32_t u, DevState* ds) {
   if (S == 0) return 0;
-  const float est = __fdividef(__ull2float_rn(S), __ull2float_rn(th.Q)) * (float)Np - (float)th.u * 2.3283064365386963e-10f;
-  long long c = (long long)ceilf(fminf(fmaxf(est, 0.0f), (float)Np));
+  const float est = u64_to_float_approx(S) * inv_Q * (float)Np - (float)(u >> 8) * 5.9604645e-8f;
+  int c = (int)ceilf(fminf(fmaxf(est, 0.0f), (float)Np));
   int it = 0;
-  while (c < Np && th.below(c, S) && it < 64) { ++c; ++it; }
-  while (c > 0 && !th.below(c - 1, S) && it < 64) { --c; ++it; }
+  while (c < Np && th.T((uint32_t)c) < S && it < 64) { ++c; ++it; }
+  while (c > 0 && th.T((uint32_t)(c - 1)) >= S && it < 64) { --c; ++it; }
   if (it >= 64) set_error(ds, ERR_INVARIANT, 3u, (uint32_t)S, (uint32_t)c);
   return c;
 }
 
-__global__ void __launch_bounds__(RS_THREADS) k_resample(ResampleArgs a) {
+// Resampler: one thread-block cluster per group, each CTA a contiguous chunk
+// of the group's slots (a multiple of 8), processed in sub-chunks of RS_SUB
+// items; thread t owns the RS_ITEMS consecutive items [t*RS_ITEMS, ...).
+
+__global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
   const int grp = blockIdx.x / C;
   const GroupDesc d = a.gd[grp];
   const int Np = d.Np;
-  const int chunk = (Np + C - 1) / C;
+  const int chunk = ((Np + C - 1) / C + 7) & ~7;
   const int lo = min(rank * chunk, Np), hi = min(lo + chunk, Np);
+  const bool single = (hi - lo) <= RS_SUB;  // the whole chunk stays in registers
   const float* __restrict__ lw = a.lw + d.base;
+  const bool vec = ((d.base & 3) == 0);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
   __shared__ float s_pub_max;
   __shared__ unsigned long long s_pub_q;
   __shared__ float s_f[RS_THREADS / 32];
-  __shared__ double s_d[RS_THREADS / 32];
   __shared__ unsigned long long s_w[RS_THREADS / 32];
+  __shared__ float s_stat[RS_THREADS / 32][8];
+  __shared__ int s_jlo, s_jhi;
   __shared__ unsigned long long s_incl[RS_SUB];
+
+  float v[RS_ITEMS];
+  auto load_sub = [&](int sub) {
+    const int i0 = sub + (int)threadIdx.x * RS_ITEMS;
+    if (vec && i0 + RS_ITEMS <= hi) {
+      const float4 x0 = *reinterpret_cast<const float4*>(lw + i0);
+      const float4 x1 = *reinterpret_cast<const float4*>(lw + i0 + 4);
+      v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
+      v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+    } else {
+#pragma unroll
+      for (int r = 0; r < RS_ITEMS; ++r) v[r] = (i0 + r < hi) ? lw[i0 + r] : -INFINITY;
+    }
+  };
 
   // group maximum over the cluster
   float m = -INFINITY;
-  for (int i = lo + threadIdx.x; i < hi; i += RS_THREADS) m = fmaxf(m, lw[i]);
+  for (int sub = lo; sub < hi; sub += RS_SUB) {
+    load_sub(sub);
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) m = fmaxf(m, v[r]);
+  }
   m = block_max<RS_THREADS>(m, s_f);
   if (threadIdx.x == 0) s_pub_max = m;
   cl.sync();
@@ -352,15 +690,23 @@ __global__ void __launch_bounds__(RS_THREADS) k_resample(ResampleArgs a) {
 
   // this CTA's total weight code, then the cluster prefix and group total
   unsigned long long qs = 0;
-  for (int i = lo + threadIdx.x; i < hi; i += RS_THREADS) qs += quantize(lw[i], M, a.qc);
+  unsigned long long qv[RS_ITEMS];
+  for (int sub = lo; sub < hi; sub += RS_SUB) {
+    if (!single) load_sub(sub);
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+      qv[r] = quantize(v[r], M, a.qc);
+      qs += qv[r];
+    }
+  }
   qs = block_sum_u64<RS_THREADS>(qs, s_w);
   if (threadIdx.x == 0) s_pub_q = qs;
   cl.sync();
   unsigned long long Sb = 0, Q = 0;
   for (int r = 0; r < C; ++r) {
-    const unsigned long long v = *cl.map_shared_rank(&s_pub_q, r);
-    if (r < rank) Sb += v;
-    Q += v;
+    const unsigned long long x = *cl.map_shared_rank(&s_pub_q, r);
+    if (r < rank) Sb += x;
+    Q += x;
   }
 
   const uint32_t u = a.u_arr ? a.u_arr[grp] : a.gs[grp].u;
@@ -373,80 +719,131 @@ __global__ void __launch_bounds__(RS_THREADS) k_resample(ResampleArgs a) {
       if (a.q_out) a.q_out[d.base + i] = 0ull;
     }
   } else {
-    const ThetaCmp th{Q, (unsigned long long)Np, u};
+    Thresholds th;
+    th.init(Q, (uint32_t)Np, u);
+    const float inv_Q = 1.0f / u64_to_float_approx(Q);
     unsigned long long carry = Sb;
     for (int sub = lo; sub < hi; sub += RS_SUB) {
       const int n = min(RS_SUB, hi - sub);
-      // warp-segmented inclusive scan: warp w owns items [w*32*RS_ITEMS, ...)
-      unsigned long long run = 0;
+      const int i0 = (int)threadIdx.x * RS_ITEMS;  // first item of this thread (sub-chunk relative)
+      if (!single) {
+        load_sub(sub);
 #pragma unroll
-      for (int r = 0; r < RS_ITEMS; ++r) {
-        const int it = warp * (32 * RS_ITEMS) + r * 32 + lane;
-        unsigned long long q = 0;
-        if (it < n) {
-          q = quantize(lw[sub + it], M, a.qc);
-          if (a.q_out) a.q_out[d.base + sub + it] = q;
-        }
-        unsigned long long v = q;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
-          if (lane >= o) v += t;
-        }
-        s_incl[it] = run + v;
-        run += __shfl_sync(0xffffffffu, v, 31);
+        for (int r = 0; r < RS_ITEMS; ++r) qv[r] = quantize(v[r], M, a.qc);
       }
-      if (lane == 0) s_w[warp] = run;
+      if (a.q_out)
+#pragma unroll
+        for (int r = 0; r < RS_ITEMS; ++r)
+          if (i0 + r < n) a.q_out[d.base + sub + i0 + r] = qv[r];
+      // exclusive scan of the thread totals: warp shuffles, then warps
+      unsigned long long tsum = 0;
+#pragma unroll
+      for (int r = 0; r < RS_ITEMS; ++r) tsum += qv[r];
+      unsigned long long x = tsum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+      }
+      if (lane == 31) s_w[warp] = x;
       __syncthreads();
       unsigned long long wpre = 0, tot = 0;
 #pragma unroll
       for (int w = 0; w < RS_THREADS / 32; ++w) {
-        const unsigned long long v = s_w[w];
-        if (w < warp) wpre += v;
-        tot += v;
+        const unsigned long long y = s_w[w];
+        if (w < warp) wpre += y;
+        tot += y;
       }
+      // inclusive prefixes of the items (absolute within the group)
+      {
+        unsigned long long S = carry + wpre + (x - tsum);
 #pragma unroll
-      for (int r = 0; r < RS_ITEMS; ++r) s_incl[warp * (32 * RS_ITEMS) + r * 32 + lane] += carry + wpre;
-      __syncthreads();
-      // outputs whose ancestor lies in this sub-chunk: binary search for the
-      // first item whose inclusive prefix exceeds the output's threshold
-      const long long jlo = count_below(th, carry, Np, a.ds);
-      const long long jhi = count_below(th, carry + tot, Np, a.ds);
-      for (long long j = jlo + threadIdx.x; j < jhi; j += RS_THREADS) {
-        const U128 lhs = mul64(((unsigned long long)j << 32) | u, Q);
-        int L = 0, Hh = n - 1;
-        while (L < Hh) {
-          const int mid = (L + Hh) >> 1;
-          if (lt128(lhs, shl32(mul64(s_incl[mid], (unsigned long long)Np)))) Hh = mid;
-          else L = mid + 1;
+        for (int r = 0; r < RS_ITEMS; ++r) {
+          S += qv[r];
+          s_incl[i0 + r] = S;
         }
-        anc[j] = (uint32_t)(obase + sub + L);
+      }
+      if (threadIdx.x == 0) {
+        s_jlo = count_below(th, carry, inv_Q, Np, u, a.ds);
+        s_jhi = count_below(th, carry + tot, inv_Q, Np, u, a.ds);
+      }
+      __syncthreads();
+      // Merge path over the item boundaries X_i = S_{i+1} (s_incl) and the
+      // thresholds Y_b = T_{jlo+b} of this sub-chunk's outputs: output j
+      // takes the first item i with T_j < S_{i+1}.  Each thread merges an
+      // equal slice of the n + m merged positions, so the work is balanced
+      // however the weight is spread.
+      {
+        const int jlo = s_jlo, m = s_jhi - s_jlo, L = n + m;
+        const int d0 = (int)(((long long)L * threadIdx.x) / RS_THREADS);
+        const int d1 = (int)(((long long)L * (threadIdx.x + 1)) / RS_THREADS);
+        // largest ia in [max(0, d0 - m), min(d0, n)] whose items all precede
+        // output d0 - ia in the merge (X_{ia-1} <= Y_{d0-ia})
+        int lo2 = max(0, d0 - m), hi2 = min(d0, n);
+        while (lo2 < hi2) {
+          const int mid = (lo2 + hi2 + 1) >> 1;  // candidate number of items consumed
+          if (s_incl[mid - 1] <= th.T((uint32_t)(jlo + d0 - mid))) lo2 = mid;
+          else hi2 = mid - 1;
+        }
+        int ia = lo2, ib = d0 - lo2;
+        if (ib < m) {
+          // T and its remainder at output jlo + ib, then advance incrementally
+          uint32_t jj = (uint32_t)(jlo + ib);
+          unsigned long long num = (unsigned long long)jj * th.B + th.F0;
+          unsigned long long qd = th.Np > 1 ? __umul64hi(num, th.M) : num;
+          uint32_t rem = (uint32_t)(num - qd * th.Np);
+          unsigned long long Tj = (unsigned long long)jj * th.A + th.F1 + qd;
+          for (int dd = d0; dd < d1; ++dd) {
+            if (ib < m && (ia >= n || Tj < s_incl[ia])) {
+              anc[jlo + ib] = (uint32_t)(obase + sub + ia);
+              ++ib;
+              rem += th.B;
+              Tj += th.A;
+              if (rem >= th.Np) {
+                rem -= th.Np;
+                Tj += 1;
+              }
+            } else {
+              ++ia;
+            }
+          }
+        }
       }
       carry += tot;
       __syncthreads();
     }
   }
 
-  // group estimate and ESS from the propagate tiles' partial sums (rank 0)
+  // group estimate and ESS from the propagate tiles' partial sums (rank 0),
+  // each tile's sums rescaled from its own maximum to the group maximum
   if (rank == 0) {
     GroupState& G = a.gs[grp];
     if (a.tile_part != nullptr) {
-      double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+      float acc[7] = {0, 0, 0, 0, 0, 0, 0};
       if (Q != 0) {
         for (int t = threadIdx.x; t < d.tile_count; t += RS_THREADS) {
           const float* tp = a.tile_part + (long long)(d.tile_begin + t) * 8;
           const float Mt = tp[0];
           if (!(Mt - M >= -87.0f)) continue;
-          const double sc = exp((double)Mt - (double)M);
-          for (int q = 0; q < 6; ++q) acc[q] += sc * (double)tp[1 + q];
-          acc[6] += sc * sc * (double)tp[7];
+          const float sc = __expf(Mt - M);
+#pragma unroll
+          for (int q = 0; q < 6; ++q) acc[q] = fmaf(sc, tp[1 + q], acc[q]);
+          acc[6] = fmaf(sc * sc, tp[7], acc[6]);
         }
       }
-      for (int q = 0; q < 7; ++q) acc[q] = block_sum_d<RS_THREADS>(acc[q], s_d);
+#pragma unroll
+      for (int q = 0; q < 7; ++q) acc[q] = warp_sum(acc[q]);
+      if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 7; ++q) s_stat[warp][q] = acc[q];
+      __syncthreads();
       if (threadIdx.x == 0) {
-        const bool ok = (Q != 0) && acc[0] > 0.0;
-        for (int q = 0; q < 5; ++q) G.xs[q] = ok ? (float)(acc[1 + q] / acc[0]) : 0.0f;
-        G.ess = ok ? (float)(acc[0] * acc[0] / acc[6]) : 0.0f;
+        float t7[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int w = 0; w < RS_THREADS / 32; ++w)
+          for (int q = 0; q < 7; ++q) t7[q] += s_stat[w][q];
+        const bool ok = (Q != 0) && t7[0] > 0.0f;
+        for (int q = 0; q < 5; ++q) G.xs[q] = ok ? t7[1 + q] / t7[0] : 0.0f;
+        G.ess = ok ? t7[0] * t7[0] / t7[6] : 0.0f;
       }
     }
     if (threadIdx.x == 0) {
@@ -461,7 +858,17 @@ __global__ void __launch_bounds__(RS_THREADS) k_resample(ResampleArgs a) {
 // Per track: the master PE's reduction (Alg. 3 steps 9-10) and weight carry
 // (step 8) for step k, then ring order (step 1) and exchange count (step 2)
 // for step k+1.  FP64 throughout: it is G-sized.
+// log W^(m) = M + ln(Q 2^-40) in FP32: log2 Q from the leading-bit position
+// and the top 24 bits of Q.
+__device__ __forceinline__ float group_log_weight(float M, unsigned long long Q) {
+  const int e = 63 - __clzll((long long)Q);
+  const uint32_t top = e >= 23 ? (uint32_t)(Q >> (e - 23)) : (uint32_t)(Q << (23 - e));
+  const float l2 = (float)(e - 23) + log2f((float)top);  // log2 Q (top is exact in FP32)
+  return M + (l2 - 40.0f) * 0.693147182f;
+}
+
 __global__ void __launch_bounds__(GL_THREADS) k_global(GlobalArgs a) {
+  constexpr int NW = GL_THREADS / 32;
   const int t = blockIdx.x;
   const TrackParams& P = a.trk[t];
   TrackState* T = a.ts + t;
@@ -469,142 +876,172 @@ __global__ void __launch_bounds__(GL_THREADS) k_global(GlobalArgs a) {
   int* ring = a.ring + P.group_off;
   const int G = P.G;
   const int k = T->k;
-  const double LN2 = 0.69314718055994530942;
-  __shared__ double s_d[GL_THREADS / 32];
+  const int m = threadIdx.x;  // one group per thread (G <= GL_THREADS)
+  const bool act = m < G;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (int)blockDim.x >> 5;  // launched with ceil(G / 32) warps
+  __shared__ float s_f[NW];
+  __shared__ int s_i[NW];
+  __shared__ float s_red[NW][6];
+  __shared__ double s_d[NW][2];
+  __shared__ float s_tot[6];
+  __shared__ double s_pe;
   __shared__ int s_ring[MAX_G];
-  __shared__ uint32_t s_r[MAX_G];
-  __shared__ int s_deg;
-  __shared__ double s_logc;
 
-  if (a.finalize) {
-    // S7 -> S8: Lambda'_m = M_m + ln(Q_m 2^-40); log c_k = LSE Lambda'
-    double lmax = -INFINITY;
-    int deg = 0;
-    for (int m = threadIdx.x; m < G; m += GL_THREADS) {
-      const unsigned long long Q = gs[m].Q;
-      const double lam = (Q != 0) ? (double)gs[m].M + log((double)Q) - 40.0 * LN2 : -INFINITY;
-      gs[m].lambda = lam;
-      lmax = fmax(lmax, lam);
-      deg += (Q == 0);
+  // every per-group input at once
+  unsigned long long Q = 0;
+  float Mg = 0.0f, xs[5] = {0, 0, 0, 0, 0}, ess = 0.0f;
+  int ring_m = m, rnext = m;
+  if (act) {
+    Q = gs[m].Q;
+    Mg = gs[m].M;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) xs[q] = gs[m].xs[q];
+    ess = gs[m].ess;
+    ring_m = ring[m];
+    rnext = a.ring_next[P.group_off + m];
+  }
+  // S7 -> S8: Lambda'_m in FP32 (finalize), or 0 (prepare step 0)
+  float lam = -INFINITY;
+  int deg = 0;
+  if (act) {
+    if (a.finalize) {
+      lam = Q != 0 ? group_log_weight(Mg, Q) : -INFINITY;
+      deg = (Q == 0);
+    } else {
+      lam = 0.0f;
     }
-    lmax = block_max_d<GL_THREADS>(lmax, s_d);
-    deg = (int)block_sum_d<GL_THREADS>((double)deg, s_d);
-    double sw = 0.0;
-    if (isfinite(lmax))
-      for (int m = threadIdx.x; m < G; m += GL_THREADS) sw += exp(gs[m].lambda - lmax);
-    sw = block_sum_d<GL_THREADS>(sw, s_d);
-    const double logc = isfinite(lmax) ? lmax + log(sw) : -INFINITY;
-    double xh[5];
-    for (int q = 0; q < 5; ++q) {
-      double acc = 0.0;
-      if (isfinite(logc))
-        for (int m = threadIdx.x; m < G; m += GL_THREADS)
-          if (gs[m].Q != 0) acc += exp(gs[m].lambda - logc) * (double)gs[m].xs[q];
-      xh[q] = block_sum_d<GL_THREADS>(acc, s_d);
-    }
-    const int hslot = k % a.history;
-    for (int m = threadIdx.x; m < G; m += GL_THREADS) {
-      GroupHist& gh = a.ghist[P.ghist_off + (long long)hslot * G + m];
-      gh.ring = ring[m];
-      gh.logW = gs[m].lambda;
-      for (int q = 0; q < 5; ++q) gh.xs[q] = gs[m].xs[q];
-      gh.ess = gs[m].ess;
-    }
-    if (threadIdx.x == 0) {
-      T->log_c = logc;
-      T->log_Z += logc;
-      for (int q = 0; q < 5; ++q) T->xhat[q] = (float)xh[q];
-      T->degenerate = deg;
-      if (deg == G) T->flags |= 1;
-      T->steps_done = k + 1;
-      HistRec& h = a.hist[P.hist_off + hslot];
-      h.step = k;
-      h.n_ex = T->n_ex;
-      h.pe_eff = T->pe_eff;
-      h.log_c = logc;
-      h.log_Z = T->log_Z;
-      for (int q = 0; q < 5; ++q) h.xhat[q] = (float)xh[q];
-      h.degenerate = deg;
-      s_deg = deg;
+  }
+  {
+    float mx = warp_max(lam);
+    const int dsum = __reduce_add_sync(0xffffffffu, deg);
+    if (lane == 0) {
+      s_f[warp] = mx;
+      s_i[warp] = dsum;
     }
     __syncthreads();
-    if (s_deg == G)  // every group lost its weight: restart from equal weights
-      for (int m = threadIdx.x; m < G; m += GL_THREADS) gs[m].lambda = 0.0;
-  } else {
-    for (int m = threadIdx.x; m < G; m += GL_THREADS) gs[m].lambda = 0.0;
-  }
-  __syncthreads();
-
-  const int k1 = a.finalize ? k + 1 : 0;
-  // Eq. 4 from the carried weights; LSE for the renormalisation (step 4)
-  double lmax = -INFINITY;
-  for (int m = threadIdx.x; m < G; m += GL_THREADS) lmax = fmax(lmax, gs[m].lambda);
-  lmax = block_max_d<GL_THREADS>(lmax, s_d);
-  double sw = 0.0, sw2 = 0.0;
-  for (int m = threadIdx.x; m < G; m += GL_THREADS) {
-    const double w = exp(gs[m].lambda - lmax);
-    sw += w;
-    sw2 += w * w;
-  }
-  sw = block_sum_d<GL_THREADS>(sw, s_d);
-  sw2 = block_sum_d<GL_THREADS>(sw2, s_d);
-  const double pe = sw * sw / sw2;
-  const double lse = lmax + log(sw);
-  if (threadIdx.x == 0) s_logc = lse;
-
-  // ring order for step k1 (Sec. IV-B): Fisher-Yates on the identity
-  const bool shuffle = (P.mode == MODE_ARNA) && k1 >= 1 && G > 1;
-  for (int p = threadIdx.x; p < G; p += GL_THREADS) {
-    s_ring[p] = p;
-    if (shuffle && p >= 1) {
-      uint32_t r;
-      if (!draw_bounded(P.key0, P.key1, P.tag, ST_RING, (uint32_t)p, (uint32_t)k1, (uint32_t)p + 1u, r))
-        set_error(a.ds, ERR_DRAW, 1u, (uint32_t)t, (uint32_t)p);
-      s_r[p] = r;
+    mx = -INFINITY;
+    deg = 0;
+    for (int w = 0; w < nw; ++w) {
+      mx = fmaxf(mx, s_f[w]);
+      deg += s_i[w];
     }
-  }
-  __syncthreads();
-  if (shuffle && threadIdx.x == 0) {
-    for (int j = G - 1; j >= 1; --j) {
-      const int r = (int)s_r[j];
-      const int tmp = s_ring[j];
-      s_ring[j] = s_ring[r];
-      s_ring[r] = tmp;
+    if (a.finalize && deg == G) {  // every group lost its weight: restart from equal weights
+      lam = act ? 0.0f : -INFINITY;
+      mx = 0.0f;
     }
-  }
-  __syncthreads();
-
-  // exchange count for step k1 (Eq. 3 with the Sec. V-A cut-off)
-  int nex = 0;
-  if (k1 >= 1 && G > 1) {
-    double rho;
-    if (P.mode == MODE_ARNA) {
-      if (!(pe < (double)P.cutoff * (double)G)) {
-        rho = 0.0;
-      } else {
-        rho = 0.5 - 0.5 * (pe - 1.0) / (double)(G - 1);
-        rho = fmin(fmax(rho, 0.0), 0.5);
+    // one pass: FP32 sums for log c and the estimate, FP64 sums for Eq. 4
+    // (the exchange count is an integer decided in FP64 on both sides)
+    const float wf = act ? __expf(lam - mx) : 0.0f;
+    float acc[6] = {wf, wf * xs[0], wf * xs[1], wf * xs[2], wf * xs[3], wf * xs[4]};
+    double dw = 0.0, dw2 = 0.0;
+    if (act) {
+      const double w = exp((double)lam - (double)mx);
+      dw = w;
+      dw2 = w * w;
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) acc[q] = warp_sum(acc[q]);
+    dw = warp_sum_d(dw);
+    dw2 = warp_sum_d(dw2);
+    if (lane == 0) {
+#pragma unroll
+      for (int q = 0; q < 6; ++q) s_red[warp][q] = acc[q];
+      s_d[warp][0] = dw;
+      s_d[warp][1] = dw2;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+      float x = 0.0f;
+      for (int w2 = 0; w2 < nw; ++w2) x += s_red[w2][threadIdx.x];
+      s_tot[threadIdx.x] = x;
+    }
+    if (threadIdx.x == (nw > 1 ? 32 : 7)) {
+      double sw = 0.0, sw2 = 0.0;
+      for (int w2 = 0; w2 < nw; ++w2) {
+        sw += s_d[w2][0];
+        sw2 += s_d[w2][1];
       }
-    } else {
-      rho = fmin(fmax((double)P.ex_ratio, 0.0), 1.0);
+      s_pe = sw * sw / sw2;  // Eq. 4 for the next step
     }
-    nex = (int)floor(rho * (double)P.Np);
-  }
-  const double lnNp = log((double)P.Np);
-  for (int p = threadIdx.x; p < G; p += GL_THREADS) {
-    ring[p] = s_ring[p];
-    gs[s_ring[p]].pred = s_ring[(p + G - 1) % G];
-    uint32_t o = 0;
-    if (nex > 0 && !draw_bounded(P.key0, P.key1, P.tag, ST_EXCH, (uint32_t)p, (uint32_t)k1, (uint32_t)P.Np, o))
-      set_error(a.ds, ERR_DRAW, 2u, (uint32_t)t, (uint32_t)p);
-    gs[p].exo = o;
-    gs[p].u = philox(P.key0, P.key1, make_uint4((uint32_t)p, 0u, (uint32_t)k1, P.tag | (ST_RESAMPLE << 4))).x;
-    gs[p].off = (float)(gs[p].lambda - lnNp - s_logc);
-  }
-  if (threadIdx.x == 0) {
-    T->n_ex = nex;
-    T->pe_eff = pe;
-    T->k = k1;
+    __syncthreads();
+    const bool all_degenerate = a.finalize && deg == G;
+    const float sw = s_tot[0];
+    const float lse = mx + logf(sw);  // LSE of the carried weights = log c_k
+    const double pe = s_pe;
+
+    if (a.finalize) {
+      const int hslot = k % a.history;
+      if (act) {
+        GroupHist& gh = a.ghist[P.ghist_off + (long long)hslot * G + m];
+        gh.ring = ring_m;
+        gh.logW = all_degenerate ? -INFINITY : (double)lam;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) gh.xs[q] = xs[q];
+        gh.ess = ess;
+      }
+      if (threadIdx.x == 0) {
+        const double logc = all_degenerate ? -INFINITY : (double)lse;
+        T->log_c = logc;
+        T->log_Z += logc;
+        HistRec& h = a.hist[P.hist_off + hslot];
+        for (int q = 0; q < 5; ++q) {
+          const float xq = all_degenerate ? NAN : s_tot[1 + q] / sw;
+          T->xhat[q] = xq;
+          h.xhat[q] = xq;
+        }
+        T->degenerate = deg;
+        if (all_degenerate) T->flags |= 1;
+        T->steps_done = k + 1;
+        h.step = k;
+        h.n_ex = T->n_ex;
+        h.pe_eff = T->pe_eff;
+        h.log_c = logc;
+        h.log_Z = T->log_Z;
+        h.degenerate = deg;
+      }
+    }
+
+    const int k1 = a.finalize ? k + 1 : 0;
+    // ring order for step k1 (Sec. IV-B), drawn one step ahead by the
+    // propagate kernel's leading blocks
+    const bool shuffled = (P.mode == MODE_ARNA) && k1 >= 1 && G > 1;
+    if (act) s_ring[m] = shuffled ? rnext : m;
+    __syncthreads();
+
+    // exchange count for step k1 (Eq. 3 with the Sec. V-A cut-off)
+    int nex = 0;
+    if (k1 >= 1 && G > 1) {
+      double rho;
+      if (P.mode == MODE_ARNA) {
+        if (!(pe < (double)P.cutoff * (double)G)) {
+          rho = 0.0;
+        } else {
+          rho = 0.5 - 0.5 * (pe - 1.0) / (double)(G - 1);
+          rho = fmin(fmax(rho, 0.0), 0.5);
+        }
+      } else {
+        rho = fmin(fmax((double)P.ex_ratio, 0.0), 1.0);
+      }
+      nex = (int)floor(rho * (double)P.Np);
+    }
+    if (act) {
+      ring[m] = s_ring[m];
+      gs[s_ring[m]].pred = s_ring[(m + G - 1) % G];
+      uint32_t o = 0;
+      if (nex > 0 && !draw_bounded(P.key0, P.key1, P.tag, ST_EXCH, (uint32_t)m, (uint32_t)k1, (uint32_t)P.Np, o))
+        set_error(a.ds, ERR_DRAW, 2u, (uint32_t)t, (uint32_t)m);
+      gs[m].exo = o;
+      gs[m].u = philox(P.key0, P.key1, make_uint4((uint32_t)m, 0u, (uint32_t)k1, P.tag | (ST_RESAMPLE << 4))).x;
+      gs[m].lambda = all_degenerate ? 0.0 : (double)lam;
+      gs[m].off = lam - logf((float)P.Np) - lse;
+    }
+    if (threadIdx.x == 0) {
+      T->n_ex = nex;
+      T->m_nex = fastdiv_magic((uint32_t)(nex > 0 ? nex : 1));
+      T->pe_eff = pe;
+      T->k = k1;
+    }
   }
 }
 
@@ -628,7 +1065,7 @@ cudaError_t launch_init(const InitArgs& a, int grid, cudaStream_t s) {
 }
 
 cudaError_t launch_frame_prep(const FrameArgs& a, int nt, int blocks_x, cudaStream_t s) {
-  k_frame_prep<<<dim3(blocks_x, nt), 256, 0, s>>>(a);
+  k_frame_prep<<<dim3(blocks_x, nt), 256, 0, s>>>(a);  // blocks_x: rows per track (grid-stride)
   return cudaGetLastError();
 }
 
@@ -680,8 +1117,9 @@ cudaError_t launch_resample(const ResampleArgs& a, int n_groups, int cluster, cu
   return cudaLaunchKernelEx(&cfg, k_resample, a);
 }
 
-cudaError_t launch_global(const GlobalArgs& a, int n_tracks, cudaStream_t s) {
-  k_global<<<n_tracks, GL_THREADS, 0, s>>>(a);
+cudaError_t launch_global(const GlobalArgs& a, int n_tracks, int max_G, cudaStream_t s) {
+  const int threads = ((max_G + 31) / 32) * 32;
+  k_global<<<n_tracks, threads < 32 ? 32 : threads, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -43,6 +43,10 @@ struct K1Args {
   float* lw;
   float* tile_part;     // 8 floats per tile
   const float* ypad;
+  const CUtensorMap* tmaps;  // one per track over its padded frame, or nullptr
+  int* ring_next;            // per track: ring order of step k+1 (ARNA)
+  int n_ring_blocks;         // leading blocks that draw ring orders
+  int n_tracks;
 };
 
 struct ResampleArgs {
@@ -63,6 +67,7 @@ struct GlobalArgs {
   TrackState* ts;
   GroupState* gs;
   int* ring;
+  const int* ring_next;  // ring of the next step, drawn by the propagate kernel
   HistRec* hist;
   GroupHist* ghist;
   int history;
@@ -74,7 +79,7 @@ cudaError_t launch_init(const InitArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_frame_prep(const FrameArgs& a, int nt, int blocks_x, cudaStream_t s);
 cudaError_t launch_propagate(const K1Args& a, int R, int grid, cudaStream_t s);
 cudaError_t launch_resample(const ResampleArgs& a, int n_groups, int cluster, cudaStream_t s);
-cudaError_t launch_global(const GlobalArgs& a, int n_tracks, cudaStream_t s);
+cudaError_t launch_global(const GlobalArgs& a, int n_tracks, int max_G, cudaStream_t s);
 cudaError_t launch_export_states(const float4* pv, const float* In, long long n, float* out, cudaStream_t s);
 cudaError_t k1_occupancy(int R, int* blocks_per_sm);
 const void* propagate_kernel(int R);

@@ -73,7 +73,8 @@ def test_query_workspace_scales_with_particles(lib):
     ("G", 0, "G must be"), ("Np", 0, "Np must be"), ("H", 0, "H and W"), ("patch_radius", 9, "patch_radius"),
     ("mode", 3, "mode"), ("init_kind", 7, "init_kind"), ("sigma_psf", 0.0, "sigma_psf"),
     ("sigma_obs", -1.0, "sigma_obs"), ("sigma_pos", float("nan"), "process noise"), ("ex_ratio", 1.5, "ex_ratio"),
-    ("track_id", 1 << 24, "track_id"), ("reserved0", 1, "reserved0"), ("G", 5000, "G must be"),
+    ("track_id", 1 << 24, "track_id"), ("reserved0", 1, "reserved0"), ("G", 1025, "G must be"),
+    ("Np", (1 << 20) + 1, "Np must be"),
 ])
 def test_invalid_configs_are_rejected_on_the_host(lib, field, value, msg):
     with pytest.raises(B.PFError) as e:

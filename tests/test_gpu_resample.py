@@ -39,7 +39,8 @@ def _weights(kind, G, Np, rng):
 
 CASES = [(1, 1, "normal"), (3, 2, "normal"), (4, 1000, "special"), (2, 4095, "wide"), (2, 4096, "normal"),
          (2, 4097, "ties"), (5, 16384, "normal"), (4, 16384, "special"), (2, 65536, "wide"),
-         (1, 131072, "normal"), (1, 200003, "wide"), (64, 16384, "normal"), (256, 4096, "special")]
+         (1, 131072, "normal"), (1, 200003, "wide"), (64, 16384, "normal"), (256, 4096, "special"),
+         (1, 1 << 20, "wide"), (4, 1 << 20, "special")]
 
 
 @pytest.mark.parametrize("G,Np,kind", CASES)
