@@ -202,6 +202,29 @@ pf_status pf_resample(const float* logw_dev, const uint32_t* u_dev, int32_t G, i
                       uint32_t* anc_dev, uint64_t* q_dev, void* workspace_dev, size_t bytes,
                       void* stream);
 
+/* Largest G pf_resample_noalloc accepts (the size of its fixed scratch). */
+#define PF_NOALLOC_MAX_GROUPS 1024
+
+/* pf_resample without a workspace: the same kernel and the same results
+ * (logw_dev, u_dev, G, Np, anc_dev, q_dev exactly as for pf_resample), for
+ * callers that cannot allocate device memory at the point where they
+ * resample -- a fixed memory budget reserved up front, a framework whose
+ * caching allocator must not be bypassed, or a latency-critical loop where
+ * cudaMalloc's implicit device synchronisation is not acceptable.  The paper
+ * has no counterpart; it is a deployment variant of pf_resample.
+ * Its scratch (about 96 KB) is a fixed device array in the library, which
+ * every GPU that loads the library holds until the process exits.  The
+ * first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress, with the device current) and should come before
+ * any stream capture.  The call allocates nothing and frees nothing.  All
+ * calls share the array, which keeps the last call's contents; each call
+ * clears what must start at zero, and calls that overlap on the GPU race.
+ * G >= 1 and G <= PF_NOALLOC_MAX_GROUPS, 1 <= Np <= 2^20, G*Np < 2^31;
+ * larger G is rejected with PF_ERR_ARG.  Errors are reported through
+ * pf_last_error(NULL).  Errors: PF_ERR_ARG, PF_ERR_CUDA. */
+pf_status pf_resample_noalloc(const float* logw_dev, const uint32_t* u_dev, int32_t G, int32_t Np,
+                              uint32_t* anc_dev, uint64_t* q_dev, void* stream);
+
 /* Kernel timing.  With enable = 1, every later pf_step records a pair of
  * CUDA events around each of its kernels, on the stream it launches them
  * on; enable = 0 stops recording.  Recording adds no synchronisation.

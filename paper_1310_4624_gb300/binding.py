@@ -21,7 +21,8 @@ STATUS_NAMES = {0: "PF_OK", 1: "PF_ERR_ARG", 2: "PF_ERR_STATE", 3: "PF_ERR_CUDA"
 
 # Every symbol include/pfarna.h declares.
 EXPORTS = ("pf_abi_version", "pf_query_workspace", "pf_init", "pf_step", "pf_estimate", "pf_exchange_stats",
-           "pf_history", "pf_particles", "pf_resample_workspace", "pf_resample", "pf_profile_enable",
+           "pf_history", "pf_particles", "pf_resample_workspace", "pf_resample", "pf_resample_noalloc",
+           "pf_profile_enable",
            "pf_profile_read", "pf_destroy", "pf_last_error")
 KERNEL_NAMES = ("frame_prep", "propagate_weight", "resample", "global")
 
@@ -83,6 +84,7 @@ def load():
     L.pf_particles.argtypes = [_P, C.c_int32, _P, _P, _P, _P, _P]
     L.pf_resample_workspace.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]
     L.pf_resample.argtypes = [_P, _P, C.c_int32, C.c_int32, _P, _P, _P, C.c_size_t, _P]
+    L.pf_resample_noalloc.argtypes = [_P, _P, C.c_int32, C.c_int32, _P, _P, _P]
     L.pf_profile_enable.argtypes = [_P, C.c_int32]
     L.pf_profile_read.argtypes = [_P, C.c_int32, _P, _P]
     L.pf_destroy.argtypes = [_P]
@@ -160,6 +162,10 @@ def pf_resample_workspace(G: int, Np: int) -> int:
 
 def pf_resample(logw_ptr, u_ptr, G: int, Np: int, anc_ptr, q_ptr, ws_ptr, nbytes: int, stream_ptr) -> None:
     _check(load().pf_resample(logw_ptr, u_ptr, G, Np, anc_ptr, q_ptr, ws_ptr, nbytes, stream_ptr), "pf_resample")
+
+
+def pf_resample_noalloc(logw_ptr, u_ptr, G: int, Np: int, anc_ptr, q_ptr, stream_ptr) -> None:
+    _check(load().pf_resample_noalloc(logw_ptr, u_ptr, G, Np, anc_ptr, q_ptr, stream_ptr), "pf_resample_noalloc")
 
 
 def pf_profile_enable(handle: int, enable: bool) -> None:

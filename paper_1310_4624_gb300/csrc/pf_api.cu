@@ -238,6 +238,12 @@ pf_status sync(pf_handle* h) {
 
 }  // namespace
 
+namespace pf {
+QuantCoeffs resample_coeffs() { return make_qc(); }
+int resample_cluster_size(int Np) { return resample_cluster(Np, true); }
+void set_handleless_error(const char* msg) { g_err = msg; }
+}  // namespace pf
+
 extern "C" {
 
 int32_t pf_abi_version(void) { return PF_ABI_VERSION; }

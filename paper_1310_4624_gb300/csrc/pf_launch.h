@@ -84,4 +84,9 @@ cudaError_t launch_export_states(const float4* pv, const float* In, long long n,
 cudaError_t k1_occupancy(int R, int* blocks_per_sm);
 const void* propagate_kernel(int R);
 
+// Host helpers shared by the C-ABI entry points (defined in pf_api.cu).
+QuantCoeffs resample_coeffs();             // weight-code coefficients
+int resample_cluster_size(int Np);         // resampler cluster size for one group of Np
+void set_handleless_error(const char* msg);  // text for pf_last_error(NULL)
+
 }  // namespace pf
