@@ -42,6 +42,33 @@ ALG_SFU_OPS = 35        # MUFU operations
 ALG_BYTES = 48          # HBM bytes of the whole step per particle
 
 
+def kernel_source_hash() -> str:
+    """sha256 of the kernel sources; ncu figures in profiles/ are tied to it."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("pf_kernels.cu", "pf_device.cuh", "pf_launch.h"):
+        with open(os.path.join(ROOT, "paper_1310_4624_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from profiles/*.md, if captured on
+    the current kernel sources (else None)."""
+    import glob
+    import re
+    src = kernel_source_hash()
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        text = open(path).read()
+        m = re.search(r"kernel sources sha256\[:16\]: ([0-9a-f]{16})", text)
+        if not m or m.group(1) != src:
+            continue
+        t = re.search(r"traffic_bytes_per_launch %s: ([0-9]+)" % re.escape(kernel), text)
+        if t:
+            return int(t.group(1)), os.path.basename(path)
+    return None, None
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -149,7 +176,7 @@ def time_filter(pf, fr, first: int, K: int, flush, profile: bool):
     return sum(a.elapsed_time(b) for a, b in evs)
 
 
-def cpu_baseline(wl, frames, truth, steps: int = 2):
+def cpu_baseline(wl, frames, truth, steps: int = 8):
     """The FP64 oracle as it stands, single-threaded, on the full workload
     population for `steps` steps after an untimed step 0."""
     import oracle as ora
@@ -288,8 +315,9 @@ def main():
     k1_launches, k1_ms = a["prof"]["propagate_weight"]
     k1_avg_s = k1_ms / 1e3 / max(1, k1_launches)
     achieved = ALG_LANE_OPS * wl.N / k1_avg_s
+    traffic, traffic_src = profiled_traffic("k_propagate_weight")
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": lane_peak / 1e12, "unit": "Tops/s",
-                "frac": achieved / lane_peak, "traffic": None,
+                "frac": achieved / lane_peak, "traffic": traffic, "traffic_source": traffic_src,
                 "kernel": "k_propagate_weight", "peak_source": "%d SMs x 128 lanes x %.0f MHz (%s sm_max_mhz)"
                 % (sms, f_max / 1e6, src),
                 "kernel_ms": k1_avg_s * 1e3,

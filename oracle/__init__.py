@@ -83,6 +83,10 @@ def lib():
         L.ora_step.argtypes = [C.POINTER(Cfg), C.c_uint32, _P, _P, _P, _P, C.POINTER(_StepOut)]
         L.ora_step.restype = C.c_int
         L.ora_run.argtypes = [C.POINTER(Cfg), _P, _P, C.c_int32] + [_P] * 8
+        L.ora_loglik_image_grad.argtypes = [C.POINTER(Cfg), _P, C.c_double, C.c_double, C.c_double, _P]
+        L.ora_loglik_image_grad.restype = C.c_double
+        L.ora_replay_grad.argtypes = [C.POINTER(Cfg), C.c_int32, _P, _P, _P, C.c_double, _P, C.c_int32, _P, _P, _P]
+        L.ora_replay_grad.restype = C.c_int
         L.ora_run.restype = C.c_int
         _lib = L
     return _lib
@@ -315,3 +319,51 @@ def run(cfg: Cfg, pop0, obs, T: int) -> RunResult:
                                   _ptr(r.n_ex), _ptr(r.pe_eff), _ptr(r.sigma), _ptr(r.Lambda),
                                   _ptr(r.gxhat), _ptr(r.pop_final))
     return r
+
+
+# ------------------------------------------------------------- gradients
+THETA = ("sigma_psf", "A", "b", "sigma_pos", "sigma_v")
+
+
+def loglik_image_grad(cfg: Cfg, frame, x: float, y: float, I: float):
+    """(l, [dl/dx, dl/dy, dl/dI, dl/dsigma_psf, dl/db])."""
+    f = _c(frame, np.float32)
+    d = np.zeros(5)
+    l = lib().ora_loglik_image_grad(C.byref(cfg), _ptr(f), x, y, I, _ptr(d))
+    return l, d
+
+
+def replay_grad(cfg: Cfg, kind: int, x0, frames, T: int, parents, lo=None, hi=None, radius: float = 0.0):
+    """(log Z, d log Z / d theta) of a replay with frozen ancestry; theta =
+    (sigma_psf, A = x0[4], background, sigma_pos, sigma_v)."""
+    N = cfg.G * cfg.Np
+    x0 = _c(x0, np.float64)
+    lo = _c(lo if lo is not None else np.zeros(5), np.float64)
+    hi = _c(hi if hi is not None else np.zeros(5), np.float64)
+    fr = _c(frames, np.float32)
+    par = _c(parents, np.int32)
+    assert par.shape == (T, N)
+    lz = np.zeros(1)
+    g = np.zeros(5)
+    lib().ora_replay_grad(C.byref(cfg), kind, _ptr(x0), _ptr(lo), _ptr(hi), radius, _ptr(fr), T, _ptr(par),
+                          _ptr(lz), _ptr(g))
+    return float(lz[0]), g
+
+
+def run_with_parents(cfg: Cfg, pop0, obs, T: int):
+    """An oracle run that also returns each step's parents (T, N) -- the
+    exchange composed with the previous resampling, track-local slots."""
+    G, Np = cfg.G, cfg.Np
+    N = G * Np
+    par = np.zeros((T, N), np.int32)
+    par[0] = np.arange(N)
+    pop, lam, logc, prev = pop0, None, [], None
+    base = np.repeat(np.arange(G, dtype=np.int64) * Np, Np)
+    for k in range(T):
+        r = step(cfg, k, obs[k], pop, lam)
+        if k > 0:
+            par[k] = prev[r.src]
+        prev = r.anc.astype(np.int64) + base
+        pop, lam = r.pop_out, r.Lambda
+        logc.append(r.logc)
+    return par, np.array(logc)

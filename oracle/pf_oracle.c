@@ -659,3 +659,147 @@ int ora_run(const ora_cfg* c, const double* pop0, const float* obs, int32_t T, d
   free(Lam);
   return failed;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Gradient of log Z with respect to theta = (sigma_psf, A, b, sigma_pos,   */
+/* sigma_v) with the resampling ancestry frozen.                             */
+/* ------------------------------------------------------------------------ */
+
+/* l of ora_loglik_image and its partial derivatives with respect to x, y, I
+ * (state) and sigma_psf, b (parameters): d[0..4] = dl/dx, dl/dy, dl/dI,
+ * dl/dsigma_psf, dl/db.  The patch centre is piecewise constant in the
+ * state, so it contributes no derivative.  Pixels outside the image read b,
+ * so their residual does not depend on b. */
+double ora_loglik_image_grad(const ora_cfg* c, const float* frame, double x, double y, double I, double d[5]) {
+  for (int q = 0; q < 5; ++q) d[q] = 0.0;
+  if (!isfinite(x) || !isfinite(y) || !isfinite(I)) return NAN;
+  double cx = floor(x + 0.5), cy = floor(y + 0.5);
+  double b = c->background, s = c->sigma_psf, s2 = 2.0 * s * s, so2 = c->sigma_obs * c->sigma_obs;
+  double acc = 0.0;
+  for (int dv = -c->R; dv <= c->R; ++dv) {
+    double v = cy + dv;
+    for (int du = -c->R; du <= c->R; ++du) {
+      double u = cx + du;
+      int inside = (u >= 0.0 && u < (double)c->W && v >= 0.0 && v < (double)c->H);
+      double z = inside ? (double)frame[(int64_t)v * c->W + (int64_t)u] : b;
+      double gx = exp(-(u - x) * (u - x) / s2);
+      double gy = exp(-(v - y) * (v - y) / s2);
+      double m = I * gx * gy;
+      double r = z - b - m;
+      acc += r * r;
+      /* dl/dtheta = -(1/so2) sum r dr/dtheta, dr/dtheta = -dm/dtheta (and -1 for b inside) */
+      d[0] += r * m * (u - x) / (s * s);
+      d[1] += r * m * (v - y) / (s * s);
+      d[2] += r * gx * gy;
+      d[3] += r * m * ((u - x) * (u - x) + (v - y) * (v - y)) / (s * s * s);
+      if (inside) d[4] += r;
+    }
+  }
+  for (int q = 0; q < 5; ++q) d[q] /= so2;
+  return -acc / (2.0 * so2);
+}
+
+/* Replay of steps 0 .. T-1 with frozen ancestry, FP64, with forward-mode
+ * tangents.  parents: T rows of N track-local slots; row k (k >= 1) gives
+ * the slot of X_{k-1} each slot of step k was propagated from (the exchange
+ * composed with the previous resampling), so its origin group is
+ * parent / Np; row 0 is not read.  The initial population is drawn as in
+ * ora_init with theta's A as the initial intensity (POINT: every particle;
+ * SHARING: group 0).  Writes log Z = sum_k log c_k and grad[5] = d log Z /
+ * d theta.  Per step (Alg. 3): X_k = NCV(X_{k-1}[parent]) (k >= 1),
+ * lw = Lambda_bar_{k-1}[origin] - log Np + l, Lambda_k,m = LSE_{i in m} lw,
+ * log c_k = LSE_m Lambda_k,m, Lambda_bar_k = Lambda_k - log c_k. */
+int ora_replay_grad(const ora_cfg* c, int32_t kind, const double* x0, const double* lo, const double* hi,
+                    double radius, const float* frames, int32_t T, const int32_t* parents, double* logZ,
+                    double* grad) {
+  int32_t G = c->G, Np = c->Np;
+  int64_t N = (int64_t)G * Np;
+  size_t fs = (size_t)c->H * (size_t)c->W;
+  double* X = (double*)malloc(sizeof(double) * (size_t)(5 * N));
+  double* Xn = (double*)malloc(sizeof(double) * (size_t)(5 * N));
+  double* dX = (double*)calloc((size_t)(25 * N), sizeof(double)); /* dX[(i*5 + d)*5 + p] */
+  double* dXn = (double*)calloc((size_t)(25 * N), sizeof(double));
+  double* lw = (double*)malloc(sizeof(double) * (size_t)N);
+  double* dlw = (double*)malloc(sizeof(double) * (size_t)(5 * N));
+  double* lbar = (double*)malloc(sizeof(double) * (size_t)G);
+  double* dlbar = (double*)calloc((size_t)(5 * G), sizeof(double));
+  double* Lam = (double*)malloc(sizeof(double) * (size_t)G);
+  double* dLam = (double*)malloc(sizeof(double) * (size_t)(5 * G));
+  ora_init(c, kind, x0, lo, hi, radius, X);
+  if (kind == ORA_INIT_POINT || kind == ORA_INIT_SHARING)
+    for (int64_t i = 0; i < N; ++i)
+      if (kind == ORA_INIT_POINT || i < Np) dX[(i * 5 + 4) * 5 + 1] = 1.0; /* dI/dA */
+  for (int32_t m = 0; m < G; ++m) lbar[m] = -log((double)G);
+  double lz = 0.0, gz[5] = {0, 0, 0, 0, 0};
+  for (int32_t k = 0; k < T; ++k) {
+    if (k >= 1) {
+      const int32_t* par = parents + (int64_t)k * N;
+      for (int32_t g = 0; g < G; ++g)
+        for (int32_t j = 0; j < Np; ++j) {
+          int64_t i = (int64_t)g * Np + j, p = par[i];
+          double e[5];
+          ora_normals(c, (uint32_t)g, (uint32_t)j, (uint32_t)k, e);
+          Xn[i] = X[p] + X[2 * N + p] + c->sigma_pos * e[0];
+          Xn[N + i] = X[N + p] + X[3 * N + p] + c->sigma_pos * e[1];
+          Xn[2 * N + i] = X[2 * N + p] + c->sigma_v * e[2];
+          Xn[3 * N + i] = X[3 * N + p] + c->sigma_v * e[3];
+          Xn[4 * N + i] = X[4 * N + p] + c->sigma_I * e[4];
+          for (int q = 0; q < 5; ++q) {
+            double px = dX[(p * 5 + 0) * 5 + q], py = dX[(p * 5 + 1) * 5 + q];
+            double pvx = dX[(p * 5 + 2) * 5 + q], pvy = dX[(p * 5 + 3) * 5 + q];
+            double pI = dX[(p * 5 + 4) * 5 + q];
+            dXn[(i * 5 + 0) * 5 + q] = px + pvx + (q == 3 ? e[0] : 0.0);
+            dXn[(i * 5 + 1) * 5 + q] = py + pvy + (q == 3 ? e[1] : 0.0);
+            dXn[(i * 5 + 2) * 5 + q] = pvx + (q == 4 ? e[2] : 0.0);
+            dXn[(i * 5 + 3) * 5 + q] = pvy + (q == 4 ? e[3] : 0.0);
+            dXn[(i * 5 + 4) * 5 + q] = pI;
+          }
+        }
+      double* t = X; X = Xn; Xn = t;
+      t = dX; dX = dXn; dXn = t;
+    }
+    /* weights and their tangents */
+    for (int64_t i = 0; i < N; ++i) {
+      int32_t o = (k == 0) ? (int32_t)(i / Np) : (int32_t)(parents[(int64_t)k * N + i] / Np);
+      double dl[5];
+      double l = ora_loglik_image_grad(c, frames + (size_t)k * fs, X[i], X[N + i], X[4 * N + i], dl);
+      lw[i] = lbar[o] - log((double)Np) + l;
+      for (int q = 0; q < 5; ++q) {
+        double v = dl[0] * dX[(i * 5 + 0) * 5 + q] + dl[1] * dX[(i * 5 + 1) * 5 + q] +
+                   dl[2] * dX[(i * 5 + 4) * 5 + q];
+        if (q == 0) v += dl[3];
+        if (q == 2) v += dl[4];
+        dlw[i * 5 + q] = dlbar[o * 5 + q] + v;
+      }
+    }
+    for (int32_t m = 0; m < G; ++m) {
+      const double* lm = lw + (int64_t)m * Np;
+      double mx = -INFINITY;
+      for (int32_t j = 0; j < Np; ++j)
+        if (lm[j] > mx) mx = lm[j];
+      double s = 0.0, ds[5] = {0, 0, 0, 0, 0};
+      for (int32_t j = 0; j < Np; ++j) {
+        double w = exp(lm[j] - mx);
+        s += w;
+        for (int q = 0; q < 5; ++q) ds[q] += w * dlw[((int64_t)m * Np + j) * 5 + q];
+      }
+      Lam[m] = mx + log(s);
+      for (int q = 0; q < 5; ++q) dLam[m * 5 + q] = ds[q] / s;
+    }
+    double lc = lse(Lam, G), dlc[5] = {0, 0, 0, 0, 0};
+    for (int32_t m = 0; m < G; ++m) {
+      double pi = exp(Lam[m] - lc);
+      for (int q = 0; q < 5; ++q) dlc[q] += pi * dLam[m * 5 + q];
+    }
+    lz += lc;
+    for (int q = 0; q < 5; ++q) gz[q] += dlc[q];
+    for (int32_t m = 0; m < G; ++m) {
+      lbar[m] = Lam[m] - lc;
+      for (int q = 0; q < 5; ++q) dlbar[m * 5 + q] = dLam[m * 5 + q] - dlc[q];
+    }
+  }
+  *logZ = lz;
+  for (int q = 0; q < 5; ++q) grad[q] = gz[q];
+  free(X); free(Xn); free(dX); free(dXn); free(lw); free(dlw); free(lbar); free(dlbar); free(Lam); free(dLam);
+  return 0;
+}
