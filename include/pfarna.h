@@ -144,6 +144,31 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
  * PF_ERR_CUDA. */
 pf_status pf_step(pf_handle* h, const float* const* frames_host, void* stream);
 
+/* pf_step with the frames taken from a device table: table_dev holds
+ * T_table x n_tracks device pointers, frame k of track t at index
+ * k * n_tracks + t, and the step's index k is read on the device, so the
+ * launch sequence has no per-step parameters.  n_tracks <= 65535.
+ * Errors: PF_ERR_ARG, PF_ERR_STATE (no table entry for this step),
+ * PF_ERR_CUDA. */
+pf_status pf_step_table(pf_handle* h, const float* const* table_dev, int32_t T_table, void* stream);
+
+/* pf_step_table through a CUDA graph: the first call (and the first after
+ * the table, T_table or the autotuned shapes change) captures the step's
+ * launches into a graph; every call launches it on `stream`.
+ * Errors: as pf_step_table. */
+pf_status pf_graph_step(pf_handle* h, const float* const* table_dev, int32_t T_table, void* stream);
+
+/* One pf_step that also chooses the launch shapes of the handle's later
+ * steps: the propagate kernel's grid (SM count x resident CTAs per SM, 1 ..
+ * the occupancy limit) and the resampler's thread-block cluster size
+ * (1, 2, 4, 8), each the fastest of the candidates timed with CUDA events
+ * on this step's data (both kernels are idempotent within a step).  Results
+ * are cached per problem shape for the process.  Synchronises the stream.
+ * k1_grid_out / cluster_out (may be NULL) receive the choices.
+ * Errors: PF_ERR_ARG, PF_ERR_STATE, PF_ERR_CUDA. */
+pf_status pf_autotune(pf_handle* h, const float* const* frames_host, int32_t* k1_grid_out, int32_t* cluster_out,
+                      void* stream);
+
 /* Wait for the handle's last stream and copy the latest global estimate
  * (n_tracks x 5 floats, may be NULL) and log marginal-likelihood estimate
  * log Z = sum_k log c_k (n_tracks doubles, may be NULL) to the host.
@@ -245,6 +270,46 @@ enum {
  * summed device duration in milliseconds; the records are then cleared.
  * Either array may be NULL.  Errors: PF_ERR_ARG, PF_ERR_CUDA. */
 pf_status pf_profile_read(pf_handle* h, int32_t n, int64_t* launches, double* total_ms);
+
+/* Parameters of the differentiable form: theta = (sigma_psf, A, b,
+ * sigma_pos, sigma_v), A being the initial intensity of the particles
+ * (init_state[4]; every particle for PF_INIT_POINT, group 0 for
+ * PF_INIT_SHARING). */
+enum {
+  PF_THETA_SIGMA_PSF = 0,
+  PF_THETA_AMPLITUDE = 1,
+  PF_THETA_BACKGROUND = 2,
+  PF_THETA_SIGMA_POS = 3,
+  PF_THETA_SIGMA_V = 4,
+  PF_THETA_COUNT = 5
+};
+
+/* Set theta (PF_THETA_COUNT floats, host) of one track; later pf_step,
+ * pf_reset and pf_backward calls use it.  Synchronous upload.
+ * Errors: PF_ERR_ARG (out of range), PF_ERR_CUDA. */
+pf_status pf_set_theta(pf_handle* h, int32_t track, const float* theta_host);
+
+/* Restart every track from a fresh initial population drawn with the
+ * current parameters (step 0 next); not for PF_INIT_USER tracks.
+ * Errors: PF_ERR_ARG, PF_ERR_STATE, PF_ERR_CUDA. */
+pf_status pf_reset(pf_handle* h, void* stream);
+
+/* Gradient of log Z = sum_{k<T} log c_k with respect to theta, with the
+ * resampling ancestry of the T steps run since pf_init / pf_reset held fixed
+ * (every track must have record_ancestors; T = steps run <= history).  The
+ * forward pass is replayed from the initial population (drawn again with
+ * the current theta) through the recorded parents and the same Philox
+ * streams, keeping states only at checkpoints every ceil(sqrt(T)) steps;
+ * the reverse sweep recomputes each segment's states and back-propagates
+ * through the group log-weights (Alg. 3 steps 4-10), the likelihood and the
+ * NCV dynamics.  frames_host: T x n_tracks device pointers, frame k of track
+ * t at index k * n_tracks + t (the frames of the forward run).
+ * dlogZ_host: n_tracks upstream derivatives.  grad_dev: n_tracks x 5 floats,
+ * dlogZ * d log Z / d theta.  logZ_dev: optional n_tracks doubles, the
+ * replayed log Z.  Enqueued on `stream`; the forward filter state is left
+ * as it was.  Errors: PF_ERR_ARG, PF_ERR_STATE, PF_ERR_CUDA. */
+pf_status pf_backward(pf_handle* h, const float* const* frames_host, int32_t T, const float* dlogZ_host,
+                      float* grad_dev, double* logZ_dev, void* stream);
 
 /* Release the handle's host metadata (the workspace stays the caller's). */
 void pf_destroy(pf_handle* h);

@@ -22,8 +22,9 @@ STATUS_NAMES = {0: "PF_OK", 1: "PF_ERR_ARG", 2: "PF_ERR_STATE", 3: "PF_ERR_CUDA"
 # Every symbol include/pfarna.h declares.
 EXPORTS = ("pf_abi_version", "pf_query_workspace", "pf_init", "pf_step", "pf_estimate", "pf_exchange_stats",
            "pf_history", "pf_particles", "pf_resample_workspace", "pf_resample", "pf_resample_noalloc",
-           "pf_profile_enable",
-           "pf_profile_read", "pf_destroy", "pf_last_error")
+           "pf_profile_enable", "pf_profile_read", "pf_set_theta", "pf_reset", "pf_backward", "pf_step_table",
+           "pf_graph_step", "pf_autotune", "pf_destroy", "pf_last_error")
+THETA_NAMES = ("sigma_psf", "amplitude", "background", "sigma_pos", "sigma_v")
 KERNEL_NAMES = ("frame_prep", "propagate_weight", "resample", "global")
 
 
@@ -87,6 +88,12 @@ def load():
     L.pf_resample_noalloc.argtypes = [_P, _P, C.c_int32, C.c_int32, _P, _P, _P]
     L.pf_profile_enable.argtypes = [_P, C.c_int32]
     L.pf_profile_read.argtypes = [_P, C.c_int32, _P, _P]
+    L.pf_set_theta.argtypes = [_P, C.c_int32, _P]
+    L.pf_step_table.argtypes = [_P, _P, C.c_int32, _P]
+    L.pf_graph_step.argtypes = [_P, _P, C.c_int32, _P]
+    L.pf_autotune.argtypes = [_P, C.POINTER(_P), _P, _P, _P]
+    L.pf_reset.argtypes = [_P, _P]
+    L.pf_backward.argtypes = [_P, C.POINTER(_P), C.c_int32, _P, _P, _P, _P]
     L.pf_destroy.argtypes = [_P]
     L.pf_destroy.restype = None
     L.pf_last_error.argtypes = [_P]
@@ -181,6 +188,37 @@ def pf_profile_read(handle: int):
     _check(load().pf_profile_read(handle, n, cnt.ctypes.data_as(_P), ms.ctypes.data_as(_P)), "pf_profile_read",
            handle)
     return {KERNEL_NAMES[i]: (int(cnt[i]), float(ms[i])) for i in range(n)}
+
+
+def pf_step_table(handle: int, table_ptr, T_table: int, stream_ptr) -> None:
+    _check(load().pf_step_table(handle, table_ptr, T_table, stream_ptr), "pf_step_table", handle)
+
+
+def pf_graph_step(handle: int, table_ptr, T_table: int, stream_ptr) -> None:
+    _check(load().pf_graph_step(handle, table_ptr, T_table, stream_ptr), "pf_graph_step", handle)
+
+
+def pf_autotune(handle: int, frame_ptrs, stream_ptr):
+    arr = (_P * len(frame_ptrs))(*frame_ptrs)
+    g = C.c_int32(0)
+    c = C.c_int32(0)
+    _check(load().pf_autotune(handle, arr, C.byref(g), C.byref(c), stream_ptr), "pf_autotune", handle)
+    return g.value, c.value
+
+
+def pf_set_theta(handle: int, track: int, theta) -> None:
+    arr = (C.c_float * 5)(*[float(v) for v in theta])
+    _check(load().pf_set_theta(handle, track, arr), "pf_set_theta", handle)
+
+
+def pf_reset(handle: int, stream_ptr) -> None:
+    _check(load().pf_reset(handle, stream_ptr), "pf_reset", handle)
+
+
+def pf_backward(handle: int, frame_ptrs, T: int, dlogZ, grad_ptr, logZ_ptr, stream_ptr) -> None:
+    arr = (_P * len(frame_ptrs))(*frame_ptrs)
+    seeds = (C.c_float * len(dlogZ))(*[float(v) for v in dlogZ])
+    _check(load().pf_backward(handle, arr, T, seeds, grad_ptr, logZ_ptr, stream_ptr), "pf_backward", handle)
 
 
 def pf_destroy(handle: int) -> None:

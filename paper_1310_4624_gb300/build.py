@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpfarna.so")
-SOURCES = ["pf_kernels.cu", "pf_api.cu", "pf_noalloc.cu"]
+SOURCES = ["pf_kernels.cu", "pf_api.cu", "pf_noalloc.cu", "pf_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-Xptxas", "-v",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -1,0 +1,374 @@
+// pf_adjoint.cu -- kernels of pf_backward: the gradient of log Z = sum_k
+// log c_k with respect to theta = (sigma_psf, A, b, sigma_pos, sigma_v) with
+// the resampling ancestry of the forward run held fixed.
+//
+// Paper: Demirel et al., "An Adaptive Distributed Resampling Algorithm with
+// Non-Proportional Allocation" (arXiv:1310.4624).  With the ancestry fixed
+// the filter (Alg. 3) is a smooth function of theta:
+//   X_k(i)   = NCV(X_{k-1}(p_k(i)); theta)            (Alg. 1 step P)
+//   lw_k(i)  = lbar_{k-1}(o(i)) - log Np + l_k(i)      (steps 4-5, U)
+//   L_k,m    = LSE_{i in m} lw_k(i)                    (step 6)
+//   log c_k  = LSE_m L_k,m,  lbar_k = L_k - log c_k    (steps 9-10)
+// with o(i) = p_k(i) div Np the origin group of the slot (the exchange puts
+// a particle of group o into slot i).  Reverse mode, seed s = d out / d log Z:
+//   dL_{T-1,m} = s pi_m,  dL_{k,m} = sum_{i : o_{k+1}(i) = m} dlw_{k+1}(i)
+//   dlw_k(i)   = dL_{k,m(i)} exp(lw_k(i) - L_k,m(i))
+// (the softmax terms of lbar cancel because sum_m dL_k,m = s at every k);
+// states back-propagate through the NCV Jacobian to their recorded parents.
+// The forward pass is replayed from the initial population and the recorded
+// parents with the same Philox streams; states are recomputed from
+// checkpoints, not stored per step.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cmath>
+#include <cstdint>
+
+#include "pf_device.cuh"
+#include "pf_launch.h"
+#include "pf_math.cuh"
+
+namespace pf {
+
+// ------------------------------------------------------------------ replay
+// Replay of step k for every slot: the state (k >= 1: NCV from the recorded
+// parent and the step's normals) and, when weights != 0, the log-weight and
+// its per-tile (max, sum exp) for the group log-weights.
+template <int R>
+__global__ void __launch_bounds__(256) k_replay(ReplayArgs a) {
+  constexpr int PAD = 2 * R + 1;
+  const int k = a.k;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ float s_m[8], s_s[8];
+  for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+    const int4 td = a.tiles[tile];
+    const TrackParams& P = a.trk[td.x];
+    const int g = td.y, Np = P.Np;
+    const long long Nt = (long long)P.G * Np;
+    float mx = -INFINITY, sm = 0.0f;
+    for (int jj = threadIdx.x; jj < td.w; jj += blockDim.x) {
+      const int j = td.z + jj;
+      const long long il = (long long)g * Np + j, i = P.part_off + il;
+      float4 s;
+      float I;
+      int o = g;
+      if (k >= 1) {
+        const long long par = a.parent[P.parent_off + (long long)(k % a.history) * Nt + il];
+        o = (int)(par / Np);
+        s = a.pv_in[P.part_off + par];
+        I = a.I_in[P.part_off + par];
+        uint4 w0 = make_uint4(j, g, k, P.tag | (ST_PROP << 4) | 0u);
+        uint4 w1 = make_uint4(j, g, k, P.tag | (ST_PROP << 4) | 1u);
+        philox2(P.key0, P.key1, w0, w1);
+        float e0, e1, e2, e3, e4, e5;
+        box_muller_fast(w0.x, w0.y, e0, e1);
+        box_muller_fast(w0.z, w0.w, e2, e3);
+        box_muller_fast(w1.x, w1.y, e4, e5);
+        s.x = fmaf(P.spos, e0, s.x + s.z);
+        s.y = fmaf(P.spos, e1, s.y + s.w);
+        s.z = fmaf(P.sv, e2, s.z);
+        s.w = fmaf(P.sv, e3, s.w);
+        I = fmaf(P.sI, e4, I);
+        a.pv_out[i] = s;
+        a.I_out[i] = I;
+      } else {
+        s = a.pv_out[i];
+        I = a.I_out[i];
+      }
+      if (a.ck_pv) {
+        a.ck_pv[i] = s;
+        a.ck_I[i] = I;
+      }
+      if (a.weights) {
+        float gxI[2 * R + 1];
+        const float cxf = floorf(s.x + 0.5f), cyf = floorf(s.y + 0.5f);
+        gauss_row<R>(cxf, s.x, P.c_psf, P.kappa, gxI);
+#pragma unroll
+        for (int c = 0; c < 2 * R + 1; ++c) gxI[c] *= I;
+        const int pu = (int)fminf(fmaxf(cxf, -(float)(R + 1)), (float)(P.W + R)) - R + PAD;
+        const int pv = (int)fminf(fmaxf(cyf, -(float)(R + 1)), (float)(P.H + R)) - R + PAD;
+        const float ss = patch_ss<R, false>(a.ypad + P.ypad_off + (long long)pv * P.pitch + pu, P.pitch, gxI,
+                                            cyf - s.y, P.c_psf, P.kappa);
+        const float lb = k >= 1 ? (float)a.lbar_prev[P.group_off + o] : -logf((float)P.G);
+        const float lw = lb - logf((float)Np) - ss * P.inv2so2;
+        if (lw == lw && lw > -INFINITY) {
+          if (lw > mx) {
+            sm = sm * __expf(mx - lw) + 1.0f;
+            mx = lw;
+          } else {
+            sm += __expf(lw - mx);
+          }
+        }
+      }
+    }
+    if (a.weights) {
+      // block (max, sum exp) of the tile
+      float m2 = warp_max(mx);
+      float s2 = (mx > -INFINITY) ? sm * __expf(mx - m2) : 0.0f;
+      s2 = warp_sum(s2);
+      if (lane == 0) {
+        s_m[warp] = m2;
+        s_s[warp] = s2;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        float M = -INFINITY;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) M = fmaxf(M, s_m[w]);
+        float S = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+          if (s_m[w] > -INFINITY) S += s_s[w] * __expf(s_m[w] - M);
+        a.tile_part[(long long)tile * 8 + 0] = M;
+        a.tile_part[(long long)tile * 8 + 1] = S;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Per track: the replayed group log-weights of step k, log c_k, lbar_k, and
+// at the last step the seed of the reverse sweep, dL = s pi.  FP64 (G-sized).
+__global__ void k_replay_groups(ReplayGroupArgs a) {
+  const int t = blockIdx.x;
+  const TrackParams& P = a.trk[t];
+  const int G = P.G, m = threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)blockDim.x >> 5;
+  __shared__ double s_d[32];
+  __shared__ double s_lc;
+  double lam = -INFINITY;
+  if (m < G) {
+    const int t0 = a.gd[P.group_off + m].tile_begin, nt = a.gd[P.group_off + m].tile_count;
+    double M = -INFINITY;
+    for (int q = 0; q < nt; ++q) M = fmax(M, (double)a.tile_part[(long long)(t0 + q) * 8]);
+    double S = 0.0;
+    if (M > -INFINITY)
+      for (int q = 0; q < nt; ++q) {
+        const double Mt = a.tile_part[(long long)(t0 + q) * 8];
+        if (Mt > -INFINITY) S += (double)a.tile_part[(long long)(t0 + q) * 8 + 1] * exp(Mt - M);
+      }
+    lam = (M > -INFINITY && S > 0.0) ? M + log(S) : -INFINITY;
+  }
+  double mx = warp_max_d(lam);
+  if (lane == 0) s_d[warp] = mx;
+  __syncthreads();
+  mx = -INFINITY;
+  for (int w = 0; w < nw; ++w) mx = fmax(mx, s_d[w]);
+  __syncthreads();
+  double e = (m < G && lam > -INFINITY) ? exp(lam - mx) : 0.0;
+  double se = warp_sum_d(e);
+  if (lane == 0) s_d[warp] = se;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < nw; ++w) tot += s_d[w];
+    s_lc = mx + log(tot);
+    a.logZ[t] += s_lc;
+  }
+  __syncthreads();
+  const double lc = s_lc;
+  if (m < G) {
+    const long long gm = P.group_off + m;
+    a.lam_hist[(long long)a.k * a.G_total + gm] = lam;
+    a.lbar_hist[(long long)a.k * a.G_total + gm] = lam - lc;
+    if (a.last) a.dlam[gm] = (double)a.seed[t] * exp(lam - lc);
+  }
+}
+
+// ------------------------------------------------------------------ adjoint
+// Log-likelihood (Sec. V model) and its partial derivatives for the
+// adjoint: d[0..4] = dl/dx, dl/dy, dl/dI, dl/dsigma_psf, dl/db.  One pass
+// over the patch with separable row sums: per row v with r = y - I gx gy,
+// R0 = sum r gx, R1 = sum r gx a, R2 = sum r gx a^2 (a the column offset), so
+// that sum r gx (u - x) = R1 + du0 R0 and sum r gx (u - x)^2 = R2 + 2 du0 R1
+// + du0^2 R0 with du0 = cx - R - x.  Pixels outside the frame count as
+// background, so only inside pixels depend on b.
+template <int R>
+__device__ __forceinline__ float loglik_grad(const float* __restrict__ yp, int pitch, int H, int W, float x, float y,
+                                             float I, const TrackParams& P, float (&d)[5]) {
+  constexpr int D = 2 * R + 1;
+  constexpr int PAD = 2 * R + 1;
+  const float cxf = floorf(x + 0.5f), cyf = floorf(y + 0.5f);
+  const int cx = (int)fminf(fmaxf(cxf, -(float)(R + 1)), (float)(W + R));
+  const int cy = (int)fminf(fmaxf(cyf, -(float)(R + 1)), (float)(H + R));
+  const float* __restrict__ row = yp + (long long)(cy - R + PAD) * pitch + (cx - R + PAD);
+  float gx[D];
+  gauss_row<R>(cxf, x, P.c_psf, P.kappa, gx);
+  float gy[D];
+  gauss_row<R>(cyf, y, P.c_psf, P.kappa, gy);
+  // inside-the-frame column / row ranges of the (true) patch
+  const float ulo = fmaxf(0.0f, (float)R - cxf), uhi = fminf((float)(2 * R), (float)(W - 1) + (float)R - cxf);
+  const float vlo = fmaxf(0.0f, (float)R - cyf), vhi = fminf((float)(2 * R), (float)(H - 1) + (float)R - cyf);
+  float ss = 0.0f, SI = 0.0f, S1 = 0.0f, Sy = 0.0f, Ss = 0.0f, Sb = 0.0f;
+  const float du0 = cxf - (float)R - x;
+#pragma unroll
+  for (int b = 0; b < D; ++b) {
+    const float* __restrict__ rp = row + (long long)b * pitch;
+    const float Igy = I * gy[b];
+    float R0 = 0.0f, R1 = 0.0f, R2 = 0.0f, Rb = 0.0f;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const float r = fmaf(-gx[a], Igy, __ldg(rp + a));
+      ss = fmaf(r, r, ss);
+      const float t = r * gx[a];
+      R0 += t;
+      R1 = fmaf(t, (float)a, R1);
+      R2 = fmaf(t, (float)(a * a), R2);
+      Rb += ((float)a >= ulo && (float)a <= uhi) ? r : 0.0f;
+    }
+    const float dv = (cyf - (float)R + (float)b) - y;
+    const float sx1 = R1 + du0 * R0;
+    const float sx2 = R2 + 2.0f * du0 * R1 + du0 * du0 * R0;
+    SI = fmaf(gy[b], R0, SI);
+    S1 = fmaf(gy[b], sx1, S1);
+    Sy = fmaf(gy[b] * dv, R0, Sy);
+    Ss = fmaf(gy[b], fmaf(dv * dv, R0, sx2), Ss);
+    if ((float)b >= vlo && (float)b <= vhi) Sb += Rb;
+  }
+  const float iso2 = 2.0f * P.inv2so2;  // 1 / sigma_obs^2
+  const float s2 = P.spsf * P.spsf;
+  d[0] = I * S1 / s2 * iso2;
+  d[1] = I * Sy / s2 * iso2;
+  d[2] = SI * iso2;
+  d[3] = I * Ss / (s2 * P.spsf) * iso2;
+  d[4] = Sb * iso2;
+  return -ss * P.inv2so2;
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
+  const int k = a.k;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ double s_g[8][5];
+  for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+    const int4 td = a.tiles[tile];
+    const TrackParams& P = a.trk[td.x];
+    const int g = td.y, Np = P.Np;
+    const long long Nt = (long long)P.G * Np;
+    const bool A_enters = (P.init_kind == INIT_POINT) || (P.init_kind == INIT_SHARING && g == 0);
+    float gacc[5] = {0, 0, 0, 0, 0};
+    for (int jj = threadIdx.x; jj < td.w; jj += blockDim.x) {
+      const int j = td.z + jj;
+      const long long il = (long long)g * Np + j, i = P.part_off + il;
+      const float4 s = a.pv[i];
+      const float I = a.In[i];
+      long long par = il;
+      int o = g;
+      if (k >= 1) {
+        par = a.parent[P.parent_off + (long long)(k % a.history) * Nt + il];
+        o = (int)(par / Np);
+      }
+      float dl[5];
+      const float l = loglik_grad<R>(a.ypad + P.ypad_off, P.pitch, P.H, P.W, s.x, s.y, I, P, dl);
+      const float lb = k >= 1 ? (float)a.lbar_prev[P.group_off + o] : -logf((float)P.G);
+      const float lw = lb - logf((float)Np) + l;
+      const float lam = (float)a.lam_k[P.group_off + g];
+      const float wbar = (lw == lw && lw - lam > -87.0f) ? __expf(lw - lam) : 0.0f;
+      const float dlw = (float)a.dlam_k[P.group_off + g] * wbar;
+      if (k >= 1 && dlw != 0.0f) atomicAdd(&a.D[P.group_off + o], (double)dlw);
+      // adjoint of the state: the likelihood term plus the children's
+      float4 c = a.Cc_pv[i];
+      float cI = a.Cc_I[i];
+      a.Cc_pv[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      a.Cc_I[i] = 0.0f;
+      c.x = fmaf(dlw, dl[0], c.x);
+      c.y = fmaf(dlw, dl[1], c.y);
+      cI = fmaf(dlw, dl[2], cI);
+      gacc[0] = fmaf(dlw, dl[3], gacc[0]);  // sigma_psf
+      gacc[2] = fmaf(dlw, dl[4], gacc[2]);  // background
+      if (k >= 1) {
+        uint4 w0 = make_uint4(j, g, k, P.tag | (ST_PROP << 4) | 0u);
+        uint4 w1 = make_uint4(j, g, k, P.tag | (ST_PROP << 4) | 1u);
+        philox2(P.key0, P.key1, w0, w1);
+        float e0, e1, e2, e3, e4, e5;
+        box_muller_fast(w0.x, w0.y, e0, e1);
+        box_muller_fast(w0.z, w0.w, e2, e3);
+        box_muller_fast(w1.x, w1.y, e4, e5);
+        gacc[3] = fmaf(c.x, e0, fmaf(c.y, e1, gacc[3]));  // sigma_pos
+        gacc[4] = fmaf(c.z, e2, fmaf(c.w, e3, gacc[4]));  // sigma_v
+        // NCV Jacobian transposed onto the parent: x <- x, vx <- x + vx, ...
+        const long long pi = P.part_off + par;
+        atomicAdd(&a.Cp_pv[pi].x, c.x);
+        atomicAdd(&a.Cp_pv[pi].y, c.y);
+        atomicAdd(&a.Cp_pv[pi].z, c.x + c.z);
+        atomicAdd(&a.Cp_pv[pi].w, c.y + c.w);
+        atomicAdd(&a.Cp_I[pi], cI);
+      } else if (A_enters) {
+        gacc[1] += cI;  // the initial intensity is A
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const float v = warp_sum(gacc[q]);
+      if (lane == 0) s_g[warp][q] = (double)v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+      double v = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += s_g[w][threadIdx.x];
+      if (v != 0.0) atomicAdd(&a.grad[td.x * 5 + threadIdx.x], v);
+    }
+    __syncthreads();
+  }
+}
+
+// dL_{k-1,m} = sum of the origin-m log-weight adjoints of step k; reset D.
+__global__ void k_adjoint_groups(double* __restrict__ dlam, double* __restrict__ D, int G_total) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < G_total; m += gridDim.x * blockDim.x) {
+    dlam[m] = D[m];
+    D[m] = 0.0;
+  }
+}
+
+__global__ void k_grad_out(const double* __restrict__ g, const double* __restrict__ lz, float* __restrict__ out,
+                           double* __restrict__ lz_out, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * 5; i += gridDim.x * blockDim.x) {
+    out[i] = (float)g[i];
+    if (lz_out && i % 5 == 0) lz_out[i / 5] = lz[i / 5];
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+cudaError_t launch_replay(const ReplayArgs& a, int R, int grid, cudaStream_t s) {
+  switch (R) {
+    case 1: k_replay<1><<<grid, 256, 0, s>>>(a); break;
+    case 2: k_replay<2><<<grid, 256, 0, s>>>(a); break;
+    case 3: k_replay<3><<<grid, 256, 0, s>>>(a); break;
+    case 4: k_replay<4><<<grid, 256, 0, s>>>(a); break;
+    case 5: k_replay<5><<<grid, 256, 0, s>>>(a); break;
+    case 6: k_replay<6><<<grid, 256, 0, s>>>(a); break;
+    case 7: k_replay<7><<<grid, 256, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_replay_groups(const ReplayGroupArgs& a, int n_tracks, int max_G, cudaStream_t s) {
+  const int threads = ((max_G + 31) / 32) * 32;
+  k_replay_groups<<<n_tracks, threads < 32 ? 32 : threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(const AdjointArgs& a, int R, int grid, cudaStream_t s) {
+  switch (R) {
+    case 1: k_adjoint<1><<<grid, 256, 0, s>>>(a); break;
+    case 2: k_adjoint<2><<<grid, 256, 0, s>>>(a); break;
+    case 3: k_adjoint<3><<<grid, 256, 0, s>>>(a); break;
+    case 4: k_adjoint<4><<<grid, 256, 0, s>>>(a); break;
+    case 5: k_adjoint<5><<<grid, 256, 0, s>>>(a); break;
+    case 6: k_adjoint<6><<<grid, 256, 0, s>>>(a); break;
+    case 7: k_adjoint<7><<<grid, 256, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_groups(double* dlam, double* D, int G_total, cudaStream_t s) {
+  k_adjoint_groups<<<(G_total + 255) / 256, 256, 0, s>>>(dlam, D, G_total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_out(const double* g, const double* lz, float* out, double* lz_out, int n, cudaStream_t s) {
+  k_grad_out<<<(n * 5 + 255) / 256, 256, 0, s>>>(g, lz, out, lz_out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace pf

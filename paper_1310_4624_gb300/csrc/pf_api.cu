@@ -7,7 +7,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/pfarna.h"
@@ -49,12 +52,34 @@ struct pf_handle {
   uint32_t* parent = nullptr;
   DevState* ds = nullptr;
   CUtensorMap* tmaps = nullptr;  // nullptr: frames read through L1 only
+  // pf_backward buffers (present when every track records its ancestry)
+  bool adjoint = false;
+  int adj_slots = 0, adj_ckpts = 0;
+  float4* rp_pv = nullptr;   // adj_slots x N_total (replay / segment states)
+  float* rp_I = nullptr;
+  float4* ck_pv = nullptr;   // adj_ckpts x N_total (checkpoints)
+  float* ck_I = nullptr;
+  float4* ca_pv[2] = {nullptr, nullptr};  // state adjoints
+  float* ca_I[2] = {nullptr, nullptr};
+  double* lam_hist = nullptr;   // history x G_total
+  double* lbar_hist = nullptr;
+  double* dlam = nullptr;       // G_total
+  double* Dacc = nullptr;       // G_total
+  double* grad = nullptr;       // n_tracks x 5
+  double* logz_rp = nullptr;    // n_tracks
+  float* seed = nullptr;        // n_tracks
+  // pf_graph_step: the captured step for one frame table
+  cudaGraphExec_t graph = nullptr;
+  const void* graph_table = nullptr;
+  int graph_T = 0;
+  int k1_occ = 1, sms = 1;
   // kernel timing (pf_profile_enable / pf_profile_read)
   int prof = 0;
   std::vector<cudaEvent_t> ev[PF_KERNEL_COUNT];  // start, stop, start, stop, ...
   ~pf_handle() {
     for (auto& v : ev)
       for (cudaEvent_t e : v) cudaEventDestroy(e);
+    if (graph) cudaGraphExecDestroy(graph);
   }
 };
 
@@ -94,6 +119,9 @@ QuantCoeffs make_qc() {
 
 struct Layout {
   size_t trk, ts, gs, gd, tiles, pv0, pv1, I0, I1, anc, lw, tp, ypad, hist, ghist, ring, ring_next, parent, ds, tmap, total;
+  size_t rp_pv, rp_I, ck_pv, ck_I, ca_pv0, ca_pv1, ca_I0, ca_I1, lam_hist, lbar_hist, dlam, Dacc, grad, logz, seed;
+  bool adjoint = false;
+  int adj_slots = 0, adj_ckpts = 0;
   long long N_total = 0, ypad_total = 0, parent_total = 0, ghist_total = 0;
   int G_total = 0, n_tiles = 0, hist_total = 0;
   int R = 5;
@@ -150,6 +178,13 @@ std::string validate(const pf_track_config* c, int n, int history) {
   return "";
 }
 
+// Checkpoint spacing of pf_backward for T steps: ceil(sqrt(T)).
+int adjoint_segment(int T) {
+  int C = 1;
+  while (C * C < T) ++C;
+  return C;
+}
+
 Layout plan(const pf_track_config* c, int n, int history) {
   Layout L{};
   L.R = c[0].patch_radius;
@@ -189,6 +224,29 @@ Layout plan(const pf_track_config* c, int n, int history) {
   L.hist = take(sizeof(HistRec) * (size_t)L.hist_total);
   L.ghist = take(sizeof(GroupHist) * (size_t)L.ghist_total);
   L.parent = take(sizeof(uint32_t) * (size_t)(L.parent_total > 0 ? L.parent_total : 1));
+  // pf_backward: every track must record its ancestry
+  L.adjoint = true;
+  for (int t = 0; t < n; ++t) L.adjoint = L.adjoint && c[t].record_ancestors;
+  if (L.adjoint) {
+    const int C = adjoint_segment(history);
+    L.adj_slots = C < 2 ? 2 : C;
+    L.adj_ckpts = (history + C - 1) / C + 1;
+    L.rp_pv = take(sizeof(float4) * (size_t)L.N_total * L.adj_slots);
+    L.rp_I = take(sizeof(float) * (size_t)L.N_total * L.adj_slots);
+    L.ck_pv = take(sizeof(float4) * (size_t)L.N_total * L.adj_ckpts);
+    L.ck_I = take(sizeof(float) * (size_t)L.N_total * L.adj_ckpts);
+    L.ca_pv0 = take(sizeof(float4) * (size_t)L.N_total);
+    L.ca_pv1 = take(sizeof(float4) * (size_t)L.N_total);
+    L.ca_I0 = take(sizeof(float) * (size_t)L.N_total);
+    L.ca_I1 = take(sizeof(float) * (size_t)L.N_total);
+    L.lam_hist = take(sizeof(double) * (size_t)history * L.G_total);
+    L.lbar_hist = take(sizeof(double) * (size_t)history * L.G_total);
+    L.dlam = take(sizeof(double) * (size_t)L.G_total);
+    L.Dacc = take(sizeof(double) * (size_t)L.G_total);
+    L.grad = take(sizeof(double) * 5 * (size_t)n);
+    L.logz = take(sizeof(double) * (size_t)n);
+    L.seed = take(sizeof(float) * (size_t)n);
+  }
   L.total = o;
   return L;
 }
@@ -228,6 +286,27 @@ cudaError_t mark(pf_handle* h, int kernel, cudaStream_t s) {
   if (r != cudaSuccess) return r;
   h->ev[kernel].push_back(e);
   return cudaEventRecord(e, s);
+}
+
+// y = z - b into the padded frames, up to MAX_FRAMES_PER_LAUNCH tracks per
+// launch.  frames: n_tracks device pointers.
+cudaError_t prep_frames(pf_handle* h, const float* const* frames, cudaStream_t s) {
+  for (int t0 = 0; t0 < h->n_tracks; t0 += MAX_FRAMES_PER_LAUNCH) {
+    const int nt = h->n_tracks - t0 < MAX_FRAMES_PER_LAUNCH ? h->n_tracks - t0 : MAX_FRAMES_PER_LAUNCH;
+    FrameArgs a;
+    a.trk = h->trk;
+    a.ypad = h->ypad;
+    a.t0 = t0;
+    a.R = h->R;
+    int maxH = 1;
+    for (int i = 0; i < nt; ++i) {
+      a.frames[i] = frames[t0 + i];
+      if (h->cfg[t0 + i].H > maxH) maxH = h->cfg[t0 + i].H;
+    }
+    cudaError_t e = launch_frame_prep(a, nt, maxH > 4096 ? 4096 : maxH, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 pf_status sync(pf_handle* h) {
@@ -301,6 +380,26 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
   h->ghist = (GroupHist*)(w + L.ghist);
   h->parent = (uint32_t*)(w + L.parent);
   h->tmaps = (CUtensorMap*)(w + L.tmap);
+  if (L.adjoint) {
+    h->adjoint = true;
+    h->adj_slots = L.adj_slots;
+    h->adj_ckpts = L.adj_ckpts;
+    h->rp_pv = (float4*)(w + L.rp_pv);
+    h->rp_I = (float*)(w + L.rp_I);
+    h->ck_pv = (float4*)(w + L.ck_pv);
+    h->ck_I = (float*)(w + L.ck_I);
+    h->ca_pv[0] = (float4*)(w + L.ca_pv0);
+    h->ca_pv[1] = (float4*)(w + L.ca_pv1);
+    h->ca_I[0] = (float*)(w + L.ca_I0);
+    h->ca_I[1] = (float*)(w + L.ca_I1);
+    h->lam_hist = (double*)(w + L.lam_hist);
+    h->lbar_hist = (double*)(w + L.lbar_hist);
+    h->dlam = (double*)(w + L.dlam);
+    h->Dacc = (double*)(w + L.Dacc);
+    h->grad = (double*)(w + L.grad);
+    h->logz_rp = (double*)(w + L.logz);
+    h->seed = (float*)(w + L.seed);
+  }
 
   // host tables
   std::vector<TrackParams> tp(n_tracks);
@@ -403,8 +502,10 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
   // (from the host's point of view) before returning; the vectors may go.
 
   const int sms = num_sms();
+  h->sms = sms;
   int occ = 1;
   if ((e = k1_occupancy(h->R, &occ)) != cudaSuccess) { pf_destroy(h); return cuda_fail(nullptr, e, "occupancy"); }
+  h->k1_occ = occ > 0 ? occ : 1;
   const long long want = (long long)sms * (occ > 0 ? occ : 1);
   h->k1_grid = (int)(h->n_tiles < want ? h->n_tiles : want);
   int n_arna = 0;
@@ -421,6 +522,20 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
   return PF_OK;
 }
 
+// The kernels of one step after frame preparation: propagate + weight,
+// resample, global step.
+static cudaError_t launch_step_kernels(pf_handle* h, cudaStream_t s) {
+  K1Args k1{h->trk, h->tiles, h->n_tiles, h->gs, h->ts, h->ds, h->pv[0], h->pv[1], h->In[0], h->In[1],
+            h->anc, h->parent, h->history, h->lw, h->tile_part, h->ypad, h->tmaps, h->ring_next,
+            h->n_ring_blocks, h->n_tracks};
+  cudaError_t e = launch_propagate(k1, h->R, h->k1_grid + h->n_ring_blocks, s);
+  if (e != cudaSuccess) return e;
+  ResampleArgs ra{h->gd, h->gs, h->tile_part, h->lw, h->anc, nullptr, nullptr, 0, h->qc, h->ds};
+  if ((e = launch_resample(ra, h->G_total, h->rs_cluster, s)) != cudaSuccess) return e;
+  GlobalArgs ga{h->trk, h->ts, h->gs, h->ring, h->ring_next, h->hist, h->ghist, h->history, 1, h->ds};
+  return launch_global(ga, h->n_tracks, h->max_G, s);
+}
+
 pf_status pf_step(pf_handle* h, const float* const* frames, void* stream) {
   if (!h) return fail(nullptr, PF_ERR_ARG, "handle is NULL");
   if (h->failed) return fail(h, PF_ERR_STATE, "handle failed earlier: " + h->err);
@@ -429,23 +544,8 @@ pf_status pf_step(pf_handle* h, const float* const* frames, void* stream) {
     if (!frames[t]) return fail(h, PF_ERR_ARG, "frame pointer of track " + std::to_string(t) + " is NULL");
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
-  // frame preparation, up to MAX_FRAMES_PER_LAUNCH tracks per launch
   if ((e = mark(h, PF_KERNEL_FRAME_PREP, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
-  for (int t0 = 0; t0 < h->n_tracks; t0 += MAX_FRAMES_PER_LAUNCH) {
-    const int nt = h->n_tracks - t0 < MAX_FRAMES_PER_LAUNCH ? h->n_tracks - t0 : MAX_FRAMES_PER_LAUNCH;
-    FrameArgs a;
-    a.trk = h->trk;
-    a.ypad = h->ypad;
-    a.t0 = t0;
-    a.R = h->R;
-    int maxH = 1;
-    for (int i = 0; i < nt; ++i) {
-      a.frames[i] = frames[t0 + i];
-      if (h->cfg[t0 + i].H > maxH) maxH = h->cfg[t0 + i].H;
-    }
-    if ((e = launch_frame_prep(a, nt, maxH > 4096 ? 4096 : maxH, s)) != cudaSuccess)
-      return cuda_fail(h, e, "k_frame_prep");
-  }
+  if ((e = prep_frames(h, frames, s)) != cudaSuccess) return cuda_fail(h, e, "k_frame_prep");
   if ((e = mark(h, PF_KERNEL_FRAME_PREP, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
   K1Args k1{h->trk, h->tiles, h->n_tiles, h->gs, h->ts, h->ds, h->pv[0], h->pv[1], h->In[0], h->In[1],
             h->anc, h->parent, h->history, h->lw, h->tile_part, h->ypad, h->tmaps, h->ring_next,
@@ -464,6 +564,163 @@ pf_status pf_step(pf_handle* h, const float* const* frames, void* stream) {
   if ((e = mark(h, PF_KERNEL_GLOBAL, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
   h->steps_run += 1;
   h->last_stream = s;
+  return PF_OK;
+}
+
+static cudaError_t launch_frames_table(pf_handle* h, const float* const* table, int T_table, cudaStream_t s) {
+  int maxH = 1;
+  for (int t = 0; t < h->n_tracks; ++t) maxH = h->cfg[t].H > maxH ? h->cfg[t].H : maxH;
+  FrameTableArgs fa{h->trk, h->ypad, h->R, table, T_table, h->n_tracks, h->ts, h->ds};
+  return launch_frame_prep_table(fa, maxH > 4096 ? 4096 : maxH, s);
+}
+
+pf_status pf_step_table(pf_handle* h, const float* const* table_dev, int32_t T_table, void* stream) {
+  if (!h) return fail(nullptr, PF_ERR_ARG, "handle is NULL");
+  if (h->failed) return fail(h, PF_ERR_STATE, "handle failed earlier: " + h->err);
+  if (!table_dev || T_table < 1) return fail(h, PF_ERR_ARG, "bad frame table");
+  if (h->n_tracks > 65535) return fail(h, PF_ERR_ARG, "frame tables serve at most 65535 tracks");
+  if (h->steps_run >= T_table) return fail(h, PF_ERR_STATE, "the frame table has no frame for this step");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if ((e = launch_frames_table(h, table_dev, T_table, s)) != cudaSuccess) return cuda_fail(h, e, "k_frame_prep_table");
+  if ((e = launch_step_kernels(h, s)) != cudaSuccess) return cuda_fail(h, e, "step kernels");
+  h->steps_run += 1;
+  h->last_stream = s;
+  return PF_OK;
+}
+
+pf_status pf_graph_step(pf_handle* h, const float* const* table_dev, int32_t T_table, void* stream) {
+  if (!h) return fail(nullptr, PF_ERR_ARG, "handle is NULL");
+  if (h->failed) return fail(h, PF_ERR_STATE, "handle failed earlier: " + h->err);
+  if (!table_dev || T_table < 1) return fail(h, PF_ERR_ARG, "bad frame table");
+  if (h->n_tracks > 65535) return fail(h, PF_ERR_ARG, "frame tables serve at most 65535 tracks");
+  if (h->steps_run >= T_table) return fail(h, PF_ERR_STATE, "the frame table has no frame for this step");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (!h->graph || h->graph_table != (const void*)table_dev || h->graph_T != T_table) {
+    if (h->graph) {
+      cudaGraphExecDestroy(h->graph);
+      h->graph = nullptr;
+    }
+    // capture the parameter-free step once; its kernels read the step index
+    // and frame pointers on the device
+    cudaStream_t cs;
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(h, e, "capture stream");
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e1 = launch_frames_table(h, table_dev, T_table, cs);
+      cudaError_t e2 = e1 == cudaSuccess ? launch_step_kernels(h, cs) : e1;
+      e = cudaStreamEndCapture(cs, &g);
+      if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return cuda_fail(h, e, "capturing the step graph");
+    h->graph_table = table_dev;
+    h->graph_T = T_table;
+  }
+  if ((e = cudaGraphLaunch(h->graph, s)) != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+  h->steps_run += 1;
+  h->last_stream = s;
+  return PF_OK;
+}
+
+// Autotuner results by problem shape (tracks, particles, groups, largest
+// group, SMs): propagate grid and resampler cluster size.
+static std::mutex g_tune_mutex;
+static std::map<std::tuple<int, long long, int, int, int>, std::pair<int, int>> g_tune_cache;
+
+pf_status pf_autotune(pf_handle* h, const float* const* frames, int32_t* k1_grid_out, int32_t* cluster_out,
+                      void* stream) {
+  if (!h) return fail(nullptr, PF_ERR_ARG, "handle is NULL");
+  if (h->failed) return fail(h, PF_ERR_STATE, "handle failed earlier: " + h->err);
+  if (!frames) return fail(h, PF_ERR_ARG, "frames is NULL");
+  for (int t = 0; t < h->n_tracks; ++t)
+    if (!frames[t]) return fail(h, PF_ERR_ARG, "NULL frame pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  int maxNp = 1;
+  for (int t = 0; t < h->n_tracks; ++t) maxNp = h->cfg[t].Np > maxNp ? h->cfg[t].Np : maxNp;
+  const auto key = std::make_tuple(h->n_tracks, h->N_total, h->G_total, maxNp, h->sms);
+  cudaError_t e;
+  if ((e = prep_frames(h, frames, s)) != cudaSuccess) return cuda_fail(h, e, "k_frame_prep");
+  bool cached = false;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      h->k1_grid = it->second.first;
+      h->rs_cluster = it->second.second;
+      cached = true;
+    }
+  }
+  if (!cached) {
+    // The propagate and resample kernels of a step are idempotent until the
+    // global step advances it, so candidates are timed on live data.
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto time_it = [&](auto&& launch, float& ms) -> cudaError_t {
+      cudaError_t r = cudaEventRecord(e0, s);
+      if (r == cudaSuccess) r = launch();
+      if (r == cudaSuccess) r = cudaEventRecord(e1, s);
+      if (r == cudaSuccess) r = cudaEventSynchronize(e1);
+      if (r == cudaSuccess) r = cudaEventElapsedTime(&ms, e0, e1);
+      return r;
+    };
+    K1Args k1{h->trk, h->tiles, h->n_tiles, h->gs, h->ts, h->ds, h->pv[0], h->pv[1], h->In[0], h->In[1],
+              h->anc, h->parent, h->history, h->lw, h->tile_part, h->ypad, h->tmaps, h->ring_next,
+              h->n_ring_blocks, h->n_tracks};
+    int best_grid = h->k1_grid;
+    float best = 1e30f;
+    for (int b = 1; b <= h->k1_occ; ++b) {
+      const long long cand = (long long)h->sms * b;
+      const int grid = (int)(cand < h->n_tiles ? cand : h->n_tiles);
+      float ms = 0.0f;
+      for (int rep = 0; rep < 2; ++rep)  // the first run also warms caches
+        if ((e = time_it([&] { return launch_propagate(k1, h->R, grid + h->n_ring_blocks, s); }, ms)) != cudaSuccess)
+          break;
+      if (e != cudaSuccess) break;
+      if (ms < best) {
+        best = ms;
+        best_grid = grid;
+      }
+      if (grid == h->n_tiles) break;
+    }
+    int best_c = h->rs_cluster;
+    best = 1e30f;
+    if (e == cudaSuccess)
+      for (int c = 1; c <= 8; c *= 2) {
+        ResampleArgs ra{h->gd, h->gs, h->tile_part, h->lw, h->anc, nullptr, nullptr, 0, h->qc, h->ds};
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2; ++rep)
+          if ((e = time_it([&] { return launch_resample(ra, h->G_total, c, s); }, ms)) != cudaSuccess) break;
+        if (e != cudaSuccess) break;
+        if (ms < best) {
+          best = ms;
+          best_c = c;
+        }
+      }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
+    h->k1_grid = best_grid;
+    h->rs_cluster = best_c;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = {best_grid, best_c};
+  }
+  // complete the step with the chosen shapes
+  if ((e = launch_step_kernels(h, s)) != cudaSuccess) return cuda_fail(h, e, "step kernels");
+  h->steps_run += 1;
+  h->last_stream = s;
+  if (h->graph) {  // a captured step holds the old shapes
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  if (k1_grid_out) *k1_grid_out = h->k1_grid;
+  if (cluster_out) *cluster_out = h->rs_cluster;
   return PF_OK;
 }
 
@@ -603,6 +860,152 @@ pf_status pf_resample(const float* logw, const uint32_t* u, int32_t G, int32_t N
   ResampleArgs ra{gd, gs, nullptr, logw, anc, (unsigned long long*)q, u, 1, make_qc(), ds};
   if ((e = launch_resample(ra, G, resample_cluster(Np, true), s)) != cudaSuccess)
     return cuda_fail(nullptr, e, "k_resample");
+  return PF_OK;
+}
+
+pf_status pf_set_theta(pf_handle* h, int32_t track, const float* theta) {
+  if (!h) return fail(nullptr, PF_ERR_ARG, "handle is NULL");
+  if (track < 0 || track >= h->n_tracks) return fail(h, PF_ERR_ARG, "track out of range");
+  if (!theta) return fail(h, PF_ERR_ARG, "theta is NULL");
+  const float spsf = theta[PF_THETA_SIGMA_PSF], A = theta[PF_THETA_AMPLITUDE], b = theta[PF_THETA_BACKGROUND];
+  const float spos = theta[PF_THETA_SIGMA_POS], sv = theta[PF_THETA_SIGMA_V];
+  if (!(std::isfinite(spsf) && spsf > 0.0f) || !std::isfinite(A) || !std::isfinite(b) || !finite_nonneg(spos) ||
+      !finite_nonneg(sv))
+    return fail(h, PF_ERR_ARG, "theta out of range (sigma_psf > 0, sigma_pos, sigma_v >= 0, all finite)");
+  pf_track_config& c = h->cfg[track];
+  c.sigma_psf = spsf;
+  c.init_state[4] = A;
+  c.background = b;
+  c.sigma_pos = spos;
+  c.sigma_v = sv;
+  TrackParams& P = h->tp[track];
+  P.spsf = spsf;
+  P.c_psf = (float)(1.4426950408889634 / (2.0 * (double)spsf * (double)spsf));
+  P.kappa = (float)std::exp2(-2.0 * (double)P.c_psf);
+  P.init_state[4] = A;
+  P.bg = b;
+  P.spos = spos;
+  P.sv = sv;
+  cudaError_t e = cudaMemcpy(h->trk + track, &P, sizeof(TrackParams), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(h, e, "uploading track parameters");
+  return PF_OK;
+}
+
+pf_status pf_reset(pf_handle* h, void* stream) {
+  if (!h) return fail(nullptr, PF_ERR_ARG, "handle is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(h->ds, 0, sizeof(DevState), s)) ||
+      (e = cudaMemsetAsync(h->ts, 0, sizeof(TrackState) * h->n_tracks, s)) ||
+      (e = cudaMemsetAsync(h->gs, 0, sizeof(GroupState) * h->G_total, s)))
+    return cuda_fail(h, e, "pf_reset");
+  InitArgs ia{h->trk, h->tiles, h->n_tiles, h->N_total, nullptr, h->pv[1], h->In[1]};
+  for (int t = 0; t < h->n_tracks; ++t)
+    if (h->cfg[t].init_kind == PF_INIT_USER) return fail(h, PF_ERR_STATE, "pf_reset cannot redraw a user population");
+  if ((e = launch_init(ia, h->k1_grid, s)) != cudaSuccess) return cuda_fail(h, e, "k_init");
+  GlobalArgs ga{h->trk, h->ts, h->gs, h->ring, h->ring_next, h->hist, h->ghist, h->history, 0, h->ds};
+  if ((e = launch_global(ga, h->n_tracks, h->max_G, s)) != cudaSuccess) return cuda_fail(h, e, "k_global");
+  h->steps_run = 0;
+  h->failed = 0;
+  h->last_stream = s;
+  return PF_OK;
+}
+
+pf_status pf_backward(pf_handle* h, const float* const* frames_host, int32_t T, const float* dlogZ_host,
+                      float* grad_dev, double* logZ_dev, void* stream) {
+  if (!h) return fail(nullptr, PF_ERR_ARG, "handle is NULL");
+  if (!h->adjoint) return fail(h, PF_ERR_STATE, "pf_backward needs record_ancestors on every track");
+  if (!frames_host || !dlogZ_host || !grad_dev) return fail(h, PF_ERR_ARG, "NULL argument");
+  if (T < 1 || T != h->steps_run) return fail(h, PF_ERR_STATE, "T must equal the number of steps run");
+  if (T > h->history) return fail(h, PF_ERR_STATE, "T exceeds the kept history");
+  for (int i = 0; i < T * h->n_tracks; ++i)
+    if (!frames_host[i]) return fail(h, PF_ERR_ARG, "NULL frame pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  const long long N = h->N_total;
+  const int C = adjoint_segment(T);
+  const int nseg = (T + C - 1) / C;
+  const int G = h->G_total;
+  auto slot_pv = [&](int i) { return h->rp_pv + (long long)i * N; };
+  auto slot_I = [&](int i) { return h->rp_I + (long long)i * N; };
+  auto ck_pv = [&](int i) { return h->ck_pv + (long long)i * N; };
+  auto ck_I = [&](int i) { return h->ck_I + (long long)i * N; };
+  if ((e = cudaMemsetAsync(h->grad, 0, sizeof(double) * 5 * h->n_tracks, s)) ||
+      (e = cudaMemsetAsync(h->logz_rp, 0, sizeof(double) * h->n_tracks, s)) ||
+      (e = cudaMemsetAsync(h->Dacc, 0, sizeof(double) * G, s)) ||
+      (e = cudaMemsetAsync(h->ca_pv[0], 0, sizeof(float4) * N, s)) ||
+      (e = cudaMemsetAsync(h->ca_pv[1], 0, sizeof(float4) * N, s)) ||
+      (e = cudaMemsetAsync(h->ca_I[0], 0, sizeof(float) * N, s)) ||
+      (e = cudaMemsetAsync(h->ca_I[1], 0, sizeof(float) * N, s)) ||
+      (e = cudaMemcpyAsync(h->seed, dlogZ_host, sizeof(float) * h->n_tracks, cudaMemcpyHostToDevice, s)))
+    return cuda_fail(h, e, "pf_backward setup");
+  const int grid = h->k1_grid;
+  // forward replay with the recorded ancestry; checkpoints every C steps
+  InitArgs ia{h->trk, h->tiles, h->n_tiles, N, nullptr, slot_pv(0), slot_I(0)};
+  if ((e = launch_init(ia, grid, s)) != cudaSuccess) return cuda_fail(h, e, "k_init");
+  for (int k = 0; k < T; ++k) {
+    if ((e = prep_frames(h, frames_host + (long long)k * h->n_tracks, s)) != cudaSuccess)
+      return cuda_fail(h, e, "k_frame_prep");
+    ReplayArgs ra{};
+    ra.trk = h->trk; ra.tiles = h->tiles; ra.n_tiles = h->n_tiles; ra.parent = h->parent; ra.history = h->history;
+    ra.k = k;
+    ra.pv_in = k >= 1 ? slot_pv((k - 1) & 1) : nullptr;
+    ra.I_in = k >= 1 ? slot_I((k - 1) & 1) : nullptr;
+    ra.pv_out = slot_pv(k & 1);
+    ra.I_out = slot_I(k & 1);
+    ra.ck_pv = (k % C == 0) ? ck_pv(k / C) : nullptr;
+    ra.ck_I = (k % C == 0) ? ck_I(k / C) : nullptr;
+    ra.weights = 1;
+    ra.ypad = h->ypad;
+    ra.lbar_prev = k >= 1 ? h->lbar_hist + (long long)(k - 1) * G : nullptr;
+    ra.tile_part = h->tile_part;
+    if ((e = launch_replay(ra, h->R, grid, s)) != cudaSuccess) return cuda_fail(h, e, "k_replay");
+    ReplayGroupArgs rg{h->trk, h->gd, h->tile_part, k, G, h->lam_hist, h->lbar_hist, h->logz_rp, h->dlam, h->seed,
+                       k == T - 1 ? 1 : 0};
+    if ((e = launch_replay_groups(rg, h->n_tracks, h->max_G, s)) != cudaSuccess)
+      return cuda_fail(h, e, "k_replay_groups");
+  }
+  // reverse sweep, segment by segment, states recomputed from checkpoints
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int k0 = sg * C, k1 = (k0 + C < T) ? k0 + C : T;
+    for (int k = k0 + 1; k < k1; ++k) {
+      ReplayArgs ra{};
+      ra.trk = h->trk; ra.tiles = h->tiles; ra.n_tiles = h->n_tiles; ra.parent = h->parent;
+      ra.history = h->history; ra.k = k;
+      ra.pv_in = (k - 1 == k0) ? ck_pv(sg) : slot_pv(k - 1 - k0);
+      ra.I_in = (k - 1 == k0) ? ck_I(sg) : slot_I(k - 1 - k0);
+      ra.pv_out = slot_pv(k - k0);
+      ra.I_out = slot_I(k - k0);
+      ra.weights = 0;
+      ra.ypad = h->ypad;
+      ra.tile_part = h->tile_part;
+      if ((e = launch_replay(ra, h->R, grid, s)) != cudaSuccess) return cuda_fail(h, e, "k_replay");
+    }
+    for (int k = k1 - 1; k >= k0; --k) {
+      if ((e = prep_frames(h, frames_host + (long long)k * h->n_tracks, s)) != cudaSuccess)
+        return cuda_fail(h, e, "k_frame_prep");
+      AdjointArgs aa{};
+      aa.trk = h->trk; aa.tiles = h->tiles; aa.n_tiles = h->n_tiles; aa.parent = h->parent;
+      aa.history = h->history; aa.k = k;
+      aa.pv = (k == k0) ? ck_pv(sg) : slot_pv(k - k0);
+      aa.In = (k == k0) ? ck_I(sg) : slot_I(k - k0);
+      aa.ypad = h->ypad;
+      aa.lbar_prev = k >= 1 ? h->lbar_hist + (long long)(k - 1) * G : nullptr;
+      aa.lam_k = h->lam_hist + (long long)k * G;
+      aa.dlam_k = h->dlam;
+      aa.D = h->Dacc;
+      aa.Cc_pv = h->ca_pv[k & 1];
+      aa.Cc_I = h->ca_I[k & 1];
+      aa.Cp_pv = h->ca_pv[(k + 1) & 1];
+      aa.Cp_I = h->ca_I[(k + 1) & 1];
+      aa.grad = h->grad;
+      if ((e = launch_adjoint(aa, h->R, grid, s)) != cudaSuccess) return cuda_fail(h, e, "k_adjoint");
+      if ((e = launch_adjoint_groups(h->dlam, h->Dacc, G, s)) != cudaSuccess) return cuda_fail(h, e, "k_adjoint_groups");
+    }
+  }
+  if ((e = launch_grad_out(h->grad, h->logz_rp, grad_dev, logZ_dev, h->n_tracks, s)) != cudaSuccess)
+    return cuda_fail(h, e, "gradient output");
+  h->last_stream = s;
   return PF_OK;
 }
 

@@ -30,89 +30,11 @@
 
 #include "pf_device.cuh"
 #include "pf_launch.h"
+#include "pf_math.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace pf {
-
-__device__ __forceinline__ float ex2(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-__device__ __forceinline__ float warp_max(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ double warp_max_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Block-wide reductions; every thread gets the result.  `sh` holds one slot
-// per warp and is free again on return.
-template <int NT>
-__device__ __forceinline__ float block_max(float v, float* sh) {
-  v = warp_max(v);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  float r = sh[0];
-#pragma unroll
-  for (int w = 1; w < NT / 32; ++w) r = fmaxf(r, sh[w]);
-  __syncthreads();
-  return r;
-}
-template <int NT>
-__device__ __forceinline__ double block_sum_d(double v, double* sh) {
-  v = warp_sum_d(v);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double r = 0.0;
-#pragma unroll
-  for (int w = 0; w < NT / 32; ++w) r += sh[w];
-  __syncthreads();
-  return r;
-}
-template <int NT>
-__device__ __forceinline__ double block_max_d(double v, double* sh) {
-  v = warp_max_d(v);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double r = sh[0];
-#pragma unroll
-  for (int w = 1; w < NT / 32; ++w) r = fmax(r, sh[w]);
-  __syncthreads();
-  return r;
-}
-template <int NT>
-__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v, unsigned long long* sh) {
-  v = warp_sum_u64(v);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  unsigned long long r = 0;
-#pragma unroll
-  for (int w = 0; w < NT / 32; ++w) r += sh[w];
-  __syncthreads();
-  return r;
-}
 
 // ===================================================================== K0
 // Initial population (Sec. V tracking / information-sharing modes), drawn
@@ -174,102 +96,28 @@ __global__ void k_frame_prep(FrameArgs a) {
   }
 }
 
+// Same, frame pointers from a device table indexed by the device-side step
+// index: table[k * n_tracks + t] (k >= T_table is reported, not read).
+__global__ void k_frame_prep_table(FrameTableArgs a) {
+  const int t = blockIdx.y;
+  const int k = a.ts[0].k;
+  if (k >= a.T_table) {
+    if (t == 0 && blockIdx.x == 0 && threadIdx.x == 0) set_error(a.ds, ERR_INDEX, 5u, (uint32_t)k, 0u);
+    return;
+  }
+  const TrackParams& P = a.trk[t];
+  const float* __restrict__ z = a.table[(long long)k * a.n_tracks + t];
+  float* __restrict__ yp = a.ypad + P.ypad_off;
+  const int pad = 2 * a.R + 1;
+  const float bg = P.bg;
+  for (int v = blockIdx.x; v < P.H; v += gridDim.x) {
+    const float* __restrict__ zr = z + (long long)v * P.W;
+    float* __restrict__ yr = yp + (long long)(v + pad) * P.pitch + pad;
+    for (int u = threadIdx.x; u < P.W; u += blockDim.x) yr[u] = __fsub_rn(__ldg(zr + u), bg);
+  }
+}
+
 // ===================================================================== K1
-// Gaussian profile values 2^(-c (u - x)^2) on the D = 2R+1 patch columns
-// u = cf - R .. cf + R, by a ratio recurrence from the centre column
-// outwards: g(u+1) = g(u) r(u), r(u+1) = r(u) 2^(-2c).  Three MUFU ex2 per
-// axis instead of D; relative error <= 2R FP32 roundings.
-template <int R>
-__device__ __forceinline__ void gauss_row(float cf, float x, float c, float kappa, float (&g)[2 * R + 1]) {
-  const float d = cf - x;                        // centre offset, |d| <= 1/2
-  g[R] = ex2(-c * d * d);
-  float up = ex2(-c * fmaf(2.0f, d, 1.0f));      // g(R+1) / g(R)
-  float dn = ex2(c * fmaf(2.0f, d, -1.0f));      // g(R-1) / g(R)
-#pragma unroll
-  for (int a = 1; a <= R; ++a) {
-    g[R + a] = g[R + a - 1] * up;
-    g[R - a] = g[R - a + 1] * dn;
-    up *= kappa;
-    dn *= kappa;
-  }
-}
-
-// One patch row: acc + sum_a (y_a - gxI[a] gy)^2, rows of shared memory
-// (compile-time pitch) or of global memory read through L1.
-template <int R>
-__device__ __forceinline__ float row_ss_smem(const float* __restrict__ rp, const float (&gxI)[2 * R + 1], float gy,
-                                             float acc) {
-#pragma unroll
-  for (int a = 0; a < 2 * R + 1; ++a) {
-    const float r = fmaf(-gxI[a], gy, rp[a]);
-    acc = fmaf(r, r, acc);
-  }
-  return acc;
-}
-template <int R>
-__device__ __forceinline__ float row_ss_global(const float* __restrict__ rp, const float (&gxI)[2 * R + 1], float gy,
-                                               float acc) {
-#pragma unroll
-  for (int a = 0; a < 2 * R + 1; ++a) {
-    const float r = fmaf(-gxI[a], gy, __ldg(rp + a));
-    acc = fmaf(r, r, acc);
-  }
-  return acc;
-}
-
-// Sum over the patch of (y - I gx gy)^2; `row(b)` is the address of patch
-// row b (0 .. 2R).  Rows are visited centre-out so that gy follows the same
-// ratio recurrence as gauss_row with four live registers; dy = cyf - y.
-template <int R, bool SMEM>
-__device__ __forceinline__ float patch_ss(const float* __restrict__ base, int pitch, const float (&gxI)[2 * R + 1],
-                                          float dy, float c, float kappa) {
-  auto row = [&](int b, float gy, float acc) {
-    if constexpr (SMEM)
-      return row_ss_smem<R>(base + b * ROI_W, gxI, gy, acc);
-    else
-      return row_ss_global<R>(base + (long long)b * pitch, gxI, gy, acc);
-  };
-  const float g = ex2(-c * dy * dy);
-  float up = ex2(-c * fmaf(2.0f, dy, 1.0f));
-  float dn = ex2(c * fmaf(2.0f, dy, -1.0f));
-  float acc = row(R, g, 0.0f);
-  float gu = g, gd = g;
-#pragma unroll
-  for (int a = 1; a <= R; ++a) {
-    gu *= up;
-    gd *= dn;
-    up *= kappa;
-    dn *= kappa;
-    acc = row(R + a, gu, acc);
-    acc = row(R - a, gd, acc);
-  }
-  return acc;
-}
-
-// Natural log of a uniform u = ((w >> 9) + 1/2) 2^-23: MUFU log2 where its
-// absolute error (2^-22 on [1/2, 2]) is small against |ln u|, and the series
-// -(t + t^2/2 + t^3/3), t = 1 - u, for the top 2^-10 of the interval.
-__device__ __forceinline__ float log_u01(float u) {
-  const float t = 1.0f - u;  // exact
-  const float series = -t * fmaf(t, fmaf(t, 0.333333343f, 0.5f), 1.0f);
-  return t < 9.765625e-4f ? series : __log2f(u) * 0.693147182f;
-}
-
-__device__ __forceinline__ float sqrt_approx(float x) {
-  float y;
-  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-// Box-Muller pair (see box_muller in pf_device.cuh for the definition).
-__device__ __forceinline__ void box_muller_fast(uint32_t wa, uint32_t wb, float& e0, float& e1) {
-  const float rho = sqrt_approx(-2.0f * log_u01(u01(wa)));
-  float s, c;
-  __sincosf(fmaf(u01(wb), 6.28318530717958647f, -3.14159265358979323f), &s, &c);
-  e0 = -rho * c;
-  e1 = -rho * s;
-}
-
 // Slot i = (group g, slot j) of step k takes the particle of slot src of the
 // exchanged population (Sec. III-A/C): group g's send set is the systematic
 // slot subsample s_{g,t} = floor((t Np + o_g) / N_ex); slot s_{r,t} of the
@@ -300,53 +148,6 @@ __device__ __forceinline__ int exchange_source(const GroupState* __restrict__ gs
   }
   return g;
 }
-
-// Two Philox4x32-10 blocks of the same key in lockstep (shared key schedule).
-__device__ __forceinline__ void philox2(uint32_t k0, uint32_t k1, uint4& c, uint4& d) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x, p1 = (unsigned long long)0xCD9E8D57u * c.z;
-    const unsigned long long q0 = (unsigned long long)0xD2511F53u * d.x, q1 = (unsigned long long)0xCD9E8D57u * d.z;
-    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
-    d = make_uint4((uint32_t)(q1 >> 32) ^ d.y ^ k0, (uint32_t)q1, (uint32_t)(q0 >> 32) ^ d.w ^ k1, (uint32_t)q0);
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
-  }
-}
-
-// Sum of 8 values over a warp by recursive halving (reduce-scatter): after
-// it, lane l holds the total of value ((l >> 2) & 7) (bit-reversed order
-// handled by the caller through `slot`).
-__device__ __forceinline__ float warp_reduce8(float (&v)[8], int lane, int& slot) {
-  float w4[4], w2[2];
-  const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float send = b16 ? v[i] : v[i + 4];
-    const float keep = b16 ? v[i + 4] : v[i];
-    w4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-  }
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const float send = b8 ? w4[i] : w4[i + 2];
-    const float keep = b8 ? w4[i + 2] : w4[i];
-    w2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-  }
-  const float send = b4 ? w2[0] : w2[1];
-  const float keep = b4 ? w2[1] : w2[0];
-  float x = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-  x += __shfl_xor_sync(0xffffffffu, x, 2);
-  x += __shfl_xor_sync(0xffffffffu, x, 1);
-  slot = (b16 ? 4 : 0) + (b8 ? 2 : 0) + (b4 ? 1 : 0);
-  return x;
-}
-
-// Order-preserving map of a float to an int (for warp max through redux).
-__device__ __forceinline__ int float_key(float f) {
-  const int i = __float_as_int(f);
-  return i ^ ((i >> 31) & 0x7fffffff);
-}
-__device__ __forceinline__ float key_float(int i) { return __int_as_float(i ^ ((i >> 31) & 0x7fffffff)); }
 
 // Fisher-Yates ring order of step k (Sec. IV-B, Alg. 3 step 1) for one
 // track, by one warp: the bounded draws r_j in [0, j] in parallel, the
@@ -1061,6 +862,11 @@ __global__ void k_export_states(const float4* __restrict__ pv, const float* __re
 // ============================================================== launchers
 cudaError_t launch_init(const InitArgs& a, int grid, cudaStream_t s) {
   k_init<<<grid, K1_THREADS, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_frame_prep_table(const FrameTableArgs& a, int blocks_x, cudaStream_t s) {
+  k_frame_prep_table<<<dim3(blocks_x, a.n_tracks), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -26,6 +26,17 @@ struct FrameArgs {
   const float* frames[MAX_FRAMES_PER_LAUNCH];
 };
 
+struct FrameTableArgs {
+  const TrackParams* trk;
+  float* ypad;
+  int R;
+  const float* const* table;  // device: T_table x n_tracks frame pointers
+  int T_table;
+  int n_tracks;
+  const TrackState* ts;
+  DevState* ds;
+};
+
 struct K1Args {
   const TrackParams* trk;
   const int4* tiles;
@@ -75,8 +86,70 @@ struct GlobalArgs {
   DevState* ds;
 };
 
+// pf_backward (pf_adjoint.cu)
+struct ReplayArgs {
+  const TrackParams* trk;
+  const int4* tiles;
+  int n_tiles;
+  const uint32_t* parent;  // recorded ancestry
+  int history;
+  int k;
+  const float4* pv_in;     // X_{k-1} (k >= 1)
+  const float* I_in;
+  float4* pv_out;          // X_k (read only at k = 0)
+  float* I_out;
+  float4* ck_pv;           // optional copy of X_k (checkpoint), or nullptr
+  float* ck_I;
+  int weights;             // 1: log-weights and per-tile (max, sum exp)
+  const float* ypad;
+  const double* lbar_prev; // lbar_{k-1} per global group (k >= 1)
+  float* tile_part;
+};
+
+struct ReplayGroupArgs {
+  const TrackParams* trk;
+  const GroupDesc* gd;
+  const float* tile_part;
+  int k;
+  int G_total;
+  double* lam_hist;        // [k][global group]
+  double* lbar_hist;
+  double* logZ;            // per track, accumulated
+  double* dlam;            // per global group: the reverse sweep's seed at the last step
+  const float* seed;       // per track
+  int last;
+};
+
+struct AdjointArgs {
+  const TrackParams* trk;
+  const int4* tiles;
+  int n_tiles;
+  const uint32_t* parent;
+  int history;
+  int k;
+  const float4* pv;        // X_k
+  const float* In;
+  const float* ypad;
+  const double* lbar_prev; // lbar_{k-1} (k >= 1)
+  const double* lam_k;     // L_k
+  const double* dlam_k;    // dL_k
+  double* D;               // dL_{k-1} accumulator per global group
+  float4* Cc_pv;           // state adjoint of X_k (read and cleared)
+  float* Cc_I;
+  float4* Cp_pv;           // state adjoint of X_{k-1} (accumulated)
+  float* Cp_I;
+  double* grad;            // per track x 5
+};
+
+cudaError_t launch_replay(const ReplayArgs& a, int R, int grid, cudaStream_t s);
+cudaError_t launch_replay_groups(const ReplayGroupArgs& a, int n_tracks, int max_G, cudaStream_t s);
+cudaError_t launch_adjoint(const AdjointArgs& a, int R, int grid, cudaStream_t s);
+cudaError_t launch_adjoint_groups(double* dlam, double* D, int G_total, cudaStream_t s);
+cudaError_t launch_grad_out(const double* g, const double* lz, float* out, double* lz_out, int n, cudaStream_t s);
+
 cudaError_t launch_init(const InitArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_frame_prep(const FrameArgs& a, int nt, int blocks_x, cudaStream_t s);
+cudaError_t launch_frame_prep_table(const FrameTableArgs& a, int blocks_x, cudaStream_t s);
 cudaError_t launch_propagate(const K1Args& a, int R, int grid, cudaStream_t s);
 cudaError_t launch_resample(const ResampleArgs& a, int n_groups, int cluster, cudaStream_t s);
 cudaError_t launch_global(const GlobalArgs& a, int n_tracks, int max_G, cudaStream_t s);

@@ -91,6 +91,27 @@ class ParticleFilter:
         B.pf_step(self.handle, ptrs, C.c_void_p(self.stream.cuda_stream))
         self.steps += 1
 
+    def frame_table(self, frames_per_track) -> torch.Tensor:
+        """Device table (T x n_tracks int64 pointers) of per-track frame
+        tensors (each (T, H, W) float32 CUDA, contiguous)."""
+        T = frames_per_track[0].shape[0]
+        ptrs = [[f[k].data_ptr() for f in frames_per_track] for k in range(T)]
+        return torch.tensor(ptrs, dtype=torch.int64, device=self.device).reshape(T, self.n_tracks)
+
+    def step_table(self, table: torch.Tensor, graph: bool = False) -> None:
+        """One step with frames from a device table (see frame_table)."""
+        fn = B.pf_graph_step if graph else B.pf_step_table
+        fn(self.handle, C.c_void_p(table.data_ptr()), table.shape[0], C.c_void_p(self.stream.cuda_stream))
+        self.steps += 1
+
+    def autotune(self, frames):
+        """One step that also picks the launch shapes; returns (grid, cluster)."""
+        if isinstance(frames, torch.Tensor) and frames.dim() == 2:
+            frames = [frames]
+        r = B.pf_autotune(self.handle, [f.data_ptr() for f in frames], C.c_void_p(self.stream.cuda_stream))
+        self.steps += 1
+        return r
+
     def profile(self, enable: bool = True) -> None:
         """Record CUDA events around each kernel of the following steps."""
         B.pf_profile_enable(self.handle, enable)
@@ -124,6 +145,36 @@ class ParticleFilter:
         return [dict(step=s.step, n_ex=s.n_ex, pe_eff=s.pe_eff, log_c=s.log_c, log_Z=s.log_Z,
                      xhat=np.array(s.xhat[:]), degenerate=s.degenerate_groups) for s in out]
 
+    def set_theta(self, theta, track: int = 0) -> None:
+        """theta = (sigma_psf, A, background, sigma_pos, sigma_v) of one track."""
+        B.pf_set_theta(self.handle, track, [float(v) for v in theta])
+
+    def reset(self) -> None:
+        """Fresh initial population with the current parameters (step 0 next)."""
+        B.pf_reset(self.handle, C.c_void_p(self.stream.cuda_stream))
+        self.steps = 0
+
+    def backward(self, frames, dlogZ=None):
+        """d log Z / d theta over the steps run so far, ancestry fixed.
+
+        frames: per step a frame tensor (one track) or a list of n_tracks
+        frame tensors, the frames of the forward run.  Returns (grad
+        (n_tracks, 5) float32 tensor, log Z of the replay (n_tracks,) float64
+        tensor)."""
+        T = len(frames)
+        ptrs = []
+        for f in frames:
+            fs = [f] if isinstance(f, torch.Tensor) else list(f)
+            assert len(fs) == self.n_tracks
+            ptrs.extend(x.data_ptr() for x in fs)
+        seeds = [1.0] * self.n_tracks if dlogZ is None else [float(v) for v in dlogZ]
+        grad = torch.empty((self.n_tracks, 5), dtype=torch.float32, device=self.device)
+        logz = torch.empty(self.n_tracks, dtype=torch.float64, device=self.device)
+        B.pf_backward(self.handle, ptrs, T, seeds, C.c_void_p(grad.data_ptr()), C.c_void_p(logz.data_ptr()),
+                      C.c_void_p(self.stream.cuda_stream))
+        self.stream.synchronize()
+        return grad, logz
+
     def particles(self, track: int = 0, parents: bool = False) -> dict:
         """Latest step's X_k (5, N), ancestors, log-weights (and parents)."""
         n = self.N[track]
@@ -154,3 +205,31 @@ def resample(logw: torch.Tensor, u: torch.Tensor, G: int, Np: int, want_q: bool 
     B.pf_resample(_ptr(logw), _ptr(u), G, Np, _ptr(anc), _ptr(q), C.c_void_p(wp), nb, C.c_void_p(s.cuda_stream))
     s.synchronize()
     return (anc, q) if want_q else anc
+
+
+class LogLikelihood(torch.autograd.Function):
+    """log Z(theta) of a single-track filter run over `frames`, differentiable
+    in theta = (sigma_psf, A, background, sigma_pos, sigma_v) with the
+    resampling ancestry of the forward run held fixed (pf_backward).
+
+    forward(theta (5,) tensor, pf, frames (T, H, W) CUDA tensor) sets theta,
+    restarts the filter, runs the T steps and returns log Z (a 0-d float64
+    tensor on the filter's device)."""
+
+    @staticmethod
+    def forward(ctx, theta, pf, frames):
+        pf.set_theta(theta.detach().cpu().tolist())
+        pf.reset()
+        for k in range(frames.shape[0]):
+            pf.step(frames[k])
+        _, logz, _ = pf.estimate()
+        ctx.pf = pf
+        ctx.frames = frames
+        ctx.theta_dtype = theta.dtype
+        ctx.theta_device = theta.device
+        return torch.tensor(float(logz[0]), dtype=torch.float64, device=frames.device)
+
+    @staticmethod
+    def backward(ctx, g):
+        grad, _ = ctx.pf.backward([ctx.frames[k] for k in range(ctx.frames.shape[0])])
+        return (g * grad[0].to(torch.float64).to(g.device)).to(ctx.theta_dtype).to(ctx.theta_device), None, None

@@ -163,3 +163,26 @@ def init_arrays(wl: Workload, truth0: np.ndarray):
     lo = np.array([0.0, 0.0, -wl.share_vmax, -wl.share_vmax, wl.share_I[0]])
     hi = np.array([wl.W - 1.0, wl.H - 1.0, wl.share_vmax, wl.share_vmax, wl.share_I[1]])
     return wl.init, x0, lo, hi, wl.share_radius
+
+
+def render_batched_torch(wls: List[Workload], device, seed: int = 0):
+    """Frames (n_tracks, T, H, W) float32 on `device` and truths (n_tracks, T,
+    5) for equally sized tracks, drawn with torch's seeded generator on the
+    device (large batched workloads; the same spot model as ``render``)."""
+    import torch
+    n, T, H, W = len(wls), wls[0].T, wls[0].H, wls[0].W
+    truths = np.stack([truth_track(wl) for wl in wls])
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    u = torch.arange(W, dtype=torch.float32, device=device)
+    v = torch.arange(H, dtype=torch.float32, device=device)
+    frames = torch.empty((n, T, H, W), dtype=torch.float32, device=device)
+    tr = torch.from_numpy(truths).to(device=device, dtype=torch.float32)
+    s2 = torch.tensor([2.0 * wl.sigma_psf ** 2 for wl in wls], dtype=torch.float32, device=device)
+    bg = torch.tensor([wl.background for wl in wls], dtype=torch.float32, device=device)
+    for k in range(T):
+        gx = torch.exp(-(u[None, :] - tr[:, k, 0:1]) ** 2 / s2[:, None])
+        gy = torch.exp(-(v[None, :] - tr[:, k, 1:2]) ** 2 / s2[:, None])
+        lam = bg[:, None, None] + tr[:, k, 4][:, None, None] * gy[:, :, None] * gx[:, None, :]
+        frames[:, k] = torch.poisson(lam, generator=gen)
+    return frames, truths

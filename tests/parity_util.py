@@ -29,9 +29,11 @@ def worst(a, b):
     return "worst at %d: %r vs %r" % (i, a.flat[i], b.flat[i])
 
 
-def run_and_compare(pf, wl, frames, truth0, steps, frames_dev):
-    """Run `steps` GPU steps of a single-track filter, comparing each."""
-    ocfg = ora.cfg_from_workload(wl)
+def run_and_compare(pf, wl, frames, truth0, steps, frames_dev, track=0, stepper=None):
+    """Run `steps` GPU steps, comparing track `track` with the oracle after
+    each.  stepper(k) advances the GPU filter (default: pf.step on the
+    frame of step k)."""
+    ocfg = ora.cfg_from_workload(wl, track=track)
     G, Np = wl.G, wl.Np
     kind, x0, lo, hi, rad = _init(wl, truth0)
     pop = ora.init_population(ocfg, kind, x0, lo, hi, rad)
@@ -39,9 +41,12 @@ def run_and_compare(pf, wl, frames, truth0, steps, frames_dev):
     prev_anc = None
     report = []
     for k in range(steps):
-        pf.step(frames_dev[k])
-        p = pf.particles(parents=True)
-        st = pf.stats(k)
+        if stepper is None:
+            pf.step(frames_dev[k])
+        else:
+            stepper(k)
+        p = pf.particles(track=track, parents=True)
+        st = pf.stats(k, track=track)
         X = p["states"].double().cpu().numpy()
         lw = p["logw"].cpu().numpy()
         anc = p["anc"].cpu().numpy().astype(np.int64)
