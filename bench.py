@@ -12,7 +12,16 @@ reduction / next-step ring and ratio.  L2 is flushed (a 256 MB write)
 between timed steps, outside the timed interval; each step is timed with
 CUDA events on the launch stream.
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Beside the headline line's own figures it reports the other forms of the
+step on their workloads: the batched form (512 independent tracks of mixed
+sizes, one graph-captured launch sequence per frame, against the same tracks
+stepped one by one), the adjoint form (forward with ancestry recording plus
+pf_backward, against the plain forward), the information-sharing start
+(steps until every group mean is within 2 px, PE_eff / G per step) and the
+tracking accuracy over 10 sequences (RMSE, ARNA against RNA 10 %).
+--no-extras skips them.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-extras]
 Under torchrun each rank runs an independent replica (its own seed and
 sequence): the path does not shard across GPUs, so N > 1 is weak scaling.
 """
@@ -46,7 +55,7 @@ def kernel_source_hash() -> str:
     """sha256 of the kernel sources; ncu figures in profiles/ are tied to it."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("pf_kernels.cu", "pf_device.cuh", "pf_launch.h"):
+    for f in ("pf_kernels.cu", "pf_device.cuh", "pf_math.cuh", "pf_launch.h"):
         with open(os.path.join(ROOT, "paper_1310_4624_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -228,6 +237,219 @@ def run_reference(args, ws, rank):
     print(json.dumps(line))
 
 
+def _events(stream, fn):
+    """Device time (ms) of fn() on `stream`, synchronised on both sides."""
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
+def bench_batched(dev, K: int, W: int, flush, n_tracks: int = 512, k_alone: int = 8):
+    """512 independent tracks (256 x 256 frames, 50-frame sequences; particle
+    counts log-uniform in [4096, 262144], groups log-uniform in [4, 128],
+    spot amplitude U[5, 20], PSF width U[1.2, 2.0]) in one handle: autotuned
+    launch shapes, frames through a device table, each step one CUDA graph
+    launch.  Against it, the same tracks in 512 handles stepped one by one
+    with pf_step (the first `k_alone` timed steps)."""
+    import torch
+    from paper_1310_4624_gb300 import synth
+    from paper_1310_4624_gb300.filter import ParticleFilter, config_from_workload
+    T = max(50, W + K + 2)
+    wls = synth.batched_tracks(n_tracks, T=T)
+    frames, truths = synth.render_batched_torch(wls, dev, seed=0)
+    cfgs = [config_from_workload(wl, truths[t][0], track_id=t) for t, wl in enumerate(wls)]
+    n_total = sum(wl.N for wl in wls)
+    pf = ParticleFilter(cfgs, history=4, device=dev)
+    table = pf.frame_table([frames[t] for t in range(n_tracks)])
+    grid, cluster = pf.autotune([frames[t, 0] for t in range(n_tracks)])
+    for _ in range(W):
+        pf.step_table(table, graph=True)
+    ms = 0.0
+    for _ in range(K):
+        flush.zero_()
+        ms += _events(pf.stream, lambda: pf.step_table(table, graph=True))
+    _, logz, st = pf.estimate()
+    pf.close()
+    # the same tracks one by one through the plain entry point
+    alone = [ParticleFilter([c], history=4, device=dev) for c in cfgs]
+    for k in range(W):
+        for t, a in enumerate(alone):
+            a.step(frames[t, k])
+    Ka = min(K, k_alone)
+
+    def one_by_one(k):
+        for t, a in enumerate(alone):
+            a.step(frames[t, k])
+    ms_alone = 0.0
+    for k in range(W, W + Ka):
+        flush.zero_()
+        ms_alone += _events(alone[0].stream, lambda: one_by_one(k))
+    for a in alone:
+        a.close()
+    del frames, table
+    return {"workload": "batched_%dtracks_256x256" % n_tracks, "tracks": n_tracks, "particles": n_total,
+            "G_range": [min(w.G for w in wls), max(w.G for w in wls)],
+            "particles_range": [min(w.N for w in wls), max(w.N for w in wls)],
+            "value": n_total * K / (ms / 1e3), "ms_per_step": ms / K, "unit": UNIT,
+            "form": "one handle, autotuned (propagate grid %d, resample cluster %d), CUDA graph per step"
+                    % (grid, cluster),
+            "one_by_one": {"value": n_total * Ka / (ms_alone / 1e3), "ms_per_step": ms_alone / Ka,
+                           "steps": Ka, "form": "512 handles, pf_step each, same stream"},
+            "speedup": (ms_alone / Ka) / (ms / K), "degenerate_status": int(st)}
+
+
+def bench_adjoint(dev, flush, reps: int = 3):
+    """Differentiable workload: 50 frames 512 x 512, G = 16 x 65536, ARNA.
+    Forward without recording, forward recording the ancestry, and
+    pf_backward (replay + adjoint of log Z over the 50 steps); each timed
+    `reps` times after a warm-up pass, L2 flushed before each pass."""
+    import torch
+    from paper_1310_4624_gb300 import synth
+    from paper_1310_4624_gb300.filter import ParticleFilter, config_from_workload
+    wl = synth.differentiable()
+    frames, truth = synth.make_sequence(wl)
+    fr = torch.from_numpy(frames).to(dev)
+    flist = [fr[k] for k in range(wl.T)]
+
+    def forward(pf):
+        pf.reset()
+        for k in range(wl.T):
+            pf.step(fr[k])
+
+    out = {}
+    for rec in (False, True):
+        pf = ParticleFilter([config_from_workload(wl, truth[0], record_ancestors=rec)], history=wl.T + 1,
+                            device=dev)
+        forward(pf)
+        if rec:
+            pf.backward(flist)
+        f_ms, b_ms = [], []
+        for _ in range(reps):
+            flush.zero_()
+            f_ms.append(_events(pf.stream, lambda: forward(pf)))
+            if rec:
+                flush.zero_()
+                grad = []
+                b_ms.append(_events(pf.stream, lambda: grad.append(pf.backward(flist))))
+        out["fwd_rec" if rec else "fwd"] = min(f_ms)
+        if rec:
+            out["bwd"] = min(b_ms)
+            g, lz = grad[-1]
+            out["grad"] = [float(v) for v in g[0].cpu()]
+            out["log_Z"] = float(lz[0])
+        if rec:
+            out["fit"] = adam_fit(pf, wl, fr, truth)
+        pf.close()
+    n = wl.N * wl.T
+    return {"fit": out["fit"], "workload": wl.name, "particles": wl.N, "steps": wl.T, "unit": UNIT,
+            "fwd": {"value": n / (out["fwd"] / 1e3), "ms": out["fwd"]},
+            "fwd_recording": {"value": n / (out["fwd_rec"] / 1e3), "ms": out["fwd_rec"]},
+            "fwd_bwd": {"value": n / ((out["fwd_rec"] + out["bwd"]) / 1e3), "ms": out["fwd_rec"] + out["bwd"]},
+            "bwd_ms": out["bwd"], "fwd_bwd_over_fwd": (out["fwd_rec"] + out["bwd"]) / out["fwd"],
+            "grad_theta": dict(zip(("sigma_psf", "A", "b", "sigma_pos", "sigma_v"), out["grad"])),
+            "log_Z": out["log_Z"], "timing": "best of %d passes, CUDA events" % reps}
+
+
+def adam_fit(pf, wl, fr, truth, iters: int = 200, lr: float = 0.02):
+    """Maximum-likelihood fit of theta = (sigma_psf, A, b, sigma_pos, sigma_v)
+    by Adam on log theta, from theta_true x 1.3, each iteration one forward
+    run (ancestry recorded) and one pf_backward (common random numbers: the
+    filter's seed is fixed)."""
+    import torch
+    from paper_1310_4624_gb300.filter import LogLikelihood
+    names = ("sigma_psf", "A", "b", "sigma_pos", "sigma_v")
+    true = np.array([wl.sigma_psf, float(np.float32(truth[0][4])), wl.background, wl.sigma_pos, wl.sigma_v])
+    logt = torch.tensor(np.log(true * 1.3), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([logt], lr=lr)
+    first = last = None
+    t0 = time.perf_counter()
+    for it in range(iters):
+        opt.zero_grad()
+        lz = LogLikelihood.apply(torch.exp(logt), pf, fr)
+        (-lz).backward()
+        opt.step()
+        v = float(lz)
+        first = v if first is None else first
+        last = v
+    dt = time.perf_counter() - t0
+    pf.set_theta(true)
+    lz_true = float(LogLikelihood.apply(torch.tensor(true), pf, fr))
+    end = np.exp(logt.detach().numpy())
+    return {"iters": iters, "lr_log_theta": lr, "theta_true": dict(zip(names, true.round(4).tolist())),
+            "theta_start": dict(zip(names, (true * 1.3).round(4).tolist())),
+            "theta_end": dict(zip(names, end.round(4).tolist())),
+            "log_Z_start": first, "log_Z_end": last, "log_Z_at_true": lz_true, "seconds": dt}
+
+
+def bench_sharing(dev):
+    """Information-sharing start: 100 frames 512 x 512, G = 256 x 4096, group
+    0 in a 2 px disc around the truth, the other groups uniform over the
+    image.  For ARNA and RNA 10 %: the first step at which every group mean is
+    within 2 px of the truth, and PE_eff / G per step."""
+    import torch
+    from paper_1310_4624_gb300 import synth
+    from paper_1310_4624_gb300.filter import ParticleFilter, config_from_workload
+    out = {}
+    frames = truth = fr = None
+    for mode in (synth.ARNA, synth.RNA):
+        wl = synth.sharing(mode=mode)
+        if frames is None:
+            frames, truth = synth.make_sequence(wl)
+            fr = torch.from_numpy(frames).to(dev)
+        pf = ParticleFilter([config_from_workload(wl, truth[0])], history=wl.T + 1, device=dev)
+        for k in range(wl.T):
+            pf.step(fr[k])
+        pe, nex, first = [], [], None
+        for k in range(wl.T):
+            st = pf.stats(k)
+            gx = st["group_xhat"]
+            d = np.hypot(gx[0] - truth[k, 0], gx[1] - truth[k, 1])
+            if first is None and np.all(d <= 2.0):
+                first = k
+            pe.append(round(st["pe_eff"] / wl.G, 4))
+            nex.append(st["n_ex"])
+        pf.close()
+        out["arna" if mode == synth.ARNA else "rna10"] = {
+            "steps_to_all_groups_within_2px": first, "pe_eff_over_G": pe[:40], "n_ex": nex[:40]}
+    out["workload"] = synth.sharing().name.rsplit("_", 1)[0]
+    return out
+
+
+def bench_accuracy(dev, n_seq: int = 10):
+    """Tracking accuracy on the tracking workload over `n_seq` sequences
+    (data seeds 0..n_seq-1, rendered on the device): position RMSE of the
+    global estimate against the truth, ARNA and RNA 10 % on identical Philox
+    streams."""
+    import torch
+    from paper_1310_4624_gb300 import synth
+    from paper_1310_4624_gb300.filter import ParticleFilter, config_from_workload
+    wls = [synth.tracking(mode=synth.ARNA, data_seed=s) for s in range(n_seq)]
+    frames, truths = synth.render_batched_torch(wls, dev, seed=1)
+    out = {}
+    for mode in (synth.ARNA, synth.RNA):
+        se, per = 0.0, []
+        for s, wl in enumerate(wls):
+            wl = wl.replace(mode=mode)
+            pf = ParticleFilter([config_from_workload(wl, truths[s][0])], history=wl.T + 1, device=dev)
+            for k in range(wl.T):
+                pf.step(frames[s, k])
+            hs = pf.history_stats(0, wl.T)
+            e = np.array([np.sum((h["xhat"][:2] - truths[s][h["step"], :2]) ** 2) for h in hs])
+            per.append(float(math.sqrt(e.mean())))
+            se += float(e.sum())
+            pf.close()
+        out["arna" if mode == synth.ARNA else "rna10"] = {
+            "rmse_px": math.sqrt(se / (n_seq * wls[0].T)), "per_sequence": [round(v, 4) for v in per]}
+    out["sequences"] = n_seq
+    out["workload"] = wls[0].name.rsplit("_", 1)[0]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -235,6 +457,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched / adjoint / sharing / accuracy forms")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     K, W = args.steps, max(3, args.warmup)
@@ -342,6 +565,13 @@ def main():
             "rna10": {"value": n_all * K / (res[synth.RNA]["ms"] / 1e3), "ms_per_step": res[synth.RNA]["ms"] / K,
                       "rmse_px": res[synth.RNA]["rmse"]},
             "arna_n_ex": a["n_ex"][:12]}
+    if not args.no_extras:
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+        line["batched"] = bench_batched(dev, K, W, flush)
+        line["adjoint"] = bench_adjoint(dev, flush)
+        line["sharing"] = bench_sharing(dev)
+        line["accuracy"] = bench_accuracy(dev)
+        del flush
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, frames, truth)
     if rank == 0:
