@@ -131,6 +131,11 @@ pf_status pf_query_workspace(const pf_track_config* cfg, int32_t n_tracks, int32
  * ignored), else may be NULL; it is read before pf_init's work completes on
  * the stream.  All tracks of one handle must share patch_radius.  The
  * workspace must stay allocated and untouched until pf_destroy.
+ * The step kernels are launched with programmatic dependent launch (each
+ * may start while the previous kernel in the stream drains, and waits for
+ * its completion before touching memory); the environment variable
+ * PFARNA_PDL=0 at pf_init selects plain stream serialisation instead.
+ * Results are identical either way.
  * Errors: PF_ERR_ARG, PF_ERR_WORKSPACE, PF_ERR_CUDA. */
 pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history, void* workspace_dev,
                   size_t bytes, const float* user_state_dev, void* stream, pf_handle** out);
@@ -139,7 +144,10 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
  * frames_host: host array of n_tracks device pointers, frame k of each
  * track (H x W float32); the frames must stay valid until the step has run
  * on `stream`.  At k = 0 there is no propagation and no exchange: the
- * initial population is weighted by frame 0.
+ * initial population is weighted by frame 0.  A step is three kernels:
+ * frame preparation, propagate + weight, and resampling whose last group
+ * per track also runs the track's global step (Alg. 3 steps 8-10, and
+ * steps 1-2 of the next step).
  * Errors: PF_ERR_ARG (NULL frame), PF_ERR_STATE (handle failed before),
  * PF_ERR_CUDA. */
 pf_status pf_step(pf_handle* h, const float* const* frames_host, void* stream);

@@ -6,6 +6,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -73,6 +74,7 @@ struct pf_handle {
   const void* graph_table = nullptr;
   int graph_T = 0;
   int k1_occ = 1, sms = 1;
+  bool pdl = true;  // programmatic dependent launch between the step kernels
   // kernel timing (pf_profile_enable / pf_profile_read)
   int prof = 0;
   std::vector<cudaEvent_t> ev[PF_KERNEL_COUNT];  // start, stop, start, stop, ...
@@ -211,7 +213,7 @@ Layout plan(const pf_track_config* c, int n, int history) {
   L.gs = take(sizeof(GroupState) * L.G_total);
   L.gd = take(sizeof(GroupDesc) * L.G_total);
   L.ring = take(sizeof(int) * L.G_total);
-  L.ring_next = take(sizeof(int) * L.G_total);
+  L.ring_next = take(sizeof(int) * 2 * (size_t)L.G_total);
   L.tiles = take(sizeof(int4) * L.n_tiles);
   L.pv0 = take(sizeof(float4) * L.N_total);
   L.pv1 = take(sizeof(float4) * L.N_total);
@@ -303,7 +305,7 @@ cudaError_t prep_frames(pf_handle* h, const float* const* frames, cudaStream_t s
       a.frames[i] = frames[t0 + i];
       if (h->cfg[t0 + i].H > maxH) maxH = h->cfg[t0 + i].H;
     }
-    cudaError_t e = launch_frame_prep(a, nt, maxH > 4096 ? 4096 : maxH, s);
+    cudaError_t e = launch_frame_prep(a, nt, maxH > 4096 ? 4096 : maxH, h->pdl, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -313,6 +315,28 @@ pf_status sync(pf_handle* h) {
   cudaError_t e = cudaStreamSynchronize(h->last_stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
   return check_device(h);
+}
+
+K1Args k1_args(const pf_handle* h) {
+  K1Args a{h->trk, h->tiles, h->n_tiles, h->gs, h->ts, h->ds, h->pv[0], h->pv[1], h->In[0], h->In[1],
+           h->anc, h->parent, h->history, h->lw, h->tile_part, h->ypad, h->tmaps, h->ring_next,
+           h->G_total, h->n_ring_blocks, h->n_tracks, TrackParams{}};
+  a.p0 = h->tp[0];
+  return a;
+}
+
+GlobalArgs global_args(const pf_handle* h, int finalize) {
+  return GlobalArgs{h->trk, h->ts, h->gs, h->ring, h->ring_next, h->G_total, h->hist, h->ghist, h->history,
+                    finalize, h->ds};
+}
+
+// fuse = 1: the resampler also runs each track's global step (the last
+// group of the track to finish); 0: resampling only (autotuner candidates).
+ResampleArgs resample_args(const pf_handle* h, int fuse) {
+  ResampleArgs ra{h->gd, h->gs, h->tile_part, h->lw, h->anc, nullptr, nullptr, 0, h->qc, h->ds};
+  ra.fuse_global = fuse;
+  ra.glob = global_args(h, 1);
+  return ra;
 }
 
 }  // namespace
@@ -358,6 +382,10 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
   h->G_total = L.G_total;
   h->n_tiles = L.n_tiles;
   h->qc = make_qc();
+  {
+    const char* v = std::getenv("PFARNA_PDL");  // "0": plain stream serialisation between step kernels
+    h->pdl = !(v && v[0] == '0');
+  }
   h->last_stream = (cudaStream_t)stream;
   char* w = (char*)workspace;
   h->ds = (DevState*)(w + L.ds);
@@ -516,24 +544,20 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
 
   InitArgs ia{h->trk, h->tiles, h->n_tiles, h->N_total, user_state, h->pv[1], h->In[1]};
   if ((e = launch_init(ia, h->k1_grid, s)) != cudaSuccess) { pf_destroy(h); return cuda_fail(nullptr, e, "k_init"); }
-  GlobalArgs ga{h->trk, h->ts, h->gs, h->ring, h->ring_next, h->hist, h->ghist, h->history, 0, h->ds};
-  if ((e = launch_global(ga, n_tracks, h->max_G, s)) != cudaSuccess) { pf_destroy(h); return cuda_fail(nullptr, e, "k_global"); }
+  if ((e = launch_global(global_args(h, 0), n_tracks, s)) != cudaSuccess) {
+    pf_destroy(h);
+    return cuda_fail(nullptr, e, "k_global");
+  }
   *out = h;
   return PF_OK;
 }
 
-// The kernels of one step after frame preparation: propagate + weight,
-// resample, global step.
+// The kernels of one step after frame preparation: propagate + weight, then
+// resample with the global step as its tail.
 static cudaError_t launch_step_kernels(pf_handle* h, cudaStream_t s) {
-  K1Args k1{h->trk, h->tiles, h->n_tiles, h->gs, h->ts, h->ds, h->pv[0], h->pv[1], h->In[0], h->In[1],
-            h->anc, h->parent, h->history, h->lw, h->tile_part, h->ypad, h->tmaps, h->ring_next,
-            h->n_ring_blocks, h->n_tracks};
-  cudaError_t e = launch_propagate(k1, h->R, h->k1_grid + h->n_ring_blocks, s);
+  cudaError_t e = launch_propagate(k1_args(h), h->R, h->k1_grid + h->n_ring_blocks, h->pdl, s);
   if (e != cudaSuccess) return e;
-  ResampleArgs ra{h->gd, h->gs, h->tile_part, h->lw, h->anc, nullptr, nullptr, 0, h->qc, h->ds};
-  if ((e = launch_resample(ra, h->G_total, h->rs_cluster, s)) != cudaSuccess) return e;
-  GlobalArgs ga{h->trk, h->ts, h->gs, h->ring, h->ring_next, h->hist, h->ghist, h->history, 1, h->ds};
-  return launch_global(ga, h->n_tracks, h->max_G, s);
+  return launch_resample(resample_args(h, 1), h->G_total, h->rs_cluster, h->pdl, s);
 }
 
 pf_status pf_step(pf_handle* h, const float* const* frames, void* stream) {
@@ -547,21 +571,14 @@ pf_status pf_step(pf_handle* h, const float* const* frames, void* stream) {
   if ((e = mark(h, PF_KERNEL_FRAME_PREP, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
   if ((e = prep_frames(h, frames, s)) != cudaSuccess) return cuda_fail(h, e, "k_frame_prep");
   if ((e = mark(h, PF_KERNEL_FRAME_PREP, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
-  K1Args k1{h->trk, h->tiles, h->n_tiles, h->gs, h->ts, h->ds, h->pv[0], h->pv[1], h->In[0], h->In[1],
-            h->anc, h->parent, h->history, h->lw, h->tile_part, h->ypad, h->tmaps, h->ring_next,
-            h->n_ring_blocks, h->n_tracks};
   if ((e = mark(h, PF_KERNEL_PROPAGATE_WEIGHT, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
-  if ((e = launch_propagate(k1, h->R, h->k1_grid + h->n_ring_blocks, s)) != cudaSuccess)
+  if ((e = launch_propagate(k1_args(h), h->R, h->k1_grid + h->n_ring_blocks, h->pdl, s)) != cudaSuccess)
     return cuda_fail(h, e, "k_propagate_weight");
   if ((e = mark(h, PF_KERNEL_PROPAGATE_WEIGHT, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
-  ResampleArgs ra{h->gd, h->gs, h->tile_part, h->lw, h->anc, nullptr, nullptr, 0, h->qc, h->ds};
   if ((e = mark(h, PF_KERNEL_RESAMPLE, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
-  if ((e = launch_resample(ra, h->G_total, h->rs_cluster, s)) != cudaSuccess) return cuda_fail(h, e, "k_resample");
+  if ((e = launch_resample(resample_args(h, 1), h->G_total, h->rs_cluster, h->pdl, s)) != cudaSuccess)
+    return cuda_fail(h, e, "k_resample");
   if ((e = mark(h, PF_KERNEL_RESAMPLE, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
-  GlobalArgs ga{h->trk, h->ts, h->gs, h->ring, h->ring_next, h->hist, h->ghist, h->history, 1, h->ds};
-  if ((e = mark(h, PF_KERNEL_GLOBAL, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
-  if ((e = launch_global(ga, h->n_tracks, h->max_G, s)) != cudaSuccess) return cuda_fail(h, e, "k_global");
-  if ((e = mark(h, PF_KERNEL_GLOBAL, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
   h->steps_run += 1;
   h->last_stream = s;
   return PF_OK;
@@ -571,7 +588,7 @@ static cudaError_t launch_frames_table(pf_handle* h, const float* const* table, 
   int maxH = 1;
   for (int t = 0; t < h->n_tracks; ++t) maxH = h->cfg[t].H > maxH ? h->cfg[t].H : maxH;
   FrameTableArgs fa{h->trk, h->ypad, h->R, table, T_table, h->n_tracks, h->ts, h->ds};
-  return launch_frame_prep_table(fa, maxH > 4096 ? 4096 : maxH, s);
+  return launch_frame_prep_table(fa, maxH > 4096 ? 4096 : maxH, h->pdl, s);
 }
 
 pf_status pf_step_table(pf_handle* h, const float* const* table_dev, int32_t T_table, void* stream) {
@@ -670,9 +687,7 @@ pf_status pf_autotune(pf_handle* h, const float* const* frames, int32_t* k1_grid
       if (r == cudaSuccess) r = cudaEventElapsedTime(&ms, e0, e1);
       return r;
     };
-    K1Args k1{h->trk, h->tiles, h->n_tiles, h->gs, h->ts, h->ds, h->pv[0], h->pv[1], h->In[0], h->In[1],
-              h->anc, h->parent, h->history, h->lw, h->tile_part, h->ypad, h->tmaps, h->ring_next,
-              h->n_ring_blocks, h->n_tracks};
+    const K1Args k1 = k1_args(h);
     int best_grid = h->k1_grid;
     float best = 1e30f;
     for (int b = 1; b <= h->k1_occ; ++b) {
@@ -680,7 +695,8 @@ pf_status pf_autotune(pf_handle* h, const float* const* frames, int32_t* k1_grid
       const int grid = (int)(cand < h->n_tiles ? cand : h->n_tiles);
       float ms = 0.0f;
       for (int rep = 0; rep < 2; ++rep)  // the first run also warms caches
-        if ((e = time_it([&] { return launch_propagate(k1, h->R, grid + h->n_ring_blocks, s); }, ms)) != cudaSuccess)
+        if ((e = time_it([&] { return launch_propagate(k1, h->R, grid + h->n_ring_blocks, false, s); }, ms)) !=
+            cudaSuccess)
           break;
       if (e != cudaSuccess) break;
       if (ms < best) {
@@ -693,10 +709,10 @@ pf_status pf_autotune(pf_handle* h, const float* const* frames, int32_t* k1_grid
     best = 1e30f;
     if (e == cudaSuccess)
       for (int c = 1; c <= 8; c *= 2) {
-        ResampleArgs ra{h->gd, h->gs, h->tile_part, h->lw, h->anc, nullptr, nullptr, 0, h->qc, h->ds};
+        const ResampleArgs ra = resample_args(h, 0);
         float ms = 0.0f;
         for (int rep = 0; rep < 2; ++rep)
-          if ((e = time_it([&] { return launch_resample(ra, h->G_total, c, s); }, ms)) != cudaSuccess) break;
+          if ((e = time_it([&] { return launch_resample(ra, h->G_total, c, false, s); }, ms)) != cudaSuccess) break;
         if (e != cudaSuccess) break;
         if (ms < best) {
           best = ms;
@@ -858,7 +874,7 @@ pf_status pf_resample(const float* logw, const uint32_t* u, int32_t G, int32_t N
       (e = cudaMemcpyAsync(gd, h.data(), sizeof(GroupDesc) * G, cudaMemcpyHostToDevice, s)))
     return cuda_fail(nullptr, e, "pf_resample setup");
   ResampleArgs ra{gd, gs, nullptr, logw, anc, (unsigned long long*)q, u, 1, make_qc(), ds};
-  if ((e = launch_resample(ra, G, resample_cluster(Np, true), s)) != cudaSuccess)
+  if ((e = launch_resample(ra, G, resample_cluster(Np, true), false, s)) != cudaSuccess)
     return cuda_fail(nullptr, e, "k_resample");
   return PF_OK;
 }
@@ -903,8 +919,7 @@ pf_status pf_reset(pf_handle* h, void* stream) {
   for (int t = 0; t < h->n_tracks; ++t)
     if (h->cfg[t].init_kind == PF_INIT_USER) return fail(h, PF_ERR_STATE, "pf_reset cannot redraw a user population");
   if ((e = launch_init(ia, h->k1_grid, s)) != cudaSuccess) return cuda_fail(h, e, "k_init");
-  GlobalArgs ga{h->trk, h->ts, h->gs, h->ring, h->ring_next, h->hist, h->ghist, h->history, 0, h->ds};
-  if ((e = launch_global(ga, h->n_tracks, h->max_G, s)) != cudaSuccess) return cuda_fail(h, e, "k_global");
+  if ((e = launch_global(global_args(h, 0), h->n_tracks, s)) != cudaSuccess) return cuda_fail(h, e, "k_global");
   h->steps_run = 0;
   h->failed = 0;
   h->last_stream = s;

@@ -80,6 +80,7 @@ struct TrackState {
   float xhat[5];
   int steps_done;
   unsigned long long m_nex;  // fast-division reciprocal of n_ex (see fastdiv)
+  unsigned int ticket;       // groups resampled so far in the current step
 };
 
 // Per-group state (global group index).

@@ -20,6 +20,7 @@
 // The step index lives on the device, so the same launch sequence serves
 // every step.
 #include <cooperative_groups.h>
+#include <utility>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -83,6 +84,8 @@ __global__ void __launch_bounds__(K1_THREADS) k_init(InitArgs a) {
 // pixels on each side, zeroed once at init) stands for "outside the image
 // counts as background".
 __global__ void k_frame_prep(FrameArgs a) {
+  grid_dep_wait();
+  grid_dep_launch();
   const int tt = blockIdx.y;
   const TrackParams& P = a.trk[a.t0 + tt];
   const float* __restrict__ z = a.frames[tt];
@@ -99,6 +102,8 @@ __global__ void k_frame_prep(FrameArgs a) {
 // Same, frame pointers from a device table indexed by the device-side step
 // index: table[k * n_tracks + t] (k >= T_table is reported, not read).
 __global__ void k_frame_prep_table(FrameTableArgs a) {
+  grid_dep_wait();
+  grid_dep_launch();
   const int t = blockIdx.y;
   const int k = a.ts[0].k;
   if (k >= a.T_table) {
@@ -118,37 +123,6 @@ __global__ void k_frame_prep_table(FrameTableArgs a) {
 }
 
 // ===================================================================== K1
-// Slot i = (group g, slot j) of step k takes the particle of slot src of the
-// exchanged population (Sec. III-A/C): group g's send set is the systematic
-// slot subsample s_{g,t} = floor((t Np + o_g) / N_ex); slot s_{r,t} of the
-// receiver r gets sender pred(r)'s slot s_{pred(r),t} with its origin
-// weight.  Returns the origin group.  Np (N_ex + 1) < 2^32 uses 32-bit
-// arithmetic with precomputed reciprocals; larger products use 64 bits.
-__device__ __forceinline__ int exchange_source(const GroupState* __restrict__ gs, int g, int j, int Np, int nex,
-                                               unsigned long long mNp, unsigned long long mnex, long long& src_local) {
-  src_local = (long long)g * Np + j;
-  if (nex <= 0) return g;
-  const uint32_t o_r = gs[g].exo;
-  if ((unsigned long long)Np * (unsigned long long)(nex + 1) < (1ull << 32)) {
-    const uint32_t jn = (uint32_t)j * (uint32_t)nex;
-    const uint32_t t = jn <= o_r ? 0u : fastdiv(jn - o_r + (uint32_t)Np - 1u, mNp);
-    if (t < (uint32_t)nex && t * (uint32_t)Np + o_r < jn + (uint32_t)nex) {
-      const int sg = gs[g].pred;
-      src_local = (long long)sg * Np + fastdiv(t * (uint32_t)Np + gs[sg].exo, mnex);
-      return sg;
-    }
-    return g;
-  }
-  const long long num = (long long)j * nex - o_r;
-  const long long t = num <= 0 ? 0 : (num + Np - 1) / Np;
-  if (t < nex && t * Np + o_r < (long long)(j + 1) * nex) {
-    const int sg = gs[g].pred;
-    src_local = (long long)sg * Np + (t * Np + gs[sg].exo) / nex;
-    return sg;
-  }
-  return g;
-}
-
 // Fisher-Yates ring order of step k (Sec. IV-B, Alg. 3 step 1) for one
 // track, by one warp: the bounded draws r_j in [0, j] in parallel, the
 // descending swaps by lane 0 in shared memory.
@@ -207,27 +181,75 @@ __device__ __forceinline__ void tma_load_2d(float* dst, const CUtensorMap* map, 
       : "memory");
 }
 
+// Slot j of group g takes particle src_j of the predecessor group (true) or
+// its own slot j (false); exchange_source with the group's exchange offsets
+// o_r (receiver) and o_s (sender) hoisted out of the particle loop.
+__device__ __forceinline__ bool exchange_from_pred(int j, int Np, int nex, uint32_t o_r, uint32_t o_s,
+                                                   unsigned long long mNp, unsigned long long mnex, int& src_j) {
+  src_j = j;
+  if (nex <= 0) return false;
+  if ((unsigned long long)Np * (unsigned long long)(nex + 1) < (1ull << 32)) {
+    const uint32_t jn = (uint32_t)j * (uint32_t)nex;
+    const uint32_t t = jn <= o_r ? 0u : fastdiv(jn - o_r + (uint32_t)Np - 1u, mNp);
+    if (t < (uint32_t)nex && t * (uint32_t)Np + o_r < jn + (uint32_t)nex) {
+      src_j = (int)fastdiv(t * (uint32_t)Np + o_s, mnex);
+      return true;
+    }
+    return false;
+  }
+  const long long num = (long long)j * nex - o_r;
+  const long long t = num <= 0 ? 0 : (num + Np - 1) / Np;
+  if (t < nex && t * Np + o_r < (long long)(j + 1) * nex) {
+    src_j = (int)((t * Np + o_s) / nex);
+    return true;
+  }
+  return false;
+}
+
+// Hint: bring [p, p + bytes) into L2 (one bulk prefetch; the range is
+// widened to 16-byte boundaries, which stay inside the workspace).
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+  const unsigned long long a0 = (unsigned long long)p & ~15ull;
+  const unsigned long long a1 = ((unsigned long long)p + bytes + 15ull) & ~15ull;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0), "r"((uint32_t)(a1 - a0)) : "memory");
+}
+
+// The previous step's ancestors, states and intensities of a tile's slot
+// range: without weight degeneracy the parents of slots j.. lie near j.
+__device__ __forceinline__ void prefetch_tile(const K1Args& a, int4 td, int k, const float4* pv_prev,
+                                              const float* I_prev) {
+  const TrackParams& P = a.trk[td.x];
+  const long long i0 = P.part_off + (long long)td.y * P.Np + td.z;
+  if (k > 0) prefetch_l2(a.anc + i0, sizeof(uint32_t) * (size_t)td.w);
+  prefetch_l2(pv_prev + i0, sizeof(float4) * (size_t)td.w);
+  prefetch_l2(I_prev + i0, sizeof(float) * (size_t)td.w);
+}
+
 // Propagate + weight: tiles of K1_TILE = K1_PPT x K1_THREADS slots of one
 // group, K1_PPT particles per thread.  Each tile stages the bounding box of
 // its particles' patches (padded frame coordinates) into shared memory with
 // TMA when it fits ROI_W x ROI_BOX_H*ROI_MAX_BOXES floats, else reads the
 // frame through L1.  Leading blocks draw the next step's ARNA rings.
-template <int R>
-__global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(K1Args a) {
+// SINGLE: one track, whose parameters come from the kernel's constant
+// parameter block (a.p0) instead of global memory.
+template <int R, bool SINGLE>
+__global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(const __grid_constant__ K1Args a) {
   constexpr int D = 2 * R + 1;
   constexpr int PAD = 2 * R + 1;
   constexpr int NW = K1_THREADS / 32;
-  const int k = a.ts[0].k;
-  const float4* __restrict__ pv_prev = (k & 1) ? a.pv0 : a.pv1;
-  const float* __restrict__ I_prev = (k & 1) ? a.I0 : a.I1;
-  float4* __restrict__ pv_cur = (k & 1) ? a.pv1 : a.pv0;
-  float* __restrict__ I_cur = (k & 1) ? a.I1 : a.I0;
   __shared__ __align__(128) float s_roi[1][ROI_FLOATS];  // the staged box (TMA target)
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ float s_red[NW][8];
   __shared__ int s_box[NW][4];
   __shared__ int s_key[NW];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  grid_dep_wait();
+  grid_dep_launch();
+  const int k = a.ts[0].k;
+  const float4* __restrict__ pv_prev = (k & 1) ? a.pv0 : a.pv1;
+  const float* __restrict__ I_prev = (k & 1) ? a.I0 : a.I1;
+  float4* __restrict__ pv_cur = (k & 1) ? a.pv1 : a.pv0;
+  float* __restrict__ I_cur = (k & 1) ? a.I1 : a.I0;
   if ((int)blockIdx.x < a.n_ring_blocks) {
     // Leading blocks: the next step's ARNA ring orders, off the critical
     // path (they depend only on the seed and the step index).
@@ -238,48 +260,75 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
         const TrackParams& P = a.trk[t];
         if (P.mode != MODE_ARNA || P.G <= 1 || P.G > RING_SMEM_G) continue;
         ring_for_step(P, t, (uint32_t)(k + 1), perm, rr, a.ds);
-        for (int p = lane; p < P.G; p += 32) a.ring_next[P.group_off + p] = perm[p];
+        for (int p = lane; p < P.G; p += 32)
+          a.ring_next[(size_t)((k + 1) & 1) * a.ring_stride + P.group_off + p] = perm[p];
         __syncwarp();
       }
     }
     return;
   }
+  const int stride = (int)gridDim.x - a.n_ring_blocks;
+  int tile = (int)blockIdx.x - a.n_ring_blocks;
   if (threadIdx.x == 0) {
     mbar_init(&s_bar, 1);
     fence_proxy_async();
+    if (tile < a.n_tiles) prefetch_tile(a, a.tiles[tile], k, pv_prev, I_prev);
   }
   __syncthreads();
   uint32_t phase = 0;
+  // SINGLE: the track's exchange count for the whole launch
+  const int nex1 = SINGLE && k > 0 ? a.ts[0].n_ex : 0;
+  const unsigned long long mnex1 = SINGLE ? a.ts[0].m_nex : 0ull;
 
-  for (int tile = blockIdx.x - a.n_ring_blocks; tile < a.n_tiles; tile += gridDim.x - a.n_ring_blocks) {
-    const int4 td = a.tiles[tile];
-    const TrackParams& P = a.trk[td.x];
+  auto run_tile = [&](const TrackParams& P, const int4 td) {
     const int g = td.y, Np = P.Np;
     const GroupState* __restrict__ gs = a.grp + P.group_off;
-    const int nex = k > 0 ? a.ts[td.x].n_ex : 0;
-    const unsigned long long mnex = a.ts[td.x].m_nex;
+    const int nex = SINGLE ? nex1 : (k > 0 ? a.ts[td.x].n_ex : 0);
+    const unsigned long long mnex = SINGLE ? mnex1 : a.ts[td.x].m_nex;
+    // the group's exchange partners and weight offsets, once per tile
+    const float off_g = gs[g].off;
+    uint32_t o_r = 0, o_s = 0;
+    int sg = g;
+    float off_s = off_g;
+    if (nex > 0) {
+      o_r = gs[g].exo;
+      sg = gs[g].pred;
+      o_s = gs[sg].exo;
+      off_s = gs[sg].off;
+    }
+    const uint32_t n_track = (uint32_t)(P.G * Np);
+    const uint32_t* __restrict__ anc_t = a.anc + P.part_off;
+    const float4* __restrict__ pvp_t = pv_prev + P.part_off;
+    const float* __restrict__ Ip_t = I_prev + P.part_off;
+    float4* __restrict__ pvc_t = pv_cur + P.part_off;
+    float* __restrict__ Ic_t = I_cur + P.part_off;
+    float* __restrict__ lw_t = a.lw + P.part_off;
+    uint32_t* __restrict__ par_t =
+        P.record ? a.parent + P.parent_off + (long long)(k % a.history) * (long long)n_track : nullptr;
     float4 s[K1_PPT];
     float I[K1_PPT];
-    int og[K1_PPT], pu[K1_PPT], pv[K1_PPT];
+    bool from_pred[K1_PPT];
+    int pu[K1_PPT], pv[K1_PPT];
     int umin = INT_MAX, umax = INT_MIN, vmin = INT_MAX, vmax = INT_MIN;
 #pragma unroll
     for (int q = 0; q < K1_PPT; ++q) {
       const int jj = threadIdx.x + q * K1_THREADS;
       const bool active = jj < td.w;
       const int j = td.z + jj;
-      const long long il = (long long)g * Np + j;
+      const int il = g * Np + j;
       s[q] = make_float4(0.f, 0.f, 0.f, 0.f);
       I[q] = 0.0f;
-      og[q] = g;
+      from_pred[q] = false;
       if (active) {
-        long long src = il;
-        og[q] = exchange_source(gs, g, j, Np, nex, P.m_Np, mnex, src);
-        const long long par = (k == 0) ? src : (long long)a.anc[P.part_off + src];
-        if (par < 0 || par >= (long long)P.G * Np) {
-          set_error(a.ds, ERR_INDEX, 1u, (uint32_t)tile, (uint32_t)par);
+        int sj;
+        from_pred[q] = exchange_from_pred(j, Np, nex, o_r, o_s, P.m_Np, mnex, sj);
+        const uint32_t src = (uint32_t)((from_pred[q] ? sg : g) * Np + sj);
+        const uint32_t par = (k == 0) ? src : anc_t[src];
+        if (par >= n_track) {
+          set_error(a.ds, ERR_INDEX, 1u, (uint32_t)tile, par);
         } else {
-          s[q] = pv_prev[P.part_off + par];
-          I[q] = I_prev[P.part_off + par];
+          s[q] = pvp_t[par];
+          I[q] = Ip_t[par];
         }
         if (k > 0) {
           // Alg. 1 step P: nearly constant velocity, unit frame interval
@@ -296,10 +345,9 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
           s[q].w = fmaf(P.sv, e3, s[q].w);
           I[q] = fmaf(P.sI, e4, I[q]);
         }
-        pv_cur[P.part_off + il] = s[q];
-        I_cur[P.part_off + il] = I[q];
-        if (P.record)
-          a.parent[P.parent_off + (long long)(k % a.history) * ((long long)P.G * Np) + il] = (uint32_t)par;
+        pvc_t[il] = s[q];
+        Ic_t[il] = I[q];
+        if (par_t) par_t[il] = par;
         // patch corner in padded-frame coordinates (centre clamped so that a
         // patch wholly off the frame reads the zero border)
         pu[q] = (int)fminf(fmaxf(floorf(s[q].x + 0.5f), -(float)(R + 1)), (float)(P.W + R)) - R + PAD;
@@ -349,7 +397,7 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
           set_error(a.ds, ERR_TIMEOUT, 4u, (uint32_t)tile, 0u);
           mbar_wait(&s_bar, phase);
         }
-        return;
+        return false;
       }
       phase ^= 1u;
     }
@@ -361,10 +409,8 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
       const int jj = threadIdx.x + q * K1_THREADS;
       lw[q] = -INFINITY;
       if (jj < td.w) {
-        float gxI[D];
-        gauss_row<R>(floorf(s[q].x + 0.5f), s[q].x, P.c_psf, P.kappa, gxI);
-#pragma unroll
-        for (int c = 0; c < D; ++c) gxI[c] *= I[q];
+        float gxI[D];  // I gx(u), u = cx - R .. cx + R
+        gauss_row_scaled<R>(floorf(s[q].x + 0.5f), s[q].x, P.c_psf, P.kappa, I[q], gxI);
         const float dy = floorf(s[q].y + 0.5f) - s[q].y;
         float ss;
         if (staged) {
@@ -373,8 +419,8 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
           ss = patch_ss<R, false>(a.ypad + P.ypad_off + (long long)pv[q] * P.pitch + pu[q], P.pitch, gxI, dy,
                                   P.c_psf, P.kappa);
         }
-        lw[q] = gs[og[q]].off - ss * P.inv2so2;
-        a.lw[P.part_off + (long long)g * Np + td.z + jj] = lw[q];
+        lw[q] = fmaf(-ss, P.inv2so2, from_pred[q] ? off_s : off_g);
+        lw_t[g * Np + td.z + jj] = lw[q];
       }
     }
 
@@ -417,6 +463,275 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
       a.tile_part[(long long)tile * 8 + threadIdx.x] = r;
     }
     __syncthreads();
+    return true;
+  };
+
+  for (; tile < a.n_tiles; tile += stride) {
+    const int4 td = a.tiles[tile];
+    if (threadIdx.x == 0 && tile + stride < a.n_tiles) prefetch_tile(a, a.tiles[tile + stride], k, pv_prev, I_prev);
+    bool ok;
+    if constexpr (SINGLE)
+      ok = run_tile(a.p0, td);
+    else
+      ok = run_tile(a.trk[td.x], td);
+    if (!ok) return;
+  }
+}
+
+// ===================================================================== K5
+// Per track: the master PE's reduction (Alg. 3 steps 9-10) and weight carry
+// (step 8) for step k, then ring order (step 1) and exchange count (step 2)
+// for step k+1.  G-sized; the exchange count is decided in FP64.
+// log W^(m) = M + ln(Q 2^-40) in FP32: log2 Q from the leading-bit position
+// and the top 24 bits of Q.
+__device__ __forceinline__ float group_log_weight(float M, unsigned long long Q) {
+  const int e = 63 - __clzll((long long)Q);
+  const uint32_t top = e >= 23 ? (uint32_t)(Q >> (e - 23)) : (uint32_t)(Q << (23 - e));
+  const float l2 = (float)(e - 23) + log2f((float)top);  // log2 Q (top is exact in FP32)
+  return M + (l2 - 40.0f) * 0.693147182f;
+}
+
+// Scratch of the global step (shared memory of the CTA running it).
+struct GlobalScratch {
+  float f[32];
+  int i[32];
+  float red[32][6];
+  double d[32][2];
+  float tot[6];
+  double pe;
+  int ring[MAX_G];
+};
+
+// The global step of track t by one CTA of NT threads, each thread owning
+// groups m = threadIdx.x + i NT.  finalize = 0 prepares step 0 only.
+// Per-group inputs are read through L2 (written by other CTAs of the same
+// launch when this runs as the resampler's tail).
+template <int NT>
+__device__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
+  constexpr int NW = NT / 32;
+  constexpr int GPT = (MAX_G + NT - 1) / NT;
+  // Every input first (the body then only computes and stores, so no load
+  // waits behind a store that might alias it): parameters, track state,
+  // per-group statistics.
+  const TrackParams* __restrict__ P = a.trk + t;
+  const int G = P->G, Np = P->Np, mode = P->mode, group_off = P->group_off, hist_off = P->hist_off;
+  const long long ghist_off = P->ghist_off;
+  const float cutoff = P->cutoff, ex_ratio = P->ex_ratio;
+  const uint32_t key0 = P->key0, key1 = P->key1, tag = P->tag;
+  TrackState* __restrict__ T = a.ts + t;
+  const int k = __ldcg(&T->k);
+  const int nex_k = __ldcg(&T->n_ex);
+  const double pe_k = __ldcg(&T->pe_eff);
+  const double logZ_k = __ldcg(&T->log_Z);
+  GroupState* __restrict__ gs = a.gs + group_off;
+  int* __restrict__ ring = a.ring + group_off;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int k1 = a.finalize ? k + 1 : 0;
+  const int* __restrict__ rnext_buf = a.ring_next + (size_t)(k1 & 1) * a.ring_stride + group_off;
+
+  unsigned long long Q[GPT];
+  float Mg[GPT], xs[GPT][5], ess[GPT], lam[GPT];
+  int ring_m[GPT], rnext[GPT];
+#pragma unroll
+  for (int i = 0; i < GPT; ++i) {
+    const int m = threadIdx.x + i * NT;
+    Q[i] = 0;
+    Mg[i] = 0.0f;
+    ess[i] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) xs[i][q] = 0.0f;
+    ring_m[i] = m;
+    rnext[i] = m;
+    if (m < G) {
+      Q[i] = __ldcg(&gs[m].Q);
+      Mg[i] = __ldcg(&gs[m].M);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) xs[i][q] = __ldcg(&gs[m].xs[q]);
+      ess[i] = __ldcg(&gs[m].ess);
+      ring_m[i] = __ldcg(&ring[m]);
+      rnext[i] = __ldcg(&rnext_buf[m]);
+    }
+  }
+  // the next step's random words (independent of the reductions below)
+  uint32_t exo[GPT], uw[GPT];
+  bool exo_ok[GPT];
+#pragma unroll
+  for (int i = 0; i < GPT; ++i) {
+    const int m = threadIdx.x + i * NT;
+    exo[i] = 0;
+    uw[i] = 0;
+    exo_ok[i] = true;
+    if (m < G) {
+      exo_ok[i] = draw_bounded(key0, key1, tag, ST_EXCH, (uint32_t)m, (uint32_t)k1, (uint32_t)Np, exo[i]);
+      uw[i] = philox(key0, key1, make_uint4((uint32_t)m, 0u, (uint32_t)k1, tag | (ST_RESAMPLE << 4))).x;
+    }
+  }
+
+  // S7 -> S8: Lambda'_m in FP32 (finalize), or 0 (prepare step 0)
+  float mx = -INFINITY;
+  int deg = 0;
+#pragma unroll
+  for (int i = 0; i < GPT; ++i) {
+    const int m = threadIdx.x + i * NT;
+    lam[i] = -INFINITY;
+    if (m < G) {
+      if (a.finalize) {
+        lam[i] = Q[i] != 0 ? group_log_weight(Mg[i], Q[i]) : -INFINITY;
+        deg += (Q[i] == 0);
+      } else {
+        lam[i] = 0.0f;
+      }
+      mx = fmaxf(mx, lam[i]);
+    }
+  }
+  mx = warp_max(mx);
+  deg = __reduce_add_sync(0xffffffffu, deg);
+  if (lane == 0) {
+    sc.f[warp] = mx;
+    sc.i[warp] = deg;
+  }
+  __syncthreads();
+  mx = -INFINITY;
+  deg = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    mx = fmaxf(mx, sc.f[w]);
+    deg += sc.i[w];
+  }
+  const bool all_degenerate = a.finalize && deg == G;
+  if (all_degenerate) {  // every group lost its weight: restart from equal weights
+#pragma unroll
+    for (int i = 0; i < GPT; ++i) lam[i] = (threadIdx.x + i * NT < G) ? 0.0f : -INFINITY;
+    mx = 0.0f;
+  }
+  // one pass: FP32 sums for log c and the estimate, FP64 sums for Eq. 4
+  // (the exchange count is an integer decided in FP64 on both sides)
+  float acc[6] = {0, 0, 0, 0, 0, 0};
+  double dw = 0.0, dw2 = 0.0;
+#pragma unroll
+  for (int i = 0; i < GPT; ++i) {
+    if (threadIdx.x + i * NT < G) {
+      const float wf = __expf(lam[i] - mx);
+      acc[0] += wf;
+#pragma unroll
+      for (int q = 0; q < 5; ++q) acc[1 + q] = fmaf(wf, xs[i][q], acc[1 + q]);
+      const double w = exp((double)lam[i] - (double)mx);
+      dw += w;
+      dw2 += w * w;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 6; ++q) acc[q] = warp_sum(acc[q]);
+  dw = warp_sum_d(dw);
+  dw2 = warp_sum_d(dw2);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) sc.red[warp][q] = acc[q];
+    sc.d[warp][0] = dw;
+    sc.d[warp][1] = dw2;
+  }
+  const bool shuffled = (mode == MODE_ARNA) && k1 >= 1 && G > 1;
+#pragma unroll
+  for (int i = 0; i < GPT; ++i) {
+    const int m = threadIdx.x + i * NT;
+    if (m < G) sc.ring[m] = shuffled ? rnext[i] : m;  // ring order of step k1 (Sec. IV-B)
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    float x = 0.0f;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) x += sc.red[w][threadIdx.x];
+    sc.tot[threadIdx.x] = x;
+  }
+  if (threadIdx.x == (NW > 1 ? 32 : 7)) {
+    double sw = 0.0, sw2 = 0.0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      sw += sc.d[w][0];
+      sw2 += sc.d[w][1];
+    }
+    const double pe = sw * sw / sw2;  // Eq. 4 for the next step
+    // exchange count for step k1 (Eq. 3 with the Sec. V-A cut-off)
+    int nex = 0;
+    if (k1 >= 1 && G > 1) {
+      double rho;
+      if (mode == MODE_ARNA) {
+        if (!(pe < (double)cutoff * (double)G)) {
+          rho = 0.0;
+        } else {
+          rho = 0.5 - 0.5 * (pe - 1.0) / (double)(G - 1);
+          rho = fmin(fmax(rho, 0.0), 0.5);
+        }
+      } else {
+        rho = fmin(fmax((double)ex_ratio, 0.0), 1.0);
+      }
+      nex = (int)floor(rho * (double)Np);
+    }
+    sc.pe = pe;
+    sc.i[0] = nex;
+  }
+  __syncthreads();
+  const float sw = sc.tot[0];
+  const float lse = mx + logf(sw);  // LSE of the carried weights = log c_k
+  const double pe = sc.pe;
+  const int nex = sc.i[0];
+  const float log_np = logf((float)Np);
+
+  if (a.finalize) {
+    const int hslot = k % a.history;
+#pragma unroll
+    for (int i = 0; i < GPT; ++i) {
+      const int m = threadIdx.x + i * NT;
+      if (m < G) {
+        GroupHist& gh = a.ghist[ghist_off + (long long)hslot * G + m];
+        gh.ring = ring_m[i];
+        gh.logW = all_degenerate ? -INFINITY : (double)lam[i];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) gh.xs[q] = xs[i][q];
+        gh.ess = ess[i];
+      }
+    }
+    if (threadIdx.x == 0) {
+      const double logc = all_degenerate ? -INFINITY : (double)lse;
+      const double logZ = logZ_k + logc;
+      float xq[5];
+      for (int q = 0; q < 5; ++q) xq[q] = all_degenerate ? NAN : sc.tot[1 + q] / sw;
+      T->log_c = logc;
+      T->log_Z = logZ;
+      for (int q = 0; q < 5; ++q) T->xhat[q] = xq[q];
+      T->degenerate = deg;
+      if (all_degenerate) T->flags |= 1;
+      T->steps_done = k + 1;
+      HistRec& h = a.hist[hist_off + hslot];
+      for (int q = 0; q < 5; ++q) h.xhat[q] = xq[q];
+      h.step = k;
+      h.n_ex = nex_k;
+      h.pe_eff = pe_k;
+      h.log_c = logc;
+      h.log_Z = logZ;
+      h.degenerate = deg;
+    }
+  }
+
+#pragma unroll
+  for (int i = 0; i < GPT; ++i) {
+    const int m = threadIdx.x + i * NT;
+    if (m < G) {
+      const int rm = sc.ring[m];
+      ring[m] = rm;
+      gs[rm].pred = sc.ring[m == 0 ? G - 1 : m - 1];
+      if (nex > 0 && !exo_ok[i]) set_error(a.ds, ERR_DRAW, 2u, (uint32_t)t, (uint32_t)m);
+      gs[m].exo = nex > 0 ? exo[i] : 0u;
+      gs[m].u = uw[i];
+      gs[m].lambda = all_degenerate ? 0.0 : (double)lam[i];
+      gs[m].off = lam[i] - log_np - lse;
+    }
+  }
+  if (threadIdx.x == 0) {
+    T->n_ex = nex;
+    T->m_nex = fastdiv_magic((uint32_t)(nex > 0 ? nex : 1));
+    T->pe_eff = pe;
+    T->k = k1;
   }
 }
 
@@ -441,6 +756,8 @@ __device__ __forceinline__ int count_below(const Thresholds& th, unsigned long l
 // items; thread t owns the RS_ITEMS consecutive items [t*RS_ITEMS, ...).
 
 __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
+  grid_dep_wait();
+  grid_dep_launch();
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -461,6 +778,7 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
   __shared__ float s_stat[RS_THREADS / 32][8];
   __shared__ int s_jlo, s_jhi;
   __shared__ unsigned long long s_incl[RS_SUB];
+  __shared__ Thresholds s_th;
 
   float v[RS_ITEMS];
   auto load_sub = [&](int sub) {
@@ -520,8 +838,11 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
       if (a.q_out) a.q_out[d.base + i] = 0ull;
     }
   } else {
-    Thresholds th;
-    th.init(Q, (uint32_t)Np, u);
+    // the threshold constants need three 64-bit divisions (a long software
+    // sequence): one thread computes them for the CTA
+    if (threadIdx.x == 0) s_th.init(Q, (uint32_t)Np, u);
+    __syncthreads();
+    const Thresholds th = s_th;
     const float inv_Q = 1.0f / u64_to_float_approx(Q);
     unsigned long long carry = Sb;
     for (int sub = lo; sub < hi; sub += RS_SUB) {
@@ -653,197 +974,35 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
     }
   }
   cl.sync();  // keep shared memory alive until every CTA has read it
+
+  // The last group of a track to finish runs the track's global step here
+  // (its rank-0 CTA): a ticket per track counts finished groups.  The
+  // writer of the group's statistics (thread 0 of rank 0) fences before
+  // taking its ticket; the last taker fences before the reads.
+  if (a.fuse_global && rank == 0) {
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned prev = atomicAdd(&a.glob.ts[d.track].ticket, 1u);
+      s_last = (prev + 1u == (unsigned)a.glob.trk[d.track].G) ? 1 : 0;
+      __threadfence();
+    }
+    __syncthreads();
+    if (s_last) {
+      global_step<RS_THREADS>(a.glob, d.track, *reinterpret_cast<GlobalScratch*>(s_incl));
+      if (threadIdx.x == 0) a.glob.ts[d.track].ticket = 0u;
+    }
+  }
 }
 
-// ===================================================================== K5
+
 // Per track: the master PE's reduction (Alg. 3 steps 9-10) and weight carry
 // (step 8) for step k, then ring order (step 1) and exchange count (step 2)
-// for step k+1.  FP64 throughout: it is G-sized.
-// log W^(m) = M + ln(Q 2^-40) in FP32: log2 Q from the leading-bit position
-// and the top 24 bits of Q.
-__device__ __forceinline__ float group_log_weight(float M, unsigned long long Q) {
-  const int e = 63 - __clzll((long long)Q);
-  const uint32_t top = e >= 23 ? (uint32_t)(Q >> (e - 23)) : (uint32_t)(Q << (23 - e));
-  const float l2 = (float)(e - 23) + log2f((float)top);  // log2 Q (top is exact in FP32)
-  return M + (l2 - 40.0f) * 0.693147182f;
-}
-
+// for step k+1.  Used to prepare step 0; during the run the same step runs
+// as the tail of the resampler.
 __global__ void __launch_bounds__(GL_THREADS) k_global(GlobalArgs a) {
-  constexpr int NW = GL_THREADS / 32;
-  const int t = blockIdx.x;
-  const TrackParams& P = a.trk[t];
-  TrackState* T = a.ts + t;
-  GroupState* gs = a.gs + P.group_off;
-  int* ring = a.ring + P.group_off;
-  const int G = P.G;
-  const int k = T->k;
-  const int m = threadIdx.x;  // one group per thread (G <= GL_THREADS)
-  const bool act = m < G;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = (int)blockDim.x >> 5;  // launched with ceil(G / 32) warps
-  __shared__ float s_f[NW];
-  __shared__ int s_i[NW];
-  __shared__ float s_red[NW][6];
-  __shared__ double s_d[NW][2];
-  __shared__ float s_tot[6];
-  __shared__ double s_pe;
-  __shared__ int s_ring[MAX_G];
-
-  // every per-group input at once
-  unsigned long long Q = 0;
-  float Mg = 0.0f, xs[5] = {0, 0, 0, 0, 0}, ess = 0.0f;
-  int ring_m = m, rnext = m;
-  if (act) {
-    Q = gs[m].Q;
-    Mg = gs[m].M;
-#pragma unroll
-    for (int q = 0; q < 5; ++q) xs[q] = gs[m].xs[q];
-    ess = gs[m].ess;
-    ring_m = ring[m];
-    rnext = a.ring_next[P.group_off + m];
-  }
-  // S7 -> S8: Lambda'_m in FP32 (finalize), or 0 (prepare step 0)
-  float lam = -INFINITY;
-  int deg = 0;
-  if (act) {
-    if (a.finalize) {
-      lam = Q != 0 ? group_log_weight(Mg, Q) : -INFINITY;
-      deg = (Q == 0);
-    } else {
-      lam = 0.0f;
-    }
-  }
-  {
-    float mx = warp_max(lam);
-    const int dsum = __reduce_add_sync(0xffffffffu, deg);
-    if (lane == 0) {
-      s_f[warp] = mx;
-      s_i[warp] = dsum;
-    }
-    __syncthreads();
-    mx = -INFINITY;
-    deg = 0;
-    for (int w = 0; w < nw; ++w) {
-      mx = fmaxf(mx, s_f[w]);
-      deg += s_i[w];
-    }
-    if (a.finalize && deg == G) {  // every group lost its weight: restart from equal weights
-      lam = act ? 0.0f : -INFINITY;
-      mx = 0.0f;
-    }
-    // one pass: FP32 sums for log c and the estimate, FP64 sums for Eq. 4
-    // (the exchange count is an integer decided in FP64 on both sides)
-    const float wf = act ? __expf(lam - mx) : 0.0f;
-    float acc[6] = {wf, wf * xs[0], wf * xs[1], wf * xs[2], wf * xs[3], wf * xs[4]};
-    double dw = 0.0, dw2 = 0.0;
-    if (act) {
-      const double w = exp((double)lam - (double)mx);
-      dw = w;
-      dw2 = w * w;
-    }
-#pragma unroll
-    for (int q = 0; q < 6; ++q) acc[q] = warp_sum(acc[q]);
-    dw = warp_sum_d(dw);
-    dw2 = warp_sum_d(dw2);
-    if (lane == 0) {
-#pragma unroll
-      for (int q = 0; q < 6; ++q) s_red[warp][q] = acc[q];
-      s_d[warp][0] = dw;
-      s_d[warp][1] = dw2;
-    }
-    __syncthreads();
-    if (threadIdx.x < 6) {
-      float x = 0.0f;
-      for (int w2 = 0; w2 < nw; ++w2) x += s_red[w2][threadIdx.x];
-      s_tot[threadIdx.x] = x;
-    }
-    if (threadIdx.x == (nw > 1 ? 32 : 7)) {
-      double sw = 0.0, sw2 = 0.0;
-      for (int w2 = 0; w2 < nw; ++w2) {
-        sw += s_d[w2][0];
-        sw2 += s_d[w2][1];
-      }
-      s_pe = sw * sw / sw2;  // Eq. 4 for the next step
-    }
-    __syncthreads();
-    const bool all_degenerate = a.finalize && deg == G;
-    const float sw = s_tot[0];
-    const float lse = mx + logf(sw);  // LSE of the carried weights = log c_k
-    const double pe = s_pe;
-
-    if (a.finalize) {
-      const int hslot = k % a.history;
-      if (act) {
-        GroupHist& gh = a.ghist[P.ghist_off + (long long)hslot * G + m];
-        gh.ring = ring_m;
-        gh.logW = all_degenerate ? -INFINITY : (double)lam;
-#pragma unroll
-        for (int q = 0; q < 5; ++q) gh.xs[q] = xs[q];
-        gh.ess = ess;
-      }
-      if (threadIdx.x == 0) {
-        const double logc = all_degenerate ? -INFINITY : (double)lse;
-        T->log_c = logc;
-        T->log_Z += logc;
-        HistRec& h = a.hist[P.hist_off + hslot];
-        for (int q = 0; q < 5; ++q) {
-          const float xq = all_degenerate ? NAN : s_tot[1 + q] / sw;
-          T->xhat[q] = xq;
-          h.xhat[q] = xq;
-        }
-        T->degenerate = deg;
-        if (all_degenerate) T->flags |= 1;
-        T->steps_done = k + 1;
-        h.step = k;
-        h.n_ex = T->n_ex;
-        h.pe_eff = T->pe_eff;
-        h.log_c = logc;
-        h.log_Z = T->log_Z;
-        h.degenerate = deg;
-      }
-    }
-
-    const int k1 = a.finalize ? k + 1 : 0;
-    // ring order for step k1 (Sec. IV-B), drawn one step ahead by the
-    // propagate kernel's leading blocks
-    const bool shuffled = (P.mode == MODE_ARNA) && k1 >= 1 && G > 1;
-    if (act) s_ring[m] = shuffled ? rnext : m;
-    __syncthreads();
-
-    // exchange count for step k1 (Eq. 3 with the Sec. V-A cut-off)
-    int nex = 0;
-    if (k1 >= 1 && G > 1) {
-      double rho;
-      if (P.mode == MODE_ARNA) {
-        if (!(pe < (double)P.cutoff * (double)G)) {
-          rho = 0.0;
-        } else {
-          rho = 0.5 - 0.5 * (pe - 1.0) / (double)(G - 1);
-          rho = fmin(fmax(rho, 0.0), 0.5);
-        }
-      } else {
-        rho = fmin(fmax((double)P.ex_ratio, 0.0), 1.0);
-      }
-      nex = (int)floor(rho * (double)P.Np);
-    }
-    if (act) {
-      ring[m] = s_ring[m];
-      gs[s_ring[m]].pred = s_ring[(m + G - 1) % G];
-      uint32_t o = 0;
-      if (nex > 0 && !draw_bounded(P.key0, P.key1, P.tag, ST_EXCH, (uint32_t)m, (uint32_t)k1, (uint32_t)P.Np, o))
-        set_error(a.ds, ERR_DRAW, 2u, (uint32_t)t, (uint32_t)m);
-      gs[m].exo = o;
-      gs[m].u = philox(P.key0, P.key1, make_uint4((uint32_t)m, 0u, (uint32_t)k1, P.tag | (ST_RESAMPLE << 4))).x;
-      gs[m].lambda = all_degenerate ? 0.0 : (double)lam;
-      gs[m].off = lam - logf((float)P.Np) - lse;
-    }
-    if (threadIdx.x == 0) {
-      T->n_ex = nex;
-      T->m_nex = fastdiv_magic((uint32_t)(nex > 0 ? nex : 1));
-      T->pe_eff = pe;
-      T->k = k1;
-    }
-  }
+  __shared__ GlobalScratch sc;
+  global_step<GL_THREADS>(a, blockIdx.x, sc);
 }
 
 // ============================================================ export helpers
@@ -865,19 +1024,47 @@ cudaError_t launch_init(const InitArgs& a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_frame_prep_table(const FrameTableArgs& a, int blocks_x, cudaStream_t s) {
-  k_frame_prep_table<<<dim3(blocks_x, a.n_tracks), 256, 0, s>>>(a);
-  return cudaGetLastError();
+// cudaLaunchKernelEx with an optional cluster shape and programmatic
+// stream serialization (see launch_* in pf_launch.h).
+template <typename... Params, typename... Args>
+static cudaError_t launch_ex(void (*kernel)(Params...), dim3 grid, dim3 block, int cluster, bool pdl,
+                             cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  int n = 0;
+  if (cluster > 0) {
+    attr[n].id = cudaLaunchAttributeClusterDimension;
+    attr[n].val.clusterDim.x = (unsigned)cluster;
+    attr[n].val.clusterDim.y = 1;
+    attr[n].val.clusterDim.z = 1;
+    ++n;
+  }
+  if (pdl) {
+    attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[n].val.programmaticStreamSerializationAllowed = 1;
+    ++n;
+  }
+  cfg.attrs = attr;
+  cfg.numAttrs = n;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
-cudaError_t launch_frame_prep(const FrameArgs& a, int nt, int blocks_x, cudaStream_t s) {
-  k_frame_prep<<<dim3(blocks_x, nt), 256, 0, s>>>(a);  // blocks_x: rows per track (grid-stride)
-  return cudaGetLastError();
+cudaError_t launch_frame_prep_table(const FrameTableArgs& a, int blocks_x, bool pdl, cudaStream_t s) {
+  return launch_ex(k_frame_prep_table, dim3(blocks_x, a.n_tracks), dim3(256), 0, pdl, s, a);
+}
+
+cudaError_t launch_frame_prep(const FrameArgs& a, int nt, int blocks_x, bool pdl, cudaStream_t s) {
+  // blocks_x: rows per track (grid-stride)
+  return launch_ex(k_frame_prep, dim3(blocks_x, nt), dim3(256), 0, pdl, s, a);
 }
 
 template <int R>
 static const void* k1_ptr() {
-  return (const void*)k_propagate_weight<R>;
+  return (const void*)k_propagate_weight<R, false>;
 }
 
 const void* propagate_kernel(int R) {
@@ -893,39 +1080,32 @@ const void* propagate_kernel(int R) {
   }
 }
 
-cudaError_t launch_propagate(const K1Args& a, int R, int grid, cudaStream_t s) {
+template <int R>
+static cudaError_t launch_propagate_r(const K1Args& a, dim3 g, bool pdl, cudaStream_t s) {
+  if (a.n_tracks == 1) return launch_ex(k_propagate_weight<R, true>, g, dim3(K1_THREADS), 0, pdl, s, a);
+  return launch_ex(k_propagate_weight<R, false>, g, dim3(K1_THREADS), 0, pdl, s, a);
+}
+
+cudaError_t launch_propagate(const K1Args& a, int R, int grid, bool pdl, cudaStream_t s) {
+  const dim3 g(grid);
   switch (R) {
-    case 1: k_propagate_weight<1><<<grid, K1_THREADS, 0, s>>>(a); break;
-    case 2: k_propagate_weight<2><<<grid, K1_THREADS, 0, s>>>(a); break;
-    case 3: k_propagate_weight<3><<<grid, K1_THREADS, 0, s>>>(a); break;
-    case 4: k_propagate_weight<4><<<grid, K1_THREADS, 0, s>>>(a); break;
-    case 5: k_propagate_weight<5><<<grid, K1_THREADS, 0, s>>>(a); break;
-    case 6: k_propagate_weight<6><<<grid, K1_THREADS, 0, s>>>(a); break;
-    case 7: k_propagate_weight<7><<<grid, K1_THREADS, 0, s>>>(a); break;
+    case 1: return launch_propagate_r<1>(a, g, pdl, s);
+    case 2: return launch_propagate_r<2>(a, g, pdl, s);
+    case 3: return launch_propagate_r<3>(a, g, pdl, s);
+    case 4: return launch_propagate_r<4>(a, g, pdl, s);
+    case 5: return launch_propagate_r<5>(a, g, pdl, s);
+    case 6: return launch_propagate_r<6>(a, g, pdl, s);
+    case 7: return launch_propagate_r<7>(a, g, pdl, s);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
-cudaError_t launch_resample(const ResampleArgs& a, int n_groups, int cluster, cudaStream_t s) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(n_groups * cluster));
-  cfg.blockDim = dim3(RS_THREADS);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)cluster;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_resample, a);
+cudaError_t launch_resample(const ResampleArgs& a, int n_groups, int cluster, bool pdl, cudaStream_t s) {
+  return launch_ex(k_resample, dim3((unsigned)(n_groups * cluster)), dim3(RS_THREADS), cluster, pdl, s, a);
 }
 
-cudaError_t launch_global(const GlobalArgs& a, int n_tracks, int max_G, cudaStream_t s) {
-  const int threads = ((max_G + 31) / 32) * 32;
-  k_global<<<n_tracks, threads < 32 ? 32 : threads, 0, s>>>(a);
+cudaError_t launch_global(const GlobalArgs& a, int n_tracks, cudaStream_t s) {
+  k_global<<<n_tracks, GL_THREADS, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -55,9 +55,25 @@ struct K1Args {
   float* tile_part;     // 8 floats per tile
   const float* ypad;
   const CUtensorMap* tmaps;  // one per track over its padded frame, or nullptr
-  int* ring_next;            // per track: ring order of step k+1 (ARNA)
+  int* ring_next;            // two buffers (by step parity) of G_total: ring order of step k+1 (ARNA)
+  int ring_stride;           // G_total
   int n_ring_blocks;         // leading blocks that draw ring orders
   int n_tracks;
+  TrackParams p0;            // n_tracks == 1: a copy of trk[0]
+};
+
+struct GlobalArgs {
+  const TrackParams* trk;
+  TrackState* ts;
+  GroupState* gs;
+  int* ring;
+  const int* ring_next;  // two buffers by step parity: ring of the next step, drawn by the propagate kernel
+  int ring_stride;
+  HistRec* hist;
+  GroupHist* ghist;
+  int history;
+  int finalize;  // 0: prepare step 0 only
+  DevState* ds;
 };
 
 struct ResampleArgs {
@@ -71,19 +87,8 @@ struct ResampleArgs {
   int local_idx;               // 1: ancestors within the group
   QuantCoeffs qc;
   DevState* ds;
-};
-
-struct GlobalArgs {
-  const TrackParams* trk;
-  TrackState* ts;
-  GroupState* gs;
-  int* ring;
-  const int* ring_next;  // ring of the next step, drawn by the propagate kernel
-  HistRec* hist;
-  GroupHist* ghist;
-  int history;
-  int finalize;  // 0: prepare step 0 only
-  DevState* ds;
+  int fuse_global;             // 1: the last group of a track to finish runs its global step
+  GlobalArgs glob;             // (fuse_global) arguments of that step, finalize = 1
 };
 
 // pf_backward (pf_adjoint.cu)
@@ -148,11 +153,15 @@ cudaError_t launch_adjoint_groups(double* dlam, double* D, int G_total, cudaStre
 cudaError_t launch_grad_out(const double* g, const double* lz, float* out, double* lz_out, int n, cudaStream_t s);
 
 cudaError_t launch_init(const InitArgs& a, int grid, cudaStream_t s);
-cudaError_t launch_frame_prep(const FrameArgs& a, int nt, int blocks_x, cudaStream_t s);
-cudaError_t launch_frame_prep_table(const FrameTableArgs& a, int blocks_x, cudaStream_t s);
-cudaError_t launch_propagate(const K1Args& a, int R, int grid, cudaStream_t s);
-cudaError_t launch_resample(const ResampleArgs& a, int n_groups, int cluster, cudaStream_t s);
-cudaError_t launch_global(const GlobalArgs& a, int n_tracks, int max_G, cudaStream_t s);
+// The step launchers take `pdl`: launch with programmatic stream
+// serialization, so the kernel's CTAs may start while the previous kernel
+// in the stream drains; every step kernel waits (griddepcontrol.wait) for
+// that kernel's completion and memory before touching any buffer.
+cudaError_t launch_frame_prep(const FrameArgs& a, int nt, int blocks_x, bool pdl, cudaStream_t s);
+cudaError_t launch_frame_prep_table(const FrameTableArgs& a, int blocks_x, bool pdl, cudaStream_t s);
+cudaError_t launch_propagate(const K1Args& a, int R, int grid, bool pdl, cudaStream_t s);
+cudaError_t launch_resample(const ResampleArgs& a, int n_groups, int cluster, bool pdl, cudaStream_t s);
+cudaError_t launch_global(const GlobalArgs& a, int n_tracks, cudaStream_t s);
 cudaError_t launch_export_states(const float4* pv, const float* In, long long n, float* out, cudaStream_t s);
 cudaError_t k1_occupancy(int R, int* blocks_per_sm);
 const void* propagate_kernel(int R);

@@ -13,6 +13,12 @@
 
 namespace pf {
 
+// Programmatic dependent launch: wait for the previous kernel in the stream
+// (its completion and memory), and allow the next kernel to start.  Both
+// are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ float ex2(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -104,6 +110,24 @@ __device__ __forceinline__ void gauss_row(float cf, float x, float c, float kapp
   g[R] = ex2(-c * d * d);
   float up = ex2(-c * fmaf(2.0f, d, 1.0f));      // g(R+1) / g(R)
   float dn = ex2(c * fmaf(2.0f, d, -1.0f));      // g(R-1) / g(R)
+#pragma unroll
+  for (int a = 1; a <= R; ++a) {
+    g[R + a] = g[R + a - 1] * up;
+    g[R - a] = g[R - a + 1] * dn;
+    up *= kappa;
+    dn *= kappa;
+  }
+}
+
+// gauss_row scaled by `scale` (the spot intensity I): the centre value is
+// scale 2^(-c d^2) and the recurrence carries the factor.
+template <int R>
+__device__ __forceinline__ void gauss_row_scaled(float cf, float x, float c, float kappa, float scale,
+                                                 float (&g)[2 * R + 1]) {
+  const float d = cf - x;
+  g[R] = scale * ex2(-c * d * d);
+  float up = ex2(-c * fmaf(2.0f, d, 1.0f));
+  float dn = ex2(c * fmaf(2.0f, d, -1.0f));
 #pragma unroll
   for (int a = 1; a <= R; ++a) {
     g[R + a] = g[R + a - 1] * up;
