@@ -75,6 +75,7 @@ struct pf_handle {
   int graph_T = 0;
   int k1_occ = 1, sms = 1;
   bool pdl = true;  // programmatic dependent launch between the step kernels
+  void* encode = nullptr;  // cuTensorMapEncodeTiled, or nullptr
   // kernel timing (pf_profile_enable / pf_profile_read)
   int prof = 0;
   std::vector<cudaEvent_t> ev[PF_KERNEL_COUNT];  // start, stop, start, stop, ...
@@ -320,8 +321,44 @@ pf_status sync(pf_handle* h) {
 K1Args k1_args(const pf_handle* h) {
   K1Args a{h->trk, h->tiles, h->n_tiles, h->gs, h->ts, h->ds, h->pv[0], h->pv[1], h->In[0], h->In[1],
            h->anc, h->parent, h->history, h->lw, h->tile_part, h->ypad, h->tmaps, h->ring_next,
-           h->G_total, h->n_ring_blocks, h->n_tracks, TrackParams{}};
+           h->G_total, h->n_ring_blocks, h->n_tracks, -1, 0, TrackParams{}, 0, nullptr, CUtensorMap{}};
   a.p0 = h->tp[0];
+  return a;
+}
+
+// A single-track step reads the caller's frame directly (no frame
+// preparation kernel) when a TMA descriptor can describe it: the driver
+// entry point is available, the frame starts on 16 bytes, its rows are a
+// multiple of 16 bytes and it holds at least one staging box.  Sets the
+// descriptor in `a` and returns true, else leaves `a` unchanged.
+bool raw_frame_map(const pf_handle* h, const float* frame, K1Args* a) {
+  if (h->n_tracks != 1 || !h->encode || !frame) return false;
+  const pf_track_config& c = h->cfg[0];
+  if (((uintptr_t)frame & 15) != 0 || (c.W % 4) != 0 || c.W < ROI_W || c.H < ROI_BOX_H) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)c.W, (cuuint64_t)c.H};
+  cuuint64_t strides[1] = {(cuuint64_t)c.W * sizeof(float)};
+  cuuint32_t box[2] = {(cuuint32_t)ROI_W, (cuuint32_t)ROI_BOX_H};
+  cuuint32_t estr[2] = {1, 1};
+  CUtensorMap m;
+  const CUresult r = ((PFN_cuTensorMapEncodeTiled_v12000)h->encode)(
+      &m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)frame, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return false;
+  a->raw_frame = 1;
+  a->zraw = frame;
+  a->zmap = m;
+  return true;
+}
+
+// k1_args for a step enqueued by the host at step index h->steps_run: the
+// propagate kernel may draw its noise before waiting for the previous kernel.
+K1Args k1_args_hinted(const pf_handle* h) {
+  K1Args a = k1_args(h);
+  if (h->steps_run >= 1) {
+    const int per_cta = (h->n_tiles + h->k1_grid - 1) / h->k1_grid;
+    a.k_hint = h->steps_run;
+    a.noise_tiles = per_cta < K1_NOISE_TILES ? per_cta : K1_NOISE_TILES;
+  }
   return a;
 }
 
@@ -515,6 +552,7 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
       ok = (r == CUDA_SUCCESS);
     }
     if (!ok) h->tmaps = nullptr;
+    if (ok) h->encode = fn;
   }
   cudaError_t e;
   if ((e = cudaMemsetAsync(w, 0, L.total, s)) != cudaSuccess) { pf_destroy(h); return cuda_fail(nullptr, e, "cudaMemsetAsync"); }
@@ -568,11 +606,14 @@ pf_status pf_step(pf_handle* h, const float* const* frames, void* stream) {
     if (!frames[t]) return fail(h, PF_ERR_ARG, "frame pointer of track " + std::to_string(t) + " is NULL");
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
-  if ((e = mark(h, PF_KERNEL_FRAME_PREP, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
-  if ((e = prep_frames(h, frames, s)) != cudaSuccess) return cuda_fail(h, e, "k_frame_prep");
-  if ((e = mark(h, PF_KERNEL_FRAME_PREP, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
+  K1Args k1 = k1_args_hinted(h);
+  if (!raw_frame_map(h, frames[0], &k1)) {
+    if ((e = mark(h, PF_KERNEL_FRAME_PREP, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
+    if ((e = prep_frames(h, frames, s)) != cudaSuccess) return cuda_fail(h, e, "k_frame_prep");
+    if ((e = mark(h, PF_KERNEL_FRAME_PREP, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
+  }
   if ((e = mark(h, PF_KERNEL_PROPAGATE_WEIGHT, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
-  if ((e = launch_propagate(k1_args(h), h->R, h->k1_grid + h->n_ring_blocks, h->pdl, s)) != cudaSuccess)
+  if ((e = launch_propagate(k1, h->R, h->k1_grid + h->n_ring_blocks, h->pdl, s)) != cudaSuccess)
     return cuda_fail(h, e, "k_propagate_weight");
   if ((e = mark(h, PF_KERNEL_PROPAGATE_WEIGHT, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
   if ((e = mark(h, PF_KERNEL_RESAMPLE, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
@@ -794,7 +835,7 @@ pf_status pf_exchange_stats(pf_handle* h, int32_t track, int32_t step, pf_step_s
     if (e != cudaSuccess) return cuda_fail(h, e, "reading group history");
     for (int m = 0; m < P.G; ++m) {
       if (ring_host) ring_host[m] = gh[m].ring;
-      if (logW_host) logW_host[m] = gh[m].logW;
+      if (logW_host) logW_host[m] = (double)gh[m].logW;
       if (xhat_host)
         for (int d = 0; d < 5; ++d) xhat_host[d * P.G + m] = gh[m].xs[d];
       if (ess_host) ess_host[m] = gh[m].ess;

@@ -22,6 +22,7 @@ constexpr int K1_TILE = K1_THREADS * K1_PPT;  // slots per tile (one group)
 #define PF_K1_MIN_BLOCKS 4
 #endif
 constexpr int K1_MIN_BLOCKS = PF_K1_MIN_BLOCKS;  // resident propagate CTAs per SM the register budget targets
+constexpr int K1_NOISE_TILES = 4;     // tiles per propagate CTA whose noise may be drawn ahead
 constexpr int ROI_W = 40;             // staged frame box width = smem row pitch (floats, = 8 mod 32 banks)
 constexpr int ROI_BOX_H = 8;          // rows per TMA box
 constexpr int ROI_MAX_BOXES = 8;      // staged rows <= 64
@@ -85,7 +86,7 @@ struct TrackState {
 
 // Per-group state (global group index).
 struct GroupState {
-  double lambda;        // carried log group weight log W^(m) (an FP32 value)
+  float lambda;         // carried log group weight log W^(m)
   float off;            // log w offset of particles originating here at step k
   int pred;             // group (track-local) that sends to this one at step k
   uint32_t exo;         // exchange offset o_g of step k
@@ -118,7 +119,7 @@ struct HistRec {
 
 // Per-group history entry.
 struct GroupHist {
-  double logW;      // log W^(m) after the step
+  float logW;       // log W^(m) after the step
   int ring;         // group at ring position p used at the step
   float xs[5];
   float ess;
@@ -251,6 +252,25 @@ struct Thresholds {
     F1 = F / np;
     F0 = (uint32_t)(F - F1 * np);
     M = np > 1 ? (~0ull) / np + 1ull : 0ull;
+  }
+  // The same with the divisions by np done through m = ceil(2^64 / np)
+  // (fastdiv_magic): q = floor(n m / 2^64) is floor(n / np) or one more
+  // (n < 2^64), fixed by one product.
+  __device__ __forceinline__ static unsigned long long udiv(unsigned long long n, uint32_t np,
+                                                            unsigned long long m) {
+    if (np <= 1) return n;
+    unsigned long long q = __umul64hi(n, m);
+    if (q * np > n) --q;
+    return q;
+  }
+  __device__ __forceinline__ void init_magic(unsigned long long Q, uint32_t np, uint32_t u, unsigned long long m) {
+    Np = np;
+    M = np > 1 ? m : 0ull;
+    A = udiv(Q, np, M);
+    B = (uint32_t)(Q - A * np);
+    const unsigned long long F = (unsigned long long)u * (Q >> 32) + (((unsigned long long)u * (uint32_t)Q) >> 32);
+    F1 = udiv(F, np, M);
+    F0 = (uint32_t)(F - F1 * np);
   }
   __device__ __forceinline__ unsigned long long T(uint32_t j) const {
     const unsigned long long n = (unsigned long long)j * B + F0;

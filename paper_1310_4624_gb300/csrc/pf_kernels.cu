@@ -20,6 +20,7 @@
 // The step index lives on the device, so the same launch sequence serves
 // every step.
 #include <cooperative_groups.h>
+#include <mutex>
 #include <utility>
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -225,6 +226,19 @@ __device__ __forceinline__ void prefetch_tile(const K1Args& a, int4 td, int k, c
   prefetch_l2(I_prev + i0, sizeof(float) * (size_t)td.w);
 }
 
+// The five process-noise normals of slot j of group g at step k (Alg. 1
+// step P): Philox stream PROP, calls 0 and 1, Box-Muller on word pairs.
+__device__ __forceinline__ void prop_noise(uint32_t key0, uint32_t key1, uint32_t tag, int j, int g, int k,
+                                           float (&e)[5]) {
+  uint4 w0 = make_uint4(j, g, k, tag | (ST_PROP << 4) | 0u);
+  uint4 w1 = make_uint4(j, g, k, tag | (ST_PROP << 4) | 1u);
+  philox2(key0, key1, w0, w1);
+  float e5;
+  box_muller_fast(w0.x, w0.y, e[0], e[1]);
+  box_muller_fast(w0.z, w0.w, e[2], e[3]);
+  box_muller_fast(w1.x, w1.y, e[4], e5);
+}
+
 // Propagate + weight: tiles of K1_TILE = K1_PPT x K1_THREADS slots of one
 // group, K1_PPT particles per thread.  Each tile stages the bounding box of
 // its particles' patches (padded frame coordinates) into shared memory with
@@ -232,6 +246,11 @@ __device__ __forceinline__ void prefetch_tile(const K1Args& a, int4 td, int k, c
 // frame through L1.  Leading blocks draw the next step's ARNA rings.
 // SINGLE: one track, whose parameters come from the kernel's constant
 // parameter block (a.p0) instead of global memory.
+// With a.k_hint >= 1 (the host's step index) the CTA draws the process
+// noise of its first a.noise_tiles tiles into shared memory before waiting
+// for the previous kernel: that work depends only on the seed, the slots
+// and the step index, so it overlaps the previous kernel's tail.  After the
+// wait the staged noise is used only if the device's step index agrees.
 template <int R, bool SINGLE>
 __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(const __grid_constant__ K1Args a) {
   constexpr int D = 2 * R + 1;
@@ -242,10 +261,33 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
   __shared__ float s_red[NW][8];
   __shared__ int s_box[NW][4];
   __shared__ int s_key[NW];
+  extern __shared__ float s_noise[];  // [noise_tiles][K1_PPT][5][K1_THREADS]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int stride = (int)gridDim.x - a.n_ring_blocks;
+  int tile = (int)blockIdx.x - a.n_ring_blocks;
+  const int kh = a.k_hint;
+  if (kh >= 1 && tile >= 0) {
+    int i = 0;
+    for (int t = tile; i < a.noise_tiles && t < a.n_tiles; t += stride, ++i) {
+      const int4 td = a.tiles[t];
+      const TrackParams& P = SINGLE ? a.p0 : a.trk[td.x];
+#pragma unroll
+      for (int q = 0; q < K1_PPT; ++q) {
+        const int jj = threadIdx.x + q * K1_THREADS;
+        if (jj < td.w) {
+          float e[5];
+          prop_noise(P.key0, P.key1, P.tag, td.z + jj, td.y, kh, e);
+          float* dst = s_noise + (size_t)((i * K1_PPT + q) * 5) * K1_THREADS + threadIdx.x;
+#pragma unroll
+          for (int c = 0; c < 5; ++c) dst[c * K1_THREADS] = e[c];
+        }
+      }
+    }
+  }
   grid_dep_wait();
   grid_dep_launch();
   const int k = a.ts[0].k;
+  const bool staged_noise = kh >= 1 && kh == k;
   const float4* __restrict__ pv_prev = (k & 1) ? a.pv0 : a.pv1;
   const float* __restrict__ I_prev = (k & 1) ? a.I0 : a.I1;
   float4* __restrict__ pv_cur = (k & 1) ? a.pv1 : a.pv0;
@@ -267,8 +309,6 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
     }
     return;
   }
-  const int stride = (int)gridDim.x - a.n_ring_blocks;
-  int tile = (int)blockIdx.x - a.n_ring_blocks;
   if (threadIdx.x == 0) {
     mbar_init(&s_bar, 1);
     fence_proxy_async();
@@ -280,7 +320,7 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
   const int nex1 = SINGLE && k > 0 ? a.ts[0].n_ex : 0;
   const unsigned long long mnex1 = SINGLE ? a.ts[0].m_nex : 0ull;
 
-  auto run_tile = [&](const TrackParams& P, const int4 td) {
+  auto run_tile = [&](const TrackParams& P, const int4 td, const int ti) {
     const int g = td.y, Np = P.Np;
     const GroupState* __restrict__ gs = a.grp + P.group_off;
     const int nex = SINGLE ? nex1 : (k > 0 ? a.ts[td.x].n_ex : 0);
@@ -332,18 +372,19 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
         }
         if (k > 0) {
           // Alg. 1 step P: nearly constant velocity, unit frame interval
-          uint4 w0 = make_uint4(j, g, k, P.tag | (ST_PROP << 4) | 0u);
-          uint4 w1 = make_uint4(j, g, k, P.tag | (ST_PROP << 4) | 1u);
-          philox2(P.key0, P.key1, w0, w1);
-          float e0, e1, e2, e3, e4, e5;
-          box_muller_fast(w0.x, w0.y, e0, e1);
-          box_muller_fast(w0.z, w0.w, e2, e3);
-          box_muller_fast(w1.x, w1.y, e4, e5);
-          s[q].x = fmaf(P.spos, e0, s[q].x + s[q].z);
-          s[q].y = fmaf(P.spos, e1, s[q].y + s[q].w);
-          s[q].z = fmaf(P.sv, e2, s[q].z);
-          s[q].w = fmaf(P.sv, e3, s[q].w);
-          I[q] = fmaf(P.sI, e4, I[q]);
+          float e[5];
+          if (staged_noise && ti < a.noise_tiles) {
+            const float* src = s_noise + (size_t)((ti * K1_PPT + q) * 5) * K1_THREADS + threadIdx.x;
+#pragma unroll
+            for (int c = 0; c < 5; ++c) e[c] = src[c * K1_THREADS];
+          } else {
+            prop_noise(P.key0, P.key1, P.tag, j, g, k, e);
+          }
+          s[q].x = fmaf(P.spos, e[0], s[q].x + s[q].z);
+          s[q].y = fmaf(P.spos, e[1], s[q].y + s[q].w);
+          s[q].z = fmaf(P.sv, e[2], s[q].z);
+          s[q].w = fmaf(P.sv, e[3], s[q].w);
+          I[q] = fmaf(P.sI, e[4], I[q]);
         }
         pvc_t[il] = s[q];
         Ic_t[il] = I[q];
@@ -378,16 +419,23 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
       vmin = min(vmin, s_box[w][2]);
       vmax = max(vmax, s_box[w][3]);
     }
-    const int u0 = umin & ~3;
+    // raw frame: the box's left edge on a 4-float boundary of the frame
+    // (a TMA requirement), in padded coordinates
+    const bool raw = SINGLE && a.raw_frame;
+    const int u0 = raw ? (((umin - PAD) & ~3) + PAD) : (umin & ~3);
     const int nbox = (vmax + D - vmin + ROI_BOX_H - 1) / ROI_BOX_H;
-    const bool staged = a.tmaps != nullptr && (umax + D - u0) <= ROI_W && nbox <= ROI_MAX_BOXES;
+    const bool staged = (raw || a.tmaps != nullptr) && (umax + D - u0) <= ROI_W && nbox <= ROI_MAX_BOXES;
 
     if (staged) {
       if (threadIdx.x == 0) {
         fence_proxy_async();  // earlier generic reads of s_roi before the async-proxy writes
         mbar_expect_tx(&s_bar, (uint32_t)(nbox * ROI_W * ROI_BOX_H * sizeof(float)));
-        for (int b = 0; b < nbox; ++b)
-          tma_load_2d(&s_roi[0][b * ROI_W * ROI_BOX_H], a.tmaps + td.x, u0, vmin + b * ROI_BOX_H, &s_bar);
+        for (int b = 0; b < nbox; ++b) {
+          if (raw)
+            tma_load_2d(&s_roi[0][b * ROI_W * ROI_BOX_H], &a.zmap, u0 - PAD, vmin - PAD + b * ROI_BOX_H, &s_bar);
+          else
+            tma_load_2d(&s_roi[0][b * ROI_W * ROI_BOX_H], a.tmaps + td.x, u0, vmin + b * ROI_BOX_H, &s_bar);
+        }
       }
       const bool ok = mbar_wait(&s_bar, phase);
       if (__syncthreads_or(!ok)) {
@@ -400,6 +448,30 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
         return false;
       }
       phase ^= 1u;
+      if (raw) {
+        // y = z - b inside the frame, 0 outside (the copy filled zeros there)
+        const int rows = nbox * ROI_BOX_H, x0 = u0 - PAD, y0 = vmin - PAD;
+        const bool inside = x0 >= 0 && y0 >= 0 && x0 + ROI_W <= P.W && y0 + rows <= P.H;
+        float4* roi4 = reinterpret_cast<float4*>(&s_roi[0][0]);
+        for (int e = threadIdx.x; e < rows * (ROI_W / 4); e += K1_THREADS) {
+          float4 v = roi4[e];
+          if (inside) {
+            v.x = __fsub_rn(v.x, P.bg);
+            v.y = __fsub_rn(v.y, P.bg);
+            v.z = __fsub_rn(v.z, P.bg);
+            v.w = __fsub_rn(v.w, P.bg);
+          } else {
+            const int r = e / (ROI_W / 4), xc = x0 + (e - r * (ROI_W / 4)) * 4;
+            const bool rin = (unsigned)(y0 + r) < (unsigned)P.H;
+            v.x = rin && (unsigned)(xc + 0) < (unsigned)P.W ? __fsub_rn(v.x, P.bg) : 0.0f;
+            v.y = rin && (unsigned)(xc + 1) < (unsigned)P.W ? __fsub_rn(v.y, P.bg) : 0.0f;
+            v.z = rin && (unsigned)(xc + 2) < (unsigned)P.W ? __fsub_rn(v.z, P.bg) : 0.0f;
+            v.w = rin && (unsigned)(xc + 3) < (unsigned)P.W ? __fsub_rn(v.w, P.bg) : 0.0f;
+          }
+          roi4[e] = v;
+        }
+        __syncthreads();
+      }
     }
 
     // Alg. 1 step U with the renormalised carried weight (Alg. 3 step 4)
@@ -415,6 +487,8 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
         float ss;
         if (staged) {
           ss = patch_ss<R, true>(&s_roi[0][(pv[q] - vmin) * ROI_W + (pu[q] - u0)], 0, gxI, dy, P.c_psf, P.kappa);
+        } else if (raw) {
+          ss = patch_ss_raw<R>(a.zraw, P.W, P.H, P.bg, pu[q] - PAD, pv[q] - PAD, gxI, dy, P.c_psf, P.kappa);
         } else {
           ss = patch_ss<R, false>(a.ypad + P.ypad_off + (long long)pv[q] * P.pitch + pu[q], P.pitch, gxI, dy,
                                   P.c_psf, P.kappa);
@@ -466,14 +540,14 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
     return true;
   };
 
-  for (; tile < a.n_tiles; tile += stride) {
+  for (int ti = 0; tile < a.n_tiles; tile += stride, ++ti) {
     const int4 td = a.tiles[tile];
     if (threadIdx.x == 0 && tile + stride < a.n_tiles) prefetch_tile(a, a.tiles[tile + stride], k, pv_prev, I_prev);
     bool ok;
     if constexpr (SINGLE)
-      ok = run_tile(a.p0, td);
+      ok = run_tile(a.p0, td, ti);
     else
-      ok = run_tile(a.trk[td.x], td);
+      ok = run_tile(a.trk[td.x], td, ti);
     if (!ok) return;
   }
 }
@@ -496,7 +570,7 @@ struct GlobalScratch {
   float f[32];
   int i[32];
   float red[32][6];
-  double d[32][2];
+  unsigned long long w[32][2];
   float tot[6];
   double pe;
   int ring[MAX_G];
@@ -526,6 +600,7 @@ __device__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
   GroupState* __restrict__ gs = a.gs + group_off;
   int* __restrict__ ring = a.ring + group_off;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwa = G > NT ? NW : (G + 31) / 32;  // warps holding groups
   const int k1 = a.finalize ? k + 1 : 0;
   const int* __restrict__ rnext_buf = a.ring_next + (size_t)(k1 & 1) * a.ring_stride + group_off;
 
@@ -593,8 +668,7 @@ __device__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
   __syncthreads();
   mx = -INFINITY;
   deg = 0;
-#pragma unroll
-  for (int w = 0; w < NW; ++w) {
+  for (int w = 0; w < nwa; ++w) {
     mx = fmaxf(mx, sc.f[w]);
     deg += sc.i[w];
   }
@@ -604,10 +678,12 @@ __device__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
     for (int i = 0; i < GPT; ++i) lam[i] = (threadIdx.x + i * NT < G) ? 0.0f : -INFINITY;
     mx = 0.0f;
   }
-  // one pass: FP32 sums for log c and the estimate, FP64 sums for Eq. 4
-  // (the exchange count is an integer decided in FP64 on both sides)
+  // one pass: FP32 sums for log c and the estimate; for Eq. 4 the FP64
+  // weights w = e^(lam - max) in (0, 1] and their squares, summed exactly
+  // as 2^-52 fixed-point integers (at most G 2^52 < 2^63), so the sums need
+  // no FP64 additions; the exchange count is decided in FP64 from them.
   float acc[6] = {0, 0, 0, 0, 0, 0};
-  double dw = 0.0, dw2 = 0.0;
+  unsigned long long iw = 0, iw2 = 0;
 #pragma unroll
   for (int i = 0; i < GPT; ++i) {
     if (threadIdx.x + i * NT < G) {
@@ -616,19 +692,19 @@ __device__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
 #pragma unroll
       for (int q = 0; q < 5; ++q) acc[1 + q] = fmaf(wf, xs[i][q], acc[1 + q]);
       const double w = exp((double)lam[i] - (double)mx);
-      dw += w;
-      dw2 += w * w;
+      iw += __double2ull_rn(w * 4503599627370496.0);
+      iw2 += __double2ull_rn(w * w * 4503599627370496.0);
     }
   }
 #pragma unroll
   for (int q = 0; q < 6; ++q) acc[q] = warp_sum(acc[q]);
-  dw = warp_sum_d(dw);
-  dw2 = warp_sum_d(dw2);
+  iw = warp_sum_u64(iw);
+  iw2 = warp_sum_u64(iw2);
   if (lane == 0) {
 #pragma unroll
     for (int q = 0; q < 6; ++q) sc.red[warp][q] = acc[q];
-    sc.d[warp][0] = dw;
-    sc.d[warp][1] = dw2;
+    sc.w[warp][0] = iw;
+    sc.w[warp][1] = iw2;
   }
   const bool shuffled = (mode == MODE_ARNA) && k1 >= 1 && G > 1;
 #pragma unroll
@@ -639,18 +715,17 @@ __device__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
   __syncthreads();
   if (threadIdx.x < 6) {
     float x = 0.0f;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) x += sc.red[w][threadIdx.x];
+    for (int w = 0; w < nwa; ++w) x += sc.red[w][threadIdx.x];
     sc.tot[threadIdx.x] = x;
   }
   if (threadIdx.x == (NW > 1 ? 32 : 7)) {
-    double sw = 0.0, sw2 = 0.0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) {
-      sw += sc.d[w][0];
-      sw2 += sc.d[w][1];
+    unsigned long long s1 = 0, s2 = 0;
+    for (int w = 0; w < nwa; ++w) {
+      s1 += sc.w[w][0];
+      s2 += sc.w[w][1];
     }
-    const double pe = sw * sw / sw2;  // Eq. 4 for the next step
+    const double sw = (double)s1, sw2 = (double)s2;
+    const double pe = sw * sw / sw2 * 2.220446049250313e-16;  // Eq. 4 for the next step (scales 2^-52)
     // exchange count for step k1 (Eq. 3 with the Sec. V-A cut-off)
     int nex = 0;
     if (k1 >= 1 && G > 1) {
@@ -685,7 +760,7 @@ __device__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
       if (m < G) {
         GroupHist& gh = a.ghist[ghist_off + (long long)hslot * G + m];
         gh.ring = ring_m[i];
-        gh.logW = all_degenerate ? -INFINITY : (double)lam[i];
+        gh.logW = all_degenerate ? -INFINITY : lam[i];
 #pragma unroll
         for (int q = 0; q < 5; ++q) gh.xs[q] = xs[i][q];
         gh.ess = ess[i];
@@ -723,7 +798,7 @@ __device__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
       if (nex > 0 && !exo_ok[i]) set_error(a.ds, ERR_DRAW, 2u, (uint32_t)t, (uint32_t)m);
       gs[m].exo = nex > 0 ? exo[i] : 0u;
       gs[m].u = uw[i];
-      gs[m].lambda = all_degenerate ? 0.0 : (double)lam[i];
+      gs[m].lambda = all_degenerate ? 0.0f : lam[i];
       gs[m].off = lam[i] - log_np - lse;
     }
   }
@@ -838,9 +913,14 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
       if (a.q_out) a.q_out[d.base + i] = 0ull;
     }
   } else {
-    // the threshold constants need three 64-bit divisions (a long software
-    // sequence): one thread computes them for the CTA
-    if (threadIdx.x == 0) s_th.init(Q, (uint32_t)Np, u);
+    // the threshold constants: one thread computes them for the CTA, with
+    // the track's precomputed reciprocal of Np when it has one
+    if (threadIdx.x == 0) {
+      if (a.glob.trk)
+        s_th.init_magic(Q, (uint32_t)Np, u, a.glob.trk[d.track].m_Np);
+      else
+        s_th.init(Q, (uint32_t)Np, u);
+    }
     __syncthreads();
     const Thresholds th = s_th;
     const float inv_Q = 1.0f / u64_to_float_approx(Q);
@@ -1026,13 +1106,13 @@ cudaError_t launch_init(const InitArgs& a, int grid, cudaStream_t s) {
 
 // cudaLaunchKernelEx with an optional cluster shape and programmatic
 // stream serialization (see launch_* in pf_launch.h).
-template <typename... Params, typename... Args>
+template <typename... Params, typename Arg>
 static cudaError_t launch_ex(void (*kernel)(Params...), dim3 grid, dim3 block, int cluster, bool pdl,
-                             cudaStream_t s, Args&&... args) {
+                             cudaStream_t s, const Arg& arg, size_t smem = 0) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[2];
   int n = 0;
@@ -1050,7 +1130,7 @@ static cudaError_t launch_ex(void (*kernel)(Params...), dim3 grid, dim3 block, i
   }
   cfg.attrs = attr;
   cfg.numAttrs = n;
-  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+  return cudaLaunchKernelEx(&cfg, kernel, arg);
 }
 
 cudaError_t launch_frame_prep_table(const FrameTableArgs& a, int blocks_x, bool pdl, cudaStream_t s) {
@@ -1080,10 +1160,26 @@ const void* propagate_kernel(int R) {
   }
 }
 
+// Shared memory of the staged noise (k_propagate_weight, a.noise_tiles).
+size_t k1_dynamic_smem(int noise_tiles) { return (size_t)noise_tiles * K1_PPT * 5 * K1_THREADS * sizeof(float); }
+
+template <int R, bool SINGLE>
+static cudaError_t launch_propagate_rs(const K1Args& a, dim3 g, bool pdl, cudaStream_t s) {
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(k_propagate_weight<R, SINGLE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)k1_dynamic_smem(K1_NOISE_TILES));
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  return launch_ex(k_propagate_weight<R, SINGLE>, g, dim3(K1_THREADS), 0, pdl, s, a,
+                   k1_dynamic_smem(a.noise_tiles));
+}
+
 template <int R>
 static cudaError_t launch_propagate_r(const K1Args& a, dim3 g, bool pdl, cudaStream_t s) {
-  if (a.n_tracks == 1) return launch_ex(k_propagate_weight<R, true>, g, dim3(K1_THREADS), 0, pdl, s, a);
-  return launch_ex(k_propagate_weight<R, false>, g, dim3(K1_THREADS), 0, pdl, s, a);
+  if (a.n_tracks == 1) return launch_propagate_rs<R, true>(a, g, pdl, s);
+  return launch_propagate_rs<R, false>(a, g, pdl, s);
 }
 
 cudaError_t launch_propagate(const K1Args& a, int R, int grid, bool pdl, cudaStream_t s) {

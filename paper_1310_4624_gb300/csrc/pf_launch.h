@@ -59,7 +59,15 @@ struct K1Args {
   int ring_stride;           // G_total
   int n_ring_blocks;         // leading blocks that draw ring orders
   int n_tracks;
+  int k_hint;                // the host's step index, or -1 (read on the device)
+  int noise_tiles;           // tiles per CTA whose noise is drawn before the wait (<= K1_NOISE_TILES)
   TrackParams p0;            // n_tracks == 1: a copy of trk[0]
+  // n_tracks == 1 and raw_frame: the step reads the caller's frame (W x H
+  // float32, row pitch W) directly, through zmap (TMA, zero fill outside)
+  // or zraw, instead of the padded frame y = z - b.
+  int raw_frame;
+  const float* zraw;
+  CUtensorMap zmap;
 };
 
 struct GlobalArgs {
@@ -164,6 +172,7 @@ cudaError_t launch_resample(const ResampleArgs& a, int n_groups, int cluster, bo
 cudaError_t launch_global(const GlobalArgs& a, int n_tracks, cudaStream_t s);
 cudaError_t launch_export_states(const float4* pv, const float* In, long long n, float* out, cudaStream_t s);
 cudaError_t k1_occupancy(int R, int* blocks_per_sm);
+size_t k1_dynamic_smem(int noise_tiles);
 const void* propagate_kernel(int R);
 
 // Host helpers shared by the C-ABI entry points (defined in pf_api.cu).

@@ -189,6 +189,43 @@ __device__ __forceinline__ float patch_ss(const float* __restrict__ base, int pi
   return acc;
 }
 
+// patch_ss on the caller's frame z (W x H, pitch W) instead of the padded
+// frame: pixel values z - b inside the frame, 0 outside; (x0, y0) is the
+// patch's corner in frame coordinates.  Same pixels, values and order as
+// patch_ss on the padded frame.
+template <int R>
+__device__ __forceinline__ float patch_ss_raw(const float* __restrict__ z, int W, int H, float bg, int x0, int y0,
+                                              const float (&gxI)[2 * R + 1], float dy, float c, float kappa) {
+  auto row = [&](int b, float gy, float acc) {
+    const int yy = y0 + b;
+    const bool rin = (unsigned)yy < (unsigned)H;
+    const float* __restrict__ rp = z + (long long)(rin ? yy : 0) * W;
+#pragma unroll
+    for (int a = 0; a < 2 * R + 1; ++a) {
+      const int xx = x0 + a;
+      const float y = (rin && (unsigned)xx < (unsigned)W) ? __fsub_rn(__ldg(rp + xx), bg) : 0.0f;
+      const float r = fmaf(-gxI[a], gy, y);
+      acc = fmaf(r, r, acc);
+    }
+    return acc;
+  };
+  const float g = ex2(-c * dy * dy);
+  float up = ex2(-c * fmaf(2.0f, dy, 1.0f));
+  float dn = ex2(c * fmaf(2.0f, dy, -1.0f));
+  float acc = row(R, g, 0.0f);
+  float gu = g, gd = g;
+#pragma unroll
+  for (int a = 1; a <= R; ++a) {
+    gu *= up;
+    gd *= dn;
+    up *= kappa;
+    dn *= kappa;
+    acc = row(R + a, gu, acc);
+    acc = row(R - a, gd, acc);
+  }
+  return acc;
+}
+
 // Natural log of a uniform u = ((w >> 9) + 1/2) 2^-23: MUFU log2 where its
 // absolute error (2^-22 on [1/2, 2]) is small against |ln u|, and the series
 // -(t + t^2/2 + t^3/3), t = 1 - u, for the top 2^-10 of the interval.
