@@ -48,7 +48,9 @@ struct pf_handle {
   GroupHist* ghist = nullptr;
   int* ring = nullptr;
   int* ring_next = nullptr;
-  int n_ring_blocks = 0;
+  uint32_t* exo_next = nullptr;
+  int n_ring_blocks = 0;  // leading blocks of the propagate kernel
+  bool finish_pending = false;  // the last step's estimate / history not yet written (k_finish)
   int max_G = 1;
   uint32_t* parent = nullptr;
   DevState* ds = nullptr;
@@ -121,7 +123,8 @@ QuantCoeffs make_qc() {
 }
 
 struct Layout {
-  size_t trk, ts, gs, gd, tiles, pv0, pv1, I0, I1, anc, lw, tp, ypad, hist, ghist, ring, ring_next, parent, ds, tmap, total;
+  size_t trk, ts, gs, gd, tiles, pv0, pv1, I0, I1, anc, lw, tp, ypad, hist, ghist, ring, ring_next, exo_next, parent, ds,
+      tmap, total;
   size_t rp_pv, rp_I, ck_pv, ck_I, ca_pv0, ca_pv1, ca_I0, ca_I1, lam_hist, lbar_hist, dlam, Dacc, grad, logz, seed;
   bool adjoint = false;
   int adj_slots = 0, adj_ckpts = 0;
@@ -215,6 +218,7 @@ Layout plan(const pf_track_config* c, int n, int history) {
   L.gd = take(sizeof(GroupDesc) * L.G_total);
   L.ring = take(sizeof(int) * L.G_total);
   L.ring_next = take(sizeof(int) * 2 * (size_t)L.G_total);
+  L.exo_next = take(sizeof(uint32_t) * 2 * (size_t)L.G_total);
   L.tiles = take(sizeof(int4) * L.n_tiles);
   L.pv0 = take(sizeof(float4) * L.N_total);
   L.pv1 = take(sizeof(float4) * L.N_total);
@@ -312,7 +316,16 @@ cudaError_t prep_frames(pf_handle* h, const float* const* frames, cudaStream_t s
   return cudaSuccess;
 }
 
+GlobalArgs global_args(const pf_handle* h, int finalize);
+
+// Wait for the handle's last stream, after completing the last step's
+// estimate, log Z and history (k_finish) if no later step has done it.
 pf_status sync(pf_handle* h) {
+  if (h->finish_pending) {
+    const cudaError_t ef = launch_finish(global_args(h, 1), h->n_tracks, h->last_stream);
+    if (ef != cudaSuccess) return cuda_fail(h, ef, "k_finish");
+    h->finish_pending = false;
+  }
   cudaError_t e = cudaStreamSynchronize(h->last_stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
   return check_device(h);
@@ -321,7 +334,8 @@ pf_status sync(pf_handle* h) {
 K1Args k1_args(const pf_handle* h) {
   K1Args a{h->trk, h->tiles, h->n_tiles, h->gs, h->ts, h->ds, h->pv[0], h->pv[1], h->In[0], h->In[1],
            h->anc, h->parent, h->history, h->lw, h->tile_part, h->ypad, h->tmaps, h->ring_next,
-           h->G_total, h->n_ring_blocks, h->n_tracks, -1, 0, TrackParams{}, 0, nullptr, CUtensorMap{}};
+           h->G_total, h->exo_next, h->hist, h->ghist, h->n_ring_blocks, h->n_tracks, -1, 0, TrackParams{}, 0,
+           nullptr, CUtensorMap{}};
   a.p0 = h->tp[0];
   return a;
 }
@@ -363,7 +377,7 @@ K1Args k1_args_hinted(const pf_handle* h) {
 }
 
 GlobalArgs global_args(const pf_handle* h, int finalize) {
-  return GlobalArgs{h->trk, h->ts, h->gs, h->ring, h->ring_next, h->G_total, h->hist, h->ghist, h->history,
+  return GlobalArgs{h->trk, h->ts, h->gs, h->ring, h->ring_next, h->G_total, h->exo_next, h->hist, h->ghist, h->history,
                     finalize, h->ds};
 }
 
@@ -432,6 +446,7 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
   h->gd = (GroupDesc*)(w + L.gd);
   h->ring = (int*)(w + L.ring);
   h->ring_next = (int*)(w + L.ring_next);
+  h->exo_next = (uint32_t*)(w + L.exo_next);
   h->tiles = (int4*)(w + L.tiles);
   h->pv[0] = (float4*)(w + L.pv0);
   h->pv[1] = (float4*)(w + L.pv1);
@@ -576,7 +591,8 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
   h->k1_grid = (int)(h->n_tiles < want ? h->n_tiles : want);
   int n_arna = 0;
   for (int t = 0; t < n_tracks; ++t) n_arna += (cfg[t].mode == PF_ARNA && cfg[t].G > 1 && cfg[t].G <= RING_SMEM_G);
-  h->n_ring_blocks = n_arna == 0 ? 0 : (n_arna < 16 ? n_arna : 16);
+  (void)n_arna;
+  h->n_ring_blocks = n_tracks < 16 ? n_tracks : 16;
   for (int t = 0; t < n_tracks; ++t) h->max_G = cfg[t].G > h->max_G ? cfg[t].G : h->max_G;
   h->rs_cluster = resample_cluster(cfg[0].Np, n_tracks == 1);
 
@@ -621,6 +637,7 @@ pf_status pf_step(pf_handle* h, const float* const* frames, void* stream) {
     return cuda_fail(h, e, "k_resample");
   if ((e = mark(h, PF_KERNEL_RESAMPLE, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
   h->steps_run += 1;
+  h->finish_pending = true;
   h->last_stream = s;
   return PF_OK;
 }
@@ -643,6 +660,7 @@ pf_status pf_step_table(pf_handle* h, const float* const* table_dev, int32_t T_t
   if ((e = launch_frames_table(h, table_dev, T_table, s)) != cudaSuccess) return cuda_fail(h, e, "k_frame_prep_table");
   if ((e = launch_step_kernels(h, s)) != cudaSuccess) return cuda_fail(h, e, "step kernels");
   h->steps_run += 1;
+  h->finish_pending = true;
   h->last_stream = s;
   return PF_OK;
 }
@@ -682,6 +700,7 @@ pf_status pf_graph_step(pf_handle* h, const float* const* table_dev, int32_t T_t
   }
   if ((e = cudaGraphLaunch(h->graph, s)) != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
   h->steps_run += 1;
+  h->finish_pending = true;
   h->last_stream = s;
   return PF_OK;
 }
@@ -771,6 +790,7 @@ pf_status pf_autotune(pf_handle* h, const float* const* frames, int32_t* k1_grid
   // complete the step with the chosen shapes
   if ((e = launch_step_kernels(h, s)) != cudaSuccess) return cuda_fail(h, e, "step kernels");
   h->steps_run += 1;
+  h->finish_pending = true;
   h->last_stream = s;
   if (h->graph) {  // a captured step holds the old shapes
     cudaGraphExecDestroy(h->graph);
@@ -962,6 +982,7 @@ pf_status pf_reset(pf_handle* h, void* stream) {
   if ((e = launch_init(ia, h->k1_grid, s)) != cudaSuccess) return cuda_fail(h, e, "k_init");
   if ((e = launch_global(global_args(h, 0), h->n_tracks, s)) != cudaSuccess) return cuda_fail(h, e, "k_global");
   h->steps_run = 0;
+  h->finish_pending = false;
   h->failed = 0;
   h->last_stream = s;
   return PF_OK;

@@ -31,6 +31,9 @@ constexpr int RING_SMEM_G = ROI_FLOATS / 2;  // ring orders drawn ahead up to th
 constexpr int RS_THREADS = 512;       // resampler CTA
 constexpr int RS_ITEMS = 8;           // items per thread per resampler sub-chunk
 constexpr int RS_SUB = RS_THREADS * RS_ITEMS;
+constexpr int RS_OUT = RS_SUB;        // resampler ancestors staged per window
+__host__ __device__ constexpr int pad8(int i) { return i + (i >> 3); }  // shared index with one spare per 8
+constexpr int RS_SUB_PAD = pad8(RS_SUB);
 constexpr int GL_THREADS = 1024;      // per-track global-step CTA, one thread per group
 constexpr int MAX_G = GL_THREADS;      // groups per track
 constexpr int MAX_FRAMES_PER_LAUNCH = 1024;
@@ -80,8 +83,10 @@ struct TrackState {
   double log_Z;      // sum of log c
   float xhat[5];
   int steps_done;
-  unsigned long long m_nex;  // fast-division reciprocal of n_ex (see fastdiv)
   unsigned int ticket;       // groups resampled so far in the current step
+  int fin_k;                 // last step whose estimate / log Z / history are complete
+  int deg_k;                 // degenerate groups of step k - 1
+  float lse_k;               // log c of step k - 1 (FP32)
 };
 
 // Per-group state (global group index).

@@ -123,6 +123,339 @@ __global__ void k_frame_prep_table(FrameTableArgs a) {
   }
 }
 
+// ===================================================================== K5
+// Per track: the master PE's reduction (Alg. 3 steps 9-10) and weight carry
+// (step 8) for step k, then ring order (step 1) and exchange count (step 2)
+// for step k+1.  G-sized; the exchange count is decided in FP64.
+// log W^(m) = M + ln(Q 2^-40) in FP32: log2 Q from the leading-bit position
+// and the top 24 bits of Q.
+__device__ __forceinline__ float group_log_weight(float M, unsigned long long Q) {
+  const int e = 63 - __clzll((long long)Q);
+  const uint32_t top = e >= 23 ? (uint32_t)(Q >> (e - 23)) : (uint32_t)(Q << (23 - e));
+  const float l2 = (float)(e - 23) + log2f((float)top);  // log2 Q (top is exact in FP32)
+  return M + (l2 - 40.0f) * 0.693147182f;
+}
+
+// Scratch of the global step (shared memory of the CTA running it).
+struct GlobalScratch {
+  float f[32];
+  int i[32];
+  float red[32][6];
+  unsigned long long w[32][2];
+  float tot[6];
+  double pe;
+  int ring[MAX_G];
+};
+
+// The global step of track t by one CTA of NT threads, each thread owning
+// groups m = threadIdx.x + i NT: what the next step needs (group weights
+// carried as offsets, Eq. 3 / Eq. 4 exchange count, ring order and
+// exchange offsets, step index) plus the history fields that it is about to
+// overwrite.  The estimate, log c, log Z and the rest of the history follow
+// in finish_step, off the critical path.  finalize = 0 prepares step 0.
+// Per-group inputs are read through L2 (written by other CTAs of the same
+// launch when this runs as the resampler's tail).
+template <int NT>
+__device__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
+  constexpr int NW = NT / 32;
+  constexpr int GPT = (MAX_G + NT - 1) / NT;
+  // Every input first (the body then only computes and stores, so no load
+  // waits behind a store that might alias it).
+  const TrackParams* __restrict__ P = a.trk + t;
+  const int G = P->G, Np = P->Np, mode = P->mode, group_off = P->group_off, hist_off = P->hist_off;
+  const long long ghist_off = P->ghist_off;
+  const float cutoff = P->cutoff, ex_ratio = P->ex_ratio;
+  TrackState* __restrict__ T = a.ts + t;
+  const int k = __ldcg(&T->k);
+  const int nex_k = __ldcg(&T->n_ex);
+  const double pe_k = __ldcg(&T->pe_eff);
+  GroupState* __restrict__ gs = a.gs + group_off;
+  int* __restrict__ ring = a.ring + group_off;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwa = G > NT ? NW : (G + 31) / 32;  // warps holding groups
+  const int k1 = a.finalize ? k + 1 : 0;
+  const int* __restrict__ rnext_buf = a.ring_next + (size_t)(k1 & 1) * a.ring_stride + group_off;
+  const uint32_t* __restrict__ exo_buf = a.exo_next + (size_t)(k1 & 1) * a.ring_stride + group_off;
+
+  unsigned long long Q[GPT];
+  float Mg[GPT], lam[GPT];
+  int ring_m[GPT], rnext[GPT];
+  uint32_t exo[GPT];
+#pragma unroll
+  for (int i = 0; i < GPT; ++i) {
+    const int m = threadIdx.x + i * NT;
+    Q[i] = 0;
+    Mg[i] = 0.0f;
+    ring_m[i] = m;
+    rnext[i] = m;
+    exo[i] = 0;
+    if (m < G) {
+      Q[i] = __ldcg(&gs[m].Q);
+      Mg[i] = __ldcg(&gs[m].M);
+      ring_m[i] = __ldcg(&ring[m]);
+      rnext[i] = __ldcg(&rnext_buf[m]);
+      exo[i] = __ldcg(&exo_buf[m]);
+    }
+  }
+
+  // S7 -> S8: Lambda'_m in FP32 (finalize), or 0 (prepare step 0)
+  float mx = -INFINITY;
+  int deg = 0;
+#pragma unroll
+  for (int i = 0; i < GPT; ++i) {
+    const int m = threadIdx.x + i * NT;
+    lam[i] = -INFINITY;
+    if (m < G) {
+      if (a.finalize) {
+        lam[i] = Q[i] != 0 ? group_log_weight(Mg[i], Q[i]) : -INFINITY;
+        deg += (Q[i] == 0);
+      } else {
+        lam[i] = 0.0f;
+      }
+      mx = fmaxf(mx, lam[i]);
+    }
+  }
+  mx = warp_max(mx);
+  deg = __reduce_add_sync(0xffffffffu, deg);
+  if (lane == 0) {
+    sc.f[warp] = mx;
+    sc.i[warp] = deg;
+  }
+  __syncthreads();
+  mx = -INFINITY;
+  deg = 0;
+  for (int w = 0; w < nwa; ++w) {
+    mx = fmaxf(mx, sc.f[w]);
+    deg += sc.i[w];
+  }
+  const bool all_degenerate = a.finalize && deg == G;
+  if (all_degenerate) {  // every group lost its weight: restart from equal weights
+#pragma unroll
+    for (int i = 0; i < GPT; ++i) lam[i] = (threadIdx.x + i * NT < G) ? 0.0f : -INFINITY;
+    mx = 0.0f;
+  }
+  // FP32 sum for log c; for Eq. 4 the FP64 weights w = e^(lam - max) in
+  // (0, 1] and their squares, summed exactly as 2^-52 fixed-point integers
+  // (at most G 2^52 < 2^63); the exchange count is decided in FP64 on both
+  // sides.
+  float wsum = 0.0f;
+  unsigned long long iw = 0, iw2 = 0;
+#pragma unroll
+  for (int i = 0; i < GPT; ++i) {
+    if (threadIdx.x + i * NT < G) {
+      wsum += __expf(lam[i] - mx);
+      const double w = exp((double)lam[i] - (double)mx);
+      iw += __double2ull_rn(w * 4503599627370496.0);
+      iw2 += __double2ull_rn(w * w * 4503599627370496.0);
+    }
+  }
+  wsum = warp_sum(wsum);
+  iw = warp_sum_u64(iw);
+  iw2 = warp_sum_u64(iw2);
+  if (lane == 0) {
+    sc.red[warp][0] = wsum;
+    sc.w[warp][0] = iw;
+    sc.w[warp][1] = iw2;
+  }
+  const bool shuffled = (mode == MODE_ARNA) && k1 >= 1 && G > 1;
+#pragma unroll
+  for (int i = 0; i < GPT; ++i) {
+    const int m = threadIdx.x + i * NT;
+    if (m < G) sc.ring[m] = shuffled ? rnext[i] : m;  // ring order of step k1 (Sec. IV-B)
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float x = 0.0f;
+    for (int w = 0; w < nwa; ++w) x += sc.red[w][0];
+    sc.tot[0] = x;
+  }
+  if (threadIdx.x == (NW > 1 ? 32 : 7)) {
+    unsigned long long s1 = 0, s2 = 0;
+    for (int w = 0; w < nwa; ++w) {
+      s1 += sc.w[w][0];
+      s2 += sc.w[w][1];
+    }
+    const double sw = (double)s1, sw2 = (double)s2;
+    const double pe = sw * sw / sw2 * 2.220446049250313e-16;  // Eq. 4 for the next step (scales 2^-52)
+    // exchange count for step k1 (Eq. 3 with the Sec. V-A cut-off)
+    int nex = 0;
+    if (k1 >= 1 && G > 1) {
+      double rho;
+      if (mode == MODE_ARNA) {
+        if (!(pe < (double)cutoff * (double)G)) {
+          rho = 0.0;
+        } else {
+          rho = 0.5 - 0.5 * (pe - 1.0) / (double)(G - 1);
+          rho = fmin(fmax(rho, 0.0), 0.5);
+        }
+      } else {
+        rho = fmin(fmax((double)ex_ratio, 0.0), 1.0);
+      }
+      nex = (int)floor(rho * (double)Np);
+    }
+    sc.pe = pe;
+    sc.i[0] = nex;
+  }
+  __syncthreads();
+  const float lse = mx + logf(sc.tot[0]);  // LSE of the carried weights = log c_k
+  const double pe = sc.pe;
+  const int nex = sc.i[0];
+  const float log_np = logf((float)Np);
+
+  if (a.finalize) {
+    // history fields the next step overwrites: ring, exchange count, PE_eff
+    const int hslot = k % a.history;
+#pragma unroll
+    for (int i = 0; i < GPT; ++i) {
+      const int m = threadIdx.x + i * NT;
+      if (m < G) a.ghist[ghist_off + (long long)hslot * G + m].ring = ring_m[i];
+    }
+    if (threadIdx.x == 0) {
+      HistRec& h = a.hist[hist_off + hslot];
+      h.step = k;
+      h.n_ex = nex_k;
+      h.pe_eff = pe_k;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < GPT; ++i) {
+    const int m = threadIdx.x + i * NT;
+    if (m < G) {
+      const int rm = sc.ring[m];
+      ring[m] = rm;
+      gs[rm].pred = sc.ring[m == 0 ? G - 1 : m - 1];
+      gs[m].exo = nex > 0 ? exo[i] : 0u;
+      gs[m].lambda = lam[i];
+      gs[m].off = lam[i] - log_np - lse;
+    }
+  }
+  if (threadIdx.x == 0) {
+    T->n_ex = nex;
+    T->pe_eff = pe;
+    T->deg_k = a.finalize ? deg : 0;
+    T->lse_k = lse;
+    if (!a.finalize) T->fin_k = -1;
+    T->k = k1;
+  }
+}
+
+// The rest of the global step of the track's last finished step kd = k - 1
+// (Alg. 3 steps 9-10 and the history): global estimate from the group
+// estimates and carried weights, log c = the carried weights' LSE, log Z,
+// per-group history.  Run once per step (guarded by fin_k) by a leading
+// block of the next propagate launch, or by k_finish before the host reads
+// the statistics; one CTA of NT threads.
+template <int NT>
+__device__ void finish_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
+  constexpr int NW = NT / 32;
+  constexpr int GPT = (MAX_G + NT - 1) / NT;
+  const TrackParams* __restrict__ P = a.trk + t;
+  TrackState* __restrict__ T = a.ts + t;
+  const int kd = __ldcg(&T->k) - 1;
+  if (kd < 0 || __ldcg(&T->fin_k) >= kd) return;  // uniform over the CTA
+  const int G = P->G, group_off = P->group_off, hist_off = P->hist_off;
+  const long long ghist_off = P->ghist_off;
+  const int deg = __ldcg(&T->deg_k);
+  const float lse = __ldcg(&T->lse_k);
+  const double logZ_prev = __ldcg(&T->log_Z);
+  const int flags = __ldcg(&T->flags);
+  const GroupState* __restrict__ gs = a.gs + group_off;
+  const bool all_degenerate = deg == G;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwa = G > NT ? NW : (G + 31) / 32;
+
+  float lam[GPT], xs[GPT][5], ess[GPT];
+  float mx = -INFINITY;
+#pragma unroll
+  for (int i = 0; i < GPT; ++i) {
+    const int m = threadIdx.x + i * NT;
+    lam[i] = -INFINITY;
+    ess[i] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) xs[i][q] = 0.0f;
+    if (m < G) {
+      lam[i] = __ldcg(&gs[m].lambda);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) xs[i][q] = __ldcg(&gs[m].xs[q]);
+      ess[i] = __ldcg(&gs[m].ess);
+      mx = fmaxf(mx, lam[i]);
+    }
+  }
+  mx = warp_max(mx);
+  if (lane == 0) sc.f[warp] = mx;
+  __syncthreads();
+  mx = -INFINITY;
+  for (int w = 0; w < nwa; ++w) mx = fmaxf(mx, sc.f[w]);
+  float acc[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+  for (int i = 0; i < GPT; ++i) {
+    if (threadIdx.x + i * NT < G) {
+      const float wf = __expf(lam[i] - mx);
+      acc[0] += wf;
+#pragma unroll
+      for (int q = 0; q < 5; ++q) acc[1 + q] = fmaf(wf, xs[i][q], acc[1 + q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 6; ++q) acc[q] = warp_sum(acc[q]);
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < 6; ++q) sc.red[warp][q] = acc[q];
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    float x = 0.0f;
+    for (int w = 0; w < nwa; ++w) x += sc.red[w][threadIdx.x];
+    sc.tot[threadIdx.x] = x;
+  }
+  __syncthreads();
+  const int hslot = kd % a.history;
+#pragma unroll
+  for (int i = 0; i < GPT; ++i) {
+    const int m = threadIdx.x + i * NT;
+    if (m < G) {
+      GroupHist& gh = a.ghist[ghist_off + (long long)hslot * G + m];
+      gh.logW = all_degenerate ? -INFINITY : lam[i];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) gh.xs[q] = xs[i][q];
+      gh.ess = ess[i];
+    }
+  }
+  if (threadIdx.x == 0) {
+    const double logc = all_degenerate ? -INFINITY : (double)lse;
+    const double logZ = logZ_prev + logc;
+    float xq[5];
+    for (int q = 0; q < 5; ++q) xq[q] = all_degenerate ? NAN : sc.tot[1 + q] / sc.tot[0];
+    HistRec& h = a.hist[hist_off + hslot];
+    for (int q = 0; q < 5; ++q) h.xhat[q] = xq[q];
+    h.log_c = logc;
+    h.log_Z = logZ;
+    h.degenerate = deg;
+    T->log_c = logc;
+    T->log_Z = logZ;
+    for (int q = 0; q < 5; ++q) T->xhat[q] = xq[q];
+    T->degenerate = deg;
+    T->flags = flags | (all_degenerate ? 1 : 0);
+    T->steps_done = kd + 1;
+    T->fin_k = kd;
+  }
+}
+
+// Per track: the master PE's reduction (Alg. 3 steps 9-10) and weight carry
+// (step 8) for step k, then ring order (step 1) and exchange count (step 2)
+// for step k+1 (global_step; finalize = 0 prepares step 0).  During the run
+// the same step runs as the tail of the resampler.
+__global__ void __launch_bounds__(GL_THREADS) k_global(GlobalArgs a) {
+  __shared__ GlobalScratch sc;
+  global_step<GL_THREADS>(a, blockIdx.x, sc);
+}
+
+// finish_step for every track (one CTA each), before the host reads the
+// statistics of the last step.
+__global__ void __launch_bounds__(K1_THREADS) k_finish(GlobalArgs a) {
+  __shared__ GlobalScratch sc;
+  finish_step<K1_THREADS>(a, blockIdx.x, sc);
+}
+
 // ===================================================================== K1
 // Fisher-Yates ring order of step k (Sec. IV-B, Alg. 3 step 1) for one
 // track, by one warp: the bounded draws r_j in [0, j] in parallel, the
@@ -186,14 +519,14 @@ __device__ __forceinline__ void tma_load_2d(float* dst, const CUtensorMap* map, 
 // its own slot j (false); exchange_source with the group's exchange offsets
 // o_r (receiver) and o_s (sender) hoisted out of the particle loop.
 __device__ __forceinline__ bool exchange_from_pred(int j, int Np, int nex, uint32_t o_r, uint32_t o_s,
-                                                   unsigned long long mNp, unsigned long long mnex, int& src_j) {
+                                                   unsigned long long mNp, int& src_j) {
   src_j = j;
   if (nex <= 0) return false;
   if ((unsigned long long)Np * (unsigned long long)(nex + 1) < (1ull << 32)) {
     const uint32_t jn = (uint32_t)j * (uint32_t)nex;
     const uint32_t t = jn <= o_r ? 0u : fastdiv(jn - o_r + (uint32_t)Np - 1u, mNp);
     if (t < (uint32_t)nex && t * (uint32_t)Np + o_r < jn + (uint32_t)nex) {
-      src_j = (int)fastdiv(t * (uint32_t)Np + o_s, mnex);
+      src_j = (int)((t * (uint32_t)Np + o_s) / (uint32_t)nex);
       return true;
     }
     return false;
@@ -293,19 +626,32 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
   float4* __restrict__ pv_cur = (k & 1) ? a.pv1 : a.pv0;
   float* __restrict__ I_cur = (k & 1) ? a.I1 : a.I0;
   if ((int)blockIdx.x < a.n_ring_blocks) {
-    // Leading blocks: the next step's ARNA ring orders, off the critical
-    // path (they depend only on the seed and the step index).
-    if (warp == 0) {
-      int* perm = reinterpret_cast<int*>(&s_roi[0][0]);
-      int* rr = perm + RING_SMEM_G;
-      for (int t = blockIdx.x; t < a.n_tracks; t += a.n_ring_blocks) {
-        const TrackParams& P = a.trk[t];
-        if (P.mode != MODE_ARNA || P.G <= 1 || P.G > RING_SMEM_G) continue;
+    // Leading blocks, off the critical path: per track the next step's
+    // exchange offsets o_g (Sec. III-C send sets) and ARNA ring order (they
+    // depend only on the seed and the step index), then the previous step's
+    // estimate, log c, log Z and history (finish_step).
+    static_assert(sizeof(GlobalScratch) <= sizeof(s_roi), "the leading blocks' scratch lives in s_roi");
+    const GlobalArgs ga{a.trk, a.ts, a.grp, nullptr, a.ring_next, a.ring_stride, a.exo_next, a.hist, a.ghist,
+                        a.history, 1, a.ds};
+    int* perm = reinterpret_cast<int*>(&s_roi[0][0]);
+    int* rr = perm + RING_SMEM_G;
+    for (int t = blockIdx.x; t < a.n_tracks; t += a.n_ring_blocks) {
+      const TrackParams& P = a.trk[t];
+      uint32_t* exo_out = a.exo_next + (size_t)((k + 1) & 1) * a.ring_stride + P.group_off;
+      for (int m = threadIdx.x; m < P.G; m += K1_THREADS) {
+        uint32_t o = 0;
+        if (P.G > 1 && !draw_bounded(P.key0, P.key1, P.tag, ST_EXCH, (uint32_t)m, (uint32_t)(k + 1), (uint32_t)P.Np, o))
+          set_error(a.ds, ERR_DRAW, 2u, (uint32_t)t, (uint32_t)m);
+        exo_out[m] = o;
+      }
+      if (warp == 0 && P.mode == MODE_ARNA && P.G > 1 && P.G <= RING_SMEM_G) {
         ring_for_step(P, t, (uint32_t)(k + 1), perm, rr, a.ds);
         for (int p = lane; p < P.G; p += 32)
           a.ring_next[(size_t)((k + 1) & 1) * a.ring_stride + P.group_off + p] = perm[p];
-        __syncwarp();
       }
+      __syncthreads();  // s_roi free for the scratch
+      finish_step<K1_THREADS>(ga, t, *reinterpret_cast<GlobalScratch*>(&s_roi[0][0]));
+      __syncthreads();
     }
     return;
   }
@@ -318,13 +664,11 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
   uint32_t phase = 0;
   // SINGLE: the track's exchange count for the whole launch
   const int nex1 = SINGLE && k > 0 ? a.ts[0].n_ex : 0;
-  const unsigned long long mnex1 = SINGLE ? a.ts[0].m_nex : 0ull;
 
   auto run_tile = [&](const TrackParams& P, const int4 td, const int ti) {
     const int g = td.y, Np = P.Np;
     const GroupState* __restrict__ gs = a.grp + P.group_off;
     const int nex = SINGLE ? nex1 : (k > 0 ? a.ts[td.x].n_ex : 0);
-    const unsigned long long mnex = SINGLE ? mnex1 : a.ts[td.x].m_nex;
     // the group's exchange partners and weight offsets, once per tile
     const float off_g = gs[g].off;
     uint32_t o_r = 0, o_s = 0;
@@ -361,7 +705,7 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
       from_pred[q] = false;
       if (active) {
         int sj;
-        from_pred[q] = exchange_from_pred(j, Np, nex, o_r, o_s, P.m_Np, mnex, sj);
+        from_pred[q] = exchange_from_pred(j, Np, nex, o_r, o_s, P.m_Np, sj);
         const uint32_t src = (uint32_t)((from_pred[q] ? sg : g) * Np + sj);
         const uint32_t par = (k == 0) ? src : anc_t[src];
         if (par >= n_track) {
@@ -552,264 +896,6 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
   }
 }
 
-// ===================================================================== K5
-// Per track: the master PE's reduction (Alg. 3 steps 9-10) and weight carry
-// (step 8) for step k, then ring order (step 1) and exchange count (step 2)
-// for step k+1.  G-sized; the exchange count is decided in FP64.
-// log W^(m) = M + ln(Q 2^-40) in FP32: log2 Q from the leading-bit position
-// and the top 24 bits of Q.
-__device__ __forceinline__ float group_log_weight(float M, unsigned long long Q) {
-  const int e = 63 - __clzll((long long)Q);
-  const uint32_t top = e >= 23 ? (uint32_t)(Q >> (e - 23)) : (uint32_t)(Q << (23 - e));
-  const float l2 = (float)(e - 23) + log2f((float)top);  // log2 Q (top is exact in FP32)
-  return M + (l2 - 40.0f) * 0.693147182f;
-}
-
-// Scratch of the global step (shared memory of the CTA running it).
-struct GlobalScratch {
-  float f[32];
-  int i[32];
-  float red[32][6];
-  unsigned long long w[32][2];
-  float tot[6];
-  double pe;
-  int ring[MAX_G];
-};
-
-// The global step of track t by one CTA of NT threads, each thread owning
-// groups m = threadIdx.x + i NT.  finalize = 0 prepares step 0 only.
-// Per-group inputs are read through L2 (written by other CTAs of the same
-// launch when this runs as the resampler's tail).
-template <int NT>
-__device__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
-  constexpr int NW = NT / 32;
-  constexpr int GPT = (MAX_G + NT - 1) / NT;
-  // Every input first (the body then only computes and stores, so no load
-  // waits behind a store that might alias it): parameters, track state,
-  // per-group statistics.
-  const TrackParams* __restrict__ P = a.trk + t;
-  const int G = P->G, Np = P->Np, mode = P->mode, group_off = P->group_off, hist_off = P->hist_off;
-  const long long ghist_off = P->ghist_off;
-  const float cutoff = P->cutoff, ex_ratio = P->ex_ratio;
-  const uint32_t key0 = P->key0, key1 = P->key1, tag = P->tag;
-  TrackState* __restrict__ T = a.ts + t;
-  const int k = __ldcg(&T->k);
-  const int nex_k = __ldcg(&T->n_ex);
-  const double pe_k = __ldcg(&T->pe_eff);
-  const double logZ_k = __ldcg(&T->log_Z);
-  GroupState* __restrict__ gs = a.gs + group_off;
-  int* __restrict__ ring = a.ring + group_off;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nwa = G > NT ? NW : (G + 31) / 32;  // warps holding groups
-  const int k1 = a.finalize ? k + 1 : 0;
-  const int* __restrict__ rnext_buf = a.ring_next + (size_t)(k1 & 1) * a.ring_stride + group_off;
-
-  unsigned long long Q[GPT];
-  float Mg[GPT], xs[GPT][5], ess[GPT], lam[GPT];
-  int ring_m[GPT], rnext[GPT];
-#pragma unroll
-  for (int i = 0; i < GPT; ++i) {
-    const int m = threadIdx.x + i * NT;
-    Q[i] = 0;
-    Mg[i] = 0.0f;
-    ess[i] = 0.0f;
-#pragma unroll
-    for (int q = 0; q < 5; ++q) xs[i][q] = 0.0f;
-    ring_m[i] = m;
-    rnext[i] = m;
-    if (m < G) {
-      Q[i] = __ldcg(&gs[m].Q);
-      Mg[i] = __ldcg(&gs[m].M);
-#pragma unroll
-      for (int q = 0; q < 5; ++q) xs[i][q] = __ldcg(&gs[m].xs[q]);
-      ess[i] = __ldcg(&gs[m].ess);
-      ring_m[i] = __ldcg(&ring[m]);
-      rnext[i] = __ldcg(&rnext_buf[m]);
-    }
-  }
-  // the next step's random words (independent of the reductions below)
-  uint32_t exo[GPT], uw[GPT];
-  bool exo_ok[GPT];
-#pragma unroll
-  for (int i = 0; i < GPT; ++i) {
-    const int m = threadIdx.x + i * NT;
-    exo[i] = 0;
-    uw[i] = 0;
-    exo_ok[i] = true;
-    if (m < G) {
-      exo_ok[i] = draw_bounded(key0, key1, tag, ST_EXCH, (uint32_t)m, (uint32_t)k1, (uint32_t)Np, exo[i]);
-      uw[i] = philox(key0, key1, make_uint4((uint32_t)m, 0u, (uint32_t)k1, tag | (ST_RESAMPLE << 4))).x;
-    }
-  }
-
-  // S7 -> S8: Lambda'_m in FP32 (finalize), or 0 (prepare step 0)
-  float mx = -INFINITY;
-  int deg = 0;
-#pragma unroll
-  for (int i = 0; i < GPT; ++i) {
-    const int m = threadIdx.x + i * NT;
-    lam[i] = -INFINITY;
-    if (m < G) {
-      if (a.finalize) {
-        lam[i] = Q[i] != 0 ? group_log_weight(Mg[i], Q[i]) : -INFINITY;
-        deg += (Q[i] == 0);
-      } else {
-        lam[i] = 0.0f;
-      }
-      mx = fmaxf(mx, lam[i]);
-    }
-  }
-  mx = warp_max(mx);
-  deg = __reduce_add_sync(0xffffffffu, deg);
-  if (lane == 0) {
-    sc.f[warp] = mx;
-    sc.i[warp] = deg;
-  }
-  __syncthreads();
-  mx = -INFINITY;
-  deg = 0;
-  for (int w = 0; w < nwa; ++w) {
-    mx = fmaxf(mx, sc.f[w]);
-    deg += sc.i[w];
-  }
-  const bool all_degenerate = a.finalize && deg == G;
-  if (all_degenerate) {  // every group lost its weight: restart from equal weights
-#pragma unroll
-    for (int i = 0; i < GPT; ++i) lam[i] = (threadIdx.x + i * NT < G) ? 0.0f : -INFINITY;
-    mx = 0.0f;
-  }
-  // one pass: FP32 sums for log c and the estimate; for Eq. 4 the FP64
-  // weights w = e^(lam - max) in (0, 1] and their squares, summed exactly
-  // as 2^-52 fixed-point integers (at most G 2^52 < 2^63), so the sums need
-  // no FP64 additions; the exchange count is decided in FP64 from them.
-  float acc[6] = {0, 0, 0, 0, 0, 0};
-  unsigned long long iw = 0, iw2 = 0;
-#pragma unroll
-  for (int i = 0; i < GPT; ++i) {
-    if (threadIdx.x + i * NT < G) {
-      const float wf = __expf(lam[i] - mx);
-      acc[0] += wf;
-#pragma unroll
-      for (int q = 0; q < 5; ++q) acc[1 + q] = fmaf(wf, xs[i][q], acc[1 + q]);
-      const double w = exp((double)lam[i] - (double)mx);
-      iw += __double2ull_rn(w * 4503599627370496.0);
-      iw2 += __double2ull_rn(w * w * 4503599627370496.0);
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < 6; ++q) acc[q] = warp_sum(acc[q]);
-  iw = warp_sum_u64(iw);
-  iw2 = warp_sum_u64(iw2);
-  if (lane == 0) {
-#pragma unroll
-    for (int q = 0; q < 6; ++q) sc.red[warp][q] = acc[q];
-    sc.w[warp][0] = iw;
-    sc.w[warp][1] = iw2;
-  }
-  const bool shuffled = (mode == MODE_ARNA) && k1 >= 1 && G > 1;
-#pragma unroll
-  for (int i = 0; i < GPT; ++i) {
-    const int m = threadIdx.x + i * NT;
-    if (m < G) sc.ring[m] = shuffled ? rnext[i] : m;  // ring order of step k1 (Sec. IV-B)
-  }
-  __syncthreads();
-  if (threadIdx.x < 6) {
-    float x = 0.0f;
-    for (int w = 0; w < nwa; ++w) x += sc.red[w][threadIdx.x];
-    sc.tot[threadIdx.x] = x;
-  }
-  if (threadIdx.x == (NW > 1 ? 32 : 7)) {
-    unsigned long long s1 = 0, s2 = 0;
-    for (int w = 0; w < nwa; ++w) {
-      s1 += sc.w[w][0];
-      s2 += sc.w[w][1];
-    }
-    const double sw = (double)s1, sw2 = (double)s2;
-    const double pe = sw * sw / sw2 * 2.220446049250313e-16;  // Eq. 4 for the next step (scales 2^-52)
-    // exchange count for step k1 (Eq. 3 with the Sec. V-A cut-off)
-    int nex = 0;
-    if (k1 >= 1 && G > 1) {
-      double rho;
-      if (mode == MODE_ARNA) {
-        if (!(pe < (double)cutoff * (double)G)) {
-          rho = 0.0;
-        } else {
-          rho = 0.5 - 0.5 * (pe - 1.0) / (double)(G - 1);
-          rho = fmin(fmax(rho, 0.0), 0.5);
-        }
-      } else {
-        rho = fmin(fmax((double)ex_ratio, 0.0), 1.0);
-      }
-      nex = (int)floor(rho * (double)Np);
-    }
-    sc.pe = pe;
-    sc.i[0] = nex;
-  }
-  __syncthreads();
-  const float sw = sc.tot[0];
-  const float lse = mx + logf(sw);  // LSE of the carried weights = log c_k
-  const double pe = sc.pe;
-  const int nex = sc.i[0];
-  const float log_np = logf((float)Np);
-
-  if (a.finalize) {
-    const int hslot = k % a.history;
-#pragma unroll
-    for (int i = 0; i < GPT; ++i) {
-      const int m = threadIdx.x + i * NT;
-      if (m < G) {
-        GroupHist& gh = a.ghist[ghist_off + (long long)hslot * G + m];
-        gh.ring = ring_m[i];
-        gh.logW = all_degenerate ? -INFINITY : lam[i];
-#pragma unroll
-        for (int q = 0; q < 5; ++q) gh.xs[q] = xs[i][q];
-        gh.ess = ess[i];
-      }
-    }
-    if (threadIdx.x == 0) {
-      const double logc = all_degenerate ? -INFINITY : (double)lse;
-      const double logZ = logZ_k + logc;
-      float xq[5];
-      for (int q = 0; q < 5; ++q) xq[q] = all_degenerate ? NAN : sc.tot[1 + q] / sw;
-      T->log_c = logc;
-      T->log_Z = logZ;
-      for (int q = 0; q < 5; ++q) T->xhat[q] = xq[q];
-      T->degenerate = deg;
-      if (all_degenerate) T->flags |= 1;
-      T->steps_done = k + 1;
-      HistRec& h = a.hist[hist_off + hslot];
-      for (int q = 0; q < 5; ++q) h.xhat[q] = xq[q];
-      h.step = k;
-      h.n_ex = nex_k;
-      h.pe_eff = pe_k;
-      h.log_c = logc;
-      h.log_Z = logZ;
-      h.degenerate = deg;
-    }
-  }
-
-#pragma unroll
-  for (int i = 0; i < GPT; ++i) {
-    const int m = threadIdx.x + i * NT;
-    if (m < G) {
-      const int rm = sc.ring[m];
-      ring[m] = rm;
-      gs[rm].pred = sc.ring[m == 0 ? G - 1 : m - 1];
-      if (nex > 0 && !exo_ok[i]) set_error(a.ds, ERR_DRAW, 2u, (uint32_t)t, (uint32_t)m);
-      gs[m].exo = nex > 0 ? exo[i] : 0u;
-      gs[m].u = uw[i];
-      gs[m].lambda = all_degenerate ? 0.0f : lam[i];
-      gs[m].off = lam[i] - log_np - lse;
-    }
-  }
-  if (threadIdx.x == 0) {
-    T->n_ex = nex;
-    T->m_nex = fastdiv_magic((uint32_t)(nex > 0 ? nex : 1));
-    T->pe_eff = pe;
-    T->k = k1;
-  }
-}
-
 // ===================================================================== K3
 // Number of outputs j in [0, Np) with (j 2^32 + u) Q < S Np 2^32: an FP32
 // estimate, then exact 128-bit corrections (the estimate is within 1).
@@ -852,8 +938,14 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
   __shared__ unsigned long long s_w[RS_THREADS / 32];
   __shared__ float s_stat[RS_THREADS / 32][8];
   __shared__ int s_jlo, s_jhi;
-  __shared__ unsigned long long s_incl[RS_SUB];
   __shared__ Thresholds s_th;
+  // dynamic: inclusive prefixes of a sub-chunk's items, then a window of
+  // ancestors staged for coalesced stores.  Both are indexed through pad8
+  // (one spare element per 8): a thread's 8 consecutive items then start 9
+  // elements after its neighbour's, spreading a warp over the banks.
+  extern __shared__ unsigned long long s_dyn_rs[];
+  unsigned long long* s_incl = s_dyn_rs;
+  uint32_t* s_out = reinterpret_cast<uint32_t*>(s_dyn_rs + RS_SUB_PAD);
 
   float v[RS_ITEMS];
   auto load_sub = [&](int sub) {
@@ -903,7 +995,15 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
     Q += x;
   }
 
-  const uint32_t u = a.u_arr ? a.u_arr[grp] : a.gs[grp].u;
+  // the group's resampling uniform word (Philox stream RESAMPLE, group, step)
+  uint32_t u;
+  if (a.u_arr) {
+    u = a.u_arr[grp];
+  } else {
+    const TrackParams* P = a.glob.trk + d.track;
+    const int kk = a.glob.ts[d.track].k;
+    u = philox(P->key0, P->key1, make_uint4((uint32_t)d.g, 0u, (uint32_t)kk, P->tag | (ST_RESAMPLE << 4))).x;
+  }
   const unsigned long long obase = a.local_idx ? 0ull : (unsigned long long)(d.g) * (unsigned long long)Np;
   uint32_t* __restrict__ anc = a.anc + d.base;
   if (Q == 0) {
@@ -962,7 +1062,7 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
 #pragma unroll
         for (int r = 0; r < RS_ITEMS; ++r) {
           S += qv[r];
-          s_incl[i0 + r] = S;
+          s_incl[pad8(i0 + r)] = S;
         }
       }
       if (threadIdx.x == 0) {
@@ -971,33 +1071,35 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
       }
       __syncthreads();
       // Merge path over the item boundaries X_i = S_{i+1} (s_incl) and the
-      // thresholds Y_b = T_{jlo+b} of this sub-chunk's outputs: output j
-      // takes the first item i with T_j < S_{i+1}.  Each thread merges an
-      // equal slice of the n + m merged positions, so the work is balanced
-      // however the weight is spread.
-      {
-        const int jlo = s_jlo, m = s_jhi - s_jlo, L = n + m;
+      // thresholds Y_b = T_{jw+b} of a window of this sub-chunk's outputs:
+      // output j takes the first item i with T_j < S_{i+1}.  Each thread
+      // merges an equal slice of the n + mw merged positions, so the work is
+      // balanced however the weight is spread.  The window's ancestors are
+      // staged in shared memory and stored with consecutive threads writing
+      // consecutive outputs.
+      for (int jw = s_jlo; jw < s_jhi; jw += RS_OUT) {
+        const int mw = min(RS_OUT, s_jhi - jw), L = n + mw;
         const int d0 = (int)(((long long)L * threadIdx.x) / RS_THREADS);
         const int d1 = (int)(((long long)L * (threadIdx.x + 1)) / RS_THREADS);
-        // largest ia in [max(0, d0 - m), min(d0, n)] whose items all precede
+        // largest ia in [max(0, d0 - mw), min(d0, n)] whose items all precede
         // output d0 - ia in the merge (X_{ia-1} <= Y_{d0-ia})
-        int lo2 = max(0, d0 - m), hi2 = min(d0, n);
+        int lo2 = max(0, d0 - mw), hi2 = min(d0, n);
         while (lo2 < hi2) {
           const int mid = (lo2 + hi2 + 1) >> 1;  // candidate number of items consumed
-          if (s_incl[mid - 1] <= th.T((uint32_t)(jlo + d0 - mid))) lo2 = mid;
+          if (s_incl[pad8(mid - 1)] <= th.T((uint32_t)(jw + d0 - mid))) lo2 = mid;
           else hi2 = mid - 1;
         }
         int ia = lo2, ib = d0 - lo2;
-        if (ib < m) {
-          // T and its remainder at output jlo + ib, then advance incrementally
-          uint32_t jj = (uint32_t)(jlo + ib);
+        if (ib < mw) {
+          // T and its remainder at output jw + ib, then advance incrementally
+          uint32_t jj = (uint32_t)(jw + ib);
           unsigned long long num = (unsigned long long)jj * th.B + th.F0;
           unsigned long long qd = th.Np > 1 ? __umul64hi(num, th.M) : num;
           uint32_t rem = (uint32_t)(num - qd * th.Np);
           unsigned long long Tj = (unsigned long long)jj * th.A + th.F1 + qd;
           for (int dd = d0; dd < d1; ++dd) {
-            if (ib < m && (ia >= n || Tj < s_incl[ia])) {
-              anc[jlo + ib] = (uint32_t)(obase + sub + ia);
+            if (ib < mw && (ia >= n || Tj < s_incl[pad8(ia)])) {
+              s_out[pad8(ib)] = (uint32_t)(obase + sub + ia);
               ++ib;
               rem += th.B;
               Tj += th.A;
@@ -1010,6 +1112,9 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
             }
           }
         }
+        __syncthreads();
+        for (int e = threadIdx.x; e < mw; e += RS_THREADS) anc[jw + e] = s_out[pad8(e)];
+        __syncthreads();
       }
       carry += tot;
       __syncthreads();
@@ -1069,21 +1174,13 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
     }
     __syncthreads();
     if (s_last) {
-      global_step<RS_THREADS>(a.glob, d.track, *reinterpret_cast<GlobalScratch*>(s_incl));
+      global_step<RS_THREADS>(a.glob, d.track, *reinterpret_cast<GlobalScratch*>(s_dyn_rs));
       if (threadIdx.x == 0) a.glob.ts[d.track].ticket = 0u;
     }
   }
 }
 
 
-// Per track: the master PE's reduction (Alg. 3 steps 9-10) and weight carry
-// (step 8) for step k, then ring order (step 1) and exchange count (step 2)
-// for step k+1.  Used to prepare step 0; during the run the same step runs
-// as the tail of the resampler.
-__global__ void __launch_bounds__(GL_THREADS) k_global(GlobalArgs a) {
-  __shared__ GlobalScratch sc;
-  global_step<GL_THREADS>(a, blockIdx.x, sc);
-}
 
 // ============================================================ export helpers
 __global__ void k_export_states(const float4* __restrict__ pv, const float* __restrict__ In, long long n,
@@ -1197,11 +1294,24 @@ cudaError_t launch_propagate(const K1Args& a, int R, int grid, bool pdl, cudaStr
 }
 
 cudaError_t launch_resample(const ResampleArgs& a, int n_groups, int cluster, bool pdl, cudaStream_t s) {
-  return launch_ex(k_resample, dim3((unsigned)(n_groups * cluster)), dim3(RS_THREADS), cluster, pdl, s, a);
+  constexpr size_t smem = RS_SUB_PAD * sizeof(unsigned long long) + pad8(RS_OUT) * sizeof(uint32_t);
+  static_assert(sizeof(GlobalScratch) <= smem, "the global step's scratch lives in the resampler's shared memory");
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(k_resample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  return launch_ex(k_resample, dim3((unsigned)(n_groups * cluster)), dim3(RS_THREADS), cluster, pdl, s, a, smem);
 }
 
 cudaError_t launch_global(const GlobalArgs& a, int n_tracks, cudaStream_t s) {
   k_global<<<n_tracks, GL_THREADS, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish(const GlobalArgs& a, int n_tracks, cudaStream_t s) {
+  k_finish<<<n_tracks, K1_THREADS, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -42,7 +42,7 @@ struct K1Args {
   const int4* tiles;
   int n_tiles;
   GroupState* grp;
-  const TrackState* ts;
+  TrackState* ts;
   DevState* ds;
   float4* pv0;
   float4* pv1;
@@ -57,7 +57,10 @@ struct K1Args {
   const CUtensorMap* tmaps;  // one per track over its padded frame, or nullptr
   int* ring_next;            // two buffers (by step parity) of G_total: ring order of step k+1 (ARNA)
   int ring_stride;           // G_total
-  int n_ring_blocks;         // leading blocks that draw ring orders
+  uint32_t* exo_next;        // two buffers (by step parity) of G_total: exchange offsets of step k+1
+  HistRec* hist;
+  GroupHist* ghist;
+  int n_ring_blocks;         // leading blocks: next step's rings and exchange offsets, previous step's history
   int n_tracks;
   int k_hint;                // the host's step index, or -1 (read on the device)
   int noise_tiles;           // tiles per CTA whose noise is drawn before the wait (<= K1_NOISE_TILES)
@@ -77,6 +80,7 @@ struct GlobalArgs {
   int* ring;
   const int* ring_next;  // two buffers by step parity: ring of the next step, drawn by the propagate kernel
   int ring_stride;
+  const uint32_t* exo_next;  // two buffers by step parity: exchange offsets of the next step
   HistRec* hist;
   GroupHist* ghist;
   int history;
@@ -170,6 +174,7 @@ cudaError_t launch_frame_prep_table(const FrameTableArgs& a, int blocks_x, bool 
 cudaError_t launch_propagate(const K1Args& a, int R, int grid, bool pdl, cudaStream_t s);
 cudaError_t launch_resample(const ResampleArgs& a, int n_groups, int cluster, bool pdl, cudaStream_t s);
 cudaError_t launch_global(const GlobalArgs& a, int n_tracks, cudaStream_t s);
+cudaError_t launch_finish(const GlobalArgs& a, int n_tracks, cudaStream_t s);
 cudaError_t launch_export_states(const float4* pv, const float* In, long long n, float* out, cudaStream_t s);
 cudaError_t k1_occupancy(int R, int* blocks_per_sm);
 size_t k1_dynamic_smem(int noise_tiles);

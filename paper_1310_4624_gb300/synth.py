@@ -12,6 +12,11 @@ Recipe (all draws from ``numpy.random.default_rng(data_seed)``):
     (64x64 frames: [16, 48)^2, the central 32x32);
   * velocity uniform in [-vmax, vmax]^2, redrawn until the whole track stays at
     least ``margin`` px inside the frame;
+  * with ``truth_noise`` (the differentiable workload, whose data come from
+    the model at the true parameters): the truth follows the nearly-constant-
+    velocity dynamics itself, x_{k+1} = x_k + v_k + sigma_pos eps,
+    v_{k+1} = v_k + sigma_v eps, intensity constant at the amplitude; the
+    whole trajectory is redrawn until it keeps the margin;
   * frame k: z(u, v) ~ Poisson(b + A exp(-((u - x_k)^2 + (v - y_k)^2) / (2 s^2)))
     as float32, pixel (u, v) = (column, row) centred at integer coordinates.
 """
@@ -55,6 +60,7 @@ class Workload:
     share_radius: float = 2.0     # information-sharing init: disc radius of group 0
     share_vmax: float = 2.0       # other groups: velocity range
     share_I: Tuple[float, float] = (1.0, 20.0)
+    truth_noise: bool = False     # truth drawn from the NCV dynamics (sigma_pos, sigma_v)
 
     @property
     def N(self) -> int:
@@ -85,7 +91,7 @@ def sharing(mode: int = ARNA, **kw) -> Workload:
 def differentiable(**kw) -> Workload:
     """50 frames 512x512, G=16 x 65536, ARNA."""
     return Workload(name="grad_512x512_G16x65536", G=16, Np=65536, H=512, W=512, T=50,
-                    mode=ARNA).replace(**kw)
+                    mode=ARNA, truth_noise=True).replace(**kw)
 
 
 def batched_tracks(n_tracks: int = 512, seed: int = 0, H: int = 256, W: int = 256, T: int = 50,
@@ -110,6 +116,19 @@ def truth_track(wl: Workload) -> np.ndarray:
     H, W, T = wl.H, wl.W, wl.T
     x0 = rng.uniform(W / 4, 3 * W / 4)
     y0 = rng.uniform(H / 4, 3 * H / 4)
+    if wl.truth_noise:
+        for _ in range(10000):
+            v = rng.uniform(-wl.vmax, wl.vmax, size=2)
+            p = np.array([x0, y0])
+            tr = np.zeros((T, 5))
+            for k in range(T):
+                tr[k, :2], tr[k, 2:4], tr[k, 4] = p, v, wl.amplitude
+                p = p + v + wl.sigma_pos * rng.standard_normal(2)
+                v = v + wl.sigma_v * rng.standard_normal(2)
+            if (tr[:, 0].min() >= wl.margin and tr[:, 0].max() <= W - 1 - wl.margin and
+                    tr[:, 1].min() >= wl.margin and tr[:, 1].max() <= H - 1 - wl.margin):
+                return tr
+        raise RuntimeError("no NCV trajectory kept the margin")  # pragma: no cover
     for _ in range(10000):
         vx, vy = rng.uniform(-wl.vmax, wl.vmax, size=2)
         xs = x0 + vx * np.arange(T)
