@@ -49,6 +49,7 @@ struct pf_handle {
   int* ring = nullptr;
   int* ring_next = nullptr;
   uint32_t* exo_next = nullptr;
+  int* tile_ctr = nullptr;
   int n_ring_blocks = 0;  // leading blocks of the propagate kernel
   bool finish_pending = false;  // the last step's estimate / history not yet written (k_finish)
   int max_G = 1;
@@ -123,7 +124,7 @@ QuantCoeffs make_qc() {
 }
 
 struct Layout {
-  size_t trk, ts, gs, gd, tiles, pv0, pv1, I0, I1, anc, lw, tp, ypad, hist, ghist, ring, ring_next, exo_next, parent, ds,
+  size_t trk, ts, gs, gd, tiles, pv0, pv1, I0, I1, anc, lw, tp, ypad, hist, ghist, ring, ring_next, exo_next, tile_ctr, parent, ds,
       tmap, total;
   size_t rp_pv, rp_I, ck_pv, ck_I, ca_pv0, ca_pv1, ca_I0, ca_I1, lam_hist, lbar_hist, dlam, Dacc, grad, logz, seed;
   bool adjoint = false;
@@ -219,6 +220,7 @@ Layout plan(const pf_track_config* c, int n, int history) {
   L.ring = take(sizeof(int) * L.G_total);
   L.ring_next = take(sizeof(int) * 2 * (size_t)L.G_total);
   L.exo_next = take(sizeof(uint32_t) * 2 * (size_t)L.G_total);
+  L.tile_ctr = take(sizeof(int));
   L.tiles = take(sizeof(int4) * L.n_tiles);
   L.pv0 = take(sizeof(float4) * L.N_total);
   L.pv1 = take(sizeof(float4) * L.N_total);
@@ -334,7 +336,7 @@ pf_status sync(pf_handle* h) {
 K1Args k1_args(const pf_handle* h) {
   K1Args a{h->trk, h->tiles, h->n_tiles, h->gs, h->ts, h->ds, h->pv[0], h->pv[1], h->In[0], h->In[1],
            h->anc, h->parent, h->history, h->lw, h->tile_part, h->ypad, h->tmaps, h->ring_next,
-           h->G_total, h->exo_next, h->hist, h->ghist, h->n_ring_blocks, h->n_tracks, -1, 0, TrackParams{}, 0,
+           h->G_total, h->exo_next, h->hist, h->ghist, h->tile_ctr, h->n_ring_blocks, h->n_tracks, TrackParams{}, 0,
            nullptr, CUtensorMap{}};
   a.p0 = h->tp[0];
   return a;
@@ -364,18 +366,6 @@ bool raw_frame_map(const pf_handle* h, const float* frame, K1Args* a) {
   return true;
 }
 
-// k1_args for a step enqueued by the host at step index h->steps_run: the
-// propagate kernel may draw its noise before waiting for the previous kernel.
-K1Args k1_args_hinted(const pf_handle* h) {
-  K1Args a = k1_args(h);
-  if (h->steps_run >= 1) {
-    const int per_cta = (h->n_tiles + h->k1_grid - 1) / h->k1_grid;
-    a.k_hint = h->steps_run;
-    a.noise_tiles = per_cta < K1_NOISE_TILES ? per_cta : K1_NOISE_TILES;
-  }
-  return a;
-}
-
 GlobalArgs global_args(const pf_handle* h, int finalize) {
   return GlobalArgs{h->trk, h->ts, h->gs, h->ring, h->ring_next, h->G_total, h->exo_next, h->hist, h->ghist, h->history,
                     finalize, h->ds};
@@ -386,6 +376,7 @@ GlobalArgs global_args(const pf_handle* h, int finalize) {
 ResampleArgs resample_args(const pf_handle* h, int fuse) {
   ResampleArgs ra{h->gd, h->gs, h->tile_part, h->lw, h->anc, nullptr, nullptr, 0, h->qc, h->ds};
   ra.fuse_global = fuse;
+  ra.tile_ctr = h->tile_ctr;
   ra.glob = global_args(h, 1);
   return ra;
 }
@@ -447,6 +438,7 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
   h->ring = (int*)(w + L.ring);
   h->ring_next = (int*)(w + L.ring_next);
   h->exo_next = (uint32_t*)(w + L.exo_next);
+  h->tile_ctr = (int*)(w + L.tile_ctr);
   h->tiles = (int4*)(w + L.tiles);
   h->pv[0] = (float4*)(w + L.pv0);
   h->pv[1] = (float4*)(w + L.pv1);
@@ -622,7 +614,7 @@ pf_status pf_step(pf_handle* h, const float* const* frames, void* stream) {
     if (!frames[t]) return fail(h, PF_ERR_ARG, "frame pointer of track " + std::to_string(t) + " is NULL");
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
-  K1Args k1 = k1_args_hinted(h);
+  K1Args k1 = k1_args(h);
   if (!raw_frame_map(h, frames[0], &k1)) {
     if ((e = mark(h, PF_KERNEL_FRAME_PREP, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
     if ((e = prep_frames(h, frames, s)) != cudaSuccess) return cuda_fail(h, e, "k_frame_prep");
@@ -755,8 +747,12 @@ pf_status pf_autotune(pf_handle* h, const float* const* frames, int32_t* k1_grid
       const int grid = (int)(cand < h->n_tiles ? cand : h->n_tiles);
       float ms = 0.0f;
       for (int rep = 0; rep < 2; ++rep)  // the first run also warms caches
-        if ((e = time_it([&] { return launch_propagate(k1, h->R, grid + h->n_ring_blocks, false, s); }, ms)) !=
-            cudaSuccess)
+        if ((e = time_it(
+                 [&] {
+                   cudaError_t r = cudaMemsetAsync(h->tile_ctr, 0, sizeof(int), s);
+                   return r != cudaSuccess ? r : launch_propagate(k1, h->R, grid + h->n_ring_blocks, false, s);
+                 },
+                 ms)) != cudaSuccess)
           break;
       if (e != cudaSuccess) break;
       if (ms < best) {
@@ -974,7 +970,8 @@ pf_status pf_reset(pf_handle* h, void* stream) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(h->ds, 0, sizeof(DevState), s)) ||
       (e = cudaMemsetAsync(h->ts, 0, sizeof(TrackState) * h->n_tracks, s)) ||
-      (e = cudaMemsetAsync(h->gs, 0, sizeof(GroupState) * h->G_total, s)))
+      (e = cudaMemsetAsync(h->gs, 0, sizeof(GroupState) * h->G_total, s)) ||
+      (e = cudaMemsetAsync(h->tile_ctr, 0, sizeof(int), s)))
     return cuda_fail(h, e, "pf_reset");
   InitArgs ia{h->trk, h->tiles, h->n_tiles, h->N_total, nullptr, h->pv[1], h->In[1]};
   for (int t = 0; t < h->n_tracks; ++t)

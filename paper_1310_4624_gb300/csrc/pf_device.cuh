@@ -22,7 +22,6 @@ constexpr int K1_TILE = K1_THREADS * K1_PPT;  // slots per tile (one group)
 #define PF_K1_MIN_BLOCKS 4
 #endif
 constexpr int K1_MIN_BLOCKS = PF_K1_MIN_BLOCKS;  // resident propagate CTAs per SM the register budget targets
-constexpr int K1_NOISE_TILES = 4;     // tiles per propagate CTA whose noise may be drawn ahead
 constexpr int ROI_W = 40;             // staged frame box width = smem row pitch (floats, = 8 mod 32 banks)
 constexpr int ROI_BOX_H = 8;          // rows per TMA box
 constexpr int ROI_MAX_BOXES = 8;      // staged rows <= 64

@@ -579,48 +579,26 @@ __device__ __forceinline__ void prop_noise(uint32_t key0, uint32_t key1, uint32_
 // frame through L1.  Leading blocks draw the next step's ARNA rings.
 // SINGLE: one track, whose parameters come from the kernel's constant
 // parameter block (a.p0) instead of global memory.
-// With a.k_hint >= 1 (the host's step index) the CTA draws the process
-// noise of its first a.noise_tiles tiles into shared memory before waiting
-// for the previous kernel: that work depends only on the seed, the slots
-// and the step index, so it overlaps the previous kernel's tail.  After the
-// wait the staged noise is used only if the device's step index agrees.
 template <int R, bool SINGLE>
 __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(const __grid_constant__ K1Args a) {
   constexpr int D = 2 * R + 1;
   constexpr int PAD = 2 * R + 1;
   constexpr int NW = K1_THREADS / 32;
-  __shared__ __align__(128) float s_roi[1][ROI_FLOATS];  // the staged box (TMA target)
+  // the staged box (TMA target) and a copy shifted left by one float, so that
+  // any patch row starts on an 8-byte boundary in one of the two (pairwise
+  // loads); 4 spare floats cover the last pair of the last row
+  __shared__ __align__(128) float s_roi[2][ROI_FLOATS + 4];
+  __shared__ int s_next[2];  // next tile, by iteration parity
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ float s_red[NW][8];
   __shared__ int s_box[NW][4];
   __shared__ int s_key[NW];
-  extern __shared__ float s_noise[];  // [noise_tiles][K1_PPT][5][K1_THREADS]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int stride = (int)gridDim.x - a.n_ring_blocks;
   int tile = (int)blockIdx.x - a.n_ring_blocks;
-  const int kh = a.k_hint;
-  if (kh >= 1 && tile >= 0) {
-    int i = 0;
-    for (int t = tile; i < a.noise_tiles && t < a.n_tiles; t += stride, ++i) {
-      const int4 td = a.tiles[t];
-      const TrackParams& P = SINGLE ? a.p0 : a.trk[td.x];
-#pragma unroll
-      for (int q = 0; q < K1_PPT; ++q) {
-        const int jj = threadIdx.x + q * K1_THREADS;
-        if (jj < td.w) {
-          float e[5];
-          prop_noise(P.key0, P.key1, P.tag, td.z + jj, td.y, kh, e);
-          float* dst = s_noise + (size_t)((i * K1_PPT + q) * 5) * K1_THREADS + threadIdx.x;
-#pragma unroll
-          for (int c = 0; c < 5; ++c) dst[c * K1_THREADS] = e[c];
-        }
-      }
-    }
-  }
   grid_dep_wait();
   grid_dep_launch();
   const int k = a.ts[0].k;
-  const bool staged_noise = kh >= 1 && kh == k;
   const float4* __restrict__ pv_prev = (k & 1) ? a.pv0 : a.pv1;
   const float* __restrict__ I_prev = (k & 1) ? a.I0 : a.I1;
   float4* __restrict__ pv_cur = (k & 1) ? a.pv1 : a.pv0;
@@ -665,7 +643,7 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
   // SINGLE: the track's exchange count for the whole launch
   const int nex1 = SINGLE && k > 0 ? a.ts[0].n_ex : 0;
 
-  auto run_tile = [&](const TrackParams& P, const int4 td, const int ti) {
+  auto run_tile = [&](const TrackParams& P, const int4 td) {
     const int g = td.y, Np = P.Np;
     const GroupState* __restrict__ gs = a.grp + P.group_off;
     const int nex = SINGLE ? nex1 : (k > 0 ? a.ts[td.x].n_ex : 0);
@@ -717,13 +695,7 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
         if (k > 0) {
           // Alg. 1 step P: nearly constant velocity, unit frame interval
           float e[5];
-          if (staged_noise && ti < a.noise_tiles) {
-            const float* src = s_noise + (size_t)((ti * K1_PPT + q) * 5) * K1_THREADS + threadIdx.x;
-#pragma unroll
-            for (int c = 0; c < 5; ++c) e[c] = src[c * K1_THREADS];
-          } else {
-            prop_noise(P.key0, P.key1, P.tag, j, g, k, e);
-          }
+          prop_noise(P.key0, P.key1, P.tag, j, g, k, e);
           s[q].x = fmaf(P.spos, e[0], s[q].x + s[q].z);
           s[q].y = fmaf(P.spos, e[1], s[q].y + s[q].w);
           s[q].z = fmaf(P.sv, e[2], s[q].z);
@@ -792,14 +764,17 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
         return false;
       }
       phase ^= 1u;
-      if (raw) {
-        // y = z - b inside the frame, 0 outside (the copy filled zeros there)
+      {
+        // raw frame: y = z - b inside the frame, 0 outside (the copy filled
+        // zeros there); then the shifted copy B[i] = A[i + 1]
         const int rows = nbox * ROI_BOX_H, x0 = u0 - PAD, y0 = vmin - PAD;
-        const bool inside = x0 >= 0 && y0 >= 0 && x0 + ROI_W <= P.W && y0 + rows <= P.H;
+        const bool inside = !raw || (x0 >= 0 && y0 >= 0 && x0 + ROI_W <= P.W && y0 + rows <= P.H);
         float4* roi4 = reinterpret_cast<float4*>(&s_roi[0][0]);
+        float* roiB = &s_roi[1][0];
         for (int e = threadIdx.x; e < rows * (ROI_W / 4); e += K1_THREADS) {
           float4 v = roi4[e];
-          if (inside) {
+          if (!raw) {
+          } else if (inside) {
             v.x = __fsub_rn(v.x, P.bg);
             v.y = __fsub_rn(v.y, P.bg);
             v.z = __fsub_rn(v.z, P.bg);
@@ -812,7 +787,10 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
             v.z = rin && (unsigned)(xc + 2) < (unsigned)P.W ? __fsub_rn(v.z, P.bg) : 0.0f;
             v.w = rin && (unsigned)(xc + 3) < (unsigned)P.W ? __fsub_rn(v.w, P.bg) : 0.0f;
           }
-          roi4[e] = v;
+          if (raw) roi4[e] = v;
+          if (e > 0) roiB[4 * e - 1] = v.x;
+          *reinterpret_cast<float2*>(roiB + 4 * e) = make_float2(v.y, v.z);
+          roiB[4 * e + 2] = v.w;
         }
         __syncthreads();
       }
@@ -830,7 +808,9 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
         const float dy = floorf(s[q].y + 0.5f) - s[q].y;
         float ss;
         if (staged) {
-          ss = patch_ss<R, true>(&s_roi[0][(pv[q] - vmin) * ROI_W + (pu[q] - u0)], 0, gxI, dy, P.c_psf, P.kappa);
+          const int c = pu[q] - u0, o = (pv[q] - vmin) * ROI_W;
+          const float* base = (c & 1) ? &s_roi[1][o + c - 1] : &s_roi[0][o + c];
+          ss = patch_ss_pairs<R>(base, gxI, dy, P.c_psf, P.kappa);
         } else if (raw) {
           ss = patch_ss_raw<R>(a.zraw, P.W, P.H, P.bg, pu[q] - PAD, pv[q] - PAD, gxI, dy, P.c_psf, P.kappa);
         } else {
@@ -884,15 +864,22 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
     return true;
   };
 
-  for (int ti = 0; tile < a.n_tiles; tile += stride, ++ti) {
+  // first tile by block index, the rest from a counter (reset by the
+  // resampler), so CTAs finish together however many tiles each ran
+  for (int it = 0; tile < a.n_tiles; ++it) {
     const int4 td = a.tiles[tile];
-    if (threadIdx.x == 0 && tile + stride < a.n_tiles) prefetch_tile(a, a.tiles[tile + stride], k, pv_prev, I_prev);
+    if (threadIdx.x == 0) {
+      const int nt = stride + atomicAdd(a.tile_ctr, 1);
+      s_next[it & 1] = nt;
+      if (nt < a.n_tiles) prefetch_tile(a, a.tiles[nt], k, pv_prev, I_prev);
+    }
     bool ok;
     if constexpr (SINGLE)
-      ok = run_tile(a.p0, td, ti);
+      ok = run_tile(a.p0, td);
     else
-      ok = run_tile(a.trk[td.x], td, ti);
+      ok = run_tile(a.trk[td.x], td);
     if (!ok) return;
+    tile = s_next[it & 1];  // written before run_tile's barriers; rewritten two tiles later
   }
 }
 
@@ -918,7 +905,7 @@ __device__ __forceinline__ int count_below(const Thresholds& th, unsigned long l
 
 __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
   grid_dep_wait();
-  grid_dep_launch();
+  if (a.tile_ctr && blockIdx.x == 0 && threadIdx.x == 0) *a.tile_ctr = 0;  // for the next propagate launch
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -1159,6 +1146,10 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
     }
   }
   cl.sync();  // keep shared memory alive until every CTA has read it
+  // The next kernel may start once every CTA is past its main work: its
+  // CTAs then fill SMs freed here and overlap the global step below, instead
+  // of taking issue slots from resampling CTAs still at work.
+  grid_dep_launch();
 
   // The last group of a track to finish runs the track's global step here
   // (its rank-0 CTA): a ticket per track counts finished groups.  The
@@ -1257,20 +1248,9 @@ const void* propagate_kernel(int R) {
   }
 }
 
-// Shared memory of the staged noise (k_propagate_weight, a.noise_tiles).
-size_t k1_dynamic_smem(int noise_tiles) { return (size_t)noise_tiles * K1_PPT * 5 * K1_THREADS * sizeof(float); }
-
 template <int R, bool SINGLE>
 static cudaError_t launch_propagate_rs(const K1Args& a, dim3 g, bool pdl, cudaStream_t s) {
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_propagate_weight<R, SINGLE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)k1_dynamic_smem(K1_NOISE_TILES));
-  });
-  if (attr_err != cudaSuccess) return attr_err;
-  return launch_ex(k_propagate_weight<R, SINGLE>, g, dim3(K1_THREADS), 0, pdl, s, a,
-                   k1_dynamic_smem(a.noise_tiles));
+  return launch_ex(k_propagate_weight<R, SINGLE>, g, dim3(K1_THREADS), 0, pdl, s, a);
 }
 
 template <int R>

@@ -60,10 +60,9 @@ struct K1Args {
   uint32_t* exo_next;        // two buffers (by step parity) of G_total: exchange offsets of step k+1
   HistRec* hist;
   GroupHist* ghist;
+  int* tile_ctr;             // dynamic tile counter (zero at launch; the resampler resets it)
   int n_ring_blocks;         // leading blocks: next step's rings and exchange offsets, previous step's history
   int n_tracks;
-  int k_hint;                // the host's step index, or -1 (read on the device)
-  int noise_tiles;           // tiles per CTA whose noise is drawn before the wait (<= K1_NOISE_TILES)
   TrackParams p0;            // n_tracks == 1: a copy of trk[0]
   // n_tracks == 1 and raw_frame: the step reads the caller's frame (W x H
   // float32, row pitch W) directly, through zmap (TMA, zero fill outside)
@@ -100,6 +99,7 @@ struct ResampleArgs {
   QuantCoeffs qc;
   DevState* ds;
   int fuse_global;             // 1: the last group of a track to finish runs its global step
+  int* tile_ctr;               // propagate kernel's tile counter to reset, or nullptr
   GlobalArgs glob;             // (fuse_global) arguments of that step, finalize = 1
 };
 
@@ -177,7 +177,6 @@ cudaError_t launch_global(const GlobalArgs& a, int n_tracks, cudaStream_t s);
 cudaError_t launch_finish(const GlobalArgs& a, int n_tracks, cudaStream_t s);
 cudaError_t launch_export_states(const float4* pv, const float* In, long long n, float* out, cudaStream_t s);
 cudaError_t k1_occupancy(int R, int* blocks_per_sm);
-size_t k1_dynamic_smem(int noise_tiles);
 const void* propagate_kernel(int R);
 
 // Host helpers shared by the C-ABI entry points (defined in pf_api.cu).

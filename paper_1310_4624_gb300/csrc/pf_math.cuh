@@ -189,6 +189,44 @@ __device__ __forceinline__ float patch_ss(const float* __restrict__ base, int pi
   return acc;
 }
 
+// patch_ss over shared-memory rows (pitch ROI_W floats) read as float pairs:
+// `base` is 8-byte aligned; row b's pixels are base[b ROI_W + 0 .. 2R] (the
+// pair loads also fetch base[.. + 2R + 1], unused).  Same pixels, order and
+// arithmetic as patch_ss.
+template <int R>
+__device__ __forceinline__ float patch_ss_pairs(const float* __restrict__ base, const float (&gxI)[2 * R + 1],
+                                                float dy, float c, float kappa) {
+  auto row = [&](int b, float gy, float acc) {
+    const float2* p2 = reinterpret_cast<const float2*>(base + b * ROI_W);
+#pragma unroll
+    for (int t = 0; t <= R; ++t) {
+      const float2 v = p2[t];
+      const float r0 = fmaf(-gxI[2 * t], gy, v.x);
+      acc = fmaf(r0, r0, acc);
+      if (2 * t + 1 <= 2 * R) {
+        const float r1 = fmaf(-gxI[2 * t + 1], gy, v.y);
+        acc = fmaf(r1, r1, acc);
+      }
+    }
+    return acc;
+  };
+  const float g = ex2(-c * dy * dy);
+  float up = ex2(-c * fmaf(2.0f, dy, 1.0f));
+  float dn = ex2(c * fmaf(2.0f, dy, -1.0f));
+  float acc = row(R, g, 0.0f);
+  float gu = g, gd = g;
+#pragma unroll
+  for (int a = 1; a <= R; ++a) {
+    gu *= up;
+    gd *= dn;
+    up *= kappa;
+    dn *= kappa;
+    acc = row(R + a, gu, acc);
+    acc = row(R - a, gd, acc);
+  }
+  return acc;
+}
+
 // patch_ss on the caller's frame z (W x H, pitch W) instead of the padded
 // frame: pixel values z - b inside the frame, 0 outside; (x0, y0) is the
 // patch's corner in frame coordinates.  Same pixels, values and order as
