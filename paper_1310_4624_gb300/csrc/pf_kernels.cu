@@ -948,18 +948,40 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
     }
   };
 
-  // group maximum over the cluster
-  float m = -INFINITY;
-  for (int sub = lo; sub < hi; sub += RS_SUB) {
-    load_sub(sub);
-#pragma unroll
-    for (int r = 0; r < RS_ITEMS; ++r) m = fmaxf(m, v[r]);
+  // the group's resampling uniform word (Philox stream RESAMPLE, group,
+  // step).  The step index is read here, before the cluster barrier that
+  // precedes every ticket below: the track's global step (run by the last
+  // ticket holder) advances it.
+  uint32_t u;
+  if (a.u_arr) {
+    u = a.u_arr[grp];
+  } else {
+    const TrackParams* P = a.glob.trk + d.track;
+    const int kk = a.glob.ts[d.track].k;
+    u = philox(P->key0, P->key1, make_uint4((uint32_t)d.g, 0u, (uint32_t)kk, P->tag | (ST_RESAMPLE << 4))).x;
   }
-  m = block_max<RS_THREADS>(m, s_f);
-  if (threadIdx.x == 0) s_pub_max = m;
-  cl.sync();
+
+  // group maximum: from the propagate tiles' maxima in a filter step, else
+  // over the cluster (the same set of log-weights either way, NaN ignored)
   float M = -INFINITY;
-  for (int r = 0; r < C; ++r) M = fmaxf(M, *cl.map_shared_rank(&s_pub_max, r));
+  if (single) load_sub(lo);  // the CTA's items, for the quantisation below
+  if (a.tile_part != nullptr) {
+    float m = -INFINITY;
+    for (int t = threadIdx.x; t < d.tile_count; t += RS_THREADS)
+      m = fmaxf(m, a.tile_part[(long long)(d.tile_begin + t) * 8]);
+    M = block_max<RS_THREADS>(m, s_f);
+  } else {
+    float m = -INFINITY;
+    for (int sub = lo; sub < hi; sub += RS_SUB) {
+      if (!single) load_sub(sub);
+#pragma unroll
+      for (int r = 0; r < RS_ITEMS; ++r) m = fmaxf(m, v[r]);
+    }
+    m = block_max<RS_THREADS>(m, s_f);
+    if (threadIdx.x == 0) s_pub_max = m;
+    cl.sync();
+    for (int r = 0; r < C; ++r) M = fmaxf(M, *cl.map_shared_rank(&s_pub_max, r));
+  }
 
   // this CTA's total weight code, then the cluster prefix and group total
   unsigned long long qs = 0;
@@ -981,16 +1003,70 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
     if (r < rank) Sb += x;
     Q += x;
   }
+  // no more reads of the other CTAs' shared memory: arrive now, wait (so
+  // that this CTA's shared memory outlives their reads) only at the end
+  auto cl_token = cl.barrier_arrive();
 
-  // the group's resampling uniform word (Philox stream RESAMPLE, group, step)
-  uint32_t u;
-  if (a.u_arr) {
-    u = a.u_arr[grp];
-  } else {
-    const TrackParams* P = a.glob.trk + d.track;
-    const int kk = a.glob.ts[d.track].k;
-    u = philox(P->key0, P->key1, make_uint4((uint32_t)d.g, 0u, (uint32_t)kk, P->tag | (ST_RESAMPLE << 4))).x;
+  // group estimate and ESS from the propagate tiles' partial sums (rank 0),
+  // each tile's sums rescaled from its own maximum to the group maximum
+  if (rank == 0) {
+    GroupState& G = a.gs[grp];
+    if (a.tile_part != nullptr) {
+      float acc[7] = {0, 0, 0, 0, 0, 0, 0};
+      if (Q != 0) {
+        for (int t = threadIdx.x; t < d.tile_count; t += RS_THREADS) {
+          const float* tp = a.tile_part + (long long)(d.tile_begin + t) * 8;
+          const float Mt = tp[0];
+          if (!(Mt - M >= -87.0f)) continue;
+          const float sc = __expf(Mt - M);
+#pragma unroll
+          for (int q = 0; q < 6; ++q) acc[q] = fmaf(sc, tp[1 + q], acc[q]);
+          acc[6] = fmaf(sc * sc, tp[7], acc[6]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 7; ++q) acc[q] = warp_sum(acc[q]);
+      if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 7; ++q) s_stat[warp][q] = acc[q];
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        float t7[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int w = 0; w < RS_THREADS / 32; ++w)
+          for (int q = 0; q < 7; ++q) t7[q] += s_stat[w][q];
+        const bool ok = (Q != 0) && t7[0] > 0.0f;
+        for (int q = 0; q < 5; ++q) G.xs[q] = ok ? t7[1 + q] / t7[0] : 0.0f;
+        G.ess = ok ? t7[0] * t7[0] / t7[6] : 0.0f;
+      }
+    }
+    if (threadIdx.x == 0) {
+      G.M = M;
+      G.Q = Q;
+    }
   }
+  // The last group of a track to report its statistics runs the track's
+  // global step (its rank-0 CTA), before its own ancestor search, so the
+  // global step overlaps the other groups' searches: a ticket per track
+  // counts groups.  The writer of the group's statistics (thread 0 of rank
+  // 0) fences before taking its ticket; the last taker fences before the
+  // reads.  The ancestors are not among the global step's inputs.
+  if (a.fuse_global && rank == 0) {
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned prev = atomicAdd(&a.glob.ts[d.track].ticket, 1u);
+      s_last = (prev + 1u == (unsigned)a.glob.trk[d.track].G) ? 1 : 0;
+      __threadfence();
+    }
+    __syncthreads();
+    if (s_last) {
+      global_step<RS_THREADS>(a.glob, d.track, *reinterpret_cast<GlobalScratch*>(s_dyn_rs));
+      if (threadIdx.x == 0) a.glob.ts[d.track].ticket = 0u;
+      __syncthreads();  // the scratch is the prefix array below
+    }
+  }
+
+
   const unsigned long long obase = a.local_idx ? 0ull : (unsigned long long)(d.g) * (unsigned long long)Np;
   uint32_t* __restrict__ anc = a.anc + d.base;
   if (Q == 0) {
@@ -1108,67 +1184,9 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
     }
   }
 
-  // group estimate and ESS from the propagate tiles' partial sums (rank 0),
-  // each tile's sums rescaled from its own maximum to the group maximum
-  if (rank == 0) {
-    GroupState& G = a.gs[grp];
-    if (a.tile_part != nullptr) {
-      float acc[7] = {0, 0, 0, 0, 0, 0, 0};
-      if (Q != 0) {
-        for (int t = threadIdx.x; t < d.tile_count; t += RS_THREADS) {
-          const float* tp = a.tile_part + (long long)(d.tile_begin + t) * 8;
-          const float Mt = tp[0];
-          if (!(Mt - M >= -87.0f)) continue;
-          const float sc = __expf(Mt - M);
-#pragma unroll
-          for (int q = 0; q < 6; ++q) acc[q] = fmaf(sc, tp[1 + q], acc[q]);
-          acc[6] = fmaf(sc * sc, tp[7], acc[6]);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 7; ++q) acc[q] = warp_sum(acc[q]);
-      if (lane == 0)
-#pragma unroll
-        for (int q = 0; q < 7; ++q) s_stat[warp][q] = acc[q];
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        float t7[7] = {0, 0, 0, 0, 0, 0, 0};
-        for (int w = 0; w < RS_THREADS / 32; ++w)
-          for (int q = 0; q < 7; ++q) t7[q] += s_stat[w][q];
-        const bool ok = (Q != 0) && t7[0] > 0.0f;
-        for (int q = 0; q < 5; ++q) G.xs[q] = ok ? t7[1 + q] / t7[0] : 0.0f;
-        G.ess = ok ? t7[0] * t7[0] / t7[6] : 0.0f;
-      }
-    }
-    if (threadIdx.x == 0) {
-      G.M = M;
-      G.Q = Q;
-    }
-  }
-  cl.sync();  // keep shared memory alive until every CTA has read it
-  // The next kernel may start once every CTA is past its main work: its
-  // CTAs then fill SMs freed here and overlap the global step below, instead
-  // of taking issue slots from resampling CTAs still at work.
+  // The next kernel may start once every CTA is past its main work.
   grid_dep_launch();
-
-  // The last group of a track to finish runs the track's global step here
-  // (its rank-0 CTA): a ticket per track counts finished groups.  The
-  // writer of the group's statistics (thread 0 of rank 0) fences before
-  // taking its ticket; the last taker fences before the reads.
-  if (a.fuse_global && rank == 0) {
-    __shared__ int s_last;
-    if (threadIdx.x == 0) {
-      __threadfence();
-      const unsigned prev = atomicAdd(&a.glob.ts[d.track].ticket, 1u);
-      s_last = (prev + 1u == (unsigned)a.glob.trk[d.track].G) ? 1 : 0;
-      __threadfence();
-    }
-    __syncthreads();
-    if (s_last) {
-      global_step<RS_THREADS>(a.glob, d.track, *reinterpret_cast<GlobalScratch*>(s_dyn_rs));
-      if (threadIdx.x == 0) a.glob.ts[d.track].ticket = 0u;
-    }
-  }
+  cl.barrier_wait(std::move(cl_token));
 }
 
 
