@@ -137,131 +137,82 @@ __device__ __forceinline__ void gauss_row_scaled(float cf, float x, float c, flo
   }
 }
 
-// One patch row: acc + sum_a (y_a - gxI[a] gy)^2, rows of shared memory
-// (compile-time pitch) or of global memory read through L1.
-template <int R>
-__device__ __forceinline__ float row_ss_smem(const float* __restrict__ rp, const float (&gxI)[2 * R + 1], float gy,
-                                             float acc) {
+// Sum over the patch of (y - I gx gy)^2 (Alg. 1 step U, Sec. V appearance
+// model).  pix(b, a) is the pixel y of patch row b (0 .. 2R), column a;
+// gxI[a] = I gx(a).  Rows are visited centre-out so that gy follows the same
+// ratio recurrence as gauss_row with four live registers (dy = cyf - y).
+// Even and odd columns accumulate separately (two independent FMA chains),
+// summed at the end.  Every variant below reads the same pixels in the same
+// order, so all give bit-identical sums.
+template <int R, class Pix>
+__device__ __forceinline__ float patch_sum(Pix pix, const float (&gxI)[2 * R + 1], float dy, float c, float kappa) {
+  float ae = 0.0f, ao = 0.0f;
+  auto row = [&](int b, float gy) {
 #pragma unroll
-  for (int a = 0; a < 2 * R + 1; ++a) {
-    const float r = fmaf(-gxI[a], gy, rp[a]);
-    acc = fmaf(r, r, acc);
-  }
-  return acc;
-}
-template <int R>
-__device__ __forceinline__ float row_ss_global(const float* __restrict__ rp, const float (&gxI)[2 * R + 1], float gy,
-                                               float acc) {
+    for (int a = 0; a < 2 * R + 1; ++a) {
+      const float r = fmaf(-gxI[a], gy, pix(b, a));
+      if (a & 1)
+        ao = fmaf(r, r, ao);
+      else
+        ae = fmaf(r, r, ae);
+    }
+  };
+  const float g = ex2(-c * dy * dy);
+  float up = ex2(-c * fmaf(2.0f, dy, 1.0f));
+  float dn = ex2(c * fmaf(2.0f, dy, -1.0f));
+  row(R, g);
+  float gu = g, gd = g;
 #pragma unroll
-  for (int a = 0; a < 2 * R + 1; ++a) {
-    const float r = fmaf(-gxI[a], gy, __ldg(rp + a));
-    acc = fmaf(r, r, acc);
+  for (int a = 1; a <= R; ++a) {
+    gu *= up;
+    gd *= dn;
+    up *= kappa;
+    dn *= kappa;
+    row(R + a, gu);
+    row(R - a, gd);
   }
-  return acc;
+  return ae + ao;
 }
 
-// Sum over the patch of (y - I gx gy)^2; `row(b)` is the address of patch
-// row b (0 .. 2R).  Rows are visited centre-out so that gy follows the same
-// ratio recurrence as gauss_row with four live registers; dy = cyf - y.
+// Rows of shared memory (pitch ROI_W) or of the padded frame in global
+// memory (read through L1).
 template <int R, bool SMEM>
 __device__ __forceinline__ float patch_ss(const float* __restrict__ base, int pitch, const float (&gxI)[2 * R + 1],
                                           float dy, float c, float kappa) {
-  auto row = [&](int b, float gy, float acc) {
-    if constexpr (SMEM)
-      return row_ss_smem<R>(base + b * ROI_W, gxI, gy, acc);
-    else
-      return row_ss_global<R>(base + (long long)b * pitch, gxI, gy, acc);
-  };
-  const float g = ex2(-c * dy * dy);
-  float up = ex2(-c * fmaf(2.0f, dy, 1.0f));
-  float dn = ex2(c * fmaf(2.0f, dy, -1.0f));
-  float acc = row(R, g, 0.0f);
-  float gu = g, gd = g;
-#pragma unroll
-  for (int a = 1; a <= R; ++a) {
-    gu *= up;
-    gd *= dn;
-    up *= kappa;
-    dn *= kappa;
-    acc = row(R + a, gu, acc);
-    acc = row(R - a, gd, acc);
-  }
-  return acc;
+  if constexpr (SMEM)
+    return patch_sum<R>([&](int b, int a) { return base[b * ROI_W + a]; }, gxI, dy, c, kappa);
+  else
+    return patch_sum<R>([&](int b, int a) { return __ldg(base + (long long)b * pitch + a); }, gxI, dy, c, kappa);
 }
 
-// patch_ss over shared-memory rows (pitch ROI_W floats) read as float pairs:
-// `base` is 8-byte aligned; row b's pixels are base[b ROI_W + 0 .. 2R] (the
-// pair loads also fetch base[.. + 2R + 1], unused).  Same pixels, order and
-// arithmetic as patch_ss.
+// Shared-memory rows read as float pairs: `base` is 8-byte aligned and row
+// b's pixels are base[b ROI_W + 0 .. 2R] (the pair loads also fetch
+// base[.. + 2R + 1], unused).
 template <int R>
 __device__ __forceinline__ float patch_ss_pairs(const float* __restrict__ base, const float (&gxI)[2 * R + 1],
                                                 float dy, float c, float kappa) {
-  auto row = [&](int b, float gy, float acc) {
-    const float2* p2 = reinterpret_cast<const float2*>(base + b * ROI_W);
-#pragma unroll
-    for (int t = 0; t <= R; ++t) {
-      const float2 v = p2[t];
-      const float r0 = fmaf(-gxI[2 * t], gy, v.x);
-      acc = fmaf(r0, r0, acc);
-      if (2 * t + 1 <= 2 * R) {
-        const float r1 = fmaf(-gxI[2 * t + 1], gy, v.y);
-        acc = fmaf(r1, r1, acc);
-      }
-    }
-    return acc;
-  };
-  const float g = ex2(-c * dy * dy);
-  float up = ex2(-c * fmaf(2.0f, dy, 1.0f));
-  float dn = ex2(c * fmaf(2.0f, dy, -1.0f));
-  float acc = row(R, g, 0.0f);
-  float gu = g, gd = g;
-#pragma unroll
-  for (int a = 1; a <= R; ++a) {
-    gu *= up;
-    gd *= dn;
-    up *= kappa;
-    dn *= kappa;
-    acc = row(R + a, gu, acc);
-    acc = row(R - a, gd, acc);
-  }
-  return acc;
+  return patch_sum<R>(
+      [&](int b, int a) {
+        const float2 v = reinterpret_cast<const float2*>(base + b * ROI_W)[a >> 1];
+        return (a & 1) ? v.y : v.x;
+      },
+      gxI, dy, c, kappa);
 }
 
-// patch_ss on the caller's frame z (W x H, pitch W) instead of the padded
-// frame: pixel values z - b inside the frame, 0 outside; (x0, y0) is the
-// patch's corner in frame coordinates.  Same pixels, values and order as
-// patch_ss on the padded frame.
+// The caller's frame z (W x H, pitch W) instead of the padded frame: pixel
+// values z - b inside the frame, 0 outside; (x0, y0) is the patch's corner
+// in frame coordinates.
 template <int R>
 __device__ __forceinline__ float patch_ss_raw(const float* __restrict__ z, int W, int H, float bg, int x0, int y0,
                                               const float (&gxI)[2 * R + 1], float dy, float c, float kappa) {
-  auto row = [&](int b, float gy, float acc) {
-    const int yy = y0 + b;
-    const bool rin = (unsigned)yy < (unsigned)H;
-    const float* __restrict__ rp = z + (long long)(rin ? yy : 0) * W;
-#pragma unroll
-    for (int a = 0; a < 2 * R + 1; ++a) {
-      const int xx = x0 + a;
-      const float y = (rin && (unsigned)xx < (unsigned)W) ? __fsub_rn(__ldg(rp + xx), bg) : 0.0f;
-      const float r = fmaf(-gxI[a], gy, y);
-      acc = fmaf(r, r, acc);
-    }
-    return acc;
-  };
-  const float g = ex2(-c * dy * dy);
-  float up = ex2(-c * fmaf(2.0f, dy, 1.0f));
-  float dn = ex2(c * fmaf(2.0f, dy, -1.0f));
-  float acc = row(R, g, 0.0f);
-  float gu = g, gd = g;
-#pragma unroll
-  for (int a = 1; a <= R; ++a) {
-    gu *= up;
-    gd *= dn;
-    up *= kappa;
-    dn *= kappa;
-    acc = row(R + a, gu, acc);
-    acc = row(R - a, gd, acc);
-  }
-  return acc;
+  return patch_sum<R>(
+      [&](int b, int a) {
+        const int yy = y0 + b, xx = x0 + a;
+        return ((unsigned)yy < (unsigned)H && (unsigned)xx < (unsigned)W)
+                   ? __fsub_rn(__ldg(z + (long long)yy * W + xx), bg)
+                   : 0.0f;
+      },
+      gxI, dy, c, kappa);
 }
 
 // Natural log of a uniform u = ((w >> 9) + 1/2) 2^-23: MUFU log2 where its
