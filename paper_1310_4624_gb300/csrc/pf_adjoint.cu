@@ -263,7 +263,22 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
       const float lam = (float)a.lam_k[P.group_off + g];
       const float wbar = (lw == lw && lw - lam > -87.0f) ? __expf(lw - lam) : 0.0f;
       const float dlw = (float)a.dlam_k[P.group_off + g] * wbar;
-      if (k >= 1 && dlw != 0.0f) atomicAdd(&a.D[P.group_off + o], (double)dlw);
+      if (k >= 1) {
+        // dL_{k-1} of the origin group: the tile's slots originate in g or in
+        // its ring predecessor, so a warp adds two sums instead of 32 terms
+        // (slots of any third origin add theirs directly)
+        const unsigned full = __activemask();
+        const int other = __reduce_max_sync(full, o != g ? o : -1);
+        const bool third = o != g && o != other;
+        const float own = warp_sum_active(full, (o == g) ? dlw : 0.0f);
+        const float pre = warp_sum_active(full, (o != g && !third) ? dlw : 0.0f);
+        const int leader = __ffs(full) - 1;
+        if (lane == leader) {
+          if (own != 0.0f) atomicAdd(&a.D[P.group_off + g], (double)own);
+          if (other >= 0 && pre != 0.0f) atomicAdd(&a.D[P.group_off + other], (double)pre);
+        }
+        if (third && dlw != 0.0f) atomicAdd(&a.D[P.group_off + o], (double)dlw);
+      }
       // adjoint of the state: the likelihood term plus the children's
       float4 c = a.Cc_pv[i];
       float cI = a.Cc_I[i];
@@ -285,12 +300,22 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
         gacc[3] = fmaf(c.x, e0, fmaf(c.y, e1, gacc[3]));  // sigma_pos
         gacc[4] = fmaf(c.z, e2, fmaf(c.w, e3, gacc[4]));  // sigma_v
         // NCV Jacobian transposed onto the parent: x <- x, vx <- x + vx, ...
+        // Resampled children of one parent sit in neighbouring slots: lanes
+        // sharing a parent add their terms first, one lane stores the sum.
         const long long pi = P.part_off + par;
-        atomicAdd(&a.Cp_pv[pi].x, c.x);
-        atomicAdd(&a.Cp_pv[pi].y, c.y);
-        atomicAdd(&a.Cp_pv[pi].z, c.x + c.z);
-        atomicAdd(&a.Cp_pv[pi].w, c.y + c.w);
-        atomicAdd(&a.Cp_I[pi], cI);
+        float t[5] = {c.x, c.y, c.x + c.z, c.y + c.w, cI};
+        const unsigned peers = __match_any_sync(__activemask(), (unsigned long long)pi);
+        if (peers != (1u << lane)) {
+#pragma unroll
+          for (int q = 0; q < 5; ++q) t[q] = warp_sum_active(peers, t[q]);
+        }
+        if (lane == __ffs(peers) - 1) {
+          atomicAdd(&a.Cp_pv[pi].x, t[0]);
+          atomicAdd(&a.Cp_pv[pi].y, t[1]);
+          atomicAdd(&a.Cp_pv[pi].z, t[2]);
+          atomicAdd(&a.Cp_pv[pi].w, t[3]);
+          atomicAdd(&a.Cp_I[pi], t[4]);
+        }
       } else if (A_enters) {
         gacc[1] += cI;  // the initial intensity is A
       }

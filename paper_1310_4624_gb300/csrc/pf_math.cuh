@@ -35,6 +35,14 @@ __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+// Sum over the lanes of `mask` (every lane of the mask calls it; the
+// result reaches all of them).
+__device__ __forceinline__ float warp_sum_active(unsigned mask, float v) {
+  if (mask == 0xffffffffu) return warp_sum(v);
+  float s = 0.0f;
+  for (unsigned m = mask; m; m &= m - 1) s += __shfl_sync(mask, v, __ffs(m) - 1);
+  return s;
+}
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
