@@ -390,7 +390,8 @@ def bench_sharing(dev):
     """Information-sharing start: 100 frames 512 x 512, G = 256 x 4096, group
     0 in a 2 px disc around the truth, the other groups uniform over the
     image.  For ARNA and RNA 10 %: the first step at which every group mean is
-    within 2 px of the truth, and PE_eff / G per step."""
+    within 2 px of the truth, the first steps at which PE_eff / G reaches 0.5
+    and 0.9 (Sec. V-B's recovery of PE_eff), and PE_eff / G per step."""
     import torch
     from paper_1310_4624_gb300 import synth
     from paper_1310_4624_gb300.filter import ParticleFilter, config_from_workload
@@ -414,37 +415,45 @@ def bench_sharing(dev):
             pe.append(round(st["pe_eff"] / wl.G, 4))
             nex.append(st["n_ex"])
         pf.close()
+
+        def first_at(level):
+            return next((k for k, v in enumerate(pe) if k >= 1 and v >= level), None)
         out["arna" if mode == synth.ARNA else "rna10"] = {
-            "steps_to_all_groups_within_2px": first, "pe_eff_over_G": pe[:40], "n_ex": nex[:40]}
+            "steps_to_all_groups_within_2px": first, "steps_to_pe_eff_0.5": first_at(0.5),
+            "steps_to_pe_eff_0.9": first_at(0.9), "pe_eff_over_G_last": pe[-1],
+            "pe_eff_over_G": pe[:40], "n_ex": nex[:40]}
     out["workload"] = synth.sharing().name.rsplit("_", 1)[0]
     return out
 
 
 def bench_accuracy(dev, n_seq: int = 10):
-    """Tracking accuracy on the tracking workload over `n_seq` sequences
-    (data seeds 0..n_seq-1, rendered on the device): position RMSE of the
-    global estimate against the truth, ARNA and RNA 10 % on identical Philox
-    streams."""
+    """Tracking accuracy and per-mode step time on the tracking workload over
+    `n_seq` sequences (data seeds 0..n_seq-1, rendered on the device):
+    position RMSE of the global estimate against the truth, for ARNA and RNA
+    with 0 %, 10 % and 50 % exchange on identical Philox streams (the paper's
+    comparison, Sec. V-A), and the mean device time per step of each (CUDA
+    events around whole 100-step runs; L2 not flushed between steps)."""
     import torch
     from paper_1310_4624_gb300 import synth
     from paper_1310_4624_gb300.filter import ParticleFilter, config_from_workload
     wls = [synth.tracking(mode=synth.ARNA, data_seed=s) for s in range(n_seq)]
     frames, truths = synth.render_batched_torch(wls, dev, seed=1)
+    modes = {"arna": dict(mode=synth.ARNA), "rna0": dict(mode=synth.RNA, ex_ratio=0.0),
+             "rna10": dict(mode=synth.RNA, ex_ratio=0.10), "rna50": dict(mode=synth.RNA, ex_ratio=0.50)}
     out = {}
-    for mode in (synth.ARNA, synth.RNA):
-        se, per = 0.0, []
+    for name, kw in modes.items():
+        se, per, ms = 0.0, [], 0.0
         for s, wl in enumerate(wls):
-            wl = wl.replace(mode=mode)
+            wl = wl.replace(**kw)
             pf = ParticleFilter([config_from_workload(wl, truths[s][0])], history=wl.T + 1, device=dev)
-            for k in range(wl.T):
-                pf.step(frames[s, k])
+            ms += _events(pf.stream, lambda: [pf.step(frames[s, k]) for k in range(wl.T)])
             hs = pf.history_stats(0, wl.T)
             e = np.array([np.sum((h["xhat"][:2] - truths[s][h["step"], :2]) ** 2) for h in hs])
             per.append(float(math.sqrt(e.mean())))
             se += float(e.sum())
             pf.close()
-        out["arna" if mode == synth.ARNA else "rna10"] = {
-            "rmse_px": math.sqrt(se / (n_seq * wls[0].T)), "per_sequence": [round(v, 4) for v in per]}
+        out[name] = {"rmse_px": math.sqrt(se / (n_seq * wls[0].T)), "per_sequence": [round(v, 4) for v in per],
+                     "ms_per_step": ms / (n_seq * wls[0].T)}
     out["sequences"] = n_seq
     out["workload"] = wls[0].name.rsplit("_", 1)[0]
     return out

@@ -24,8 +24,9 @@ constexpr int K1_TILE = K1_THREADS * K1_PPT;  // slots per tile (one group)
 constexpr int K1_MIN_BLOCKS = PF_K1_MIN_BLOCKS;  // resident propagate CTAs per SM the register budget targets
 constexpr int ROI_W = 40;             // staged frame box width = smem row pitch (floats, = 8 mod 32 banks)
 constexpr int ROI_BOX_H = 8;          // rows per TMA box
-constexpr int ROI_MAX_BOXES = 8;      // staged rows <= 64
-constexpr int ROI_FLOATS = ROI_W * ROI_BOX_H * ROI_MAX_BOXES;
+constexpr int ROI_MAX_BOXES = 8;      // boxes per staged box
+constexpr int ROI_ROWS = ROI_BOX_H * ROI_MAX_BOXES;  // staged rows at most (64)
+constexpr int ROI_FLOATS = ROI_W * ROI_ROWS;
 constexpr int RING_SMEM_G = ROI_FLOATS / 2;  // ring orders drawn ahead up to this G
 constexpr int RS_THREADS = 512;       // resampler CTA
 constexpr int RS_ITEMS = 8;           // items per thread per resampler sub-chunk

@@ -574,9 +574,10 @@ __device__ __forceinline__ void prop_noise(uint32_t key0, uint32_t key1, uint32_
 
 // Propagate + weight: tiles of K1_TILE = K1_PPT x K1_THREADS slots of one
 // group, K1_PPT particles per thread.  Each tile stages the bounding box of
-// its particles' patches (padded frame coordinates) into shared memory with
-// TMA when it fits ROI_W x ROI_BOX_H*ROI_MAX_BOXES floats, else reads the
-// frame through L1.  Leading blocks draw the next step's ARNA rings.
+// its particles' patches (at most ROI_W x ROI_ROWS floats) in shared memory
+// by TMA; tiles whose patches do not fit read the frame through L1.
+// Leading blocks draw the next step's rings and exchange offsets and finish
+// the previous step.
 // SINGLE: one track, whose parameters come from the kernel's constant
 // parameter block (a.p0) instead of global memory.
 template <int R, bool SINGLE>
@@ -822,21 +823,19 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
       }
     }
 
-    // Per-tile partial sums for the group estimate, relative to the tile max.
+    // Per-tile partial sums for the group estimate, relative to the tile
+    // max: each warp sums relative to its own max, and the 8 writers rescale
+    // the warps' sums to the tile max (one barrier).
     int key = INT_MIN;
 #pragma unroll
     for (int q = 0; q < K1_PPT; ++q)
       if (lw[q] == lw[q]) key = max(key, float_key(lw[q]));  // NaN does not count
     key = __reduce_max_sync(0xffffffffu, key);
-    if (lane == 0) s_key[warp] = key;
-    __syncthreads();
-#pragma unroll
-    for (int w = 0; w < NW; ++w) key = max(key, s_key[w]);
-    const float Mt = key_float(key);
+    const float Mw = key == INT_MIN ? -INFINITY : key_float(key);
     float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
     for (int q = 0; q < K1_PPT; ++q) {
-      const float e = (lw[q] - Mt >= -87.0f) ? __expf(lw[q] - Mt) : 0.0f;
+      const float e = (lw[q] - Mw >= -87.0f) ? __expf(lw[q] - Mw) : 0.0f;
       v[0] += e;
       v[1] = fmaf(e, s[q].x, v[1]);
       v[2] = fmaf(e, s[q].y, v[2]);
@@ -848,15 +847,25 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
     int slot;
     const float x = warp_reduce8(v, lane, slot);
     if ((lane & 3) == 0) s_red[warp][slot] = x;
+    if (lane == 0) s_key[warp] = key;
     __syncthreads();
     if (threadIdx.x < 8) {
+      int kt = INT_MIN;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) kt = max(kt, s_key[w]);
+      const float Mt = key_float(kt);
       float r;
       if (threadIdx.x == 0) {
         r = Mt;
       } else {
         r = 0.0f;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) r += s_red[w][threadIdx.x - 1];
+        for (int w = 0; w < NW; ++w) {
+          const float mw = s_key[w] == INT_MIN ? -INFINITY : key_float(s_key[w]);
+          float sc = (mw - Mt >= -87.0f) ? __expf(mw - Mt) : 0.0f;
+          if (threadIdx.x == 7) sc *= sc;  // sums of e^2
+          r = fmaf(sc, s_red[w][threadIdx.x - 1], r);
+        }
       }
       a.tile_part[(long long)tile * 8 + threadIdx.x] = r;
     }
