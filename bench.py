@@ -389,40 +389,112 @@ def adam_fit(pf, wl, fr, truth, iters: int = 200, lr: float = 0.02):
 def bench_sharing(dev):
     """Information-sharing start: 100 frames 512 x 512, G = 256 x 4096, group
     0 in a 2 px disc around the truth, the other groups uniform over the
-    image.  For ARNA and RNA 10 %: the first step at which every group mean is
+    image.  For ARNA and RNA 10 %, under the patch-residual likelihood and
+    the frame likelihood ratio: the first step at which every group mean is
     within 2 px of the truth, the first steps at which PE_eff / G reaches 0.5
-    and 0.9 (Sec. V-B's recovery of PE_eff), and PE_eff / G per step."""
+    and 0.9 (Sec. V-B's recovery of PE_eff), the final estimate's error, and
+    PE_eff / G per step."""
     import torch
     from paper_1310_4624_gb300 import synth
     from paper_1310_4624_gb300.filter import ParticleFilter, config_from_workload
     out = {}
     frames = truth = fr = None
-    for mode in (synth.ARNA, synth.RNA):
-        wl = synth.sharing(mode=mode)
-        if frames is None:
-            frames, truth = synth.make_sequence(wl)
-            fr = torch.from_numpy(frames).to(dev)
-        pf = ParticleFilter([config_from_workload(wl, truth[0])], history=wl.T + 1, device=dev)
-        for k in range(wl.T):
-            pf.step(fr[k])
-        pe, nex, first = [], [], None
-        for k in range(wl.T):
-            st = pf.stats(k)
-            gx = st["group_xhat"]
-            d = np.hypot(gx[0] - truth[k, 0], gx[1] - truth[k, 1])
-            if first is None and np.all(d <= 2.0):
-                first = k
-            pe.append(round(st["pe_eff"] / wl.G, 4))
-            nex.append(st["n_ex"])
-        pf.close()
+    for obs_name, obs in (("patch", 0), ("frame", 1)):
+        res = {}
+        for mode in (synth.ARNA, synth.RNA):
+            wl = synth.sharing(mode=mode, obs_model=obs)
+            if frames is None:
+                frames, truth = synth.make_sequence(wl)
+                fr = torch.from_numpy(frames).to(dev)
+            pf = ParticleFilter([config_from_workload(wl, truth[0])], history=wl.T + 1, device=dev)
+            for k in range(wl.T):
+                pf.step(fr[k])
+            pe, nex, first = [], [], None
+            for k in range(wl.T):
+                st = pf.stats(k)
+                gx = st["group_xhat"]
+                d = np.hypot(gx[0] - truth[k, 0], gx[1] - truth[k, 1])
+                if first is None and np.all(d <= 2.0):
+                    first = k
+                pe.append(round(st["pe_eff"] / wl.G, 4))
+                nex.append(st["n_ex"])
+            xhat, _, _ = pf.estimate()
+            pf.close()
 
-        def first_at(level):
-            return next((k for k, v in enumerate(pe) if k >= 1 and v >= level), None)
-        out["arna" if mode == synth.ARNA else "rna10"] = {
-            "steps_to_all_groups_within_2px": first, "steps_to_pe_eff_0.5": first_at(0.5),
-            "steps_to_pe_eff_0.9": first_at(0.9), "pe_eff_over_G_last": pe[-1],
-            "pe_eff_over_G": pe[:40], "n_ex": nex[:40]}
+            def first_at(level):
+                return next((k for k, v in enumerate(pe) if k >= 1 and v >= level), None)
+            res["arna" if mode == synth.ARNA else "rna10"] = {
+                "steps_to_all_groups_within_2px": first, "steps_to_pe_eff_0.5": first_at(0.5),
+                "steps_to_pe_eff_0.9": first_at(0.9), "pe_eff_over_G_last": pe[-1],
+                "final_error_px": float(np.hypot(*(xhat[0, :2] - truth[-1, :2]))),
+                "pe_eff_over_G": pe[:40], "n_ex": nex[:40]}
+        out[obs_name] = res
     out["workload"] = synth.sharing().name.rsplit("_", 1)[0]
+    return out
+
+
+def bench_pe_eff_recovery(dev, G_list=(24, 96, 192, 384), Np: int = 4096, T: int = 30):
+    """PE_eff / G per iteration from the information-sharing start (group 0
+    at the truth, the others spread over the image), for 24, 96, 192 and 384
+    groups of 4096 particles, ARNA against RNA with 10 % and 50 % exchange,
+    under the frame likelihood ratio (with which spread-out groups can find
+    the spot).  The quantity of Sec. V-B's recovery figure; the paper quotes
+    it after 10 and 20 iterations."""
+    import torch
+    from paper_1310_4624_gb300 import synth
+    from paper_1310_4624_gb300.filter import ParticleFilter, config_from_workload
+    out = {}
+    base = synth.sharing(T=T, obs_model=1)
+    frames, truth = synth.make_sequence(base)
+    fr = torch.from_numpy(frames).to(dev)
+    modes = {"arna": dict(mode=synth.ARNA), "rna10": dict(mode=synth.RNA, ex_ratio=0.10),
+             "rna50": dict(mode=synth.RNA, ex_ratio=0.50)}
+    for G in G_list:
+        row = {}
+        for name, kw in modes.items():
+            wl = base.replace(G=G, Np=Np, **kw)
+            pf = ParticleFilter([config_from_workload(wl, truth[0])], history=T + 1, device=dev)
+            for k in range(T):
+                pf.step(fr[k])
+            pe = [h["pe_eff"] / G for h in pf.history_stats(0, T)]
+            pf.close()
+            row[name] = {"at_10": round(pe[10], 4), "at_20": round(pe[min(20, T - 1)], 4),
+                         "curve": [round(v, 4) for v in pe]}
+        out["G%d" % G] = row
+    out["particles_per_group"] = Np
+    return out
+
+
+def bench_rmse_vs_groups(dev, G_list=(24, 96, 192, 384), Np: int = 40, n_seq: int = 5):
+    """Tracking accuracy with a constant 40 particles per group, initialised
+    at the target (Sec. V-A's accuracy figure): position RMSE over `n_seq`
+    tracking sequences for 24 ... 384 groups, ARNA against RNA with 10 % and
+    50 % exchange."""
+    import torch
+    from paper_1310_4624_gb300 import synth
+    from paper_1310_4624_gb300.filter import ParticleFilter, config_from_workload
+    wls = [synth.tracking(data_seed=s) for s in range(n_seq)]
+    frames, truths = synth.render_batched_torch(wls, dev, seed=2)
+    modes = {"arna": dict(mode=synth.ARNA), "rna10": dict(mode=synth.RNA, ex_ratio=0.10),
+             "rna50": dict(mode=synth.RNA, ex_ratio=0.50)}
+    out = {}
+    for G in G_list:
+        row = {}
+        for name, kw in modes.items():
+            se, n = 0.0, 0
+            for s, wl0 in enumerate(wls):
+                wl = wl0.replace(G=G, Np=Np, **kw)
+                pf = ParticleFilter([config_from_workload(wl, truths[s][0])], history=wl.T + 1, device=dev)
+                for k in range(wl.T):
+                    pf.step(frames[s, k])
+                for h in pf.history_stats(0, wl.T):
+                    se += float(np.sum((h["xhat"][:2] - truths[s][h["step"], :2]) ** 2))
+                    n += 1
+                pf.close()
+            row[name] = round(math.sqrt(se / n), 4)
+        out["G%d" % G] = row
+    out["particles_per_group"] = Np
+    out["sequences"] = n_seq
     return out
 
 
@@ -558,6 +630,8 @@ def main():
                 "kernel": "k_propagate_weight", "peak_source": "%d SMs x 128 lanes x %.0f MHz (%s sm_max_mhz)"
                 % (sms, f_max / 1e6, src),
                 "kernel_ms": k1_avg_s * 1e3,
+                "frac_at_sampled_clock": (achieved / (sms * 128 * a["clocks"]["sm_mhz"] * 1e6)
+                                          if a["clocks"] and a["clocks"].get("sm_mhz") else None),
                 "hbm_frac": ALG_BYTES * wl.N / k1_avg_s / (float(peaks["hbm_gbs"]) * 1e9),
                 "sfu_frac": ALG_SFU_OPS * wl.N / k1_avg_s / (sms * 16 * f_max)}
     kernels = {n: {"launches": c, "ms_per_launch": ms / max(1, c), "share": ms / max(1e-12, sum(
@@ -585,6 +659,8 @@ def main():
         line["adjoint"] = bench_adjoint(dev, flush)
         line["sharing"] = bench_sharing(dev)
         line["accuracy"] = bench_accuracy(dev)
+        line["pe_eff_recovery"] = bench_pe_eff_recovery(dev)
+        line["rmse_vs_groups"] = bench_rmse_vs_groups(dev)
         del flush
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, frames, truth)

@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define PF_ABI_VERSION 1
+#define PF_ABI_VERSION 2
 
 typedef enum pf_status {
   PF_OK = 0,
@@ -71,11 +71,22 @@ enum {
   PF_INIT_USER = 3     /* copied from pf_init's user_state_dev */
 };
 
-/* One track's filter.  Observation model (Sec. V, Fig. 1): a Gaussian spot
- * of width sigma_psf and amplitude I on background `background`; the
- * log-likelihood of a particle is -sum (z - background - I gx gy)^2 /
- * (2 sigma_obs^2) over the (2 patch_radius + 1)^2 pixels around its nearest
- * pixel, pixels outside the frame counting as background.  Dynamics: nearly
+/* Observation models (obs_model).  Both describe a Gaussian spot of width
+ * sigma_psf and amplitude I on background `background` (Sec. V, Fig. 1)
+ * with Gaussian noise sigma_obs, the spot truncated to the (2 patch_radius
+ * + 1)^2 pixels around the particle's nearest pixel, pixels outside the
+ * frame counting as background:
+ *  PF_OBS_PATCH: l = -sum_patch (z - b - I gx gy)^2 / (2 sigma_obs^2), the
+ *    residual of the patch alone;
+ *  PF_OBS_FRAME: the likelihood of the whole frame divided by that of the
+ *    background alone, l = -sum_patch [(z - b - I gx gy)^2 - (z - b)^2] /
+ *    (2 sigma_obs^2) (pixels off the patch cancel): particles over plain
+ *    background score about 0, so a search from a spread-out start finds
+ *    the spot (the information-sharing scenario of Sec. V-B); log Z is then
+ *    the log of that ratio. */
+enum { PF_OBS_PATCH = 0, PF_OBS_FRAME = 1 };
+
+/* One track's filter.  Observation model: obs_model above.  Dynamics: nearly
  * constant velocity with unit frame interval and independent Gaussian noise
  * sigma_pos (position), sigma_v (velocity), sigma_I (intensity). */
 typedef struct pf_track_config {
@@ -93,7 +104,7 @@ typedef struct pf_track_config {
   float init_lo[5];
   float init_hi[5];
   float init_radius;
-  int32_t reserved0;    /* must be 0 */
+  int32_t obs_model;    /* PF_OBS_PATCH (default) or PF_OBS_FRAME */
   uint64_t seed;        /* Philox4x32-10 key */
   uint32_t track_id;    /* Philox stream id of this track, < 2^24 */
   int32_t record_ancestors; /* 1: keep per-step ancestry for pf_backward */

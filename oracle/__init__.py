@@ -22,7 +22,7 @@ import numpy as np
 from . import build as _build
 
 RNA, ARNA = 0, 1
-OBS_IMAGE, OBS_POINT = 0, 1
+OBS_IMAGE, OBS_POINT, OBS_FRAME = 0, 1, 2
 INIT_POINT, INIT_UNIFORM, INIT_SHARING = 0, 1, 2
 
 
@@ -73,6 +73,8 @@ def lib():
         L.ora_propagate.argtypes = [C.POINTER(Cfg), C.c_uint32, _P, _P]
         L.ora_loglik_image.argtypes = [C.POINTER(Cfg), _P, C.c_double, C.c_double, C.c_double]
         L.ora_loglik_image.restype = C.c_double
+        L.ora_loglik_frame.argtypes = [C.POINTER(Cfg), _P, C.c_double, C.c_double, C.c_double]
+        L.ora_loglik_frame.restype = C.c_double
         L.ora_loglik_image_batch.argtypes = [C.POINTER(Cfg), _P, _P, C.c_int64, _P]
         L.ora_exp2_coeffs.argtypes = [_P]
         L.ora_quantize.argtypes = [_P, C.c_int32, _P]
@@ -114,7 +116,8 @@ def cfg_from_workload(wl, track: int = 0) -> Cfg:
     Real parameters are rounded to FP32 first: the GPU library receives them
     as FP32, and both sides must work from the same numbers."""
     f = lambda v: float(np.float32(v))  # noqa: E731
-    return make_cfg(G=wl.G, Np=wl.Np, H=wl.H, W=wl.W, R=wl.patch_radius, mode=wl.mode,
+    obs = OBS_FRAME if getattr(wl, "obs_model", 0) == 1 else OBS_IMAGE
+    return make_cfg(G=wl.G, Np=wl.Np, H=wl.H, W=wl.W, R=wl.patch_radius, mode=wl.mode, obs_kind=obs,
                     sigma_psf=f(wl.sigma_psf), background=f(wl.background), sigma_obs=f(wl.sigma_obs),
                     sigma_pos=f(wl.sigma_pos), sigma_v=f(wl.sigma_v), sigma_I=f(wl.sigma_I),
                     ex_ratio=f(wl.ex_ratio), cutoff=f(wl.pe_eff_cutoff), seed=wl.seed, track=track)
@@ -206,6 +209,12 @@ def propagate(cfg: Cfg, k: int, pop) -> np.ndarray:
 def loglik_image(cfg: Cfg, frame, x: float, y: float, I: float) -> float:
     f = _c(frame, np.float32)
     return lib().ora_loglik_image(C.byref(cfg), _ptr(f), x, y, I)
+
+
+def loglik_frame(cfg: Cfg, frame, x: float, y: float, I: float) -> float:
+    """The frame likelihood ratio (ora_loglik_frame) of one state."""
+    f = _c(frame, np.float32)
+    return lib().ora_loglik_frame(C.byref(cfg), _ptr(f), x, y, I)
 
 
 def loglik_image_many(cfg: Cfg, frame, states) -> np.ndarray:

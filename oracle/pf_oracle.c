@@ -49,6 +49,7 @@
 
 #define ORA_OBS_IMAGE 0
 #define ORA_OBS_POINT 1
+#define ORA_OBS_FRAME 2
 
 #define ORA_INIT_POINT 0
 #define ORA_INIT_UNIFORM 1
@@ -64,7 +65,7 @@ typedef struct {
   int32_t G, Np, H, W;
   int32_t R;        /* patch radius: the likelihood patch is (2R+1)^2 pixels */
   int32_t mode;     /* ORA_RNA or ORA_ARNA */
-  int32_t obs_kind; /* ORA_OBS_IMAGE (the paper's model) or ORA_OBS_POINT */
+  int32_t obs_kind; /* ORA_OBS_IMAGE (patch residual), ORA_OBS_FRAME (frame likelihood ratio) or ORA_OBS_POINT */
   int32_t pad0;
   double sigma_psf, background, sigma_obs;
   double sigma_pos, sigma_v, sigma_I;
@@ -329,9 +330,40 @@ double ora_loglik_image(const ora_cfg* c, const float* frame, double x, double y
   return -acc / (2.0 * c->sigma_obs * c->sigma_obs);
 }
 
-/* ora_loglik_image for each column of a 5 x n state array. */
+/* The Gaussian likelihood of the whole frame z_k (Sec. II's p(z_k | x_k))
+ * with the spot model of ora_loglik_image (zero outside the patch), as a
+ * ratio to the likelihood of the background alone: every pixel off the
+ * patch contributes equally to both and cancels, leaving
+ *   l = -sum_patch [ (zbar - b - I gx gy)^2 - (zbar - b)^2 ] / (2 sigma_obs^2).
+ * Particles over plain background then score about 0 instead of the patch
+ * residual of the noise alone. */
+double ora_loglik_frame(const ora_cfg* c, const float* frame, double x, double y, double I) {
+  if (!isfinite(x) || !isfinite(y) || !isfinite(I)) return NAN;
+  double cx = floor(x + 0.5), cy = floor(y + 0.5);
+  double b = c->background, s2 = 2.0 * c->sigma_psf * c->sigma_psf;
+  double acc = 0.0;
+  for (int dv = -c->R; dv <= c->R; ++dv) {
+    double v = cy + dv;
+    for (int du = -c->R; du <= c->R; ++du) {
+      double u = cx + du;
+      double z = b;
+      if (u >= 0.0 && u < (double)c->W && v >= 0.0 && v < (double)c->H)
+        z = (double)frame[(int64_t)v * c->W + (int64_t)u];
+      double gx = exp(-(u - x) * (u - x) / s2);
+      double gy = exp(-(v - y) * (v - y) / s2);
+      double r = z - b - I * gx * gy;
+      acc += r * r - (z - b) * (z - b);
+    }
+  }
+  return -acc / (2.0 * c->sigma_obs * c->sigma_obs);
+}
+
+/* The image likelihood of c->obs_kind (ora_loglik_frame for ORA_OBS_FRAME,
+ * else ora_loglik_image) for each column of a 5 x n state array. */
 void ora_loglik_image_batch(const ora_cfg* c, const float* frame, const double* states, int64_t n, double* out) {
-  for (int64_t i = 0; i < n; ++i) out[i] = ora_loglik_image(c, frame, states[i], states[n + i], states[4 * n + i]);
+  for (int64_t i = 0; i < n; ++i)
+    out[i] = (c->obs_kind == ORA_OBS_FRAME) ? ora_loglik_frame(c, frame, states[i], states[n + i], states[4 * n + i])
+                                            : ora_loglik_image(c, frame, states[i], states[n + i], states[4 * n + i]);
 }
 
 /* Linear-Gaussian observation of the position (z = (x, y) + noise), used
@@ -526,8 +558,9 @@ int ora_step(const ora_cfg* c, uint32_t k, const float* obs, const double* pop_i
     ora_propagate(c, k, pop, o->X);
   for (int64_t i = 0; i < N; ++i) {
     double x = o->X[i], y = o->X[N + i], I = o->X[4 * N + i];
-    double l = (c->obs_kind == ORA_OBS_POINT) ? ora_loglik_point(c, obs, x, y)
-                                               : ora_loglik_image(c, obs, x, y, I);
+    double l = (c->obs_kind == ORA_OBS_POINT)   ? ora_loglik_point(c, obs, x, y)
+               : (c->obs_kind == ORA_OBS_FRAME) ? ora_loglik_frame(c, obs, x, y, I)
+                                                : ora_loglik_image(c, obs, x, y, I);
     o->loglik[i] = l;
     o->lw[i] = Lam[o->origin[i]] - log((double)Np) - lse_lam + l;
   }
@@ -665,11 +698,13 @@ int ora_run(const ora_cfg* c, const double* pop0, const float* obs, int32_t T, d
 /* sigma_v) with the resampling ancestry frozen.                             */
 /* ------------------------------------------------------------------------ */
 
-/* l of ora_loglik_image and its partial derivatives with respect to x, y, I
- * (state) and sigma_psf, b (parameters): d[0..4] = dl/dx, dl/dy, dl/dI,
- * dl/dsigma_psf, dl/db.  The patch centre is piecewise constant in the
- * state, so it contributes no derivative.  Pixels outside the image read b,
- * so their residual does not depend on b. */
+/* l of ora_loglik_image (ora_loglik_frame when obs_kind is ORA_OBS_FRAME)
+ * and its partial derivatives with respect to x, y, I (state) and
+ * sigma_psf, b (parameters): d[0..4] = dl/dx, dl/dy, dl/dI, dl/dsigma_psf,
+ * dl/db.  The patch centre is piecewise constant in the state, so it
+ * contributes no derivative.  Pixels outside the image read b, so their
+ * residual does not depend on b.  The frame model's extra term
+ * (zbar - b)^2 depends on b only. */
 double ora_loglik_image_grad(const ora_cfg* c, const float* frame, double x, double y, double I, double d[5]) {
   for (int q = 0; q < 5; ++q) d[q] = 0.0;
   if (!isfinite(x) || !isfinite(y) || !isfinite(I)) return NAN;
@@ -687,6 +722,10 @@ double ora_loglik_image_grad(const ora_cfg* c, const float* frame, double x, dou
       double m = I * gx * gy;
       double r = z - b - m;
       acc += r * r;
+      if (c->obs_kind == ORA_OBS_FRAME) {
+        acc -= (z - b) * (z - b);
+        if (inside) d[4] -= z - b;
+      }
       /* dl/dtheta = -(1/so2) sum r dr/dtheta, dr/dtheta = -dm/dtheta (and -1 for b inside) */
       d[0] += r * m * (u - x) / (s * s);
       d[1] += r * m * (v - y) / (s * s);

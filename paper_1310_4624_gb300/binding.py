@@ -37,7 +37,7 @@ class pf_track_config(C.Structure):
         ("ex_ratio", C.c_float), ("pe_eff_cutoff", C.c_float),
         ("init_kind", C.c_int32),
         ("init_state", C.c_float * 5), ("init_lo", C.c_float * 5), ("init_hi", C.c_float * 5),
-        ("init_radius", C.c_float), ("reserved0", C.c_int32),
+        ("init_radius", C.c_float), ("obs_model", C.c_int32),
         ("seed", C.c_uint64), ("track_id", C.c_uint32), ("record_ancestors", C.c_int32),
     ]
 

@@ -87,8 +87,9 @@ __global__ void __launch_bounds__(256) k_replay(ReplayArgs a) {
         for (int c = 0; c < 2 * R + 1; ++c) gxI[c] *= I;
         const int pu = (int)fminf(fmaxf(cxf, -(float)(R + 1)), (float)(P.W + R)) - R + PAD;
         const int pv = (int)fminf(fmaxf(cyf, -(float)(R + 1)), (float)(P.H + R)) - R + PAD;
-        const float ss = patch_ss<R, false>(a.ypad + P.ypad_off + (long long)pv * P.pitch + pu, P.pitch, gxI,
-                                            cyf - s.y, P.c_psf, P.kappa);
+        const float* base = a.ypad + P.ypad_off + (long long)pv * P.pitch + pu;
+        const float ss = P.obs_model == 1 ? patch_ss<R, true, false>(base, P.pitch, gxI, cyf - s.y, P.c_psf, P.kappa)
+                                          : patch_ss<R, false, false>(base, P.pitch, gxI, cyf - s.y, P.c_psf, P.kappa);
         const float lb = k >= 1 ? (float)a.lbar_prev[P.group_off + o] : -logf((float)P.G);
         const float lw = lb - logf((float)Np) - ss * P.inv2so2;
         if (lw == lw && lw > -INFINITY) {
@@ -197,7 +198,7 @@ __device__ __forceinline__ float loglik_grad(const float* __restrict__ yp, int p
   // inside-the-frame column / row ranges of the (true) patch
   const float ulo = fmaxf(0.0f, (float)R - cxf), uhi = fminf((float)(2 * R), (float)(W - 1) + (float)R - cxf);
   const float vlo = fmaxf(0.0f, (float)R - cyf), vhi = fminf((float)(2 * R), (float)(H - 1) + (float)R - cyf);
-  float ss = 0.0f, SI = 0.0f, S1 = 0.0f, Sy = 0.0f, Ss = 0.0f, Sb = 0.0f;
+  float ss = 0.0f, SI = 0.0f, S1 = 0.0f, Sy = 0.0f, Ss = 0.0f, Sb = 0.0f, Y2 = 0.0f, Y1 = 0.0f;
   const float du0 = cxf - (float)R - x;
 #pragma unroll
   for (int b = 0; b < D; ++b) {
@@ -206,8 +207,11 @@ __device__ __forceinline__ float loglik_grad(const float* __restrict__ yp, int p
     float R0 = 0.0f, R1 = 0.0f, R2 = 0.0f, Rb = 0.0f;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      const float r = fmaf(-gx[a], Igy, __ldg(rp + a));
+      const float yv = __ldg(rp + a);  // y = z - b, 0 outside the frame
+      const float r = fmaf(-gx[a], Igy, yv);
       ss = fmaf(r, r, ss);
+      Y2 = fmaf(yv, yv, Y2);
+      Y1 += yv;
       const float t = r * gx[a];
       R0 += t;
       R1 = fmaf(t, (float)a, R1);
@@ -230,6 +234,12 @@ __device__ __forceinline__ float loglik_grad(const float* __restrict__ yp, int p
   d[2] = SI * iso2;
   d[3] = I * Ss / (s2 * P.spsf) * iso2;
   d[4] = Sb * iso2;
+  if (P.obs_model == 1) {
+    // frame likelihood ratio: + sum y^2 / (2 sigma_obs^2), whose only
+    // parameter is b (dy/db = -1 inside the frame, y = 0 outside)
+    d[4] -= Y1 * iso2;
+    return -(ss - Y2) * P.inv2so2;
+  }
   return -ss * P.inv2so2;
 }
 

@@ -174,7 +174,7 @@ std::string validate(const pf_track_config* c, int n, int history) {
     if (!(x.ex_ratio >= 0.0f && x.ex_ratio <= 1.0f)) return bad("ex_ratio must be in [0, 1]");
     if (!std::isfinite(x.pe_eff_cutoff)) return bad("pe_eff_cutoff must be finite");
     if (x.track_id >= (1u << 24)) return bad("track_id must be < 2^24");
-    if (x.reserved0 != 0) return bad("reserved0 must be 0");
+    if (x.obs_model != PF_OBS_PATCH && x.obs_model != PF_OBS_FRAME) return bad("obs_model must be PF_OBS_PATCH or PF_OBS_FRAME");
     for (int d = 0; d < 5; ++d)
       if (!std::isfinite(x.init_state[d]) || !std::isfinite(x.init_lo[d]) || !std::isfinite(x.init_hi[d]))
         return bad("init_state / init_lo / init_hi must be finite");
@@ -497,6 +497,7 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
     P.key1 = (uint32_t)(c.seed >> 32);
     P.tag = c.track_id << 8;
     P.record = c.record_ancestors ? 1 : 0;
+    P.obs_model = c.obs_model;
     P.part_off = part;
     P.group_off = gro;
     P.tile_off = tio;

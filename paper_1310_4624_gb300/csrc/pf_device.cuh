@@ -60,6 +60,7 @@ struct TrackParams {
   unsigned long long m_Np;  // fast-division reciprocal of Np
   uint32_t key0, key1, tag;   // Philox key; tag = track_id << 8
   int record;
+  int obs_model;              // 0: patch residual, 1: frame likelihood ratio
   long long part_off;         // first particle of the track (global slot)
   int group_off;              // first group of the track (global group)
   int tile_off;               // first propagate tile of the track

@@ -808,15 +808,21 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
         gauss_row_scaled<R>(floorf(s[q].x + 0.5f), s[q].x, P.c_psf, P.kappa, I[q], gxI);
         const float dy = floorf(s[q].y + 0.5f) - s[q].y;
         float ss;
+        const bool frame_model = P.obs_model == 1;
         if (staged) {
           const int c = pu[q] - u0, o = (pv[q] - vmin) * ROI_W;
           const float* base = (c & 1) ? &s_roi[1][o + c - 1] : &s_roi[0][o + c];
-          ss = patch_ss_pairs<R>(base, gxI, dy, P.c_psf, P.kappa);
+          ss = frame_model ? patch_ss_pairs<R, true>(base, gxI, dy, P.c_psf, P.kappa)
+                           : patch_ss_pairs<R, false>(base, gxI, dy, P.c_psf, P.kappa);
         } else if (raw) {
-          ss = patch_ss_raw<R>(a.zraw, P.W, P.H, P.bg, pu[q] - PAD, pv[q] - PAD, gxI, dy, P.c_psf, P.kappa);
+          ss = frame_model
+                   ? patch_ss_raw<R, true>(a.zraw, P.W, P.H, P.bg, pu[q] - PAD, pv[q] - PAD, gxI, dy, P.c_psf, P.kappa)
+                   : patch_ss_raw<R, false>(a.zraw, P.W, P.H, P.bg, pu[q] - PAD, pv[q] - PAD, gxI, dy, P.c_psf,
+                                            P.kappa);
         } else {
-          ss = patch_ss<R, false>(a.ypad + P.ypad_off + (long long)pv[q] * P.pitch + pu[q], P.pitch, gxI, dy,
-                                  P.c_psf, P.kappa);
+          const float* base = a.ypad + P.ypad_off + (long long)pv[q] * P.pitch + pu[q];
+          ss = frame_model ? patch_ss<R, true, false>(base, P.pitch, gxI, dy, P.c_psf, P.kappa)
+                           : patch_ss<R, false, false>(base, P.pitch, gxI, dy, P.c_psf, P.kappa);
         }
         lw[q] = fmaf(-ss, P.inv2so2, from_pred[q] ? off_s : off_g);
         lw_t[g * Np + td.z + jj] = lw[q];

@@ -145,24 +145,41 @@ __device__ __forceinline__ void gauss_row_scaled(float cf, float x, float c, flo
   }
 }
 
-// Sum over the patch of (y - I gx gy)^2 (Alg. 1 step U, Sec. V appearance
-// model).  pix(b, a) is the pixel y of patch row b (0 .. 2R), column a;
-// gxI[a] = I gx(a).  Rows are visited centre-out so that gy follows the same
-// ratio recurrence as gauss_row with four live registers (dy = cyf - y).
-// Even and odd columns accumulate separately (two independent FMA chains),
-// summed at the end.  Every variant below reads the same pixels in the same
-// order, so all give bit-identical sums.
-template <int R, class Pix>
+// The likelihood's patch sum (Alg. 1 step U, Sec. V appearance model).
+// pix(b, a) is the pixel y = z - b of patch row b (0 .. 2R), column a (0
+// outside the frame); gxI[a] = I gx(a).  Rows are visited centre-out so that
+// gy follows the same ratio recurrence as gauss_row with four live
+// registers (dy = cyf - y).
+//  FRAME = false (patch residual): sum (y - I gx gy)^2; even and odd
+//    columns accumulate on two FMA chains, summed at the end.
+//  FRAME = true (frame likelihood ratio): sum [(y - I gx gy)^2 - y^2]
+//    = sum m (m - 2y) with m = I gx gy, per pixel (its rounding stays
+//    relative to the terms, which stay small where the ratio is small).
+// Every pixel source below reads the same pixels in the same order, so all
+// give bit-identical sums.
+template <int R, bool FRAME, class Pix>
 __device__ __forceinline__ float patch_sum(Pix pix, const float (&gxI)[2 * R + 1], float dy, float c, float kappa) {
-  float ae = 0.0f, ao = 0.0f;
+  float ae = 0.0f, ao = 0.0f;  // even and odd columns
   auto row = [&](int b, float gy) {
+    if constexpr (FRAME) {
 #pragma unroll
-    for (int a = 0; a < 2 * R + 1; ++a) {
-      const float r = fmaf(-gxI[a], gy, pix(b, a));
-      if (a & 1)
-        ao = fmaf(r, r, ao);
-      else
-        ae = fmaf(r, r, ae);
+      for (int a = 0; a < 2 * R + 1; ++a) {
+        const float m = gxI[a] * gy;
+        const float t = fmaf(-2.0f, pix(b, a), m);
+        if (a & 1)
+          ao = fmaf(m, t, ao);
+        else
+          ae = fmaf(m, t, ae);
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < 2 * R + 1; ++a) {
+        const float r = fmaf(-gxI[a], gy, pix(b, a));
+        if (a & 1)
+          ao = fmaf(r, r, ao);
+        else
+          ae = fmaf(r, r, ae);
+      }
     }
   };
   const float g = ex2(-c * dy * dy);
@@ -184,22 +201,23 @@ __device__ __forceinline__ float patch_sum(Pix pix, const float (&gxI)[2 * R + 1
 
 // Rows of shared memory (pitch ROI_W) or of the padded frame in global
 // memory (read through L1).
-template <int R, bool SMEM>
+template <int R, bool FRAME, bool SMEM>
 __device__ __forceinline__ float patch_ss(const float* __restrict__ base, int pitch, const float (&gxI)[2 * R + 1],
                                           float dy, float c, float kappa) {
   if constexpr (SMEM)
-    return patch_sum<R>([&](int b, int a) { return base[b * ROI_W + a]; }, gxI, dy, c, kappa);
+    return patch_sum<R, FRAME>([&](int b, int a) { return base[b * ROI_W + a]; }, gxI, dy, c, kappa);
   else
-    return patch_sum<R>([&](int b, int a) { return __ldg(base + (long long)b * pitch + a); }, gxI, dy, c, kappa);
+    return patch_sum<R, FRAME>([&](int b, int a) { return __ldg(base + (long long)b * pitch + a); }, gxI, dy, c,
+                               kappa);
 }
 
 // Shared-memory rows read as float pairs: `base` is 8-byte aligned and row
 // b's pixels are base[b ROI_W + 0 .. 2R] (the pair loads also fetch
 // base[.. + 2R + 1], unused).
-template <int R>
+template <int R, bool FRAME>
 __device__ __forceinline__ float patch_ss_pairs(const float* __restrict__ base, const float (&gxI)[2 * R + 1],
                                                 float dy, float c, float kappa) {
-  return patch_sum<R>(
+  return patch_sum<R, FRAME>(
       [&](int b, int a) {
         const float2 v = reinterpret_cast<const float2*>(base + b * ROI_W)[a >> 1];
         return (a & 1) ? v.y : v.x;
@@ -210,10 +228,10 @@ __device__ __forceinline__ float patch_ss_pairs(const float* __restrict__ base, 
 // The caller's frame z (W x H, pitch W) instead of the padded frame: pixel
 // values z - b inside the frame, 0 outside; (x0, y0) is the patch's corner
 // in frame coordinates.
-template <int R>
+template <int R, bool FRAME>
 __device__ __forceinline__ float patch_ss_raw(const float* __restrict__ z, int W, int H, float bg, int x0, int y0,
                                               const float (&gxI)[2 * R + 1], float dy, float c, float kappa) {
-  return patch_sum<R>(
+  return patch_sum<R, FRAME>(
       [&](int b, int a) {
         const int yy = y0 + b, xx = x0 + a;
         return ((unsigned)yy < (unsigned)H && (unsigned)xx < (unsigned)W)

@@ -34,7 +34,7 @@ def config_from_workload(wl: Workload, truth0=None, track_id: int = 0, record_an
         c.init_lo[d] = lo[d]
         c.init_hi[d] = hi[d]
     c.init_radius = wl.share_radius
-    c.reserved0 = 0
+    c.obs_model = getattr(wl, "obs_model", 0)
     c.seed = wl.seed
     c.track_id = track_id
     c.record_ancestors = 1 if record_ancestors else 0

@@ -61,6 +61,7 @@ class Workload:
     share_vmax: float = 2.0       # other groups: velocity range
     share_I: Tuple[float, float] = (1.0, 20.0)
     truth_noise: bool = False     # truth drawn from the NCV dynamics (sigma_pos, sigma_v)
+    obs_model: int = 0            # 0: patch residual, 1: frame likelihood ratio
 
     @property
     def N(self) -> int:

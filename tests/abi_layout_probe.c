@@ -15,7 +15,7 @@ int main(void) {
   F(pf_track_config, sigma_v); F(pf_track_config, sigma_I); F(pf_track_config, ex_ratio);
   F(pf_track_config, pe_eff_cutoff); F(pf_track_config, init_kind); F(pf_track_config, init_state);
   F(pf_track_config, init_lo); F(pf_track_config, init_hi); F(pf_track_config, init_radius);
-  F(pf_track_config, reserved0); F(pf_track_config, seed); F(pf_track_config, track_id);
+  F(pf_track_config, obs_model); F(pf_track_config, seed); F(pf_track_config, track_id);
   F(pf_track_config, record_ancestors);
   printf("pf_step_stats sizeof %zu\n", sizeof(pf_step_stats));
   F(pf_step_stats, step); F(pf_step_stats, n_ex); F(pf_step_stats, pe_eff); F(pf_step_stats, log_c);

@@ -36,7 +36,7 @@ def test_header_declares_what_the_binding_wraps():
 def test_library_exports_every_declared_symbol(lib):
     for name in declared_functions():
         assert hasattr(lib, name), name
-    assert lib.pf_abi_version() == 1
+    assert lib.pf_abi_version() == 2
 
 
 def test_struct_layout_matches_ctypes(tmp_path):
@@ -73,7 +73,7 @@ def test_query_workspace_scales_with_particles(lib):
     ("G", 0, "G must be"), ("Np", 0, "Np must be"), ("H", 0, "H and W"), ("patch_radius", 9, "patch_radius"),
     ("mode", 3, "mode"), ("init_kind", 7, "init_kind"), ("sigma_psf", 0.0, "sigma_psf"),
     ("sigma_obs", -1.0, "sigma_obs"), ("sigma_pos", float("nan"), "process noise"), ("ex_ratio", 1.5, "ex_ratio"),
-    ("track_id", 1 << 24, "track_id"), ("reserved0", 1, "reserved0"), ("G", 1025, "G must be"),
+    ("track_id", 1 << 24, "track_id"), ("obs_model", 2, "obs_model"), ("G", 1025, "G must be"),
     ("Np", (1 << 20) + 1, "Np must be"),
 ])
 def test_invalid_configs_are_rejected_on_the_host(lib, field, value, msg):

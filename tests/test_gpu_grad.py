@@ -44,7 +44,8 @@ def _oracle(wl, frames, truth, parents):
 
 CASES = [("arna", synth.small_rna(G=3, Np=256, H=48, W=48, mode=synth.ARNA, T=6)),
          ("rna", synth.small_rna(G=4, Np=200, H=40, W=56, mode=synth.RNA, T=5, seed=3, data_seed=2)),
-         ("sharing", synth.sharing(G=4, Np=256, H=64, W=64, mode=synth.ARNA, T=5))]
+         ("sharing", synth.sharing(G=4, Np=256, H=64, W=64, mode=synth.ARNA, T=5)),
+         ("frame_model", synth.small_rna(G=3, Np=256, H=48, W=48, mode=synth.ARNA, T=5, obs_model=1))]
 
 
 @pytest.mark.parametrize("name,wl", CASES, ids=[c[0] for c in CASES])

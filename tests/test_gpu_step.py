@@ -41,6 +41,8 @@ SMALL = [
     ("sharing_rna", synth.sharing(G=6, Np=200, H=64, W=64, mode=synth.RNA)),
     ("full_ratio", synth.small_rna(G=3, Np=64, ex_ratio=1.0)),
     ("patch_r3", synth.small_rna(G=2, Np=128, patch_radius=3)),
+    ("frame_model", synth.small_rna(G=4, Np=512, mode=synth.ARNA, obs_model=1)),
+    ("frame_model_sharing", synth.sharing(G=8, Np=512, H=64, W=64, mode=synth.ARNA, obs_model=1)),
 ]
 
 
@@ -61,4 +63,11 @@ def test_tracking_scale_matches_oracle(dev, mode):
 def test_sharing_scale_matches_oracle(dev):
     """Information-sharing workload shape: 512x512, G=256 x 4096, ARNA."""
     rep = _run(dev, synth.sharing(mode=synth.ARNA), 3)
+    assert rep[1]["n_ex"] > 0
+
+
+def test_sharing_scale_frame_model_matches_oracle(dev):
+    """The same with the frame likelihood ratio, on the staged and the
+    raw-frame paths (the start spreads particles over the whole image)."""
+    rep = _run(dev, synth.sharing(mode=synth.ARNA, obs_model=1), 3)
     assert rep[1]["n_ex"] > 0

@@ -164,6 +164,77 @@ def test_likelihood_off_image_closed_form(ora):
     assert math.isnan(ora.loglik_image(cfg, frame, float("nan"), 3.0, 1.0))
 
 
+def _whole_frame_loglik(frame, b, spsf, sobs, R, x, y, I):
+    """Gaussian log-likelihood of the whole frame under the spot model (zero
+    outside the (2R+1)^2 patch) minus that of the background alone, each
+    summed over every pixel of the frame (brute force; the patch must lie in
+    the frame)."""
+    H, W = frame.shape
+    cx, cy = math.floor(x + 0.5), math.floor(y + 0.5)
+    m = np.zeros((H, W))
+    for v in range(cy - R, cy + R + 1):
+        for u in range(cx - R, cx + R + 1):
+            m[v, u] = I * math.exp(-((u - x) ** 2 + (v - y) ** 2) / (2 * spsf ** 2))
+    yv = frame.astype(np.float64) - b
+    return (-((yv - m) ** 2).sum() + (yv ** 2).sum()) / (2 * sobs ** 2)
+
+
+def test_frame_likelihood_is_the_whole_frame_ratio(ora):
+    """The frame model (Sec. II's p(z_k | x_k) of the whole image, divided by
+    the background-only likelihood) restricted to the patch equals the
+    brute-force sums over every pixel of the frame."""
+    wl = synth.small_rna()
+    frames, truth = synth.make_sequence(wl, T=1)
+    cfg = ora.make_cfg(G=1, Np=1, H=64, W=64, sigma_psf=1.5, sigma_obs=1.3, background=1.0, obs_kind=ora.OBS_FRAME)
+    rng = np.random.default_rng(5)
+    pts = [(truth[0, 0], truth[0, 1], 10.0), (30.49, 30.5, 4.0)]
+    pts += [tuple(rng.uniform([6, 6, 0], [57, 57, 20])) for _ in range(30)]
+    for (x, y, I) in pts:
+        got = ora.loglik_frame(cfg, frames[0], x, y, I)
+        want = _whole_frame_loglik(frames[0], 1.0, 1.5, 1.3, 5, x, y, I)
+        assert abs(got - want) <= 1e-9 * max(1.0, abs(want))
+    # the spot outscores plain background, unlike the patch residual with
+    # Poisson noise above sigma_obs at the spot
+    far = ora.loglik_frame(cfg, frames[0], 5.5, 58.5, 2.0)
+    assert ora.loglik_frame(cfg, frames[0], truth[0, 0], truth[0, 1], 10.0) > far + 50.0
+
+
+def test_frame_likelihood_over_background_closed_form(ora):
+    """On a frame that is exactly the background, y = 0 and the frame model
+    reduces to -I^2 sum gx^2 sum gy^2 / (2 sigma_obs^2), on or off the frame."""
+    cfg = ora.make_cfg(G=1, Np=1, sigma_psf=1.2, sigma_obs=0.8, obs_kind=ora.OBS_FRAME)
+    frame = np.full((64, 64), 1.0, np.float32)
+    for (x, y, I) in [(30.3, 20.2, 6.0), (-100.3, 20.2, 6.0), (2.1, 62.7, 3.0)]:
+        cx, cy = math.floor(x + 0.5), math.floor(y + 0.5)
+        s2 = 2 * 1.2 ** 2
+        gx = np.exp(-(np.arange(cx - 5, cx + 6) - x) ** 2 / s2)
+        gy = np.exp(-(np.arange(cy - 5, cy + 6) - y) ** 2 / s2)
+        want = -(I ** 2) * (gx ** 2).sum() * (gy ** 2).sum() / (2 * 0.8 ** 2)
+        assert abs(ora.loglik_frame(cfg, frame, x, y, I) - want) < 1e-9 * abs(want)
+
+
+def test_frame_likelihood_gradient_by_differences(ora):
+    """dl/d(x, y, I, sigma_psf, b) of the frame model against FP64 central
+    differences of the oracle's own frame likelihood."""
+    wl = synth.small_rna()
+    frames, truth = synth.make_sequence(wl, T=1)
+    base = dict(G=1, Np=1, H=64, W=64, sigma_psf=1.5, sigma_obs=1.1, background=1.0, obs_kind=ora.OBS_FRAME)
+    cfg = ora.make_cfg(**base)
+    x, y, I = truth[0, 0] + 0.3, truth[0, 1] - 0.2, 9.0
+    l, d = ora.loglik_image_grad(cfg, frames[0], x, y, I)
+    assert abs(l - ora.loglik_frame(cfg, frames[0], x, y, I)) < 1e-9 * abs(l)
+    h = 1e-5
+    fd = [(ora.loglik_frame(cfg, frames[0], x + h, y, I) - ora.loglik_frame(cfg, frames[0], x - h, y, I)) / (2 * h),
+          (ora.loglik_frame(cfg, frames[0], x, y + h, I) - ora.loglik_frame(cfg, frames[0], x, y - h, I)) / (2 * h),
+          (ora.loglik_frame(cfg, frames[0], x, y, I + h) - ora.loglik_frame(cfg, frames[0], x, y, I - h)) / (2 * h)]
+    for key, q in (("sigma_psf", 3), ("background", 4)):
+        up = ora.make_cfg(**{**base, key: base[key] + h})
+        dn = ora.make_cfg(**{**base, key: base[key] - h})
+        fd.append((ora.loglik_frame(up, frames[0], x, y, I) - ora.loglik_frame(dn, frames[0], x, y, I)) / (2 * h))
+    for q in range(5):
+        assert abs(d[q] - fd[q]) <= 1e-5 * max(1.0, abs(fd[q])), (q, d[q], fd[q])
+
+
 # ------------------------------------------------------------- whole steps
 def test_single_group_step_is_plain_sir(ora):
     """G = 1: the estimate and log c are those of one SIR step (Alg. 1)."""
