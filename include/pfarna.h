@@ -330,6 +330,22 @@ pf_status pf_reset(pf_handle* h, void* stream);
 pf_status pf_backward(pf_handle* h, const float* const* frames_host, int32_t T, const float* dlogZ_host,
                       float* grad_dev, double* logZ_dev, void* stream);
 
+/* Checkpoint and resume.  A filter's whole state lives in its workspace
+ * and a few host counters, and every random draw is a counter-based Philox
+ * word, so a restored filter continues exactly as the saved one would.
+ * pf_checkpoint_bytes: the size of a checkpoint of `h`.
+ * pf_save: waits for the handle's work on `stream` and copies its state to
+ * `host` (bytes >= pf_checkpoint_bytes).
+ * pf_load: restores a checkpoint into `h`, which must have been created
+ * with the same configurations and history as the saved handle (it may be
+ * the same handle); enqueued on `stream` and synchronised.  No counterpart
+ * in the paper (its runs are not resumed).
+ * Errors: PF_ERR_ARG (NULL, too small, not a checkpoint of a filter of this
+ * configuration), PF_ERR_CUDA. */
+pf_status pf_checkpoint_bytes(const pf_handle* h, size_t* bytes);
+pf_status pf_save(pf_handle* h, void* host, size_t bytes, void* stream);
+pf_status pf_load(pf_handle* h, const void* host, size_t bytes, void* stream);
+
 /* Release the handle's host metadata (the workspace stays the caller's). */
 void pf_destroy(pf_handle* h);
 

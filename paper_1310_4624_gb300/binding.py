@@ -23,7 +23,8 @@ STATUS_NAMES = {0: "PF_OK", 1: "PF_ERR_ARG", 2: "PF_ERR_STATE", 3: "PF_ERR_CUDA"
 EXPORTS = ("pf_abi_version", "pf_query_workspace", "pf_init", "pf_step", "pf_estimate", "pf_exchange_stats",
            "pf_history", "pf_particles", "pf_resample_workspace", "pf_resample", "pf_resample_noalloc",
            "pf_profile_enable", "pf_profile_read", "pf_set_theta", "pf_reset", "pf_backward", "pf_step_table",
-           "pf_graph_step", "pf_autotune", "pf_destroy", "pf_last_error")
+           "pf_graph_step", "pf_autotune", "pf_checkpoint_bytes", "pf_save", "pf_load", "pf_destroy",
+           "pf_last_error")
 THETA_NAMES = ("sigma_psf", "amplitude", "background", "sigma_pos", "sigma_v")
 KERNEL_NAMES = ("frame_prep", "propagate_weight", "resample", "global")
 
@@ -93,6 +94,9 @@ def load():
     L.pf_graph_step.argtypes = [_P, _P, C.c_int32, _P]
     L.pf_autotune.argtypes = [_P, C.POINTER(_P), _P, _P, _P]
     L.pf_reset.argtypes = [_P, _P]
+    L.pf_checkpoint_bytes.argtypes = [_P, C.POINTER(C.c_size_t)]
+    L.pf_save.argtypes = [_P, _P, C.c_size_t, _P]
+    L.pf_load.argtypes = [_P, _P, C.c_size_t, _P]
     L.pf_backward.argtypes = [_P, C.POINTER(_P), C.c_int32, _P, _P, _P, _P]
     L.pf_destroy.argtypes = [_P]
     L.pf_destroy.restype = None
@@ -219,6 +223,23 @@ def pf_backward(handle: int, frame_ptrs, T: int, dlogZ, grad_ptr, logZ_ptr, stre
     arr = (_P * len(frame_ptrs))(*frame_ptrs)
     seeds = (C.c_float * len(dlogZ))(*[float(v) for v in dlogZ])
     _check(load().pf_backward(handle, arr, T, seeds, grad_ptr, logZ_ptr, stream_ptr), "pf_backward", handle)
+
+
+def pf_checkpoint_bytes(handle: int) -> int:
+    n = C.c_size_t(0)
+    _check(load().pf_checkpoint_bytes(handle, C.byref(n)), "pf_checkpoint_bytes", handle)
+    return n.value
+
+
+def pf_save(handle: int, buf, stream_ptr) -> None:
+    """buf: a writable buffer (bytearray / numpy uint8) of pf_checkpoint_bytes."""
+    mv = (C.c_char * len(buf)).from_buffer(buf)
+    _check(load().pf_save(handle, C.addressof(mv), len(buf), stream_ptr), "pf_save", handle)
+
+
+def pf_load(handle: int, buf, stream_ptr) -> None:
+    mv = (C.c_char * len(buf)).from_buffer(buf)
+    _check(load().pf_load(handle, C.addressof(mv), len(buf), stream_ptr), "pf_load", handle)
 
 
 def pf_destroy(handle: int) -> None:

@@ -78,6 +78,10 @@ struct pf_handle {
   int graph_T = 0;
   int k1_occ = 1, sms = 1;
   bool pdl = true;  // programmatic dependent launch between the step kernels
+  char* ws = nullptr;        // the workspace, its size, and the byte range of the TMA
+  size_t ws_total = 0;       // descriptors in it (they hold this workspace's addresses)
+  size_t tmap_off = 0, tmap_bytes = 0;
+  unsigned long long cfg_sig = 0;  // signature of the configurations and history
   void* encode = nullptr;  // cuTensorMapEncodeTiled, or nullptr
   // kernel timing (pf_profile_enable / pf_profile_read)
   int prof = 0;
@@ -577,6 +581,21 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
 
   const int sms = num_sms();
   h->sms = sms;
+  h->ws = w;
+  h->ws_total = L.total;
+  h->tmap_off = L.tmap;
+  h->tmap_bytes = sizeof(CUtensorMap) * (size_t)n_tracks;
+  {
+    // FNV-1a over the configurations and the history length
+    unsigned long long sig = 1469598103934665603ull;
+    auto mix = [&](const void* p, size_t n) {
+      for (size_t i = 0; i < n; ++i) sig = (sig ^ ((const unsigned char*)p)[i]) * 1099511628211ull;
+    };
+    mix(cfg, sizeof(pf_track_config) * (size_t)n_tracks);
+    mix(&history, sizeof history);
+    mix(&L.total, sizeof L.total);
+    h->cfg_sig = sig;
+  }
   int occ = 1;
   if ((e = k1_occupancy(h->R, &occ)) != cudaSuccess) { pf_destroy(h); return cuda_fail(nullptr, e, "occupancy"); }
   h->k1_occ = occ > 0 ? occ : 1;
@@ -1111,6 +1130,69 @@ pf_status pf_profile_read(pf_handle* h, int32_t n, int64_t* launches, double* to
   for (auto& v : h->ev) {
     for (cudaEvent_t e : v) cudaEventDestroy(e);
     v.clear();
+  }
+  return PF_OK;
+}
+
+// Checkpoint: a header, then the workspace except the TMA descriptors.
+struct CheckpointHeader {
+  unsigned long long magic, sig, ws_total;
+  int32_t abi, steps_run, finish_pending, k1_grid, rs_cluster, pad;
+};
+static const unsigned long long kCheckpointMagic = 0x6b70635f666e7270ull;  // "prnf_cpk"
+
+pf_status pf_checkpoint_bytes(const pf_handle* h, size_t* bytes) {
+  if (!h || !bytes) return fail(nullptr, PF_ERR_ARG, "NULL argument");
+  *bytes = sizeof(CheckpointHeader) + h->ws_total - h->tmap_bytes;
+  return PF_OK;
+}
+
+pf_status pf_save(pf_handle* h, void* host, size_t bytes, void* stream) {
+  if (!h || !host) return fail(h, PF_ERR_ARG, "NULL argument");
+  size_t need = 0;
+  pf_checkpoint_bytes(h, &need);
+  if (bytes < need) return fail(h, PF_ERR_ARG, "checkpoint buffer too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  CheckpointHeader hd{kCheckpointMagic, h->cfg_sig, h->ws_total, PF_ABI_VERSION, h->steps_run,
+                      h->finish_pending ? 1 : 0, h->k1_grid, h->rs_cluster, 0};
+  std::memcpy(host, &hd, sizeof hd);
+  char* dst = (char*)host + sizeof hd;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(dst, h->ws, h->tmap_off, cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaMemcpyAsync(dst + h->tmap_off, h->ws + h->tmap_off + h->tmap_bytes,
+                           h->ws_total - h->tmap_off - h->tmap_bytes, cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaStreamSynchronize(s)))
+    return cuda_fail(h, e, "pf_save");
+  return PF_OK;
+}
+
+pf_status pf_load(pf_handle* h, const void* host, size_t bytes, void* stream) {
+  if (!h || !host) return fail(h, PF_ERR_ARG, "NULL argument");
+  size_t need = 0;
+  pf_checkpoint_bytes(h, &need);
+  CheckpointHeader hd{};
+  if (bytes < sizeof hd) return fail(h, PF_ERR_ARG, "not a checkpoint");
+  std::memcpy(&hd, host, sizeof hd);
+  if (hd.magic != kCheckpointMagic || hd.abi != PF_ABI_VERSION) return fail(h, PF_ERR_ARG, "not a checkpoint");
+  if (hd.sig != h->cfg_sig || hd.ws_total != h->ws_total || bytes < need)
+    return fail(h, PF_ERR_ARG, "checkpoint of a filter with other configurations");
+  cudaStream_t s = (cudaStream_t)stream;
+  const char* src = (const char*)host + sizeof hd;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(h->ws, src, h->tmap_off, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(h->ws + h->tmap_off + h->tmap_bytes, src + h->tmap_off,
+                           h->ws_total - h->tmap_off - h->tmap_bytes, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaStreamSynchronize(s)))
+    return cuda_fail(h, e, "pf_load");
+  h->steps_run = hd.steps_run;
+  h->finish_pending = hd.finish_pending != 0;
+  h->k1_grid = hd.k1_grid;
+  h->rs_cluster = hd.rs_cluster;
+  h->failed = 0;
+  h->last_stream = s;
+  if (h->graph) {  // a captured step may hold other launch shapes
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
   }
   return PF_OK;
 }

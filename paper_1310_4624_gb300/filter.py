@@ -6,6 +6,7 @@ stream; every step of the filter runs in the library's kernels.
 from __future__ import annotations
 
 import ctypes as C
+import struct
 from typing import List, Optional, Sequence
 
 import numpy as np
@@ -144,6 +145,19 @@ class ParticleFilter:
         out = B.pf_history(self.handle, track, first, count)
         return [dict(step=s.step, n_ex=s.n_ex, pe_eff=s.pe_eff, log_c=s.log_c, log_Z=s.log_Z,
                      xhat=np.array(s.xhat[:]), degenerate=s.degenerate_groups) for s in out]
+
+    def save(self) -> bytearray:
+        """A checkpoint of the whole filter state (host memory)."""
+        buf = bytearray(B.pf_checkpoint_bytes(self.handle))
+        B.pf_save(self.handle, buf, C.c_void_p(self.stream.cuda_stream))
+        return buf
+
+    def load(self, buf: bytearray) -> None:
+        """Restore a checkpoint taken from a filter of the same configurations."""
+        B.pf_load(self.handle, buf, C.c_void_p(self.stream.cuda_stream))
+        # the checkpoint header: magic, signature, workspace bytes (u64 each),
+        # then the ABI version and the step count (int32)
+        self.steps = struct.unpack_from("<i", bytes(buf[28:32]))[0]
 
     def set_theta(self, theta, track: int = 0) -> None:
         """theta = (sigma_psf, A, background, sigma_pos, sigma_v) of one track."""
