@@ -23,6 +23,7 @@
 #include <climits>
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "pf_device.cuh"
 #include "pf_launch.h"
@@ -45,6 +46,8 @@ __global__ void __launch_bounds__(256) k_replay(ReplayArgs a) {
     const TrackParams& P = a.trk[td.x];
     const int g = td.y, Np = P.Np;
     const long long Nt = (long long)P.G * Np;
+    const int hslot = k % a.history;
+    const float log_G = logf((float)P.G), log_Np = logf((float)Np);
     float mx = -INFINITY, sm = 0.0f;
     for (int jj = threadIdx.x; jj < td.w; jj += blockDim.x) {
       const int j = td.z + jj;
@@ -53,8 +56,8 @@ __global__ void __launch_bounds__(256) k_replay(ReplayArgs a) {
       float I;
       int o = g;
       if (k >= 1) {
-        const long long par = a.parent[P.parent_off + (long long)(k % a.history) * Nt + il];
-        o = (int)(par / Np);
+        const long long par = a.parent[P.parent_off + (long long)hslot * Nt + il];
+        o = (int)fastdiv((uint32_t)par, P.m_Np);  // origin group (par < 2^31)
         s = a.pv_in[P.part_off + par];
         I = a.I_in[P.part_off + par];
         uint4 w0 = make_uint4(j, g, k, P.tag | (ST_PROP << 4) | 0u);
@@ -90,8 +93,8 @@ __global__ void __launch_bounds__(256) k_replay(ReplayArgs a) {
         const float* base = a.ypad + P.ypad_off + (long long)pv * P.pitch + pu;
         const float ss = P.obs_model == 1 ? patch_ss<R, true, false>(base, P.pitch, gxI, cyf - s.y, P.c_psf, P.kappa)
                                           : patch_ss<R, false, false>(base, P.pitch, gxI, cyf - s.y, P.c_psf, P.kappa);
-        const float lb = k >= 1 ? (float)a.lbar_prev[P.group_off + o] : -logf((float)P.G);
-        const float lw = lb - logf((float)Np) - ss * P.inv2so2;
+        const float lb = k >= 1 ? (float)a.lbar_prev[P.group_off + o] : -log_G;
+        const float lw = lb - log_Np - ss * P.inv2so2;
         if (lw == lw && lw > -INFINITY) {
           if (lw > mx) {
             sm = sm * __expf(mx - lw) + 1.0f;
@@ -128,35 +131,43 @@ __global__ void __launch_bounds__(256) k_replay(ReplayArgs a) {
 
 // Per track: the replayed group log-weights of step k, log c_k, lbar_k, and
 // at the last step the seed of the reverse sweep, dL = s pi.  FP64 (G-sized).
-__global__ void k_replay_groups(ReplayGroupArgs a) {
+__global__ void __launch_bounds__(256) k_replay_groups(ReplayGroupArgs a) {
   const int t = blockIdx.x;
   const TrackParams& P = a.trk[t];
-  const int G = P.G, m = threadIdx.x;
+  const int G = P.G;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)blockDim.x >> 5;
+  __shared__ double s_lam[MAX_G];
   __shared__ double s_d[32];
   __shared__ double s_lc;
-  double lam = -INFINITY;
-  if (m < G) {
+  // L_k,m = LSE over the group's slots, from its tiles' (max, sum exp): a
+  // warp per group, its lanes over the tiles
+  for (int m = warp; m < G; m += nw) {
     const int t0 = a.gd[P.group_off + m].tile_begin, nt = a.gd[P.group_off + m].tile_count;
-    double M = -INFINITY;
-    for (int q = 0; q < nt; ++q) M = fmax(M, (double)a.tile_part[(long long)(t0 + q) * 8]);
-    double S = 0.0;
+    float M = -INFINITY;
+    for (int q = lane; q < nt; q += 32) M = fmaxf(M, a.tile_part[(long long)(t0 + q) * 8]);
+    M = warp_max(M);
+    float S = 0.0f;
     if (M > -INFINITY)
-      for (int q = 0; q < nt; ++q) {
-        const double Mt = a.tile_part[(long long)(t0 + q) * 8];
-        if (Mt > -INFINITY) S += (double)a.tile_part[(long long)(t0 + q) * 8 + 1] * exp(Mt - M);
+      for (int q = lane; q < nt; q += 32) {
+        const float Mt = a.tile_part[(long long)(t0 + q) * 8];
+        if (Mt > -INFINITY) S = fmaf(a.tile_part[(long long)(t0 + q) * 8 + 1], expf(Mt - M), S);
       }
-    lam = (M > -INFINITY && S > 0.0) ? M + log(S) : -INFINITY;
+    S = warp_sum(S);
+    if (lane == 0) s_lam[m] = (M > -INFINITY && S > 0.0f) ? (double)M + log((double)S) : -INFINITY;
   }
-  double mx = warp_max_d(lam);
+  __syncthreads();
+  double mx = -INFINITY;
+  for (int m = threadIdx.x; m < G; m += blockDim.x) mx = fmax(mx, s_lam[m]);
+  mx = warp_max_d(mx);
   if (lane == 0) s_d[warp] = mx;
   __syncthreads();
   mx = -INFINITY;
   for (int w = 0; w < nw; ++w) mx = fmax(mx, s_d[w]);
   __syncthreads();
-  double e = (m < G && lam > -INFINITY) ? exp(lam - mx) : 0.0;
-  double se = warp_sum_d(e);
-  if (lane == 0) s_d[warp] = se;
+  double e = 0.0;
+  for (int m = threadIdx.x; m < G; m += blockDim.x) e += s_lam[m] > -INFINITY ? exp(s_lam[m] - mx) : 0.0;
+  e = warp_sum_d(e);
+  if (lane == 0) s_d[warp] = e;
   __syncthreads();
   if (threadIdx.x == 0) {
     double tot = 0.0;
@@ -166,7 +177,8 @@ __global__ void k_replay_groups(ReplayGroupArgs a) {
   }
   __syncthreads();
   const double lc = s_lc;
-  if (m < G) {
+  for (int m = threadIdx.x; m < G; m += blockDim.x) {
+    const double lam = s_lam[m];
     const long long gm = P.group_off + m;
     a.lam_hist[(long long)a.k * a.G_total + gm] = lam;
     a.lbar_hist[(long long)a.k * a.G_total + gm] = lam - lc;
@@ -200,33 +212,46 @@ __device__ __forceinline__ float loglik_grad(const float* __restrict__ yp, int p
   const float vlo = fmaxf(0.0f, (float)R - cyf), vhi = fminf((float)(2 * R), (float)(H - 1) + (float)R - cyf);
   float ss = 0.0f, SI = 0.0f, S1 = 0.0f, Sy = 0.0f, Ss = 0.0f, Sb = 0.0f, Y2 = 0.0f, Y1 = 0.0f;
   const float du0 = cxf - (float)R - x;
+  // patches wholly inside the frame (almost all) sum the b-derivative's
+  // residuals without per-pixel masks
+  const bool inside = ulo == 0.0f && uhi == (float)(2 * R) && vlo == 0.0f && vhi == (float)(2 * R);
+  auto rows = [&](auto inside_tag) {
+    constexpr bool IN = decltype(inside_tag)::value;
 #pragma unroll
-  for (int b = 0; b < D; ++b) {
-    const float* __restrict__ rp = row + (long long)b * pitch;
-    const float Igy = I * gy[b];
-    float R0 = 0.0f, R1 = 0.0f, R2 = 0.0f, Rb = 0.0f;
+    for (int b = 0; b < D; ++b) {
+      const float* __restrict__ rp = row + (long long)b * pitch;
+      const float Igy = I * gy[b];
+      float R0 = 0.0f, R1 = 0.0f, R2 = 0.0f, Rb = 0.0f;
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const float yv = __ldg(rp + a);  // y = z - b, 0 outside the frame
-      const float r = fmaf(-gx[a], Igy, yv);
-      ss = fmaf(r, r, ss);
-      Y2 = fmaf(yv, yv, Y2);
-      Y1 += yv;
-      const float t = r * gx[a];
-      R0 += t;
-      R1 = fmaf(t, (float)a, R1);
-      R2 = fmaf(t, (float)(a * a), R2);
-      Rb += ((float)a >= ulo && (float)a <= uhi) ? r : 0.0f;
+      for (int a = 0; a < D; ++a) {
+        const float yv = __ldg(rp + a);  // y = z - b, 0 outside the frame
+        const float r = fmaf(-gx[a], Igy, yv);
+        ss = fmaf(r, r, ss);
+        Y2 = fmaf(yv, yv, Y2);
+        Y1 += yv;
+        const float t = r * gx[a];
+        R0 += t;
+        R1 = fmaf(t, (float)a, R1);
+        R2 = fmaf(t, (float)(a * a), R2);
+        if constexpr (IN)
+          Rb += r;
+        else
+          Rb += ((float)a >= ulo && (float)a <= uhi) ? r : 0.0f;
+      }
+      const float dv = (cyf - (float)R + (float)b) - y;
+      const float sx1 = R1 + du0 * R0;
+      const float sx2 = R2 + 2.0f * du0 * R1 + du0 * du0 * R0;
+      SI = fmaf(gy[b], R0, SI);
+      S1 = fmaf(gy[b], sx1, S1);
+      Sy = fmaf(gy[b] * dv, R0, Sy);
+      Ss = fmaf(gy[b], fmaf(dv * dv, R0, sx2), Ss);
+      if (IN || ((float)b >= vlo && (float)b <= vhi)) Sb += Rb;
     }
-    const float dv = (cyf - (float)R + (float)b) - y;
-    const float sx1 = R1 + du0 * R0;
-    const float sx2 = R2 + 2.0f * du0 * R1 + du0 * du0 * R0;
-    SI = fmaf(gy[b], R0, SI);
-    S1 = fmaf(gy[b], sx1, S1);
-    Sy = fmaf(gy[b] * dv, R0, Sy);
-    Ss = fmaf(gy[b], fmaf(dv * dv, R0, sx2), Ss);
-    if ((float)b >= vlo && (float)b <= vhi) Sb += Rb;
-  }
+  };
+  if (inside)
+    rows(std::true_type{});
+  else
+    rows(std::false_type{});
   const float iso2 = 2.0f * P.inv2so2;  // 1 / sigma_obs^2
   const float s2 = P.spsf * P.spsf;
   d[0] = I * S1 / s2 * iso2;
@@ -244,7 +269,7 @@ __device__ __forceinline__ float loglik_grad(const float* __restrict__ yp, int p
 }
 
 template <int R>
-__global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
+__global__ void __launch_bounds__(256, 3) k_adjoint(AdjointArgs a) {
   const int k = a.k;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ double s_g[8][5];
@@ -253,6 +278,8 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
     const TrackParams& P = a.trk[td.x];
     const int g = td.y, Np = P.Np;
     const long long Nt = (long long)P.G * Np;
+    const int hslot = k % a.history;
+    const float log_G = logf((float)P.G), log_Np = logf((float)Np);
     const bool A_enters = (P.init_kind == INIT_POINT) || (P.init_kind == INIT_SHARING && g == 0);
     float gacc[5] = {0, 0, 0, 0, 0};
     for (int jj = threadIdx.x; jj < td.w; jj += blockDim.x) {
@@ -263,13 +290,13 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjointArgs a) {
       long long par = il;
       int o = g;
       if (k >= 1) {
-        par = a.parent[P.parent_off + (long long)(k % a.history) * Nt + il];
-        o = (int)(par / Np);
+        par = a.parent[P.parent_off + (long long)hslot * Nt + il];
+        o = (int)fastdiv((uint32_t)par, P.m_Np);  // origin group (par < 2^31)
       }
       float dl[5];
       const float l = loglik_grad<R>(a.ypad + P.ypad_off, P.pitch, P.H, P.W, s.x, s.y, I, P, dl);
-      const float lb = k >= 1 ? (float)a.lbar_prev[P.group_off + o] : -logf((float)P.G);
-      const float lw = lb - logf((float)Np) + l;
+      const float lb = k >= 1 ? (float)a.lbar_prev[P.group_off + o] : -log_G;
+      const float lw = lb - log_Np + l;
       const float lam = (float)a.lam_k[P.group_off + g];
       const float wbar = (lw == lw && lw - lam > -87.0f) ? __expf(lw - lam) : 0.0f;
       const float dlw = (float)a.dlam_k[P.group_off + g] * wbar;
@@ -377,8 +404,8 @@ cudaError_t launch_replay(const ReplayArgs& a, int R, int grid, cudaStream_t s) 
 }
 
 cudaError_t launch_replay_groups(const ReplayGroupArgs& a, int n_tracks, int max_G, cudaStream_t s) {
-  const int threads = ((max_G + 31) / 32) * 32;
-  k_replay_groups<<<n_tracks, threads < 32 ? 32 : threads, 0, s>>>(a);
+  (void)max_G;
+  k_replay_groups<<<n_tracks, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
