@@ -146,7 +146,10 @@ pf_status pf_query_workspace(const pf_track_config* cfg, int32_t n_tracks, int32
  * may start while the previous kernel in the stream drains, and waits for
  * its completion before touching memory); the environment variable
  * PFARNA_PDL=0 at pf_init selects plain stream serialisation instead.
- * Results are identical either way.
+ * Results are identical either way.  PFARNA_TEST_WITHHOLD_COPY=1 at pf_init
+ * (failure-detection tests only) makes the propagate kernel issue no
+ * frame-staging copy, so its bounded wait (0.2 s) runs out: the step ends
+ * early and the next synchronising call reports PF_ERR_TIMEOUT.
  * Errors: PF_ERR_ARG, PF_ERR_WORKSPACE, PF_ERR_CUDA. */
 pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history, void* workspace_dev,
                   size_t bytes, const float* user_state_dev, void* stream, pf_handle** out);

@@ -79,6 +79,7 @@ struct pf_handle {
   int graph_T = 0;
   int k1_occ = 1, sms = 1;
   bool pdl = true;  // programmatic dependent launch between the step kernels
+  bool test_withhold_copy = false;  // PFARNA_TEST_WITHHOLD_COPY=1 at pf_init (failure-detection tests)
   char* ws = nullptr;        // the workspace, its size, and the byte range of the TMA
   size_t ws_total = 0;       // descriptors in it (they hold this workspace's addresses)
   size_t tmap_off = 0, tmap_bytes = 0;
@@ -349,7 +350,7 @@ K1Args k1_args(const pf_handle* h) {
   K1Args a{h->trk, h->tiles, h->n_tiles, h->gs, h->ts, h->ds, h->pv[0], h->pv[1], h->In[0], h->In[1],
            h->anc, h->parent, h->history, h->lw, h->tile_part, h->ypad, h->tmaps, h->ring_next,
            h->G_total, h->exo_next, h->hist, h->ghist, h->tile_ctr, h->n_ring_blocks, h->n_tracks, TrackParams{}, 0,
-           nullptr, CUtensorMap{}};
+           nullptr, h->test_withhold_copy ? 1 : 0, CUtensorMap{}};
   a.p0 = h->tp[0];
   return a;
 }
@@ -440,6 +441,8 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
   {
     const char* v = std::getenv("PFARNA_PDL");  // "0": plain stream serialisation between step kernels
     h->pdl = !(v && v[0] == '0');
+    const char* tw = std::getenv("PFARNA_TEST_WITHHOLD_COPY");
+    h->test_withhold_copy = tw && tw[0] == '1';
   }
   h->last_stream = (cudaStream_t)stream;
   char* w = (char*)workspace;

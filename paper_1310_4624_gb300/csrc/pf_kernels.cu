@@ -501,11 +501,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for phase `parity`; false if it did not complete.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for phase `parity`, for at most MBAR_WAIT_NS; false if it did not
+// complete (a copy that never lands ends the wait instead of the kernel).
+constexpr unsigned long long MBAR_WAIT_NS = 200000000ull;  // 0.2 s
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < (1u << 22); ++it)
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-  return false;
+    if ((it & 255u) == 0u && global_ns() - t0 > MBAR_WAIT_NS) return false;
+  }
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tma_load_2d(float* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
@@ -744,7 +754,7 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
     const bool staged = (raw || a.tmaps != nullptr) && (umax + D - u0) <= ROI_W && nbox <= ROI_MAX_BOXES;
 
     if (staged) {
-      if (threadIdx.x == 0) {
+      if (threadIdx.x == 0 && !a.test_withhold_copy) {
         fence_proxy_async();  // earlier generic reads of s_roi before the async-proxy writes
         mbar_expect_tx(&s_bar, (uint32_t)(nbox * ROI_W * ROI_BOX_H * sizeof(float)));
         for (int b = 0; b < nbox; ++b) {
@@ -921,6 +931,10 @@ __device__ __forceinline__ int count_below(const Thresholds& th, unsigned long l
 __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
   grid_dep_wait();
   if (a.tile_ctr && blockIdx.x == 0 && threadIdx.x == 0) *a.tile_ctr = 0;  // for the next propagate launch
+  // A propagate launch that timed out or met an out-of-range ancestor left
+  // weights that mean nothing: resample nothing.  Only the kernels before
+  // this one set these two bits, so every CTA of a cluster decides alike.
+  if (a.ds && (*reinterpret_cast<volatile const unsigned int*>(&a.ds->err) & (ERR_TIMEOUT | ERR_INDEX)) != 0u) return;
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();

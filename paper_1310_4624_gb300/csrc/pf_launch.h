@@ -69,6 +69,7 @@ struct K1Args {
   // or zraw, instead of the padded frame y = z - b.
   int raw_frame;
   const float* zraw;
+  int test_withhold_copy;    // failure-detection test: issue no staging copy, so the bounded wait runs out
   CUtensorMap zmap;
 };
 
