@@ -23,17 +23,19 @@ from . import build as _build
 
 RNA, ARNA = 0, 1
 OBS_IMAGE, OBS_POINT, OBS_FRAME = 0, 1, 2
+RESAMPLE_ALWAYS, RESAMPLE_ESS = 0, 1
 INIT_POINT, INIT_UNIFORM, INIT_SHARING = 0, 1, 2
 
 
 class Cfg(C.Structure):
     _fields_ = [
         ("G", C.c_int32), ("Np", C.c_int32), ("H", C.c_int32), ("W", C.c_int32),
-        ("R", C.c_int32), ("mode", C.c_int32), ("obs_kind", C.c_int32), ("pad0", C.c_int32),
+        ("R", C.c_int32), ("mode", C.c_int32), ("obs_kind", C.c_int32), ("resample_rule", C.c_int32),
         ("sigma_psf", C.c_double), ("background", C.c_double), ("sigma_obs", C.c_double),
         ("sigma_pos", C.c_double), ("sigma_v", C.c_double), ("sigma_I", C.c_double),
         ("ex_ratio", C.c_double), ("cutoff", C.c_double),
         ("seed", C.c_uint64), ("track", C.c_uint32), ("pad1", C.c_uint32),
+        ("ess_fraction", C.c_double),
     ]
 
 
@@ -43,7 +45,7 @@ _P = C.c_void_p
 class _StepOut(C.Structure):
     _fields_ = [(n, _P) for n in (
         "sigma", "n_ex", "pe_eff", "src", "origin", "X", "loglik", "lw", "q", "anc",
-        "Lambda_out", "gxhat", "gess", "logc", "xhat", "pop_out", "degenerate")]
+        "Lambda_out", "gxhat", "gess", "logc", "xhat", "pop_out", "degenerate", "omega", "resampled")]
 
 
 _lib = None
@@ -82,9 +84,13 @@ def lib():
         L.ora_resample_uniform.argtypes = [C.POINTER(Cfg), C.c_uint32, C.c_uint32]
         L.ora_resample_uniform.restype = C.c_uint32
         L.ora_init.argtypes = [C.POINTER(Cfg), C.c_int32, _P, _P, _P, C.c_double, _P]
-        L.ora_step.argtypes = [C.POINTER(Cfg), C.c_uint32, _P, _P, _P, _P, C.POINTER(_StepOut)]
+        L.ora_ess_code.argtypes = [C.c_double]
+        L.ora_ess_code.restype = C.c_uint32
+        L.ora_ess_test.argtypes = [_P, C.c_int32, C.c_double]
+        L.ora_ess_test.restype = C.c_int
+        L.ora_step.argtypes = [C.POINTER(Cfg), C.c_uint32, _P, _P, _P, _P, _P, C.POINTER(_StepOut)]
         L.ora_step.restype = C.c_int
-        L.ora_run.argtypes = [C.POINTER(Cfg), _P, _P, C.c_int32] + [_P] * 8
+        L.ora_run.argtypes = [C.POINTER(Cfg), _P, _P, C.c_int32] + [_P] * 9
         L.ora_loglik_image_grad.argtypes = [C.POINTER(Cfg), _P, C.c_double, C.c_double, C.c_double, _P]
         L.ora_loglik_image_grad.restype = C.c_double
         L.ora_replay_grad.argtypes = [C.POINTER(Cfg), C.c_int32, _P, _P, _P, C.c_double, _P, C.c_int32, _P, _P, _P]
@@ -104,10 +110,11 @@ def _c(a, dtype):
 
 def make_cfg(G, Np, H=64, W=64, R=5, mode=RNA, obs_kind=OBS_IMAGE, sigma_psf=1.5, background=1.0,
              sigma_obs=1.0, sigma_pos=0.5, sigma_v=0.1, sigma_I=0.5, ex_ratio=0.1, cutoff=0.99,
-             seed=0, track=0) -> Cfg:
+             seed=0, track=0, resample_rule=RESAMPLE_ALWAYS, ess_fraction=0.5) -> Cfg:
     return Cfg(G=G, Np=Np, H=H, W=W, R=R, mode=mode, obs_kind=obs_kind, sigma_psf=sigma_psf,
                background=background, sigma_obs=sigma_obs, sigma_pos=sigma_pos, sigma_v=sigma_v,
-               sigma_I=sigma_I, ex_ratio=ex_ratio, cutoff=cutoff, seed=seed, track=track)
+               sigma_I=sigma_I, ex_ratio=ex_ratio, cutoff=cutoff, seed=seed, track=track,
+               resample_rule=resample_rule, ess_fraction=ess_fraction)
 
 
 def cfg_from_workload(wl, track: int = 0) -> Cfg:
@@ -120,7 +127,8 @@ def cfg_from_workload(wl, track: int = 0) -> Cfg:
     return make_cfg(G=wl.G, Np=wl.Np, H=wl.H, W=wl.W, R=wl.patch_radius, mode=wl.mode, obs_kind=obs,
                     sigma_psf=f(wl.sigma_psf), background=f(wl.background), sigma_obs=f(wl.sigma_obs),
                     sigma_pos=f(wl.sigma_pos), sigma_v=f(wl.sigma_v), sigma_I=f(wl.sigma_I),
-                    ex_ratio=f(wl.ex_ratio), cutoff=f(wl.pe_eff_cutoff), seed=wl.seed, track=track)
+                    ex_ratio=f(wl.ex_ratio), cutoff=f(wl.pe_eff_cutoff), seed=wl.seed, track=track,
+                    resample_rule=getattr(wl, "resample_rule", 0), ess_fraction=f(getattr(wl, "ess_fraction", 0.5)))
 
 
 # ---------------------------------------------------------------- primitives
@@ -281,27 +289,42 @@ class StepResult:
     pop_out: np.ndarray
     degenerate: int
     all_degenerate: bool
+    omega: np.ndarray      # (N,) log weight of each output slot within its group
+    resampled: np.ndarray  # (G,) 1 where the group resampled
 
 
-def step(cfg: Cfg, k: int, obs, pop_in, Lambda_in=None, lw_override=None) -> StepResult:
+def ess_code(ess_fraction: float) -> int:
+    return int(lib().ora_ess_code(float(ess_fraction)))
+
+
+def ess_test(q, ess_fraction: float) -> bool:
+    """Alg. 1's N_eff < N_thresh test on one group's weight codes."""
+    q = _c(q, np.uint64)
+    return bool(lib().ora_ess_test(_ptr(q), len(q), float(ess_fraction)))
+
+
+def step(cfg: Cfg, k: int, obs, pop_in, Lambda_in=None, lw_override=None, omega_in=None) -> StepResult:
     G, Np = cfg.G, cfg.Np
     N = G * Np
     obs = _c(obs, np.float32)
     pop = _c(pop_in, np.float64)
     Lam = _c(Lambda_in if Lambda_in is not None else np.zeros(G), np.float64)
     lwo = None if lw_override is None else _c(lw_override, np.float32)
+    om = None if omega_in is None else _c(omega_in, np.float64)
     a = dict(sigma=np.zeros(G, np.int32), n_ex=np.zeros(1, np.int32), pe_eff=np.zeros(1),
              src=np.zeros(N, np.int32), origin=np.zeros(N, np.int32), X=np.zeros((5, N)),
              loglik=np.zeros(N), lw=np.zeros(N), q=np.zeros(N, np.uint64), anc=np.zeros(N, np.int32),
              Lambda_out=np.zeros(G), gxhat=np.zeros((5, G)), gess=np.zeros(G), logc=np.zeros(1),
-             xhat=np.zeros(5), pop_out=np.zeros((5, N)), degenerate=np.zeros(1, np.int32))
+             xhat=np.zeros(5), pop_out=np.zeros((5, N)), degenerate=np.zeros(1, np.int32),
+             omega=np.zeros(N), resampled=np.zeros(G, np.int32))
     so = _StepOut(**{n: _ptr(v) for n, v in a.items()})
-    rc = lib().ora_step(C.byref(cfg), k, _ptr(obs), _ptr(pop), _ptr(Lam), _ptr(lwo), C.byref(so))
+    rc = lib().ora_step(C.byref(cfg), k, _ptr(obs), _ptr(pop), _ptr(Lam), _ptr(om), _ptr(lwo), C.byref(so))
     return StepResult(sigma=a["sigma"], n_ex=int(a["n_ex"][0]), pe_eff=float(a["pe_eff"][0]),
                       src=a["src"], origin=a["origin"], X=a["X"], loglik=a["loglik"], lw=a["lw"],
                       q=a["q"], anc=a["anc"], Lambda=a["Lambda_out"], gxhat=a["gxhat"], gess=a["gess"],
                       logc=float(a["logc"][0]), xhat=a["xhat"], pop_out=a["pop_out"],
-                      degenerate=int(a["degenerate"][0]), all_degenerate=bool(rc))
+                      degenerate=int(a["degenerate"][0]), all_degenerate=bool(rc), omega=a["omega"],
+                      resampled=a["resampled"])
 
 
 @dataclasses.dataclass
@@ -313,6 +336,7 @@ class RunResult:
     sigma: np.ndarray     # (T, G)
     Lambda: np.ndarray    # (T, G)
     gxhat: np.ndarray     # (T, 5, G)
+    n_resampled: np.ndarray  # (T,) groups that resampled
     pop_final: np.ndarray  # (5, N)
     failed_step: int
 
@@ -323,10 +347,11 @@ def run(cfg: Cfg, pop0, obs, T: int) -> RunResult:
     obs = _c(obs, np.float32)
     r = RunResult(xhat=np.zeros((T, 5)), logc=np.zeros(T), n_ex=np.zeros(T, np.int32),
                   pe_eff=np.zeros(T), sigma=np.zeros((T, G), np.int32), Lambda=np.zeros((T, G)),
-                  gxhat=np.zeros((T, 5, G)), pop_final=np.zeros((5, N)), failed_step=-1)
+                  gxhat=np.zeros((T, 5, G)), n_resampled=np.zeros(T, np.int32), pop_final=np.zeros((5, N)),
+                  failed_step=-1)
     r.failed_step = lib().ora_run(C.byref(cfg), _ptr(pop0), _ptr(obs), T, _ptr(r.xhat), _ptr(r.logc),
                                   _ptr(r.n_ex), _ptr(r.pe_eff), _ptr(r.sigma), _ptr(r.Lambda),
-                                  _ptr(r.gxhat), _ptr(r.pop_final))
+                                  _ptr(r.gxhat), _ptr(r.n_resampled), _ptr(r.pop_final))
     return r
 
 
@@ -354,8 +379,10 @@ def replay_grad(cfg: Cfg, kind: int, x0, frames, T: int, parents, lo=None, hi=No
     assert par.shape == (T, N)
     lz = np.zeros(1)
     g = np.zeros(5)
-    lib().ora_replay_grad(C.byref(cfg), kind, _ptr(x0), _ptr(lo), _ptr(hi), radius, _ptr(fr), T, _ptr(par),
-                          _ptr(lz), _ptr(g))
+    rc = lib().ora_replay_grad(C.byref(cfg), kind, _ptr(x0), _ptr(lo), _ptr(hi), radius, _ptr(fr), T, _ptr(par),
+                               _ptr(lz), _ptr(g))
+    if rc != 0:
+        raise ValueError("replay_grad needs resample_rule = RESAMPLE_ALWAYS")
     return float(lz[0]), g
 
 

@@ -51,6 +51,9 @@
 #define ORA_OBS_POINT 1
 #define ORA_OBS_FRAME 2
 
+#define ORA_RESAMPLE_ALWAYS 0
+#define ORA_RESAMPLE_ESS 1
+
 #define ORA_INIT_POINT 0
 #define ORA_INIT_UNIFORM 1
 #define ORA_INIT_SHARING 2
@@ -66,7 +69,7 @@ typedef struct {
   int32_t R;        /* patch radius: the likelihood patch is (2R+1)^2 pixels */
   int32_t mode;     /* ORA_RNA or ORA_ARNA */
   int32_t obs_kind; /* ORA_OBS_IMAGE (patch residual), ORA_OBS_FRAME (frame likelihood ratio) or ORA_OBS_POINT */
-  int32_t pad0;
+  int32_t resample_rule; /* ORA_RESAMPLE_ALWAYS (Alg. 2/3) or ORA_RESAMPLE_ESS (Alg. 1's N_eff test per group) */
   double sigma_psf, background, sigma_obs;
   double sigma_pos, sigma_v, sigma_I;
   double ex_ratio; /* RNA: fixed N_ex / N_p */
@@ -74,6 +77,7 @@ typedef struct {
   uint64_t seed;
   uint32_t track;
   uint32_t pad1;
+  double ess_fraction; /* ORA_RESAMPLE_ESS: N_thresh = ess_fraction * Np */
 } ora_cfg;
 
 /* ------------------------------------------------------------------------ */
@@ -456,6 +460,36 @@ uint32_t ora_resample_uniform(const ora_cfg* c, uint32_t g, uint32_t k) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Alg. 1's resampling test, per group: resample when the effective sample  */
+/* size N_eff = 1 / sum_i w_i^2 of the normalised weights falls below       */
+/* N_thresh (Sec. II: when too few particles carry relatively high weight). */
+/* Taken on the resampler's weight codes so that both sides decide alike:   */
+/* w_i = c_i / sum c with c_i = q_i >> 20 (in [0, 2^20]), so               */
+/* N_eff = (sum c)^2 / sum c^2; N_thresh = t Np / 2^16 with                 */
+/* t = round(ess_fraction 2^16).  In exact integers:                        */
+/*   resample  iff  2^16 (sum c)^2 < t Np sum c^2.                          */
+/* Returns 1 to resample.  Q = 0 (no finite weight) returns 1: such a group */
+/* resamples as the identity.                                               */
+/* ------------------------------------------------------------------------ */
+uint32_t ora_ess_code(double ess_fraction) {
+  double f = ess_fraction < 0.0 ? 0.0 : (ess_fraction > 1.0 ? 1.0 : ess_fraction);
+  return (uint32_t)floor(f * 65536.0 + 0.5);
+}
+
+int ora_ess_test(const uint64_t* q, int32_t n, double ess_fraction) {
+  u128 Q = 0, s1 = 0, s2 = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    uint64_t c = q[i] >> 20;
+    Q += q[i];
+    s1 += c;
+    s2 += (u128)c * c;
+  }
+  if (Q == 0) return 1;
+  u128 t = ora_ess_code(ess_fraction);
+  return ((s1 * s1) << 16) < t * (u128)n * s2;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Initial population (Sec. V "tracking" and "information sharing" modes).  */
 /* INIT stream, index j, group g, step 0: call 0 words 0..3, call 1 word 0.  */
 /*  POINT:    every particle at x0.                                          */
@@ -513,6 +547,8 @@ typedef struct {
   double* xhat;       /* [5]   S8 global estimate */
   double* pop_out;    /* [5N]  resampled population (input of step k+1) */
   int32_t* degenerate;/* [1]   groups with no finite weight */
+  double* omega;      /* [N]   log of each output slot's weight within its group (S10) */
+  int32_t* resampled; /* [G]   1 where the group resampled at this step */
 } ora_step_out;
 
 static double lse(const double* v, int64_t n) {
@@ -525,16 +561,19 @@ static double lse(const double* v, int64_t n) {
   return mx + log(s);
 }
 
-/* pop_in: the population after step k-1's resampling (5 x N, SoA), every
- * particle of group m carrying weight W_m / Np with W_m = exp(Lambda_in[m])
- * (Alg. 3 step 8).  At k = 0 pop_in is the initial sample and Lambda_in is
- * ignored (all groups equal).  obs: the frame (H x W, row-major) or, for
+/* pop_in: the population after step k-1's resampling (5 x N, SoA), the
+ * particle in slot i of group m carrying weight W_m w_i with
+ * W_m = exp(Lambda_in[m]) and w_i = exp(omega_in[i]) its weight within the
+ * group (Alg. 3 step 8: w_i = 1 / Np after resampling; omega_in may then be
+ * NULL).  A group that skipped resampling under ORA_RESAMPLE_ESS carries its
+ * particles' own normalised weights instead.  At k = 0 pop_in is the initial
+ * sample, Lambda_in and omega_in are ignored (all weights equal).  obs: the frame (H x W, row-major) or, for
  * ORA_OBS_POINT, two floats.  lw_override: if not NULL, steps S7-S9 (group
  * weights, estimates, resampling) use these FP32 log-weights instead of the
  * oracle's own (so both sides can be fed identical weights); o->lw still
  * receives the oracle's own.  Returns 0, or 1 if every group is degenerate. */
 int ora_step(const ora_cfg* c, uint32_t k, const float* obs, const double* pop_in,
-             const double* Lambda_in, const float* lw_override, ora_step_out* o) {
+             const double* Lambda_in, const double* omega_in, const float* lw_override, ora_step_out* o) {
   int32_t G = c->G, Np = c->Np;
   int64_t N = (int64_t)G * Np;
   double* Lam = (double*)malloc(sizeof(double) * (size_t)G);
@@ -548,8 +587,11 @@ int ora_step(const ora_cfg* c, uint32_t k, const float* obs, const double* pop_i
   double* pop = (double*)malloc(sizeof(double) * (size_t)(5 * N));
   ora_exchange(c, k, o->sigma, *o->n_ex, pop_in, pop, o->src, o->origin);
 
-  /* S4 (Alg. 3 step 4): log w_i = Lambda_origin - log Np - LSE(Lambda) */
+  /* S4 (Alg. 3 step 4): log w_i = Lambda_origin + omega_i - LSE(Lambda),
+   * omega_i = -log Np after resampling; an exchanged particle keeps its own */
   double lse_lam = lse(Lam, G);
+  double* om = (double*)malloc(sizeof(double) * (size_t)N);
+  for (int64_t i = 0; i < N; ++i) om[i] = (k == 0 || !omega_in) ? -log((double)Np) : omega_in[o->src[i]];
 
   /* S5, S6 (Alg. 3 step 5) */
   if (k == 0)
@@ -562,7 +604,7 @@ int ora_step(const ora_cfg* c, uint32_t k, const float* obs, const double* pop_i
                : (c->obs_kind == ORA_OBS_FRAME) ? ora_loglik_frame(c, obs, x, y, I)
                                                 : ora_loglik_image(c, obs, x, y, I);
     o->loglik[i] = l;
-    o->lw[i] = Lam[o->origin[i]] - log((double)Np) - lse_lam + l;
+    o->lw[i] = Lam[o->origin[i]] + om[i] - lse_lam + l;
   }
 
   /* With lw_override the remaining steps (S7-S9) use those log-weights, so
@@ -612,17 +654,33 @@ int ora_step(const ora_cfg* c, uint32_t k, const float* obs, const double* pop_i
     o->xhat[d] = acc;
   }
 
-  /* S9 (Alg. 3 step 7): per-group systematic resampling on FP32 codes */
+  /* S9 (Alg. 3 step 7): per-group systematic resampling on FP32 codes; under
+   * ORA_RESAMPLE_ESS only where Alg. 1's N_eff test asks for it.  S10: a
+   * resampled group's particles weigh 1 / Np within it, the others keep
+   * w_i = w~_i / W'_m. */
   float* lwf = (float*)malloc(sizeof(float) * (size_t)Np);
   for (int32_t m = 0; m < G; ++m) {
     for (int32_t j = 0; j < Np; ++j)
       lwf[j] = lw_override ? lw_override[(int64_t)m * Np + j] : (float)o->lw[(int64_t)m * Np + j];
     uint64_t* qm = o->q + (int64_t)m * Np;
+    int32_t* am = o->anc + (int64_t)m * Np;
+    double* omm = o->omega + (int64_t)m * Np;
     ora_quantize(lwf, Np, qm);
-    ora_resample(qm, Np, ora_resample_uniform(c, (uint32_t)m, k), o->anc + (int64_t)m * Np);
+    int res = c->resample_rule != ORA_RESAMPLE_ESS || ora_ess_test(qm, Np, c->ess_fraction);
+    o->resampled[m] = res;
+    if (res) {
+      ora_resample(qm, Np, ora_resample_uniform(c, (uint32_t)m, k), am);
+      for (int32_t j = 0; j < Np; ++j) omm[j] = -log((double)Np);
+    } else {
+      for (int32_t j = 0; j < Np; ++j) {
+        am[j] = j;
+        omm[j] = lwe[(int64_t)m * Np + j] - o->Lambda_out[m];
+      }
+    }
   }
   free(lwf);
   free(lwbuf);
+  free(om);
 
   /* S10 (Alg. 3 step 8): the resampled population; group weights carried */
   for (int d = 0; d < 5; ++d)
@@ -639,13 +697,13 @@ int ora_step(const ora_cfg* c, uint32_t k, const float* obs, const double* pop_i
 
 /* A whole run of T steps from the initial population pop0 (5 x N).
  * Per-step outputs (caller-allocated, step-major): xhat[T*5], logc[T],
- * n_ex[T], pe_eff[T], sigma[T*G], Lambda[T*G], gxhat[T*5*G].  Any per-step
- * pointer may be NULL.  obs: T frames (H*W floats each) or T points (2
+ * n_ex[T], pe_eff[T], sigma[T*G], Lambda[T*G], gxhat[T*5*G], n_resampled[T]
+ * (groups that resampled).  Any per-step pointer may be NULL.  obs: T frames (H*W floats each) or T points (2
  * floats each).  Returns the first step at which every group was degenerate,
  * or -1. */
 int ora_run(const ora_cfg* c, const double* pop0, const float* obs, int32_t T, double* xhat,
             double* logc, int32_t* n_ex, double* pe_eff, int32_t* sigma, double* Lambda,
-            double* gxhat, double* pop_final) {
+            double* gxhat, int32_t* n_resampled, double* pop_final) {
   int32_t G = c->G, Np = c->Np;
   int64_t N = (int64_t)G * Np;
   size_t fs = (c->obs_kind == ORA_OBS_POINT) ? 2 : (size_t)c->H * (size_t)c->W;
@@ -670,9 +728,13 @@ int ora_run(const ora_cfg* c, const double* pop0, const float* obs, int32_t T, d
   o.xhat = (double*)malloc(sizeof(double) * 5);
   o.pop_out = (double*)malloc(sizeof(double) * (size_t)(5 * N));
   o.degenerate = (int32_t*)malloc(sizeof(int32_t));
+  o.omega = (double*)malloc(sizeof(double) * (size_t)N);
+  o.resampled = (int32_t*)malloc(sizeof(int32_t) * (size_t)G);
+  double* omega = (double*)malloc(sizeof(double) * (size_t)N);
+  for (int64_t i = 0; i < N; ++i) omega[i] = -log((double)Np);
   int failed = -1;
   for (int32_t k = 0; k < T; ++k) {
-    int rc = ora_step(c, (uint32_t)k, obs + (size_t)k * fs, pop, Lam, NULL, &o);
+    int rc = ora_step(c, (uint32_t)k, obs + (size_t)k * fs, pop, Lam, omega, NULL, &o);
     if (rc && failed < 0) failed = k;
     if (xhat) memcpy(xhat + (size_t)k * 5, o.xhat, sizeof(double) * 5);
     if (logc) logc[k] = *o.logc;
@@ -681,13 +743,19 @@ int ora_run(const ora_cfg* c, const double* pop0, const float* obs, int32_t T, d
     if (sigma) memcpy(sigma + (size_t)k * G, o.sigma, sizeof(int32_t) * (size_t)G);
     if (Lambda) memcpy(Lambda + (size_t)k * G, o.Lambda_out, sizeof(double) * (size_t)G);
     if (gxhat) memcpy(gxhat + (size_t)k * 5 * G, o.gxhat, sizeof(double) * (size_t)(5 * G));
+    if (n_resampled) {
+      n_resampled[k] = 0;
+      for (int32_t m = 0; m < G; ++m) n_resampled[k] += o.resampled[m];
+    }
     memcpy(Lam, o.Lambda_out, sizeof(double) * (size_t)G);
+    memcpy(omega, o.omega, sizeof(double) * (size_t)N);
     memcpy(pop, o.pop_out, sizeof(double) * (size_t)(5 * N));
   }
   if (pop_final) memcpy(pop_final, pop, sizeof(double) * (size_t)(5 * N));
   free(o.sigma); free(o.n_ex); free(o.pe_eff); free(o.src); free(o.origin); free(o.X);
   free(o.loglik); free(o.lw); free(o.q); free(o.anc); free(o.Lambda_out); free(o.gxhat);
   free(o.gess); free(o.logc); free(o.xhat); free(o.pop_out); free(o.degenerate);
+  free(o.omega); free(o.resampled); free(omega);
   free(pop);
   free(Lam);
   return failed;
@@ -751,6 +819,8 @@ double ora_loglik_image_grad(const ora_cfg* c, const float* frame, double x, dou
 int ora_replay_grad(const ora_cfg* c, int32_t kind, const double* x0, const double* lo, const double* hi,
                     double radius, const float* frames, int32_t T, const int32_t* parents, double* logZ,
                     double* grad) {
+  /* every step resamples here: a replay does not carry per-particle weights */
+  if (c->resample_rule != ORA_RESAMPLE_ALWAYS) return -1;
   int32_t G = c->G, Np = c->Np;
   int64_t N = (int64_t)G * Np;
   size_t fs = (size_t)c->H * (size_t)c->W;

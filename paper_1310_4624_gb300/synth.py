@@ -62,6 +62,8 @@ class Workload:
     share_I: Tuple[float, float] = (1.0, 20.0)
     truth_noise: bool = False     # truth drawn from the NCV dynamics (sigma_pos, sigma_v)
     obs_model: int = 0            # 0: patch residual, 1: frame likelihood ratio
+    resample_rule: int = 0        # 0: every step (Alg. 2/3), 1: when N_eff < ess_fraction Np (Alg. 1)
+    ess_fraction: float = 0.5
 
     @property
     def N(self) -> int:
