@@ -503,18 +503,22 @@ def bench_accuracy(dev, n_seq: int = 10):
     `n_seq` sequences (data seeds 0..n_seq-1, rendered on the device):
     position RMSE of the global estimate against the truth, for ARNA and RNA
     with 0 %, 10 % and 50 % exchange on identical Philox streams (the paper's
-    comparison, Sec. V-A), and the mean device time per step of each (CUDA
-    events around whole 100-step runs; L2 not flushed between steps)."""
+    comparison, Sec. V-A), ARNA and RNA 10 % that resample a group only when
+    its N_eff falls below Np / 2 (Alg. 1's test), and the mean device time
+    per step of each (CUDA events around whole 100-step runs; L2 not flushed
+    between steps) with the mean number of groups that resampled per step."""
     import torch
     from paper_1310_4624_gb300 import synth
     from paper_1310_4624_gb300.filter import ParticleFilter, config_from_workload
     wls = [synth.tracking(mode=synth.ARNA, data_seed=s) for s in range(n_seq)]
     frames, truths = synth.render_batched_torch(wls, dev, seed=1)
     modes = {"arna": dict(mode=synth.ARNA), "rna0": dict(mode=synth.RNA, ex_ratio=0.0),
-             "rna10": dict(mode=synth.RNA, ex_ratio=0.10), "rna50": dict(mode=synth.RNA, ex_ratio=0.50)}
+             "rna10": dict(mode=synth.RNA, ex_ratio=0.10), "rna50": dict(mode=synth.RNA, ex_ratio=0.50),
+             "arna_ess50": dict(mode=synth.ARNA, resample_rule=1, ess_fraction=0.5),
+             "rna10_ess50": dict(mode=synth.RNA, ex_ratio=0.10, resample_rule=1, ess_fraction=0.5)}
     out = {}
     for name, kw in modes.items():
-        se, per, ms = 0.0, [], 0.0
+        se, per, ms, nres = 0.0, [], 0.0, 0
         for s, wl in enumerate(wls):
             wl = wl.replace(**kw)
             pf = ParticleFilter([config_from_workload(wl, truths[s][0])], history=wl.T + 1, device=dev)
@@ -523,9 +527,11 @@ def bench_accuracy(dev, n_seq: int = 10):
             e = np.array([np.sum((h["xhat"][:2] - truths[s][h["step"], :2]) ** 2) for h in hs])
             per.append(float(math.sqrt(e.mean())))
             se += float(e.sum())
+            nres += sum(h["resampled"] for h in hs)
             pf.close()
         out[name] = {"rmse_px": math.sqrt(se / (n_seq * wls[0].T)), "per_sequence": [round(v, 4) for v in per],
-                     "ms_per_step": ms / (n_seq * wls[0].T)}
+                     "ms_per_step": ms / (n_seq * wls[0].T),
+                     "resampled_groups_per_step": nres / (n_seq * wls[0].T)}
     out["sequences"] = n_seq
     out["workload"] = wls[0].name.rsplit("_", 1)[0]
     return out

@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define PF_ABI_VERSION 2
+#define PF_ABI_VERSION 3
 
 typedef enum pf_status {
   PF_OK = 0,
@@ -86,6 +86,30 @@ enum {
  *    the log of that ratio. */
 enum { PF_OBS_PATCH = 0, PF_OBS_FRAME = 1 };
 
+/* When a group resamples (resample_rule).
+ *  PF_RESAMPLE_ALWAYS: every group at every step (Alg. 2 / Alg. 3).
+ *  PF_RESAMPLE_ESS: Alg. 1's test, per group: group m resamples at step k
+ *    only when its effective sample size N_eff = (sum w)^2 / sum w^2 is
+ *    below N_thresh = ess_fraction * Np; a group that does not resample
+ *    keeps its particles in place with their own weights, which they carry
+ *    into the next step (and through the ring exchange).  The test is taken
+ *    exactly on the resampler's integer weight codes q: with c_i = q_i >> 20,
+ *    resample iff 2^16 (sum c)^2 < t Np sum c^2, t = round(ess_fraction
+ *    2^16).  A group without finite weight resamples as the identity. */
+enum { PF_RESAMPLE_ALWAYS = 0, PF_RESAMPLE_ESS = 1 };
+
+/* Which slots a group sends (send_rule; Sec. III-C: each PE randomly selects
+ * N_ex particles).  A receiver puts the particles into its own send slots,
+ * the t-th sent slot of the sender into the t-th send slot of the receiver.
+ *  PF_SEND_SYSTEMATIC: slots floor((t Np + o_g) / N_ex), t < N_ex, with a
+ *    uniform offset o_g per group and step: every slot with probability
+ *    N_ex / Np, spread evenly over the slots.
+ *  PF_SEND_KEYED: slots pi_g(t), t < N_ex, of a keyed pseudo-random
+ *    permutation of [0, Np) per group and step (a four-round Feistel network
+ *    on ceil(log2 Np) bits with cycle walking, round keys from the Philox
+ *    stream of the exchange): a uniformly random-looking subset. */
+enum { PF_SEND_SYSTEMATIC = 0, PF_SEND_KEYED = 1 };
+
 /* One track's filter.  Observation model: obs_model above.  Dynamics: nearly
  * constant velocity with unit frame interval and independent Gaussian noise
  * sigma_pos (position), sigma_v (velocity), sigma_I (intensity). */
@@ -108,6 +132,9 @@ typedef struct pf_track_config {
   uint64_t seed;        /* Philox4x32-10 key */
   uint32_t track_id;    /* Philox stream id of this track, < 2^24 */
   int32_t record_ancestors; /* 1: keep per-step ancestry for pf_backward */
+  int32_t resample_rule;    /* PF_RESAMPLE_ALWAYS (0) or PF_RESAMPLE_ESS */
+  float ess_fraction;       /* PF_RESAMPLE_ESS: N_thresh / Np, in [0, 1] */
+  int32_t send_rule;        /* PF_SEND_SYSTEMATIC (0) or PF_SEND_KEYED */
 } pf_track_config;
 
 /* Statistics of one completed step of one track. */
@@ -119,6 +146,7 @@ typedef struct pf_step_stats {
   double log_Z;              /* sum of log_c over steps 0 .. k */
   float xhat[5];             /* global estimate x^_k (Alg. 3 step 10) */
   int32_t degenerate_groups; /* groups whose weights were all zero / NaN */
+  int32_t resampled_groups;  /* groups that resampled at step k (all of them under PF_RESAMPLE_ALWAYS) */
 } pf_step_stats;
 
 typedef struct pf_handle pf_handle;
@@ -158,10 +186,11 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
  * frames_host: host array of n_tracks device pointers, frame k of each
  * track (H x W float32); the frames must stay valid until the step has run
  * on `stream`.  At k = 0 there is no propagation and no exchange: the
- * initial population is weighted by frame 0.  A step is three kernels:
- * frame preparation, propagate + weight, and resampling whose last group
- * per track also runs the track's global step (Alg. 3 steps 8-10, and
- * steps 1-2 of the next step).
+ * initial population is weighted by frame 0.  A step is two kernels,
+ * propagate + weight and resampling, whose last group per track also runs
+ * the track's global step (Alg. 3 steps 8-10, and steps 1-2 of the next
+ * step); a batch of tracks, or a single track whose frame a TMA descriptor
+ * cannot describe, adds a frame-preparation kernel before them.
  * Errors: PF_ERR_ARG (NULL frame), PF_ERR_STATE (handle failed before),
  * PF_ERR_CUDA. */
 pf_status pf_step(pf_handle* h, const float* const* frames_host, void* stream);
@@ -184,7 +213,8 @@ pf_status pf_graph_step(pf_handle* h, const float* const* table_dev, int32_t T_t
  * steps: the propagate kernel's grid (SM count x resident CTAs per SM, 1 ..
  * the occupancy limit) and the resampler's thread-block cluster size
  * (1, 2, 4, 8), each the fastest of the candidates timed with CUDA events
- * on this step's data (both kernels are idempotent within a step).  Results
+ * on this step's data (the propagate candidates first: it is idempotent
+ * until a resampler replaces the ancestors it reads).  Results
  * are cached per problem shape for the process.  Synchronises the stream.
  * k1_grid_out / cluster_out (may be NULL) receive the choices.
  * Errors: PF_ERR_ARG, PF_ERR_STATE, PF_ERR_CUDA. */
@@ -329,7 +359,8 @@ pf_status pf_reset(pf_handle* h, void* stream);
  * dlogZ_host: n_tracks upstream derivatives.  grad_dev: n_tracks x 5 floats,
  * dlogZ * d log Z / d theta.  logZ_dev: optional n_tracks doubles, the
  * replayed log Z.  Enqueued on `stream`; the forward filter state is left
- * as it was.  Errors: PF_ERR_ARG, PF_ERR_STATE, PF_ERR_CUDA. */
+ * as it was.  Tracks must use PF_RESAMPLE_ALWAYS (the replay resamples at
+ * every step).  Errors: PF_ERR_ARG, PF_ERR_STATE, PF_ERR_CUDA. */
 pf_status pf_backward(pf_handle* h, const float* const* frames_host, int32_t T, const float* dlogZ_host,
                       float* grad_dev, double* logZ_dev, void* stream);
 

@@ -24,6 +24,7 @@ from . import build as _build
 RNA, ARNA = 0, 1
 OBS_IMAGE, OBS_POINT, OBS_FRAME = 0, 1, 2
 RESAMPLE_ALWAYS, RESAMPLE_ESS = 0, 1
+SEND_SYSTEMATIC, SEND_KEYED = 0, 1
 INIT_POINT, INIT_UNIFORM, INIT_SHARING = 0, 1, 2
 
 
@@ -34,7 +35,7 @@ class Cfg(C.Structure):
         ("sigma_psf", C.c_double), ("background", C.c_double), ("sigma_obs", C.c_double),
         ("sigma_pos", C.c_double), ("sigma_v", C.c_double), ("sigma_I", C.c_double),
         ("ex_ratio", C.c_double), ("cutoff", C.c_double),
-        ("seed", C.c_uint64), ("track", C.c_uint32), ("pad1", C.c_uint32),
+        ("seed", C.c_uint64), ("track", C.c_uint32), ("send_rule", C.c_int32),
         ("ess_fraction", C.c_double),
     ]
 
@@ -84,6 +85,13 @@ def lib():
         L.ora_resample_uniform.argtypes = [C.POINTER(Cfg), C.c_uint32, C.c_uint32]
         L.ora_resample_uniform.restype = C.c_uint32
         L.ora_init.argtypes = [C.POINTER(Cfg), C.c_int32, _P, _P, _P, C.c_double, _P]
+        L.ora_perm_bits.argtypes = [C.c_uint32]
+        L.ora_perm_bits.restype = C.c_int
+        L.ora_send_keys.argtypes = [C.POINTER(Cfg), C.c_uint32, C.c_uint32, _P]
+        L.ora_send_perm.argtypes = [C.c_uint32, C.c_uint32, _P]
+        L.ora_send_perm.restype = C.c_uint32
+        L.ora_send_perm_inv.argtypes = [C.c_uint32, C.c_uint32, _P]
+        L.ora_send_perm_inv.restype = C.c_uint32
         L.ora_ess_code.argtypes = [C.c_double]
         L.ora_ess_code.restype = C.c_uint32
         L.ora_ess_test.argtypes = [_P, C.c_int32, C.c_double]
@@ -110,11 +118,11 @@ def _c(a, dtype):
 
 def make_cfg(G, Np, H=64, W=64, R=5, mode=RNA, obs_kind=OBS_IMAGE, sigma_psf=1.5, background=1.0,
              sigma_obs=1.0, sigma_pos=0.5, sigma_v=0.1, sigma_I=0.5, ex_ratio=0.1, cutoff=0.99,
-             seed=0, track=0, resample_rule=RESAMPLE_ALWAYS, ess_fraction=0.5) -> Cfg:
+             seed=0, track=0, resample_rule=RESAMPLE_ALWAYS, ess_fraction=0.5, send_rule=SEND_SYSTEMATIC) -> Cfg:
     return Cfg(G=G, Np=Np, H=H, W=W, R=R, mode=mode, obs_kind=obs_kind, sigma_psf=sigma_psf,
                background=background, sigma_obs=sigma_obs, sigma_pos=sigma_pos, sigma_v=sigma_v,
                sigma_I=sigma_I, ex_ratio=ex_ratio, cutoff=cutoff, seed=seed, track=track,
-               resample_rule=resample_rule, ess_fraction=ess_fraction)
+               resample_rule=resample_rule, ess_fraction=ess_fraction, send_rule=send_rule)
 
 
 def cfg_from_workload(wl, track: int = 0) -> Cfg:
@@ -128,7 +136,8 @@ def cfg_from_workload(wl, track: int = 0) -> Cfg:
                     sigma_psf=f(wl.sigma_psf), background=f(wl.background), sigma_obs=f(wl.sigma_obs),
                     sigma_pos=f(wl.sigma_pos), sigma_v=f(wl.sigma_v), sigma_I=f(wl.sigma_I),
                     ex_ratio=f(wl.ex_ratio), cutoff=f(wl.pe_eff_cutoff), seed=wl.seed, track=track,
-                    resample_rule=getattr(wl, "resample_rule", 0), ess_fraction=f(getattr(wl, "ess_fraction", 0.5)))
+                    resample_rule=getattr(wl, "resample_rule", 0), ess_fraction=f(getattr(wl, "ess_fraction", 0.5)),
+                    send_rule=getattr(wl, "send_rule", 0))
 
 
 # ---------------------------------------------------------------- primitives
@@ -291,6 +300,27 @@ class StepResult:
     all_degenerate: bool
     omega: np.ndarray      # (N,) log weight of each output slot within its group
     resampled: np.ndarray  # (G,) 1 where the group resampled
+
+
+def perm_bits(n: int) -> int:
+    return int(lib().ora_perm_bits(n))
+
+
+def send_keys(cfg: Cfg, g: int, k: int) -> np.ndarray:
+    """The four Feistel round keys of group g's send permutation at step k."""
+    key = np.zeros(4, np.uint32)
+    lib().ora_send_keys(C.byref(cfg), g, k, _ptr(key))
+    return key
+
+
+def send_perm(t: int, n: int, key) -> int:
+    key = _c(key, np.uint32)
+    return int(lib().ora_send_perm(t, n, _ptr(key)))
+
+
+def send_perm_inv(j: int, n: int, key) -> int:
+    key = _c(key, np.uint32)
+    return int(lib().ora_send_perm_inv(j, n, _ptr(key)))
 
 
 def ess_code(ess_fraction: float) -> int:

@@ -51,6 +51,9 @@
 #define ORA_OBS_POINT 1
 #define ORA_OBS_FRAME 2
 
+#define ORA_SEND_SYSTEMATIC 0
+#define ORA_SEND_KEYED 1
+
 #define ORA_RESAMPLE_ALWAYS 0
 #define ORA_RESAMPLE_ESS 1
 
@@ -76,7 +79,7 @@ typedef struct {
   double cutoff;   /* ARNA: no exchange once PE_eff >= cutoff * G */
   uint64_t seed;
   uint32_t track;
-  uint32_t pad1;
+  int32_t send_rule;   /* ORA_SEND_SYSTEMATIC or ORA_SEND_KEYED (which slots a group sends) */
   double ess_fraction; /* ORA_RESAMPLE_ESS: N_thresh = ess_fraction * Np */
 } ora_cfg;
 
@@ -254,7 +257,84 @@ uint32_t ora_exchange_offset(const ora_cfg* c, uint32_t g, uint32_t k) {
   return ora_draw_bounded(c, ORA_STREAM_EXCH, g, k, (uint32_t)c->Np);
 }
 
-/* pop_in / pop_out: 5 x N SoA (component-major), N = G*Np, slot = g*Np + j.
+/* ------------------------------------------------------------------------ */
+/* Random send sets (Sec. III-C: each PE "randomly selects" the particles it */
+/* sends), ORA_SEND_KEYED: group g's t-th sent slot at step k is             */
+/* pi_g(t), t < N_ex, for a keyed pseudo-random permutation pi_g of [0, Np): */
+/* a four-round Feistel network (Luby and Rackoff, SIAM J. Comput. 1988) on  */
+/* b = ceil(log2 Np) bits, walked onto [0, Np) by repeating it while the     */
+/* value is out of range (cycle walking: Black and Rogaway, "Ciphers with    */
+/* arbitrary finite domains", CT-RSA 2002).  The b bits split into a high    */
+/* half L of floor(b/2) bits and a low half R of the rest; a round maps      */
+/* (L, R) to (R, L xor (F(R xor key_i) mod 2^|L|)), so the halves trade      */
+/* places and sizes, and four rounds restore the sizes.  F is the mixer      */
+/*   h = x * 0x9E3779B1; h ^= h >> 16; h *= 0x7FEB352D; h ^= h >> 15         */
+/* (32-bit wrap-around).  key_0..3: the four Philox words of the EXCH stream, */
+/* call 1, counter (g, 0, k).                                               */
+/* ------------------------------------------------------------------------ */
+static uint32_t feistel_mix(uint32_t x) {
+  uint32_t h = x * 0x9E3779B1u;
+  h ^= h >> 16;
+  h *= 0x7FEB352Du;
+  h ^= h >> 15;
+  return h;
+}
+
+static uint32_t low_mask(int n) { return n >= 32 ? 0xffffffffu : ((1u << n) - 1u); }
+
+int ora_perm_bits(uint32_t n) {
+  int b = 0;
+  while (b < 32 && (1u << b) < n) ++b;
+  return b;
+}
+
+static uint32_t feistel_fwd(uint32_t x, int b, const uint32_t key[4]) {
+  int sl = b / 2, sr = b - sl;
+  uint32_t L = x >> sr, R = x & low_mask(sr);
+  for (int i = 0; i < 4; ++i) {
+    uint32_t nl = R, nr = L ^ (feistel_mix(R ^ key[i]) & low_mask(sl));
+    L = nl;
+    R = nr;
+    int t = sl; sl = sr; sr = t;
+  }
+  return (L << sr) | R;
+}
+
+static uint32_t feistel_inv(uint32_t y, int b, const uint32_t key[4]) {
+  int sl = b / 2, sr = b - sl;
+  uint32_t L = y >> sr, R = y & low_mask(sr);
+  for (int i = 3; i >= 0; --i) {
+    uint32_t nr = L, nl = R ^ (feistel_mix(L ^ key[i]) & low_mask(sr));
+    L = nl;
+    R = nr;
+    int t = sl; sl = sr; sr = t;
+  }
+  return (L << sr) | R;
+}
+
+void ora_send_keys(const ora_cfg* c, uint32_t g, uint32_t k, uint32_t key[4]) {
+  philox_stream(c, g, 0u, k, ORA_STREAM_EXCH, 1u, key);
+}
+
+uint32_t ora_send_perm(uint32_t t, uint32_t n, const uint32_t key[4]) {
+  int b = ora_perm_bits(n);
+  uint32_t x = t;
+  do x = feistel_fwd(x, b, key); while (x >= n);
+  return x;
+}
+
+uint32_t ora_send_perm_inv(uint32_t j, uint32_t n, const uint32_t key[4]) {
+  int b = ora_perm_bits(n);
+  uint32_t x = j;
+  do x = feistel_inv(x, b, key); while (x >= n);
+  return x;
+}
+
+/* S3: group sigma_p sends its t-th send slot (t < n_ex) to the t-th send
+ * slot of sigma_{p+1}.  Send slots: ORA_SEND_SYSTEMATIC, the systematic
+ * subsample floor((t Np + o_g) / n_ex) with a uniform offset o_g in [0, Np);
+ * ORA_SEND_KEYED, pi_g(t) of the keyed permutation above.
+ * pop_in / pop_out: 5 x N SoA (component-major), N = G*Np, slot = g*Np + j.
  * src[i]: the slot that slot i's particle came from; origin[i]: its group. */
 void ora_exchange(const ora_cfg* c, uint32_t k, const int32_t* sigma, int32_t n_ex,
                   const double* pop_in, double* pop_out, int32_t* src, int32_t* origin) {
@@ -265,18 +345,26 @@ void ora_exchange(const ora_cfg* c, uint32_t k, const int32_t* sigma, int32_t n_
     origin[i] = (int32_t)(i / Np);
   }
   if (n_ex > 0) {
+    const int keyed = c->send_rule == ORA_SEND_KEYED;
     uint32_t* o = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)G);
-    for (int32_t g = 0; g < G; ++g) o[g] = ora_exchange_offset(c, (uint32_t)g, k);
+    uint32_t* key = (uint32_t*)malloc(sizeof(uint32_t) * 4 * (size_t)G);
+    for (int32_t g = 0; g < G; ++g) {
+      o[g] = ora_exchange_offset(c, (uint32_t)g, k);
+      ora_send_keys(c, (uint32_t)g, k, key + 4 * g);
+    }
     for (int32_t p = 0; p < G; ++p) {
       int32_t g = sigma[p], r = sigma[(p + 1) % G];
       for (int32_t t = 0; t < n_ex; ++t) {
-        int64_t s_g = ((int64_t)t * Np + o[g]) / n_ex;
-        int64_t s_r = ((int64_t)t * Np + o[r]) / n_ex;
+        int64_t s_g = keyed ? (int64_t)ora_send_perm((uint32_t)t, (uint32_t)Np, key + 4 * g)
+                            : ((int64_t)t * Np + o[g]) / n_ex;
+        int64_t s_r = keyed ? (int64_t)ora_send_perm((uint32_t)t, (uint32_t)Np, key + 4 * r)
+                            : ((int64_t)t * Np + o[r]) / n_ex;
         src[(int64_t)r * Np + s_r] = (int32_t)((int64_t)g * Np + s_g);
         origin[(int64_t)r * Np + s_r] = g;
       }
     }
     free(o);
+    free(key);
   }
   for (int d = 0; d < 5; ++d)
     for (int64_t i = 0; i < N; ++i) pop_out[d * N + i] = pop_in[d * N + src[i]];

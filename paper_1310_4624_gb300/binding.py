@@ -15,6 +15,8 @@ PF_OK, PF_ERR_ARG, PF_ERR_STATE, PF_ERR_CUDA, PF_ERR_WORKSPACE, PF_ERR_DEGENERAT
     PF_ERR_DEVICE = range(8)
 PF_RNA, PF_ARNA = 0, 1
 PF_INIT_POINT, PF_INIT_UNIFORM, PF_INIT_SHARING, PF_INIT_USER = range(4)
+PF_RESAMPLE_ALWAYS, PF_RESAMPLE_ESS = 0, 1
+PF_SEND_SYSTEMATIC, PF_SEND_KEYED = 0, 1
 
 STATUS_NAMES = {0: "PF_OK", 1: "PF_ERR_ARG", 2: "PF_ERR_STATE", 3: "PF_ERR_CUDA", 4: "PF_ERR_WORKSPACE",
                 5: "PF_ERR_DEGENERATE", 6: "PF_ERR_TIMEOUT", 7: "PF_ERR_DEVICE"}
@@ -40,6 +42,7 @@ class pf_track_config(C.Structure):
         ("init_state", C.c_float * 5), ("init_lo", C.c_float * 5), ("init_hi", C.c_float * 5),
         ("init_radius", C.c_float), ("obs_model", C.c_int32),
         ("seed", C.c_uint64), ("track_id", C.c_uint32), ("record_ancestors", C.c_int32),
+        ("resample_rule", C.c_int32), ("ess_fraction", C.c_float), ("send_rule", C.c_int32),
     ]
 
 
@@ -47,7 +50,7 @@ class pf_step_stats(C.Structure):
     _fields_ = [
         ("step", C.c_int32), ("n_ex", C.c_int32),
         ("pe_eff", C.c_double), ("log_c", C.c_double), ("log_Z", C.c_double),
-        ("xhat", C.c_float * 5), ("degenerate_groups", C.c_int32),
+        ("xhat", C.c_float * 5), ("degenerate_groups", C.c_int32), ("resampled_groups", C.c_int32),
     ]
 
 

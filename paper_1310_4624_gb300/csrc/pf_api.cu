@@ -42,7 +42,7 @@ struct pf_handle {
   float4* pv[2] = {nullptr, nullptr};
   float* In[2] = {nullptr, nullptr};
   uint32_t* anc = nullptr;
-  float* lw = nullptr;
+  float* lw = nullptr;   // two buffers lw_stride(N_total) apart; with carry_any step k writes buffer k & 1, else buffer 0
   float* tile_part = nullptr;
   float* ypad = nullptr;
   HistRec* hist = nullptr;
@@ -50,6 +50,7 @@ struct pf_handle {
   int* ring = nullptr;
   int* ring_next = nullptr;
   uint32_t* exo_next = nullptr;
+  uint4* keys_next = nullptr;  // two buffers (by step parity) of G_total: send-permutation keys of step k+1
   int* tile_ctr = nullptr;
   int n_ring_blocks = 0;  // leading blocks of the propagate kernel
   bool finish_pending = false;  // the last step's estimate / history not yet written (k_finish)
@@ -80,6 +81,8 @@ struct pf_handle {
   int k1_occ = 1, sms = 1;
   bool pdl = true;  // programmatic dependent launch between the step kernels
   bool test_withhold_copy = false;  // PFARNA_TEST_WITHHOLD_COPY=1 at pf_init (failure-detection tests)
+  bool carry_any = false;           // some track resamples by Alg. 1's test (PF_RESAMPLE_ESS)
+  bool variants = false;            // carry_any, or some track uses PF_SEND_KEYED
   char* ws = nullptr;        // the workspace, its size, and the byte range of the TMA
   size_t ws_total = 0;       // descriptors in it (they hold this workspace's addresses)
   size_t tmap_off = 0, tmap_bytes = 0;
@@ -137,7 +140,8 @@ QuantCoeffs make_qc() {
 }
 
 struct Layout {
-  size_t trk, ts, gs, gd, tiles, pv0, pv1, I0, I1, anc, lw, tp, ypad, hist, ghist, ring, ring_next, exo_next, tile_ctr, parent, ds,
+  size_t trk, ts, gs, gd, tiles, pv0, pv1, I0, I1, anc, lw, tp, ypad, hist, ghist, ring, ring_next, exo_next, keys_next,
+      tile_ctr, parent, ds,
       tmap, total;
   size_t rp_pv, rp_I, ck_pv, ck_I, ca_pv0, ca_pv1, ca_I0, ca_I1, lam_hist, lbar_hist, dlam, Dacc, grad, logz, seed;
   bool adjoint = false;
@@ -146,6 +150,11 @@ struct Layout {
   int G_total = 0, n_tiles = 0, hist_total = 0;
   int R = 5;
 };
+
+// Distance of the second log-weight buffer from the first: a multiple of
+// 64 floats, so that both keep the 16-byte alignment the resampler's
+// vector loads rely on.
+long long lw_stride(long long N_total) { return (N_total + 63) / 64 * 64; }
 
 // Padded frame geometry: a border of 2R+1 zero pixels, rows 16-byte
 // aligned, and at least one TMA box in each dimension.
@@ -188,6 +197,11 @@ std::string validate(const pf_track_config* c, int n, int history) {
     if (!std::isfinite(x.pe_eff_cutoff)) return bad("pe_eff_cutoff must be finite");
     if (x.track_id >= (1u << 24)) return bad("track_id must be < 2^24");
     if (x.obs_model != PF_OBS_PATCH && x.obs_model != PF_OBS_FRAME) return bad("obs_model must be PF_OBS_PATCH or PF_OBS_FRAME");
+    if (x.resample_rule != PF_RESAMPLE_ALWAYS && x.resample_rule != PF_RESAMPLE_ESS)
+      return bad("resample_rule must be PF_RESAMPLE_ALWAYS or PF_RESAMPLE_ESS");
+    if (!(x.ess_fraction >= 0.0f && x.ess_fraction <= 1.0f)) return bad("ess_fraction must be in [0, 1]");
+    if (x.send_rule != PF_SEND_SYSTEMATIC && x.send_rule != PF_SEND_KEYED)
+      return bad("send_rule must be PF_SEND_SYSTEMATIC or PF_SEND_KEYED");
     for (int d = 0; d < 5; ++d)
       if (!std::isfinite(x.init_state[d]) || !std::isfinite(x.init_lo[d]) || !std::isfinite(x.init_hi[d]))
         return bad("init_state / init_lo / init_hi must be finite");
@@ -233,6 +247,7 @@ Layout plan(const pf_track_config* c, int n, int history) {
   L.ring = take(sizeof(int) * L.G_total);
   L.ring_next = take(sizeof(int) * 2 * (size_t)L.G_total);
   L.exo_next = take(sizeof(uint32_t) * 2 * (size_t)L.G_total);
+  L.keys_next = take(sizeof(uint4) * 2 * (size_t)L.G_total);
   L.tile_ctr = take(sizeof(int));
   L.tiles = take(sizeof(int4) * L.n_tiles);
   L.pv0 = take(sizeof(float4) * L.N_total);
@@ -240,7 +255,7 @@ Layout plan(const pf_track_config* c, int n, int history) {
   L.I0 = take(sizeof(float) * L.N_total);
   L.I1 = take(sizeof(float) * L.N_total);
   L.anc = take(sizeof(uint32_t) * L.N_total);
-  L.lw = take(sizeof(float) * L.N_total);
+  L.lw = take(sizeof(float) * (size_t)lw_stride(L.N_total) * 2);
   L.tp = take(sizeof(float) * 8 * (size_t)L.n_tiles);
   L.ypad = take(sizeof(float) * (size_t)L.ypad_total);
   L.hist = take(sizeof(HistRec) * (size_t)L.hist_total);
@@ -348,9 +363,9 @@ pf_status sync(pf_handle* h) {
 
 K1Args k1_args(const pf_handle* h) {
   K1Args a{h->trk, h->tiles, h->n_tiles, h->gs, h->ts, h->ds, h->pv[0], h->pv[1], h->In[0], h->In[1],
-           h->anc, h->parent, h->history, h->lw, h->tile_part, h->ypad, h->tmaps, h->ring_next,
+           h->anc, h->parent, h->history, h->lw, h->lw + lw_stride(h->N_total), h->tile_part, h->ypad, h->tmaps, h->ring_next,
            h->G_total, h->exo_next, h->hist, h->ghist, h->tile_ctr, h->n_ring_blocks, h->n_tracks, TrackParams{}, 0,
-           nullptr, h->test_withhold_copy ? 1 : 0, CUtensorMap{}};
+           nullptr, h->test_withhold_copy ? 1 : 0, h->variants ? 1 : 0, h->keys_next, CUtensorMap{}};
   a.p0 = h->tp[0];
   return a;
 }
@@ -387,7 +402,8 @@ GlobalArgs global_args(const pf_handle* h, int finalize) {
 // fuse = 1: the resampler also runs each track's global step (the last
 // group of the track to finish); 0: resampling only (autotuner candidates).
 ResampleArgs resample_args(const pf_handle* h, int fuse) {
-  ResampleArgs ra{h->gd, h->gs, h->tile_part, h->lw, h->anc, nullptr, nullptr, 0, h->qc, h->ds};
+  ResampleArgs ra{h->gd,  h->gs,  h->tile_part, h->lw, h->carry_any ? h->lw + lw_stride(h->N_total) : nullptr,
+                  h->anc, nullptr, nullptr,      0,     h->qc, h->ds};
   ra.fuse_global = fuse;
   ra.tile_ctr = h->tile_ctr;
   ra.glob = global_args(h, 1);
@@ -454,6 +470,7 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
   h->ring = (int*)(w + L.ring);
   h->ring_next = (int*)(w + L.ring_next);
   h->exo_next = (uint32_t*)(w + L.exo_next);
+  h->keys_next = (uint4*)(w + L.keys_next);
   h->tile_ctr = (int*)(w + L.tile_ctr);
   h->tiles = (int4*)(w + L.tiles);
   h->pv[0] = (float4*)(w + L.pv0);
@@ -514,6 +531,11 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
     P.tag = c.track_id << 8;
     P.record = c.record_ancestors ? 1 : 0;
     P.obs_model = c.obs_model;
+    P.resample_rule = c.resample_rule;
+    P.ess_t = (uint32_t)std::floor((double)c.ess_fraction * 65536.0 + 0.5);
+    P.send_rule = c.send_rule;
+    P.perm_bits = 0;
+    while ((1 << P.perm_bits) < c.Np) ++P.perm_bits;
     P.part_off = part;
     P.group_off = gro;
     P.tile_off = tio;
@@ -617,7 +639,11 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
   for (int t = 0; t < n_tracks; ++t) n_arna += (cfg[t].mode == PF_ARNA && cfg[t].G > 1 && cfg[t].G <= RING_SMEM_G);
   (void)n_arna;
   h->n_ring_blocks = n_tracks < 16 ? n_tracks : 16;
-  for (int t = 0; t < n_tracks; ++t) h->max_G = cfg[t].G > h->max_G ? cfg[t].G : h->max_G;
+  for (int t = 0; t < n_tracks; ++t) {
+    h->max_G = cfg[t].G > h->max_G ? cfg[t].G : h->max_G;
+    if (cfg[t].resample_rule == PF_RESAMPLE_ESS) h->carry_any = true;
+    if (cfg[t].resample_rule == PF_RESAMPLE_ESS || cfg[t].send_rule == PF_SEND_KEYED) h->variants = true;
+  }
   h->rs_cluster = resample_cluster(cfg[0].Np, n_tracks == 1);
 
   InitArgs ia{h->trk, h->tiles, h->n_tiles, h->N_total, user_state, h->pv[1], h->In[1]};
@@ -648,7 +674,7 @@ pf_status pf_step(pf_handle* h, const float* const* frames, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
   K1Args k1 = k1_args(h);
-  if (!raw_frame_map(h, frames[0], &k1)) {
+  if (h->variants || !raw_frame_map(h, frames[0], &k1)) {
     if ((e = mark(h, PF_KERNEL_FRAME_PREP, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
     if ((e = prep_frames(h, frames, s)) != cudaSuccess) return cuda_fail(h, e, "k_frame_prep");
     if ((e = mark(h, PF_KERNEL_FRAME_PREP, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
@@ -762,8 +788,10 @@ pf_status pf_autotune(pf_handle* h, const float* const* frames, int32_t* k1_grid
     }
   }
   if (!cached) {
-    // The propagate and resample kernels of a step are idempotent until the
-    // global step advances it, so candidates are timed on live data.
+    // Within a step the propagate kernel is idempotent until a resampler
+    // replaces the ancestors it reads, and the resampler is idempotent until
+    // the global step advances the step: the propagate candidates are timed
+    // first, then the resampler's, on live data.
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -819,8 +847,14 @@ pf_status pf_autotune(pf_handle* h, const float* const* frames, int32_t* k1_grid
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     g_tune_cache[key] = {best_grid, best_c};
   }
-  // complete the step with the chosen shapes
-  if ((e = launch_step_kernels(h, s)) != cudaSuccess) return cuda_fail(h, e, "step kernels");
+  // Complete the step with the chosen shapes.  When candidates were timed,
+  // the propagate candidates (which run first) have left this step's states
+  // and weights, and the resampler candidates have replaced the ancestors
+  // the propagate kernel reads, so only the resampler runs again, now with
+  // the global step.
+  e = cached ? launch_step_kernels(h, s)
+             : launch_resample(resample_args(h, 1), h->G_total, h->rs_cluster, false, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "step kernels");
   h->steps_run += 1;
   h->finish_pending = true;
   h->last_stream = s;
@@ -880,6 +914,7 @@ pf_status pf_exchange_stats(pf_handle* h, int32_t track, int32_t step, pf_step_s
     out->log_Z = r.log_Z;
     for (int d = 0; d < 5; ++d) out->xhat[d] = r.xhat[d];
     out->degenerate_groups = r.degenerate;
+    out->resampled_groups = r.resampled;
   }
   if (ring_host || logW_host || xhat_host || ess_host) {
     std::vector<GroupHist> gh(P.G);
@@ -922,7 +957,8 @@ pf_status pf_particles(pf_handle* h, int32_t track, float* states, uint32_t* anc
     return cuda_fail(h, e, "export states");
   if (anc && (e = cudaMemcpyAsync(anc, h->anc + P.part_off, sizeof(uint32_t) * Nt, cudaMemcpyDeviceToDevice, s)))
     return cuda_fail(h, e, "copy ancestors");
-  if (logw && (e = cudaMemcpyAsync(logw, h->lw + P.part_off, sizeof(float) * Nt, cudaMemcpyDeviceToDevice, s)))
+  if (logw && (e = cudaMemcpyAsync(logw, h->lw + (h->carry_any ? (k & 1) * lw_stride(h->N_total) : 0) + P.part_off, sizeof(float) * Nt,
+                                   cudaMemcpyDeviceToDevice, s)))
     return cuda_fail(h, e, "copy log-weights");
   if (parent &&
       (e = cudaMemcpyAsync(parent, h->parent + P.parent_off + (long long)(k % h->history) * Nt, sizeof(uint32_t) * Nt,
@@ -967,7 +1003,7 @@ pf_status pf_resample(const float* logw, const uint32_t* u, int32_t G, int32_t N
   if ((e = cudaMemsetAsync(ds, 0, sizeof(DevState), s)) ||
       (e = cudaMemcpyAsync(gd, h.data(), sizeof(GroupDesc) * G, cudaMemcpyHostToDevice, s)))
     return cuda_fail(nullptr, e, "pf_resample setup");
-  ResampleArgs ra{gd, gs, nullptr, logw, anc, (unsigned long long*)q, u, 1, make_qc(), ds};
+  ResampleArgs ra{gd, gs, nullptr, logw, nullptr, anc, (unsigned long long*)q, u, 1, make_qc(), ds};
   if ((e = launch_resample(ra, G, resample_cluster(Np, true), false, s)) != cudaSuccess)
     return cuda_fail(nullptr, e, "k_resample");
   return PF_OK;
@@ -1027,6 +1063,9 @@ pf_status pf_backward(pf_handle* h, const float* const* frames_host, int32_t T, 
   NvtxRange nvtx_range("pf_backward");
   if (!h) return fail(nullptr, PF_ERR_ARG, "handle is NULL");
   if (!h->adjoint) return fail(h, PF_ERR_STATE, "pf_backward needs record_ancestors on every track");
+  for (int t = 0; t < h->n_tracks; ++t)
+    if (h->tp[t].resample_rule != PF_RESAMPLE_ALWAYS)
+      return fail(h, PF_ERR_ARG, "pf_backward needs resample_rule PF_RESAMPLE_ALWAYS on every track");
   if (!frames_host || !dlogZ_host || !grad_dev) return fail(h, PF_ERR_ARG, "NULL argument");
   if (T < 1 || T != h->steps_run) return fail(h, PF_ERR_STATE, "T must equal the number of steps run");
   if (T > h->history) return fail(h, PF_ERR_STATE, "T exceeds the kept history");

@@ -61,6 +61,10 @@ struct TrackParams {
   uint32_t key0, key1, tag;   // Philox key; tag = track_id << 8
   int record;
   int obs_model;              // 0: patch residual, 1: frame likelihood ratio
+  int resample_rule;          // 0: every step, 1: Alg. 1's N_eff test per group
+  uint32_t ess_t;             // N_thresh = ess_t Np / 2^16
+  int send_rule;              // 0: systematic send slots, 1: keyed permutation (Sec. III-C)
+  int perm_bits;              // ceil(log2 Np): the keyed permutation's domain bits
   long long part_off;         // first particle of the track (global slot)
   int group_off;              // first group of the track (global group)
   int tile_off;               // first propagate tile of the track
@@ -88,6 +92,7 @@ struct TrackState {
   int fin_k;                 // last step whose estimate / log Z / history are complete
   int deg_k;                 // degenerate groups of step k - 1
   float lse_k;               // log c of step k - 1 (FP32)
+  int res_k;                 // groups that resampled at step k - 1
 };
 
 // Per-group state (global group index).
@@ -98,7 +103,8 @@ struct GroupState {
   uint32_t exo;         // exchange offset o_g of step k
   uint32_t u;           // resampling uniform word of step k
   float M;              // group max log-weight (step k)
-  int pad0;
+  int carry;            // 1: the group skipped resampling at step k - 1, its
+                        // particles carry their own log-weights into step k
   unsigned long long Q; // group total weight code (step k)
   float xs[5];          // group estimate x^^m (step k)
   float ess;            // group ESS (step k)
@@ -121,6 +127,7 @@ struct HistRec {
   double pe_eff, log_c, log_Z;
   float xhat[5];
   int degenerate;
+  int resampled;
 };
 
 // Per-group history entry.
@@ -130,6 +137,18 @@ struct GroupHist {
   float xs[5];
   float ess;
 };
+
+// Alg. 1's resampling test N_eff < N_thresh on a group's weight codes: with
+// c_i = q_i >> 20, s1 = sum c and s2 = sum c^2, N_eff = s1^2 / s2 and
+// N_thresh = t Np / 2^16, so the test is 2^16 s1^2 < t Np s2, compared in
+// exact 128-bit integers (s1 <= 2^40, s2 <= 2^60, t <= 2^16, Np <= 2^20).
+__device__ __forceinline__ bool ess_below(unsigned long long s1, unsigned long long s2, uint32_t Np, uint32_t t) {
+  const unsigned long long alo = s1 * s1, ahi = __umul64hi(s1, s1);
+  const unsigned long long a_hi = (ahi << 16) | (alo >> 48), a_lo = alo << 16;
+  const unsigned long long m = (unsigned long long)t * Np;
+  const unsigned long long b_lo = m * s2, b_hi = __umul64hi(m, s2);
+  return a_hi < b_hi || (a_hi == b_hi && a_lo < b_lo);
+}
 
 struct DevState {
   unsigned int err;

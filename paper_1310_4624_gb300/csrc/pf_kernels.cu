@@ -179,7 +179,7 @@ __device__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
 
   unsigned long long Q[GPT];
   float Mg[GPT], lam[GPT];
-  int ring_m[GPT], rnext[GPT];
+  int ring_m[GPT], rnext[GPT], cy[GPT];
   uint32_t exo[GPT];
 #pragma unroll
   for (int i = 0; i < GPT; ++i) {
@@ -189,9 +189,11 @@ __device__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
     ring_m[i] = m;
     rnext[i] = m;
     exo[i] = 0;
+    cy[i] = 0;
     if (m < G) {
       Q[i] = __ldcg(&gs[m].Q);
       Mg[i] = __ldcg(&gs[m].M);
+      if (a.finalize) cy[i] = __ldcg(&gs[m].carry);
       ring_m[i] = __ldcg(&ring[m]);
       rnext[i] = __ldcg(&rnext_buf[m]);
       exo[i] = __ldcg(&exo_buf[m]);
@@ -208,7 +210,7 @@ __device__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
     if (m < G) {
       if (a.finalize) {
         lam[i] = Q[i] != 0 ? group_log_weight(Mg[i], Q[i]) : -INFINITY;
-        deg += (Q[i] == 0);
+        deg += (Q[i] == 0) + (cy[i] ? 0 : 65536);  // degenerate and resampled groups (G < 2^15)
       } else {
         lam[i] = 0.0f;
       }
@@ -228,6 +230,8 @@ __device__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
     mx = fmaxf(mx, sc.f[w]);
     deg += sc.i[w];
   }
+  const int res = deg >> 16;
+  deg &= 0xffff;
   const bool all_degenerate = a.finalize && deg == G;
   if (all_degenerate) {  // every group lost its weight: restart from equal weights
 #pragma unroll
@@ -326,13 +330,17 @@ __device__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
       gs[rm].pred = sc.ring[m == 0 ? G - 1 : m - 1];
       gs[m].exo = nex > 0 ? exo[i] : 0u;
       gs[m].lambda = lam[i];
-      gs[m].off = lam[i] - log_np - lse;
+      // S4: a resampled group's particles weigh W_m / Np, a group that kept
+      // its particles passes their own log-weights on (log w~ - LSE)
+      gs[m].off = cy[i] ? -lse : lam[i] - log_np - lse;
+      if (!a.finalize) gs[m].carry = 0;
     }
   }
   if (threadIdx.x == 0) {
     T->n_ex = nex;
     T->pe_eff = pe;
     T->deg_k = a.finalize ? deg : 0;
+    T->res_k = a.finalize ? res : 0;
     T->lse_k = lse;
     if (!a.finalize) T->fin_k = -1;
     T->k = k1;
@@ -430,6 +438,7 @@ __device__ void finish_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
     h.log_c = logc;
     h.log_Z = logZ;
     h.degenerate = deg;
+    h.resampled = __ldcg(&T->res_k);
     T->log_c = logc;
     T->log_Z = logZ;
     for (int q = 0; q < 5; ++q) T->xhat[q] = xq[q];
@@ -550,6 +559,74 @@ __device__ __forceinline__ bool exchange_from_pred(int j, int Np, int nex, uint3
   return false;
 }
 
+// Keyed send sets (Sec. III-C, "randomly selects"): group g sends slots
+// pi_g(t), t < N_ex, of a keyed permutation of [0, Np): a four-round Feistel
+// network (Luby-Rackoff) on b = ceil(log2 Np) bits, the high half L of
+// floor(b/2) bits and the low half R of the rest; a round maps (L, R) to
+// (R, L xor (F(R xor key_i) mod 2^|L|)), so the halves trade places and
+// sizes; values >= Np walk on through the network until they land in
+// [0, Np) (cycle walking, Black-Rogaway), which ends within 2^b rounds of
+// the walk since the network permutes [0, 2^b).  F: h = x * 0x9E3779B1,
+// h ^= h >> 16, h *= 0x7FEB352D, h ^= h >> 15.
+__device__ __forceinline__ uint32_t feistel_f(uint32_t x) {
+  uint32_t h = x * 0x9E3779B1u;
+  h ^= h >> 16;
+  h *= 0x7FEB352Du;
+  return h ^ (h >> 15);
+}
+
+__device__ __forceinline__ uint32_t send_perm(uint32_t t, uint32_t n, int b, uint4 key) {
+  const uint32_t kk[4] = {key.x, key.y, key.z, key.w};
+  uint32_t x = t;
+  do {
+    int sl = b >> 1, sr = b - sl;
+    uint32_t L = x >> sr, R = x & ((1u << sr) - 1u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t nr = L ^ (feistel_f(R ^ kk[i]) & ((1u << sl) - 1u));
+      L = R;
+      R = nr;
+      const int s = sl;
+      sl = sr;
+      sr = s;
+    }
+    x = (L << sr) | R;
+  } while (x >= n);
+  return x;
+}
+
+__device__ __forceinline__ uint32_t send_perm_inv(uint32_t j, uint32_t n, int b, uint4 key) {
+  const uint32_t kk[4] = {key.x, key.y, key.z, key.w};
+  uint32_t x = j;
+  do {
+    int sl = b >> 1, sr = b - sl;
+    uint32_t L = x >> sr, R = x & ((1u << sr) - 1u);
+#pragma unroll
+    for (int i = 3; i >= 0; --i) {
+      const uint32_t nl = R ^ (feistel_f(L ^ kk[i]) & ((1u << sr) - 1u));
+      R = L;
+      L = nl;
+      const int s = sl;
+      sl = sr;
+      sr = s;
+    }
+    x = (L << sr) | R;
+  } while (x >= n);
+  return x;
+}
+
+// Slot j of the receiver takes the predecessor's slot pi_s(t) when
+// t = pi_r^-1(j) < N_ex (keys k_r of the receiver, k_s of the sender).
+__device__ __forceinline__ bool exchange_keyed(int j, int Np, int nex, int b, uint4 k_r, uint4 k_s, int& src_j) {
+  const uint32_t t = send_perm_inv((uint32_t)j, (uint32_t)Np, b, k_r);
+  if (t < (uint32_t)nex) {
+    src_j = (int)send_perm(t, (uint32_t)Np, b, k_s);
+    return true;
+  }
+  src_j = j;
+  return false;
+}
+
 // Hint: bring [p, p + bytes) into L2 (one bulk prefetch; the range is
 // widened to 16-byte boundaries, which stay inside the workspace).
 __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
@@ -590,7 +667,7 @@ __device__ __forceinline__ void prop_noise(uint32_t key0, uint32_t key1, uint32_
 // the previous step.
 // SINGLE: one track, whose parameters come from the kernel's constant
 // parameter block (a.p0) instead of global memory.
-template <int R, bool SINGLE>
+template <int R, bool SINGLE, bool VARIANTS>
 __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(const __grid_constant__ K1Args a) {
   constexpr int D = 2 * R + 1;
   constexpr int PAD = 2 * R + 1;
@@ -627,11 +704,15 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
     for (int t = blockIdx.x; t < a.n_tracks; t += a.n_ring_blocks) {
       const TrackParams& P = a.trk[t];
       uint32_t* exo_out = a.exo_next + (size_t)((k + 1) & 1) * a.ring_stride + P.group_off;
+      uint4* keys_out = a.keys_next + (size_t)((k + 1) & 1) * a.ring_stride + P.group_off;
       for (int m = threadIdx.x; m < P.G; m += K1_THREADS) {
         uint32_t o = 0;
         if (P.G > 1 && !draw_bounded(P.key0, P.key1, P.tag, ST_EXCH, (uint32_t)m, (uint32_t)(k + 1), (uint32_t)P.Np, o))
           set_error(a.ds, ERR_DRAW, 2u, (uint32_t)t, (uint32_t)m);
         exo_out[m] = o;
+        // keyed send sets: the permutation's round keys (EXCH stream, call 1)
+        if (P.send_rule == 1 && P.G > 1)
+          keys_out[m] = philox(P.key0, P.key1, make_uint4((uint32_t)m, 0u, (uint32_t)(k + 1), P.tag | (ST_EXCH << 4) | 1u));
       }
       if (warp == 0 && P.mode == MODE_ARNA && P.G > 1 && P.G <= RING_SMEM_G) {
         ring_for_step(P, t, (uint32_t)(k + 1), perm, rr, a.ds);
@@ -669,13 +750,24 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
       o_s = gs[sg].exo;
       off_s = gs[sg].off;
     }
+    // keyed send sets: the receiver's and the sender's permutation keys
+    const bool keyed = VARIANTS && P.send_rule == 1 && nex > 0;
+    uint4 key_r = make_uint4(0u, 0u, 0u, 0u), key_s = key_r;
+    if (keyed) {
+      const uint4* kb = a.keys_next + (size_t)(k & 1) * a.ring_stride + P.group_off;
+      key_r = kb[g];
+      key_s = kb[sg];
+    }
+    // bit 0: this group kept its particles at the last step, bit 1: the
+    // sending group did; their particles pass their own log-weights on
+    const int cmask = (VARIANTS && k > 0) ? (gs[g].carry | (gs[sg].carry << 1)) : 0;
     const uint32_t n_track = (uint32_t)(P.G * Np);
     const uint32_t* __restrict__ anc_t = a.anc + P.part_off;
     const float4* __restrict__ pvp_t = pv_prev + P.part_off;
     const float* __restrict__ Ip_t = I_prev + P.part_off;
     float4* __restrict__ pvc_t = pv_cur + P.part_off;
     float* __restrict__ Ic_t = I_cur + P.part_off;
-    float* __restrict__ lw_t = a.lw + P.part_off;
+    float* __restrict__ lw_t = ((VARIANTS && (k & 1)) ? a.lw1 : a.lw) + P.part_off;
     uint32_t* __restrict__ par_t =
         P.record ? a.parent + P.parent_off + (long long)(k % a.history) * (long long)n_track : nullptr;
     float4 s[K1_PPT];
@@ -694,7 +786,8 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
       from_pred[q] = false;
       if (active) {
         int sj;
-        from_pred[q] = exchange_from_pred(j, Np, nex, o_r, o_s, P.m_Np, sj);
+        from_pred[q] = keyed ? exchange_keyed(j, Np, nex, P.perm_bits, key_r, key_s, sj)
+                             : exchange_from_pred(j, Np, nex, o_r, o_s, P.m_Np, sj);
         const uint32_t src = (uint32_t)((from_pred[q] ? sg : g) * Np + sj);
         const uint32_t par = (k == 0) ? src : anc_t[src];
         if (par >= n_track) {
@@ -702,6 +795,11 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
         } else {
           s[q] = pvp_t[par];
           I[q] = Ip_t[par];
+          // A group that kept its particles passes their own log-weights on:
+          // the particle's weight offset is parked in its output slot until
+          // the likelihood is added (no register held across the patch sum).
+          if (VARIANTS && ((cmask >> (from_pred[q] ? 1 : 0)) & 1))
+            lw_t[il] = (from_pred[q] ? off_s : off_g) + ((k & 1) ? a.lw : a.lw1)[P.part_off + par];
         }
         if (k > 0) {
           // Alg. 1 step P: nearly constant velocity, unit frame interval
@@ -834,7 +932,8 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
           ss = frame_model ? patch_ss<R, true, false>(base, P.pitch, gxI, dy, P.c_psf, P.kappa)
                            : patch_ss<R, false, false>(base, P.pitch, gxI, dy, P.c_psf, P.kappa);
         }
-        lw[q] = fmaf(-ss, P.inv2so2, from_pred[q] ? off_s : off_g);
+        const bool carried = VARIANTS && ((cmask >> (from_pred[q] ? 1 : 0)) & 1);
+        lw[q] = fmaf(-ss, P.inv2so2, carried ? lw_t[g * Np + td.z + jj] : (from_pred[q] ? off_s : off_g));
         lw_t[g * Np + td.z + jj] = lw[q];
       }
     }
@@ -944,12 +1043,20 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
   const int chunk = ((Np + C - 1) / C + 7) & ~7;
   const int lo = min(rank * chunk, Np), hi = min(lo + chunk, Np);
   const bool single = (hi - lo) <= RS_SUB;  // the whole chunk stays in registers
-  const float* __restrict__ lw = a.lw + d.base;
+  // In a filter step: the track's step index (read before the cluster
+  // barrier that precedes every ticket below, since the track's global step,
+  // run by the last ticket holder, advances it), which picks the log-weight
+  // buffer and the resampling uniform.
+  const TrackParams* __restrict__ Pt = a.glob.trk ? a.glob.trk + d.track : nullptr;
+  const int kk = a.u_arr ? 0 : a.glob.ts[d.track].k;
+  const float* __restrict__ lw = ((a.lw1 && (kk & 1)) ? a.lw1 : a.lw) + d.base;
+  const bool ess_rule = Pt && Pt->resample_rule == 1;
   const bool vec = ((d.base & 3) == 0);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
   __shared__ float s_pub_max;
   __shared__ unsigned long long s_pub_q;
+  __shared__ unsigned long long s_pub_e[2];
   __shared__ float s_f[RS_THREADS / 32];
   __shared__ unsigned long long s_w[RS_THREADS / 32];
   __shared__ float s_stat[RS_THREADS / 32][8];
@@ -977,18 +1084,12 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
     }
   };
 
-  // the group's resampling uniform word (Philox stream RESAMPLE, group,
-  // step).  The step index is read here, before the cluster barrier that
-  // precedes every ticket below: the track's global step (run by the last
-  // ticket holder) advances it.
+  // the group's resampling uniform word (Philox stream RESAMPLE, group, step)
   uint32_t u;
-  if (a.u_arr) {
+  if (a.u_arr)
     u = a.u_arr[grp];
-  } else {
-    const TrackParams* P = a.glob.trk + d.track;
-    const int kk = a.glob.ts[d.track].k;
-    u = philox(P->key0, P->key1, make_uint4((uint32_t)d.g, 0u, (uint32_t)kk, P->tag | (ST_RESAMPLE << 4))).x;
-  }
+  else
+    u = philox(Pt->key0, Pt->key1, make_uint4((uint32_t)d.g, 0u, (uint32_t)kk, Pt->tag | (ST_RESAMPLE << 4))).x;
 
   // group maximum: from the propagate tiles' maxima in a filter step, else
   // over the cluster (the same set of log-weights either way, NaN ignored)
@@ -1012,8 +1113,9 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
     for (int r = 0; r < C; ++r) M = fmaxf(M, *cl.map_shared_rank(&s_pub_max, r));
   }
 
-  // this CTA's total weight code, then the cluster prefix and group total
-  unsigned long long qs = 0;
+  // this CTA's total weight code, then the cluster prefix and group total;
+  // under Alg. 1's test also the sums of c = q >> 20 and c^2
+  unsigned long long qs = 0, e1 = 0, e2 = 0;
   unsigned long long qv[RS_ITEMS];
   for (int sub = lo; sub < hi; sub += RS_SUB) {
     if (!single) load_sub(sub);
@@ -1021,17 +1123,37 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
     for (int r = 0; r < RS_ITEMS; ++r) {
       qv[r] = quantize(v[r], M, a.qc);
       qs += qv[r];
+      if (ess_rule) {
+        const unsigned long long c = qv[r] >> 20;
+        e1 += c;
+        e2 += c * c;
+      }
     }
   }
   qs = block_sum_u64<RS_THREADS>(qs, s_w);
-  if (threadIdx.x == 0) s_pub_q = qs;
+  if (ess_rule) {
+    e1 = block_sum_u64<RS_THREADS>(e1, s_w);
+    e2 = block_sum_u64<RS_THREADS>(e2, s_w);
+  }
+  if (threadIdx.x == 0) {
+    s_pub_q = qs;
+    s_pub_e[0] = e1;
+    s_pub_e[1] = e2;
+  }
   cl.sync();
-  unsigned long long Sb = 0, Q = 0;
+  unsigned long long Sb = 0, Q = 0, E1 = 0, E2 = 0;
   for (int r = 0; r < C; ++r) {
     const unsigned long long x = *cl.map_shared_rank(&s_pub_q, r);
     if (r < rank) Sb += x;
     Q += x;
+    if (ess_rule) {
+      E1 += *cl.map_shared_rank(&s_pub_e[0], r);
+      E2 += *cl.map_shared_rank(&s_pub_e[1], r);
+    }
   }
+  // Alg. 1: resample only when N_eff < N_thresh (every CTA of the cluster
+  // decides alike from the same sums)
+  const bool resample = !ess_rule || Q == 0 || ess_below(E1, E2, (uint32_t)Np, Pt->ess_t);
   // no more reads of the other CTAs' shared memory: arrive now, wait (so
   // that this CTA's shared memory outlives their reads) only at the end
   auto cl_token = cl.barrier_arrive();
@@ -1071,6 +1193,7 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
     if (threadIdx.x == 0) {
       G.M = M;
       G.Q = Q;
+      G.carry = resample ? 0 : 1;
     }
   }
   // The last group of a track to report its statistics runs the track's
@@ -1098,8 +1221,8 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
 
   const unsigned long long obase = a.local_idx ? 0ull : (unsigned long long)(d.g) * (unsigned long long)Np;
   uint32_t* __restrict__ anc = a.anc + d.base;
-  if (Q == 0) {
-    // no finite weight: identity
+  if (Q == 0 || !resample) {
+    // no finite weight, or Alg. 1's test keeps the particles: identity
     for (int i = lo + threadIdx.x; i < hi; i += RS_THREADS) {
       anc[i] = (uint32_t)(obase + i);
       if (a.q_out) a.q_out[d.base + i] = 0ull;
@@ -1279,7 +1402,7 @@ cudaError_t launch_frame_prep(const FrameArgs& a, int nt, int blocks_x, bool pdl
 
 template <int R>
 static const void* k1_ptr() {
-  return (const void*)k_propagate_weight<R, false>;
+  return (const void*)k_propagate_weight<R, false, false>;
 }
 
 const void* propagate_kernel(int R) {
@@ -1295,15 +1418,19 @@ const void* propagate_kernel(int R) {
   }
 }
 
-template <int R, bool SINGLE>
+template <int R, bool SINGLE, bool VARIANTS>
 static cudaError_t launch_propagate_rs(const K1Args& a, dim3 g, bool pdl, cudaStream_t s) {
-  return launch_ex(k_propagate_weight<R, SINGLE>, g, dim3(K1_THREADS), 0, pdl, s, a);
+  return launch_ex(k_propagate_weight<R, SINGLE, VARIANTS>, g, dim3(K1_THREADS), 0, pdl, s, a);
 }
 
+// Instances: one track, several tracks, and tracks that use a method
+// variant (groups that carry their particles' own weights under Alg. 1's
+// resampling test, or keyed send sets; any track count, frames prepared).
 template <int R>
 static cudaError_t launch_propagate_r(const K1Args& a, dim3 g, bool pdl, cudaStream_t s) {
-  if (a.n_tracks == 1) return launch_propagate_rs<R, true>(a, g, pdl, s);
-  return launch_propagate_rs<R, false>(a, g, pdl, s);
+  if (a.variants) return launch_propagate_rs<R, false, true>(a, g, pdl, s);
+  if (a.n_tracks == 1) return launch_propagate_rs<R, true, false>(a, g, pdl, s);
+  return launch_propagate_rs<R, false, false>(a, g, pdl, s);
 }
 
 cudaError_t launch_propagate(const K1Args& a, int R, int grid, bool pdl, cudaStream_t s) {

@@ -51,7 +51,8 @@ struct K1Args {
   const uint32_t* anc;  // previous step's ancestors (track-local slots)
   uint32_t* parent;     // ancestry records or nullptr
   int history;
-  float* lw;
+  float* lw;            // log-weights; with carry, two buffers by step parity: step k
+  float* lw1;           // writes lw (k even) or lw1 (k odd) and reads the other one
   float* tile_part;     // 8 floats per tile
   const float* ypad;
   const CUtensorMap* tmaps;  // one per track over its padded frame, or nullptr
@@ -70,6 +71,9 @@ struct K1Args {
   int raw_frame;
   const float* zraw;
   int test_withhold_copy;    // failure-detection test: issue no staging copy, so the bounded wait runs out
+  int variants;              // 1: some track resamples by Alg. 1's test (groups may carry weights) or
+                             // uses keyed send sets: launches the variants instance (frames prepared)
+  uint4* keys_next;          // two buffers (by step parity) of G_total: keyed send-permutation keys of step k+1
   CUtensorMap zmap;
 };
 
@@ -93,6 +97,7 @@ struct ResampleArgs {
   GroupState* gs;
   const float* tile_part;      // nullptr: no group estimate
   const float* lw;
+  const float* lw1;            // filter step with carry: the weights are lw1 at odd steps (nullptr: always lw)
   uint32_t* anc;
   unsigned long long* q_out;   // nullptr: not stored
   const uint32_t* u_arr;       // nullptr: GroupState::u

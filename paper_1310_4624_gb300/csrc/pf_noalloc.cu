@@ -103,7 +103,7 @@ extern "C" pf_status pf_resample_noalloc(const float* logw, const uint32_t* u, i
   k_noalloc_groups<<<(G + 255) / 256, 256, 0, s>>>(gd, G, Np);
   if ((e = cudaGetLastError()) != cudaSuccess)
     return fail(PF_ERR_CUDA, std::string("k_noalloc_groups: ") + cudaGetErrorString(e));
-  ResampleArgs ra{gd, gs, nullptr, logw, anc, reinterpret_cast<unsigned long long*>(q), u, 1, resample_coeffs(), ds};
+  ResampleArgs ra{gd, gs, nullptr, logw, nullptr, anc, reinterpret_cast<unsigned long long*>(q), u, 1, resample_coeffs(), ds};
   if ((e = launch_resample(ra, G, resample_cluster_size(Np), false, s)) != cudaSuccess)
     return fail(PF_ERR_CUDA, std::string("k_resample: ") + cudaGetErrorString(e));
   return PF_OK;

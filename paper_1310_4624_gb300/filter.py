@@ -39,6 +39,9 @@ def config_from_workload(wl: Workload, truth0=None, track_id: int = 0, record_an
     c.seed = wl.seed
     c.track_id = track_id
     c.record_ancestors = 1 if record_ancestors else 0
+    c.resample_rule = getattr(wl, "resample_rule", 0)
+    c.ess_fraction = getattr(wl, "ess_fraction", 0.5)
+    c.send_rule = getattr(wl, "send_rule", 0)
     return c
 
 
@@ -138,13 +141,14 @@ class ParticleFilter:
                                 logW.ctypes.data_as(C.c_void_p), gx.ctypes.data_as(C.c_void_p),
                                 ess.ctypes.data_as(C.c_void_p))
         return dict(step=s.step, n_ex=s.n_ex, pe_eff=s.pe_eff, log_c=s.log_c, log_Z=s.log_Z,
-                    xhat=np.array(s.xhat[:]), degenerate=s.degenerate_groups, ring=ring, logW=logW,
-                    group_xhat=gx, group_ess=ess)
+                    xhat=np.array(s.xhat[:]), degenerate=s.degenerate_groups, resampled=s.resampled_groups,
+                    ring=ring, logW=logW, group_xhat=gx, group_ess=ess)
 
     def history_stats(self, first: int, count: int, track: int = 0) -> List[dict]:
         out = B.pf_history(self.handle, track, first, count)
         return [dict(step=s.step, n_ex=s.n_ex, pe_eff=s.pe_eff, log_c=s.log_c, log_Z=s.log_Z,
-                     xhat=np.array(s.xhat[:]), degenerate=s.degenerate_groups) for s in out]
+                     xhat=np.array(s.xhat[:]), degenerate=s.degenerate_groups, resampled=s.resampled_groups)
+                for s in out]
 
     def save(self) -> bytearray:
         """A checkpoint of the whole filter state (host memory)."""

@@ -64,6 +64,7 @@ class Workload:
     obs_model: int = 0            # 0: patch residual, 1: frame likelihood ratio
     resample_rule: int = 0        # 0: every step (Alg. 2/3), 1: when N_eff < ess_fraction Np (Alg. 1)
     ess_fraction: float = 0.5
+    send_rule: int = 0            # 0: systematic slot subsample, 1: keyed random permutation (Sec. III-C)
 
     @property
     def N(self) -> int:

@@ -2,8 +2,10 @@
 
 For every step k the oracle is given exactly what the GPU had: the
 resampled population of step k-1 (X_{k-1}[anc_{k-1}]), the carried group
-log-weights Lambda_{k-1}, the frame, and, for the resampler and the group
-reductions, the GPU's FP32 log-weights.  Integer results (ring order, N_ex,
+log-weights Lambda_{k-1}, the particles' carried within-group log-weights
+(under the N_eff-threshold rule; from the GPU's FP32 log-weights), the frame,
+and, for the resampler and the group reductions, the GPU's FP32
+log-weights.  Integer results (ring order, N_ex,
 ancestry, ancestors) must match bit for bit; real results within the
 tolerance below.
 """
@@ -42,6 +44,7 @@ def run_and_compare(pf, wl, frames, truth0, steps, frames_dev, track=0, stepper=
     kind, x0, lo, hi, rad = _init(wl, truth0)
     pop = ora.init_population(ocfg, kind, x0, lo, hi, rad)
     lam = None
+    om = None
     prev_anc = None
     report = []
     for k in range(steps):
@@ -55,7 +58,7 @@ def run_and_compare(pf, wl, frames, truth0, steps, frames_dev, track=0, stepper=
         lw = p["logw"].cpu().numpy()
         anc = p["anc"].cpu().numpy().astype(np.int64)
         par = p["parent"].cpu().numpy().astype(np.int64)
-        r = ora.step(ocfg, k, frames[k], pop, lam, lw_override=lw)
+        r = ora.step(ocfg, k, frames[k], pop, lam, lw_override=lw, omega_in=om)
         assert np.array_equal(r.sigma, st["ring"]), "step %d ring %s vs %s" % (k, r.sigma, st["ring"])
         assert r.n_ex == st["n_ex"], "step %d N_ex %d vs %d" % (k, r.n_ex, st["n_ex"])
         assert abs(r.pe_eff - st["pe_eff"]) <= 1e-9 * max(1.0, abs(r.pe_eff)), "step %d PE_eff" % k
@@ -72,14 +75,17 @@ def run_and_compare(pf, wl, frames, truth0, steps, frames_dev, track=0, stepper=
         want_anc = r.anc.astype(np.int64) + np.repeat(np.arange(G, dtype=np.int64) * Np, Np)
         assert np.array_equal(anc, want_anc), "step %d ancestors differ at %d slots" % (
             k, int((anc != want_anc).sum()))
+        assert st["resampled"] == int(r.resampled.sum()), "step %d resampled groups %d vs %d" % (
+            k, st["resampled"], int(r.resampled.sum()))
         assert close(st["logW"], r.Lambda), "step %d group log-weights: %s" % (k, worst(st["logW"], r.Lambda))
         assert close(st["group_xhat"], r.gxhat), "step %d group estimates" % k
         assert close(st["group_ess"], r.gess, rtol=1e-4, atol=1e-3), "step %d group ESS" % k
         assert close([st["log_c"]], [r.logc]), "step %d log c" % k
         assert close(st["xhat"], r.xhat), "step %d estimate" % k
-        report.append(dict(k=k, n_ex=r.n_ex, pe_eff=r.pe_eff, logc=r.logc))
+        report.append(dict(k=k, n_ex=r.n_ex, pe_eff=r.pe_eff, logc=r.logc, resampled=int(r.resampled.sum())))
         pop = X[:, anc]
         lam = st["logW"]
+        om = r.omega
         prev_anc = anc
     return report
 

@@ -36,7 +36,7 @@ def test_header_declares_what_the_binding_wraps():
 def test_library_exports_every_declared_symbol(lib):
     for name in declared_functions():
         assert hasattr(lib, name), name
-    assert lib.pf_abi_version() == 2
+    assert lib.pf_abi_version() == 3
 
 
 def test_struct_layout_matches_ctypes(tmp_path):
@@ -74,7 +74,8 @@ def test_query_workspace_scales_with_particles(lib):
     ("mode", 3, "mode"), ("init_kind", 7, "init_kind"), ("sigma_psf", 0.0, "sigma_psf"),
     ("sigma_obs", -1.0, "sigma_obs"), ("sigma_pos", float("nan"), "process noise"), ("ex_ratio", 1.5, "ex_ratio"),
     ("track_id", 1 << 24, "track_id"), ("obs_model", 2, "obs_model"), ("G", 1025, "G must be"),
-    ("Np", (1 << 20) + 1, "Np must be"),
+    ("Np", (1 << 20) + 1, "Np must be"), ("resample_rule", 2, "resample_rule"), ("ess_fraction", 1.5, "ess_fraction"),
+    ("ess_fraction", float("nan"), "ess_fraction"), ("send_rule", 2, "send_rule"),
 ])
 def test_invalid_configs_are_rejected_on_the_host(lib, field, value, msg):
     with pytest.raises(B.PFError) as e:

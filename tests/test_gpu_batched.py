@@ -48,9 +48,17 @@ def _equal(a, b):
             assert x == y
 
 
-def test_batch_equals_tracks_run_alone(dev):
+@pytest.mark.parametrize("mixed", [False, True])
+def test_batch_equals_tracks_run_alone(dev, mixed):
+    """mixed: two tracks resample by Alg. 1's N_eff test and one uses keyed
+    send sets, so the batch runs the variants instance of the propagate
+    kernel for every track."""
     from paper_1310_4624_gb300.filter import ParticleFilter
     wls = _tracks()
+    if mixed:
+        wls[1] = wls[1].replace(resample_rule=1, ess_fraction=0.5)
+        wls[4] = wls[4].replace(resample_rule=1, ess_fraction=0.8)
+        wls[2] = wls[2].replace(send_rule=1)
     seqs = [synth.make_sequence(wl) for wl in wls]
     frs = [torch.from_numpy(f).to(dev) for f, _ in seqs]
     cfgs = _configs(wls, seqs)
@@ -79,10 +87,14 @@ def test_every_batched_track_matches_oracle(dev):
         batch.close()
 
 
-@pytest.mark.parametrize("how", ["table", "graph", "autotune"])
+@pytest.mark.parametrize("how", ["table", "graph", "autotune", "autotune_k2"])
 def test_table_graph_and_autotuned_steps_equal_plain_steps(dev, how):
+    """autotune_k2 tunes a shape no other test uses (so the candidates are
+    timed) at step 2, where the propagate kernel reads the ancestors."""
     from paper_1310_4624_gb300.filter import ParticleFilter
     wls = _tracks()
+    if how == "autotune_k2":
+        wls = [wl.replace(resample_rule=1, ess_fraction=0.6) for wl in wls[:4]]
     seqs = [synth.make_sequence(wl) for wl in wls]
     frs = [torch.from_numpy(f).to(dev).contiguous() for f, _ in seqs]
     cfgs = _configs(wls, seqs, record=False)
@@ -91,9 +103,9 @@ def test_table_graph_and_autotuned_steps_equal_plain_steps(dev, how):
     table = alt.frame_table(frs)
     for k in range(wls[0].T):
         ref.step([fr[k] for fr in frs])
-        if how == "autotune" and k == 0:
+        if (how == "autotune" and k == 0) or (how == "autotune_k2" and k == 2):
             alt.autotune([fr[k] for fr in frs])
-        elif how == "autotune":
+        elif how.startswith("autotune"):
             alt.step([fr[k] for fr in frs])
         else:
             alt.step_table(table, graph=(how == "graph"))

@@ -48,3 +48,20 @@ def test_withheld_copy_times_out_and_context_survives(dev):
     x, lz, st = good.estimate()
     assert st == B.PF_OK and abs(x[0, 0] - truth[-1, 0]) < 3.0
     good.close()
+
+
+def test_backward_refuses_threshold_resampling(dev):
+    """pf_backward replays every-step resampling only: a track under Alg. 1's
+    N_eff test is refused with PF_ERR_ARG (no launch)."""
+    from paper_1310_4624_gb300 import binding as B
+    from paper_1310_4624_gb300.filter import ParticleFilter, config_from_workload
+    wl = synth.small_rna(G=2, Np=256, T=2, resample_rule=1)
+    frames, truth = synth.make_sequence(wl)
+    fr = torch.from_numpy(frames).to(dev)
+    pf = ParticleFilter([config_from_workload(wl, truth[0], record_ancestors=True)], history=4, device=dev)
+    for k in range(wl.T):
+        pf.step(fr[k])
+    with pytest.raises(B.PFError) as err:
+        pf.backward([fr[k] for k in range(wl.T)])
+    assert err.value.status == B.PF_ERR_ARG
+    pf.close()

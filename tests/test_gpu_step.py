@@ -43,6 +43,17 @@ SMALL = [
     ("patch_r3", synth.small_rna(G=2, Np=128, patch_radius=3)),
     ("frame_model", synth.small_rna(G=4, Np=512, mode=synth.ARNA, obs_model=1)),
     ("frame_model_sharing", synth.sharing(G=8, Np=512, H=64, W=64, mode=synth.ARNA, obs_model=1)),
+    # Alg. 1's N_eff test per group: groups that keep their particles carry their weights
+    ("ess_rna", synth.small_rna(resample_rule=1, ess_fraction=0.5)),
+    ("ess_arna_sharing", synth.sharing(G=8, Np=512, H=64, W=64, mode=synth.ARNA, resample_rule=1, ess_fraction=0.5)),
+    ("ess_never_rna50", synth.small_rna(G=3, Np=700, ex_ratio=0.5, resample_rule=1, ess_fraction=0.0)),
+    ("ess_frame_model", synth.sharing(G=6, Np=400, H=64, W=64, mode=synth.ARNA, obs_model=1, resample_rule=1,
+                                      ess_fraction=0.7)),
+    # keyed random send sets (Sec. III-C): Feistel permutations, power-of-two and ragged Np
+    ("keyed_rna", synth.small_rna(send_rule=1)),
+    ("keyed_arna_ragged", synth.small_rna(G=5, Np=300, H=40, W=40, mode=synth.ARNA, ex_ratio=0.3, send_rule=1)),
+    ("keyed_sharing_ess", synth.sharing(G=8, Np=700, H=64, W=64, mode=synth.ARNA, send_rule=1, resample_rule=1,
+                                        ess_fraction=0.5)),
 ]
 
 
@@ -50,6 +61,11 @@ SMALL = [
 def test_small_configs_match_oracle(dev, name, wl):
     rep = _run(dev, wl, 6)
     assert len(rep) == 6
+    if name.startswith("ess_never"):
+        assert all(r["resampled"] == 0 for r in rep)
+    elif name in ("ess_rna", "ess_arna_sharing"):
+        # the test decided both ways over the run
+        assert any(r["resampled"] < wl.G for r in rep) and any(r["resampled"] > 0 for r in rep), rep
 
 
 @pytest.mark.parametrize("mode", [synth.RNA, synth.ARNA])

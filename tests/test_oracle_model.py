@@ -42,9 +42,10 @@ def test_rna_fixed_ratio(ora):
 
 
 # ------------------------------------------------------------------ exchange
+@pytest.mark.parametrize("send_rule", [0, 1])
 @pytest.mark.parametrize("mode,G,Np,nex", [(0, 4, 50, 5), (1, 7, 33, 16), (1, 2, 10, 5), (0, 3, 8, 8)])
-def test_exchange_is_a_size_and_weight_conserving_bijection(ora, mode, G, Np, nex):
-    cfg = ora.make_cfg(G=G, Np=Np, mode=mode, seed=4)
+def test_exchange_is_a_size_and_weight_conserving_bijection(ora, mode, G, Np, nex, send_rule):
+    cfg = ora.make_cfg(G=G, Np=Np, mode=mode, seed=4, send_rule=send_rule)
     N = G * Np
     pop = np.arange(5 * N, dtype=np.float64).reshape(5, N)
     for k in (1, 2, 9):
@@ -71,9 +72,10 @@ def test_exchange_zero_is_identity(ora):
     assert np.array_equal(out, pop) and np.array_equal(src, np.arange(30))
 
 
-def test_exchange_inclusion_probability(ora):
+@pytest.mark.parametrize("send_rule", [0, 1])
+def test_exchange_inclusion_probability(ora, send_rule):
     """Every slot is sent (and refilled) with probability N_ex / Np."""
-    cfg = ora.make_cfg(G=2, Np=10, seed=8)
+    cfg = ora.make_cfg(G=2, Np=10, seed=8, send_rule=send_rule)
     nex, K = 3, 4000
     hits = np.zeros(10)
     pop = np.zeros((5, 20))
@@ -82,6 +84,45 @@ def test_exchange_inclusion_probability(ora):
         hits += org[:10] != 0
     p = nex / 10
     assert np.all(np.abs(hits / K - p) < 5 * math.sqrt(p * (1 - p) / K))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 16, 17, 100, 1000, 1024, 4097])
+def test_keyed_send_permutation_is_a_bijection_with_its_inverse(ora, n):
+    cfg = ora.make_cfg(G=3, Np=max(n, 1), seed=12)
+    for g, k in ((0, 1), (2, 7)):
+        key = ora.send_keys(cfg, g, k)
+        fwd = np.array([ora.send_perm(t, n, key) for t in range(n)])
+        assert np.array_equal(np.sort(fwd), np.arange(n))
+        assert all(ora.send_perm_inv(int(fwd[t]), n, key) == t for t in range(n))
+    assert [ora.perm_bits(v) for v in (1, 2, 3, 4, 5, 1 << 20)] == [0, 1, 2, 2, 3, 20]
+
+
+def test_keyed_send_sets_are_uniform_random_subsets(ora):
+    """Sec. III-C: each group randomly selects the particles it sends.  Over
+    steps, the keyed send set of N_ex = 10 of 40 slots behaves as a uniform
+    random subset: every slot with probability 1/4, two neighbouring slots
+    together with probability 10*9/(40*39) (the systematic subsample, one slot
+    in every four, never sends neighbours), and the count in the first half
+    hypergeometric (mean 5, variance 10*(1/2)(1/2)(30/39))."""
+    cfg = ora.make_cfg(G=1, Np=40, seed=21)
+    n, m, K = 40, 10, 6000
+    single = np.zeros(n)
+    pairs = 0
+    half = []
+    for k in range(1, K + 1):
+        key = ora.send_keys(cfg, 0, k)
+        sent = np.zeros(n, bool)
+        sent[[ora.send_perm(t, n, key) for t in range(m)]] = True
+        single += sent
+        pairs += int(np.sum(sent[:-1] & sent[1:]))
+        half.append(int(sent[:20].sum()))
+    p = m / n
+    assert np.all(np.abs(single / K - p) < 5 * math.sqrt(p * (1 - p) / K))
+    pp = m * (m - 1) / (n * (n - 1))
+    assert abs(pairs / (K * (n - 1)) - pp) < 5 * math.sqrt(pp / (K * (n - 1))) * 2
+    half = np.array(half, float)
+    assert abs(half.mean() - 5.0) < 5 * math.sqrt(1.923 / K)
+    assert abs(half.var() - 10 * 0.25 * 30 / 39) < 0.15
 
 
 # ---------------------------------------------------------------- propagate
