@@ -389,8 +389,9 @@ def adam_fit(pf, wl, fr, truth, iters: int = 200, lr: float = 0.02):
 def bench_sharing(dev):
     """Information-sharing start: 100 frames 512 x 512, G = 256 x 4096, group
     0 in a 2 px disc around the truth, the other groups uniform over the
-    image.  For ARNA and RNA 10 %, under the patch-residual likelihood and
-    the frame likelihood ratio: the first step at which every group mean is
+    image.  For ARNA, RNA 10 % and ARNA with keyed random send sets, under
+    the patch-residual likelihood and the frame likelihood ratio: the first
+    step at which every group mean is
     within 2 px of the truth, the first steps at which PE_eff / G reaches 0.5
     and 0.9 (Sec. V-B's recovery of PE_eff), the final estimate's error, and
     PE_eff / G per step."""
@@ -401,8 +402,8 @@ def bench_sharing(dev):
     frames = truth = fr = None
     for obs_name, obs in (("patch", 0), ("frame", 1)):
         res = {}
-        for mode in (synth.ARNA, synth.RNA):
-            wl = synth.sharing(mode=mode, obs_model=obs)
+        for name, mode, send in (("arna", synth.ARNA, 0), ("rna10", synth.RNA, 0), ("arna_keyed", synth.ARNA, 1)):
+            wl = synth.sharing(mode=mode, obs_model=obs, send_rule=send)
             if frames is None:
                 frames, truth = synth.make_sequence(wl)
                 fr = torch.from_numpy(frames).to(dev)
@@ -423,7 +424,7 @@ def bench_sharing(dev):
 
             def first_at(level):
                 return next((k for k, v in enumerate(pe) if k >= 1 and v >= level), None)
-            res["arna" if mode == synth.ARNA else "rna10"] = {
+            res[name] = {
                 "steps_to_all_groups_within_2px": first, "steps_to_pe_eff_0.5": first_at(0.5),
                 "steps_to_pe_eff_0.9": first_at(0.9), "pe_eff_over_G_last": pe[-1],
                 "final_error_px": float(np.hypot(*(xhat[0, :2] - truth[-1, :2]))),
@@ -515,6 +516,7 @@ def bench_accuracy(dev, n_seq: int = 10):
     modes = {"arna": dict(mode=synth.ARNA), "rna0": dict(mode=synth.RNA, ex_ratio=0.0),
              "rna10": dict(mode=synth.RNA, ex_ratio=0.10), "rna50": dict(mode=synth.RNA, ex_ratio=0.50),
              "arna_ess50": dict(mode=synth.ARNA, resample_rule=1, ess_fraction=0.5),
+             "arna_keyed": dict(mode=synth.ARNA, send_rule=1),
              "rna10_ess50": dict(mode=synth.RNA, ex_ratio=0.10, resample_rule=1, ess_fraction=0.5)}
     out = {}
     for name, kw in modes.items():

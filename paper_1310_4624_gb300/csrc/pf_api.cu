@@ -363,7 +363,7 @@ pf_status sync(pf_handle* h) {
 
 K1Args k1_args(const pf_handle* h) {
   K1Args a{h->trk, h->tiles, h->n_tiles, h->gs, h->ts, h->ds, h->pv[0], h->pv[1], h->In[0], h->In[1],
-           h->anc, h->parent, h->history, h->lw, h->lw + lw_stride(h->N_total), h->tile_part, h->ypad, h->tmaps, h->ring_next,
+           h->anc, h->parent, h->history, h->lw, h->carry_any ? h->lw + lw_stride(h->N_total) : h->lw, h->tile_part, h->ypad, h->tmaps, h->ring_next,
            h->G_total, h->exo_next, h->hist, h->ghist, h->tile_ctr, h->n_ring_blocks, h->n_tracks, TrackParams{}, 0,
            nullptr, h->test_withhold_copy ? 1 : 0, h->variants ? 1 : 0, h->keys_next, CUtensorMap{}};
   a.p0 = h->tp[0];

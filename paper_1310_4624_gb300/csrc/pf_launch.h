@@ -51,8 +51,9 @@ struct K1Args {
   const uint32_t* anc;  // previous step's ancestors (track-local slots)
   uint32_t* parent;     // ancestry records or nullptr
   int history;
-  float* lw;            // log-weights; with carry, two buffers by step parity: step k
-  float* lw1;           // writes lw (k even) or lw1 (k odd) and reads the other one
+  float* lw;            // log-weights; with carried weights, two buffers by step parity:
+  float* lw1;           // step k writes lw (k even) or lw1 (k odd) and reads the other one
+                        // (lw1 == lw when no track carries weights)
   float* tile_part;     // 8 floats per tile
   const float* ypad;
   const CUtensorMap* tmaps;  // one per track over its padded frame, or nullptr
