@@ -31,7 +31,7 @@ constexpr int RING_SMEM_G = ROI_FLOATS / 2;  // ring orders drawn ahead up to th
 constexpr int RS_THREADS = 512;       // resampler CTA
 constexpr int RS_ITEMS = 8;           // items per thread per resampler sub-chunk
 constexpr int RS_SUB = RS_THREADS * RS_ITEMS;
-constexpr int RS_OUT = RS_SUB;        // resampler ancestors staged per window
+constexpr int RS_WIN = 2 * RS_SUB;    // resampler merge window: items and outputs merged at once (ancestors staged)
 __host__ __device__ constexpr int pad8(int i) { return i + (i >> 3); }  // shared index with one spare per 8
 constexpr int RS_SUB_PAD = pad8(RS_SUB);
 constexpr int GL_THREADS = 1024;      // per-track global-step CTA, one thread per group

@@ -1023,6 +1023,97 @@ __device__ __forceinline__ int count_below(const Thresholds& th, unsigned long l
   return c;
 }
 
+// Block-wide split of a merge at diagonal p: the number of items among its
+// first p positions, for items i < n with boundaries X_i = s_incl[pad8(i)]
+// and outputs j0 + b, b < no, with thresholds T: the largest i in
+// [max(0, p - no), min(p, n)] with X_{i-1} <= T_{j0+p-i}.  A
+// RS_THREADS-ary search that every thread of the block enters.
+__device__ __noinline__ int merge_split(const unsigned long long* s_incl, const Thresholds& th, int j0, int n, int no, int p) {
+  int lo = max(0, p - no), hi = min(p, n);
+  while (lo < hi) {
+    const int m = hi - lo;
+    const bool fine = m <= RS_THREADS;  // then candidates lo + 1 .. hi, else RS_THREADS evenly spaced
+    const int c = fine ? lo + 1 + (int)threadIdx.x : lo + (int)(((long long)(threadIdx.x + 1) * m) / RS_THREADS);
+    const bool ok = (!fine || (int)threadIdx.x < m) && s_incl[pad8(c - 1)] <= th.T((uint32_t)(j0 + p - c));
+    const int cnt = __syncthreads_count(ok);  // the predicate holds for a prefix of the candidates
+    if (fine) {
+      lo += cnt;
+      hi = lo;
+    } else {
+      const int nlo = cnt == 0 ? lo : lo + (int)(((long long)cnt * m) / RS_THREADS);
+      const int nhi = cnt == RS_THREADS ? hi : lo + (int)(((long long)(cnt + 1) * m) / RS_THREADS) - 1;
+      lo = nlo;
+      hi = nhi;
+    }
+  }
+  return lo;
+}
+
+// The merge of one resampler sub-chunk: n items with boundaries
+// X_i = s_incl[pad8(i)] against outputs j in [jlo, jhi); ancestors
+// obase_sub + item, stored to anc[j].  Every thread of the block enters.
+// (Not inlined: it runs with registers of its own.)
+__device__ __noinline__ void merge_windows(const unsigned long long* __restrict__ s_incl, uint32_t* __restrict__ s_out,
+                                           const Thresholds& th_s, int jlo, int jhi, int n,
+                                           unsigned long long obase_sub, uint32_t* __restrict__ anc) {
+  const Thresholds th = th_s;
+  // Merge path over the item boundaries X_i = S_{i+1} (s_incl) and the
+  // thresholds Y_j = T_j of this sub-chunk's outputs j in [jlo, jhi):
+  // output j takes the first item i with T_j < S_{i+1}.  The merged
+  // sequence (n items, no outputs) is cut into windows of at most RS_WIN
+  // positions, each split at its diagonal by a block-wide search, so that
+  // every item and output is merged once however the weight is spread
+  // over the CTAs; within a window each thread merges an equal slice.  A
+  // window's ancestors are staged in shared memory and stored with
+  // consecutive threads writing consecutive outputs.
+  const int no = jhi - jlo, Lt = n + no;
+  int ia0 = 0, ib0 = 0;  // items and outputs merged before the window
+  for (int p0 = 0; p0 < Lt; p0 += RS_WIN) {
+    const int p1 = min(Lt, p0 + RS_WIN);
+    const int ia1 = p1 == Lt ? n : merge_split(s_incl, th, jlo, n, no, p1);
+    const int nw = ia1 - ia0, mw = (p1 - ia1) - ib0, L = p1 - p0;
+    const int jw = jlo + ib0;
+    const int d0 = (int)(((long long)L * threadIdx.x) / RS_THREADS);
+    const int d1 = (int)(((long long)L * (threadIdx.x + 1)) / RS_THREADS);
+    // largest ia in [max(0, d0 - mw), min(d0, nw)] whose items all precede
+    // output d0 - ia of the window in the merge (X_{ia0+ia-1} <= Y_{jw+d0-ia})
+    int lo2 = max(0, d0 - mw), hi2 = min(d0, nw);
+    while (lo2 < hi2) {
+      const int mid = (lo2 + hi2 + 1) >> 1;  // candidate number of items consumed
+      if (s_incl[pad8(ia0 + mid - 1)] <= th.T((uint32_t)(jw + d0 - mid))) lo2 = mid;
+      else hi2 = mid - 1;
+    }
+    int ia = lo2, ib = d0 - lo2;
+    if (ib < mw) {
+      // T and its remainder at output jw + ib, then advance incrementally
+      uint32_t jj = (uint32_t)(jw + ib);
+      unsigned long long num = (unsigned long long)jj * th.B + th.F0;
+      unsigned long long qd = th.Np > 1 ? __umul64hi(num, th.M) : num;
+      uint32_t rem = (uint32_t)(num - qd * th.Np);
+      unsigned long long Tj = (unsigned long long)jj * th.A + th.F1 + qd;
+      for (int dd = d0; dd < d1; ++dd) {
+        if (ib < mw && (ia >= nw || Tj < s_incl[pad8(ia0 + ia)])) {
+          s_out[pad8(ib)] = (uint32_t)(obase_sub + ia0 + ia);
+          ++ib;
+          rem += th.B;
+          Tj += th.A;
+          if (rem >= th.Np) {
+            rem -= th.Np;
+            Tj += 1;
+          }
+        } else {
+          ++ia;
+        }
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < mw; e += RS_THREADS) anc[jw + e] = s_out[pad8(e)];
+    __syncthreads();
+    ia0 = ia1;
+    ib0 += mw;
+  }
+}
+
 // Resampler: one thread-block cluster per group, each CTA a contiguous chunk
 // of the group's slots (a multiple of 8), processed in sub-chunks of RS_SUB
 // items; thread t owns the RS_ITEMS consecutive items [t*RS_ITEMS, ...).
@@ -1285,52 +1376,7 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
         s_jhi = count_below(th, carry + tot, inv_Q, Np, u, a.ds);
       }
       __syncthreads();
-      // Merge path over the item boundaries X_i = S_{i+1} (s_incl) and the
-      // thresholds Y_b = T_{jw+b} of a window of this sub-chunk's outputs:
-      // output j takes the first item i with T_j < S_{i+1}.  Each thread
-      // merges an equal slice of the n + mw merged positions, so the work is
-      // balanced however the weight is spread.  The window's ancestors are
-      // staged in shared memory and stored with consecutive threads writing
-      // consecutive outputs.
-      for (int jw = s_jlo; jw < s_jhi; jw += RS_OUT) {
-        const int mw = min(RS_OUT, s_jhi - jw), L = n + mw;
-        const int d0 = (int)(((long long)L * threadIdx.x) / RS_THREADS);
-        const int d1 = (int)(((long long)L * (threadIdx.x + 1)) / RS_THREADS);
-        // largest ia in [max(0, d0 - mw), min(d0, n)] whose items all precede
-        // output d0 - ia in the merge (X_{ia-1} <= Y_{d0-ia})
-        int lo2 = max(0, d0 - mw), hi2 = min(d0, n);
-        while (lo2 < hi2) {
-          const int mid = (lo2 + hi2 + 1) >> 1;  // candidate number of items consumed
-          if (s_incl[pad8(mid - 1)] <= th.T((uint32_t)(jw + d0 - mid))) lo2 = mid;
-          else hi2 = mid - 1;
-        }
-        int ia = lo2, ib = d0 - lo2;
-        if (ib < mw) {
-          // T and its remainder at output jw + ib, then advance incrementally
-          uint32_t jj = (uint32_t)(jw + ib);
-          unsigned long long num = (unsigned long long)jj * th.B + th.F0;
-          unsigned long long qd = th.Np > 1 ? __umul64hi(num, th.M) : num;
-          uint32_t rem = (uint32_t)(num - qd * th.Np);
-          unsigned long long Tj = (unsigned long long)jj * th.A + th.F1 + qd;
-          for (int dd = d0; dd < d1; ++dd) {
-            if (ib < mw && (ia >= n || Tj < s_incl[pad8(ia)])) {
-              s_out[pad8(ib)] = (uint32_t)(obase + sub + ia);
-              ++ib;
-              rem += th.B;
-              Tj += th.A;
-              if (rem >= th.Np) {
-                rem -= th.Np;
-                Tj += 1;
-              }
-            } else {
-              ++ia;
-            }
-          }
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < mw; e += RS_THREADS) anc[jw + e] = s_out[pad8(e)];
-        __syncthreads();
-      }
+      merge_windows(s_incl, s_out, s_th, s_jlo, s_jhi, n, obase + sub, anc);
       carry += tot;
       __syncthreads();
     }
@@ -1448,7 +1494,7 @@ cudaError_t launch_propagate(const K1Args& a, int R, int grid, bool pdl, cudaStr
 }
 
 cudaError_t launch_resample(const ResampleArgs& a, int n_groups, int cluster, bool pdl, cudaStream_t s) {
-  constexpr size_t smem = RS_SUB_PAD * sizeof(unsigned long long) + pad8(RS_OUT) * sizeof(uint32_t);
+  constexpr size_t smem = RS_SUB_PAD * sizeof(unsigned long long) + pad8(RS_WIN) * sizeof(uint32_t);
   static_assert(sizeof(GlobalScratch) <= smem, "the global step's scratch lives in the resampler's shared memory");
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
