@@ -1119,12 +1119,6 @@ __device__ __noinline__ void merge_windows(const unsigned long long* __restrict_
 // items; thread t owns the RS_ITEMS consecutive items [t*RS_ITEMS, ...).
 
 __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
-  grid_dep_wait();
-  if (a.tile_ctr && blockIdx.x == 0 && threadIdx.x == 0) *a.tile_ctr = 0;  // for the next propagate launch
-  // A propagate launch that timed out or met an out-of-range ancestor left
-  // weights that mean nothing: resample nothing.  Only the kernels before
-  // this one set these two bits, so every CTA of a cluster decides alike.
-  if (a.ds && (*reinterpret_cast<volatile const unsigned int*>(&a.ds->err) & (ERR_TIMEOUT | ERR_INDEX)) != 0u) return;
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -1175,12 +1169,20 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
     }
   };
 
-  // the group's resampling uniform word (Philox stream RESAMPLE, group, step)
-  uint32_t u;
-  if (a.u_arr)
-    u = a.u_arr[grp];
-  else
+  // The group's resampling uniform word (Philox stream RESAMPLE, group,
+  // step).  In a filter step it depends only on the seed and the step index
+  // (set by the previous step's global step, complete before the propagate
+  // kernel ran), so it is drawn before waiting for the propagate kernel.
+  uint32_t u = 0;
+  if (!a.u_arr)
     u = philox(Pt->key0, Pt->key1, make_uint4((uint32_t)d.g, 0u, (uint32_t)kk, Pt->tag | (ST_RESAMPLE << 4))).x;
+  grid_dep_wait();
+  if (a.u_arr) u = a.u_arr[grp];
+  if (a.tile_ctr && blockIdx.x == 0 && threadIdx.x == 0) *a.tile_ctr = 0;  // for the next propagate launch
+  // A propagate launch that timed out or met an out-of-range ancestor left
+  // weights that mean nothing: resample nothing.  Only the kernels before
+  // this one set these two bits, so every CTA of a cluster decides alike.
+  if (a.ds && (*reinterpret_cast<volatile const unsigned int*>(&a.ds->err) & (ERR_TIMEOUT | ERR_INDEX)) != 0u) return;
 
   // group maximum: from the propagate tiles' maxima in a filter step, else
   // over the cluster (the same set of log-weights either way, NaN ignored)
