@@ -25,6 +25,7 @@ RNA, ARNA = 0, 1
 OBS_IMAGE, OBS_POINT, OBS_FRAME = 0, 1, 2
 RESAMPLE_ALWAYS, RESAMPLE_ESS = 0, 1
 SEND_SYSTEMATIC, SEND_KEYED = 0, 1
+TOPO_RING, TOPO_NODE_RING, TOPO_HYPERCUBE = 0, 1, 2
 INIT_POINT, INIT_UNIFORM, INIT_SHARING = 0, 1, 2
 
 
@@ -36,7 +37,7 @@ class Cfg(C.Structure):
         ("sigma_pos", C.c_double), ("sigma_v", C.c_double), ("sigma_I", C.c_double),
         ("ex_ratio", C.c_double), ("cutoff", C.c_double),
         ("seed", C.c_uint64), ("track", C.c_uint32), ("send_rule", C.c_int32),
-        ("ess_fraction", C.c_double),
+        ("ess_fraction", C.c_double), ("topology", C.c_int32), ("node_groups", C.c_int32),
     ]
 
 
@@ -66,6 +67,9 @@ def lib():
         L.ora_fisher_yates.argtypes = [C.c_int32, _P, _P]
         L.ora_ring.argtypes = [C.POINTER(Cfg), C.c_uint32, _P]
         L.ora_pred.argtypes = [C.c_int32, _P, _P]
+        L.ora_pred_topo.argtypes = [C.POINTER(Cfg), _P, _P]
+        L.ora_hyper_dims.argtypes = [C.c_int32]
+        L.ora_hyper_dims.restype = C.c_int32
         L.ora_pe_eff.argtypes = [C.c_int32, _P]
         L.ora_pe_eff.restype = C.c_double
         L.ora_n_ex.argtypes = [C.POINTER(Cfg), C.c_uint32, _P, _P]
@@ -118,11 +122,13 @@ def _c(a, dtype):
 
 def make_cfg(G, Np, H=64, W=64, R=5, mode=RNA, obs_kind=OBS_IMAGE, sigma_psf=1.5, background=1.0,
              sigma_obs=1.0, sigma_pos=0.5, sigma_v=0.1, sigma_I=0.5, ex_ratio=0.1, cutoff=0.99,
-             seed=0, track=0, resample_rule=RESAMPLE_ALWAYS, ess_fraction=0.5, send_rule=SEND_SYSTEMATIC) -> Cfg:
+             seed=0, track=0, resample_rule=RESAMPLE_ALWAYS, ess_fraction=0.5, send_rule=SEND_SYSTEMATIC,
+             topology=TOPO_RING, node_groups=1) -> Cfg:
     return Cfg(G=G, Np=Np, H=H, W=W, R=R, mode=mode, obs_kind=obs_kind, sigma_psf=sigma_psf,
                background=background, sigma_obs=sigma_obs, sigma_pos=sigma_pos, sigma_v=sigma_v,
                sigma_I=sigma_I, ex_ratio=ex_ratio, cutoff=cutoff, seed=seed, track=track,
-               resample_rule=resample_rule, ess_fraction=ess_fraction, send_rule=send_rule)
+               resample_rule=resample_rule, ess_fraction=ess_fraction, send_rule=send_rule, topology=topology,
+               node_groups=node_groups)
 
 
 def cfg_from_workload(wl, track: int = 0) -> Cfg:
@@ -137,7 +143,8 @@ def cfg_from_workload(wl, track: int = 0) -> Cfg:
                     sigma_pos=f(wl.sigma_pos), sigma_v=f(wl.sigma_v), sigma_I=f(wl.sigma_I),
                     ex_ratio=f(wl.ex_ratio), cutoff=f(wl.pe_eff_cutoff), seed=wl.seed, track=track,
                     resample_rule=getattr(wl, "resample_rule", 0), ess_fraction=f(getattr(wl, "ess_fraction", 0.5)),
-                    send_rule=getattr(wl, "send_rule", 0))
+                    send_rule=getattr(wl, "send_rule", 0), topology=getattr(wl, "topology", 0),
+                    node_groups=getattr(wl, "node_groups", 1))
 
 
 # ---------------------------------------------------------------- primitives
@@ -187,6 +194,18 @@ def pred(sigma) -> np.ndarray:
     out = np.zeros(s.size, np.int32)
     lib().ora_pred(s.size, _ptr(s), _ptr(out))
     return out
+
+
+def pred_topo(cfg: Cfg, sigma) -> np.ndarray:
+    """The sender of every group under the track's topology."""
+    s = _c(sigma, np.int32)
+    out = np.zeros(s.size, np.int32)
+    lib().ora_pred_topo(C.byref(cfg), _ptr(s), _ptr(out))
+    return out
+
+
+def hyper_dims(G: int) -> int:
+    return int(lib().ora_hyper_dims(G))
 
 
 def pe_eff(Lam) -> float:

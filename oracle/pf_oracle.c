@@ -51,6 +51,10 @@
 #define ORA_OBS_POINT 1
 #define ORA_OBS_FRAME 2
 
+#define ORA_TOPO_RING 0
+#define ORA_TOPO_NODE_RING 1
+#define ORA_TOPO_HYPERCUBE 2
+
 #define ORA_SEND_SYSTEMATIC 0
 #define ORA_SEND_KEYED 1
 
@@ -81,6 +85,8 @@ typedef struct {
   uint32_t track;
   int32_t send_rule;   /* ORA_SEND_SYSTEMATIC or ORA_SEND_KEYED (which slots a group sends) */
   double ess_fraction; /* ORA_RESAMPLE_ESS: N_thresh = ess_fraction * Np */
+  int32_t topology;    /* ORA_TOPO_RING, ORA_TOPO_NODE_RING or ORA_TOPO_HYPERCUBE (Sec. VI) */
+  int32_t node_groups; /* ORA_TOPO_NODE_RING: groups per node */
 } ora_cfg;
 
 /* ------------------------------------------------------------------------ */
@@ -137,14 +143,20 @@ void ora_bounded_batch(const uint32_t* w, int64_t n, uint32_t s, int32_t* out) {
   }
 }
 
-/* A uniform integer in [0, s) for (stream, index c0, step k): attempt a uses
- * counter (c0, a, k, tag) word 0; rejected attempts move on to a + 1. */
-uint32_t ora_draw_bounded(const ora_cfg* c, uint32_t stream, uint32_t c0, uint32_t k, uint32_t s) {
+/* A uniform integer in [0, s) for (stream, call, index c0, step k): attempt
+ * a uses counter (c0, a, k, tag | call) word 0; rejected attempts move on to
+ * a + 1. */
+static uint32_t draw_bounded_call(const ora_cfg* c, uint32_t stream, uint32_t call, uint32_t c0, uint32_t k,
+                                  uint32_t s) {
   for (uint32_t a = 0;; ++a) {
     uint32_t w[4], v;
-    philox_stream(c, c0, a, k, stream, 0u, w);
+    philox_stream(c, c0, a, k, stream, call, w);
     if (ora_bounded(w[0], s, &v)) return v;
   }
+}
+
+uint32_t ora_draw_bounded(const ora_cfg* c, uint32_t stream, uint32_t c0, uint32_t k, uint32_t s) {
+  return draw_bounded_call(c, stream, 0u, c0, k, s);
 }
 
 /* Five standard normals for the particle in slot j of group g at step k, by
@@ -183,14 +195,65 @@ void ora_fisher_yates(int32_t G, const uint32_t* r, int32_t* sigma) {
   }
 }
 
-/* Ring order sigma for step k: ring position p holds group sigma[p], and
- * group sigma[p] sends to sigma[p+1 mod G].  RNA: the fixed ring (identity,
- * P_m -> P_{m+1}).  ARNA: a fresh Fisher-Yates shuffle of the identity at
- * every step k >= 1, draw j from stream RING, index j, step k. */
+/* Hypercube dimensions: ceil(log2 G). */
+int32_t ora_hyper_dims(int32_t G) {
+  int32_t D = 0;
+  while ((1 << D) < G) ++D;
+  return D;
+}
+
+/* Communication topology of step k (Sec. IV-B; Sec. VI for the others).
+ * ORA_TOPO_RING: ring order sigma, ring position p holds group sigma[p],
+ *   which sends to sigma[p+1 mod G].  RNA: the fixed ring (identity,
+ *   P_m -> P_{m+1}).  ARNA: a fresh Fisher-Yates shuffle of the identity at
+ *   every step k >= 1, draw j from stream RING, index j, step k.
+ * ORA_TOPO_NODE_RING (Sec. VI: neighbouring PEs of the ring on the same
+ *   node): groups form nodes of node_groups consecutive groups (the last
+ *   may be smaller).  ARNA: the ring visits the nodes in a shuffled order
+ *   (Fisher-Yates over the nodes, draw j from RING call 1, index j) and each
+ *   node's groups in a shuffled order (Fisher-Yates over its groups, draw j
+ *   from RING call 2, index n node_groups + j), so only one ring edge per
+ *   node leaves it.  RNA: the fixed ring, which is already node by node.
+ * ORA_TOPO_HYPERCUBE (Sec. VI: another regular graph of low degree): at
+ *   step k >= 1 every group g exchanges with its partner g xor 2^d (itself
+ *   when that is >= G) along dimension d of the ceil(log2 G)-cube; RNA
+ *   cycles d = (k - 1) mod D, ARNA draws d uniformly (RING call 3, index 0).
+ *   sigma[g] is then g's partner.
+ * At k = 0 (no exchange) and for G = 1 sigma is the identity. */
 void ora_ring(const ora_cfg* c, uint32_t k, int32_t* sigma) {
   int32_t G = c->G;
-  if (c->mode != ORA_ARNA || k == 0 || G == 1) {
-    for (int32_t g = 0; g < G; ++g) sigma[g] = g;
+  for (int32_t g = 0; g < G; ++g) sigma[g] = g;
+  if (k == 0 || G == 1) return;
+  if (c->topology == ORA_TOPO_HYPERCUBE) {
+    int32_t D = ora_hyper_dims(G);
+    uint32_t d = c->mode == ORA_ARNA ? draw_bounded_call(c, ORA_STREAM_RING, 3u, 0u, k, (uint32_t)D)
+                                     : (k - 1u) % (uint32_t)D;
+    for (int32_t g = 0; g < G; ++g) {
+      int32_t p = g ^ (1 << d);
+      sigma[g] = p < G ? p : g;
+    }
+    return;
+  }
+  if (c->mode != ORA_ARNA) return;
+  if (c->topology == ORA_TOPO_NODE_RING) {
+    int32_t B = c->node_groups < 1 ? 1 : c->node_groups;
+    int32_t NN = (G + B - 1) / B;
+    uint32_t* r = (uint32_t*)calloc((size_t)(NN > B ? NN : B), sizeof(uint32_t));
+    int32_t* nodes = (int32_t*)malloc(sizeof(int32_t) * (size_t)NN);
+    int32_t* members = (int32_t*)malloc(sizeof(int32_t) * (size_t)B);
+    for (int32_t j = 1; j < NN; ++j) r[j] = draw_bounded_call(c, ORA_STREAM_RING, 1u, (uint32_t)j, k, (uint32_t)j + 1u);
+    ora_fisher_yates(NN, r, nodes);
+    int32_t pos = 0;
+    for (int32_t q = 0; q < NN; ++q) {
+      int32_t n = nodes[q], base = n * B, sz = (G - base < B) ? G - base : B;
+      for (int32_t j = 1; j < sz; ++j)
+        r[j] = draw_bounded_call(c, ORA_STREAM_RING, 2u, (uint32_t)(base + j), k, (uint32_t)j + 1u);
+      ora_fisher_yates(sz, r, members);
+      for (int32_t i = 0; i < sz; ++i) sigma[pos++] = base + members[i];
+    }
+    free(r);
+    free(nodes);
+    free(members);
     return;
   }
   uint32_t* r = (uint32_t*)calloc((size_t)G, sizeof(uint32_t));
@@ -202,6 +265,15 @@ void ora_ring(const ora_cfg* c, uint32_t k, int32_t* sigma) {
 /* pred[g]: the group that sends to g under ring order sigma. */
 void ora_pred(int32_t G, const int32_t* sigma, int32_t* pred) {
   for (int32_t p = 0; p < G; ++p) pred[sigma[p]] = sigma[(p + G - 1) % G];
+}
+
+/* pred[g] for the track's topology: the ring's predecessor, or for the
+ * hypercube the partner itself (the exchange is mutual). */
+void ora_pred_topo(const ora_cfg* c, const int32_t* sigma, int32_t* pred) {
+  if (c->topology == ORA_TOPO_HYPERCUBE)
+    for (int32_t g = 0; g < c->G; ++g) pred[g] = sigma[g];
+  else
+    ora_pred(c->G, sigma, pred);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -330,8 +402,9 @@ uint32_t ora_send_perm_inv(uint32_t j, uint32_t n, const uint32_t key[4]) {
   return x;
 }
 
-/* S3: group sigma_p sends its t-th send slot (t < n_ex) to the t-th send
- * slot of sigma_{p+1}.  Send slots: ORA_SEND_SYSTEMATIC, the systematic
+/* S3: group pred(r) sends its t-th send slot (t < n_ex) to the t-th send
+ * slot of r, pred from sigma as in ora_pred_topo (on a ring, sigma_p sends
+ * to sigma_{p+1}).  Send slots: ORA_SEND_SYSTEMATIC, the systematic
  * subsample floor((t Np + o_g) / n_ex) with a uniform offset o_g in [0, Np);
  * ORA_SEND_KEYED, pi_g(t) of the keyed permutation above.
  * pop_in / pop_out: 5 x N SoA (component-major), N = G*Np, slot = g*Np + j.
@@ -352,8 +425,10 @@ void ora_exchange(const ora_cfg* c, uint32_t k, const int32_t* sigma, int32_t n_
       o[g] = ora_exchange_offset(c, (uint32_t)g, k);
       ora_send_keys(c, (uint32_t)g, k, key + 4 * g);
     }
-    for (int32_t p = 0; p < G; ++p) {
-      int32_t g = sigma[p], r = sigma[(p + 1) % G];
+    int32_t* pred = (int32_t*)malloc(sizeof(int32_t) * (size_t)G);
+    ora_pred_topo(c, sigma, pred);
+    for (int32_t r = 0; r < G; ++r) {
+      int32_t g = pred[r];
       for (int32_t t = 0; t < n_ex; ++t) {
         int64_t s_g = keyed ? (int64_t)ora_send_perm((uint32_t)t, (uint32_t)Np, key + 4 * g)
                             : ((int64_t)t * Np + o[g]) / n_ex;
@@ -365,6 +440,7 @@ void ora_exchange(const ora_cfg* c, uint32_t k, const int32_t* sigma, int32_t n_
     }
     free(o);
     free(key);
+    free(pred);
   }
   for (int d = 0; d < 5; ++d)
     for (int64_t i = 0; i < N; ++i) pop_out[d * N + i] = pop_in[d * N + src[i]];

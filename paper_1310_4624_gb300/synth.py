@@ -65,6 +65,8 @@ class Workload:
     resample_rule: int = 0        # 0: every step (Alg. 2/3), 1: when N_eff < ess_fraction Np (Alg. 1)
     ess_fraction: float = 0.5
     send_rule: int = 0            # 0: systematic slot subsample, 1: keyed random permutation (Sec. III-C)
+    topology: int = 0             # 0: ring (Sec. IV-B), 1: node-aware ring, 2: hypercube (Sec. VI)
+    node_groups: int = 1          # topology 1: groups per node
 
     @property
     def N(self) -> int:

@@ -42,22 +42,22 @@ def test_rna_fixed_ratio(ora):
 
 
 # ------------------------------------------------------------------ exchange
-@pytest.mark.parametrize("send_rule", [0, 1])
+@pytest.mark.parametrize("send_rule,topology", [(0, 0), (1, 0), (0, 1), (0, 2), (1, 2)])
 @pytest.mark.parametrize("mode,G,Np,nex", [(0, 4, 50, 5), (1, 7, 33, 16), (1, 2, 10, 5), (0, 3, 8, 8)])
-def test_exchange_is_a_size_and_weight_conserving_bijection(ora, mode, G, Np, nex, send_rule):
-    cfg = ora.make_cfg(G=G, Np=Np, mode=mode, seed=4, send_rule=send_rule)
+def test_exchange_is_a_size_and_weight_conserving_bijection(ora, mode, G, Np, nex, send_rule, topology):
+    cfg = ora.make_cfg(G=G, Np=Np, mode=mode, seed=4, send_rule=send_rule, topology=topology, node_groups=3)
     N = G * Np
     pop = np.arange(5 * N, dtype=np.float64).reshape(5, N)
     for k in (1, 2, 9):
         sig = ora.ring(cfg, k)
-        pr = ora.pred(sig)
+        pr = ora.pred_topo(cfg, sig)
         out, src, org = ora.exchange(cfg, k, sig, nex, pop)
         assert np.array_equal(np.sort(src), np.arange(N))            # bijection
         assert np.array_equal(out, pop[:, src])
         for r in range(G):
             sl = slice(r * Np, (r + 1) * Np)
             recv = org[sl] != r
-            assert recv.sum() == (nex if G > 1 else 0)               # fixed counts
+            assert recv.sum() == (nex if pr[r] != r else 0)           # fixed counts
             assert np.all(org[sl][recv] == pr[r])                    # from pred only
             assert np.all(src[sl][recv] // Np == pr[r])
             assert np.all(src[sl][~recv] == np.arange(r * Np, (r + 1) * Np)[~recv])
