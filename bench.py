@@ -389,9 +389,10 @@ def adam_fit(pf, wl, fr, truth, iters: int = 200, lr: float = 0.02):
 def bench_sharing(dev):
     """Information-sharing start: 100 frames 512 x 512, G = 256 x 4096, group
     0 in a 2 px disc around the truth, the other groups uniform over the
-    image.  For ARNA, RNA 10 % and ARNA with keyed random send sets, under
-    the patch-residual likelihood and the frame likelihood ratio: the first
-    step at which every group mean is
+    image.  For ARNA, RNA 10 %, ARNA with keyed random send sets, and the
+    topologies of Sec. VI (ARNA on a ring that keeps nodes of 16 groups
+    together; ARNA and RNA 10 % on the hypercube), under the patch-residual
+    likelihood and the frame likelihood ratio: the first step at which every group mean is
     within 2 px of the truth, the first steps at which PE_eff / G reaches 0.5
     and 0.9 (Sec. V-B's recovery of PE_eff), the final estimate's error, and
     PE_eff / G per step."""
@@ -402,8 +403,13 @@ def bench_sharing(dev):
     frames = truth = fr = None
     for obs_name, obs in (("patch", 0), ("frame", 1)):
         res = {}
-        for name, mode, send in (("arna", synth.ARNA, 0), ("rna10", synth.RNA, 0), ("arna_keyed", synth.ARNA, 1)):
-            wl = synth.sharing(mode=mode, obs_model=obs, send_rule=send)
+        runs = (("arna", dict(mode=synth.ARNA)), ("rna10", dict(mode=synth.RNA)),
+                ("arna_keyed", dict(mode=synth.ARNA, send_rule=1)),
+                ("arna_node_ring16", dict(mode=synth.ARNA, topology=1, node_groups=16)),
+                ("arna_hypercube", dict(mode=synth.ARNA, topology=2)),
+                ("rna10_hypercube", dict(mode=synth.RNA, topology=2)))
+        for name, kw in runs:
+            wl = synth.sharing(obs_model=obs, **kw)
             if frames is None:
                 frames, truth = synth.make_sequence(wl)
                 fr = torch.from_numpy(frames).to(dev)

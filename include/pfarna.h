@@ -110,6 +110,21 @@ enum { PF_RESAMPLE_ALWAYS = 0, PF_RESAMPLE_ESS = 1 };
  *    stream of the exchange): a uniformly random-looking subset. */
 enum { PF_SEND_SYSTEMATIC = 0, PF_SEND_KEYED = 1 };
 
+/* Who exchanges with whom (topology; Sec. IV-B, and Sec. VI's future work).
+ *  PF_TOPO_RING: the ring of Alg. 2 (fixed, PF_RNA) or a fresh random ring
+ *    every step (PF_ARNA).
+ *  PF_TOPO_NODE_RING: groups form nodes of node_groups consecutive groups
+ *    (for instance the groups sharing a die or a machine); PF_ARNA's random
+ *    ring visits the nodes in a random order and each node's groups in a
+ *    random order, so one ring edge per node leaves it.  PF_RNA: the fixed
+ *    ring, which already runs node by node.
+ *  PF_TOPO_HYPERCUBE: at step k every group exchanges N_ex particles with
+ *    its partner g xor 2^d along one dimension d of the ceil(log2 G)-cube (no
+ *    exchange for a group whose partner would be >= G); PF_RNA cycles d,
+ *    PF_ARNA draws it at random every step.  The ring order reported by
+ *    pf_exchange_stats is then each group's partner. */
+enum { PF_TOPO_RING = 0, PF_TOPO_NODE_RING = 1, PF_TOPO_HYPERCUBE = 2 };
+
 /* One track's filter.  Observation model: obs_model above.  Dynamics: nearly
  * constant velocity with unit frame interval and independent Gaussian noise
  * sigma_pos (position), sigma_v (velocity), sigma_I (intensity). */
@@ -135,6 +150,8 @@ typedef struct pf_track_config {
   int32_t resample_rule;    /* PF_RESAMPLE_ALWAYS (0) or PF_RESAMPLE_ESS */
   float ess_fraction;       /* PF_RESAMPLE_ESS: N_thresh / Np, in [0, 1] */
   int32_t send_rule;        /* PF_SEND_SYSTEMATIC (0) or PF_SEND_KEYED */
+  int32_t topology;         /* PF_TOPO_RING (0), PF_TOPO_NODE_RING or PF_TOPO_HYPERCUBE */
+  int32_t node_groups;      /* PF_TOPO_NODE_RING: groups per node, >= 1 */
 } pf_track_config;
 
 /* Statistics of one completed step of one track. */

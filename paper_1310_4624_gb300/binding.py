@@ -17,6 +17,7 @@ PF_RNA, PF_ARNA = 0, 1
 PF_INIT_POINT, PF_INIT_UNIFORM, PF_INIT_SHARING, PF_INIT_USER = range(4)
 PF_RESAMPLE_ALWAYS, PF_RESAMPLE_ESS = 0, 1
 PF_SEND_SYSTEMATIC, PF_SEND_KEYED = 0, 1
+PF_TOPO_RING, PF_TOPO_NODE_RING, PF_TOPO_HYPERCUBE = 0, 1, 2
 
 STATUS_NAMES = {0: "PF_OK", 1: "PF_ERR_ARG", 2: "PF_ERR_STATE", 3: "PF_ERR_CUDA", 4: "PF_ERR_WORKSPACE",
                 5: "PF_ERR_DEGENERATE", 6: "PF_ERR_TIMEOUT", 7: "PF_ERR_DEVICE"}
@@ -43,6 +44,7 @@ class pf_track_config(C.Structure):
         ("init_radius", C.c_float), ("obs_model", C.c_int32),
         ("seed", C.c_uint64), ("track_id", C.c_uint32), ("record_ancestors", C.c_int32),
         ("resample_rule", C.c_int32), ("ess_fraction", C.c_float), ("send_rule", C.c_int32),
+        ("topology", C.c_int32), ("node_groups", C.c_int32),
     ]
 
 

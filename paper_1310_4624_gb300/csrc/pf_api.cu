@@ -202,6 +202,9 @@ std::string validate(const pf_track_config* c, int n, int history) {
     if (!(x.ess_fraction >= 0.0f && x.ess_fraction <= 1.0f)) return bad("ess_fraction must be in [0, 1]");
     if (x.send_rule != PF_SEND_SYSTEMATIC && x.send_rule != PF_SEND_KEYED)
       return bad("send_rule must be PF_SEND_SYSTEMATIC or PF_SEND_KEYED");
+    if (x.topology != PF_TOPO_RING && x.topology != PF_TOPO_NODE_RING && x.topology != PF_TOPO_HYPERCUBE)
+      return bad("topology must be PF_TOPO_RING, PF_TOPO_NODE_RING or PF_TOPO_HYPERCUBE");
+    if (x.topology == PF_TOPO_NODE_RING && x.node_groups < 1) return bad("node_groups must be >= 1");
     for (int d = 0; d < 5; ++d)
       if (!std::isfinite(x.init_state[d]) || !std::isfinite(x.init_lo[d]) || !std::isfinite(x.init_hi[d]))
         return bad("init_state / init_lo / init_hi must be finite");
@@ -534,6 +537,10 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
     P.resample_rule = c.resample_rule;
     P.ess_t = (uint32_t)std::floor((double)c.ess_fraction * 65536.0 + 0.5);
     P.send_rule = c.send_rule;
+    P.topology = c.topology;
+    P.node_groups = c.node_groups < 1 ? 1 : c.node_groups;
+    P.hyper_dims = 0;
+    while ((1 << P.hyper_dims) < c.G) ++P.hyper_dims;
     P.perm_bits = 0;
     while ((1 << P.perm_bits) < c.Np) ++P.perm_bits;
     P.part_off = part;

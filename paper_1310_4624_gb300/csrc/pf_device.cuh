@@ -40,6 +40,7 @@ constexpr int MAX_FRAMES_PER_LAUNCH = 1024;
 
 // Philox stream ids (counter word 3 = track << 8 | stream << 4 | call).
 constexpr uint32_t ST_INIT = 0, ST_PROP = 1, ST_RESAMPLE = 2, ST_RING = 3, ST_EXCH = 4;
+constexpr int TOPO_RING = 0, TOPO_NODE_RING = 1, TOPO_HYPERCUBE = 2;
 
 // Device error word bits.
 constexpr uint32_t ERR_INDEX = 1u, ERR_TIMEOUT = 2u, ERR_INVARIANT = 4u, ERR_DRAW = 8u;
@@ -64,6 +65,9 @@ struct TrackParams {
   int resample_rule;          // 0: every step, 1: Alg. 1's N_eff test per group
   uint32_t ess_t;             // N_thresh = ess_t Np / 2^16
   int send_rule;              // 0: systematic send slots, 1: keyed permutation (Sec. III-C)
+  int topology;               // 0: ring, 1: node-aware ring, 2: hypercube (Sec. VI)
+  int node_groups;            // topology 1: groups per node
+  int hyper_dims;             // ceil(log2 G)
   int perm_bits;              // ceil(log2 Np): the keyed permutation's domain bits
   long long part_off;         // first particle of the track (global slot)
   int group_off;              // first group of the track (global group)

@@ -261,11 +261,14 @@ __device__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
     sc.w[warp][0] = iw;
     sc.w[warp][1] = iw2;
   }
-  const bool shuffled = (mode == MODE_ARNA) && k1 >= 1 && G > 1;
+  // ring order of step k1 (Sec. IV-B), drawn one step ahead; for the
+  // hypercube each group's partner
+  const int topo = P->topology;
+  const bool shuffled = k1 >= 1 && G > 1 && (mode == MODE_ARNA || topo == TOPO_HYPERCUBE);
 #pragma unroll
   for (int i = 0; i < GPT; ++i) {
     const int m = threadIdx.x + i * NT;
-    if (m < G) sc.ring[m] = shuffled ? rnext[i] : m;  // ring order of step k1 (Sec. IV-B)
+    if (m < G) sc.ring[m] = shuffled ? rnext[i] : m;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -327,7 +330,10 @@ __device__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
     if (m < G) {
       const int rm = sc.ring[m];
       ring[m] = rm;
-      gs[rm].pred = sc.ring[m == 0 ? G - 1 : m - 1];
+      if (topo == TOPO_HYPERCUBE)
+        gs[m].pred = rm;  // mutual exchange with the partner
+      else
+        gs[rm].pred = sc.ring[m == 0 ? G - 1 : m - 1];
       gs[m].exo = nex > 0 ? exo[i] : 0u;
       gs[m].lambda = lam[i];
       // S4: a resampled group's particles weigh W_m / Np, a group that kept
@@ -487,6 +493,75 @@ __device__ void ring_for_step(const TrackParams& P, int track, uint32_t k, int* 
       const int tmp = out[j];
       out[j] = out[r];
       out[r] = tmp;
+    }
+  }
+  __syncwarp();
+}
+
+// The exchange pattern of step k for the other topologies (Sec. VI), by one
+// warp, into out[0 .. G): TOPO_NODE_RING (ARNA): nodes of node_groups
+// consecutive groups, the ring visiting the nodes in a Fisher-Yates order
+// (draw j from RING call 1, index j) and each node's groups in a
+// Fisher-Yates order (draw j from RING call 2, index n node_groups + j);
+// TOPO_HYPERCUBE: out[g] = g's partner g xor 2^d (g itself when that is
+// >= G), d = (k - 1) mod D (RNA) or drawn from RING call 3, index 0 (ARNA).
+__device__ void topology_for_step(const TrackParams& P, int track, uint32_t k, int* __restrict__ out,
+                                  int* __restrict__ sh, DevState* ds) {
+  const int lane = threadIdx.x & 31;
+  const int G = P.G;
+  if (P.topology == TOPO_HYPERCUBE) {
+    uint32_t d = 0;
+    if (P.mode == MODE_ARNA) {
+      if (!draw_bounded(P.key0, P.key1, P.tag | 3u, ST_RING, 0u, k, (uint32_t)P.hyper_dims, d))
+        set_error(ds, ERR_DRAW, 3u, (uint32_t)track, 0u);
+    } else {
+      d = (k - 1u) % (uint32_t)P.hyper_dims;
+    }
+    for (int g = lane; g < G; g += 32) {
+      const int p = g ^ (1 << d);
+      out[g] = p < G ? p : g;
+    }
+    __syncwarp();
+    return;
+  }
+  // node-aware ring.  Scratch: node draws (NN), node order (NN), member
+  // draws by group (G), one node's member order (B): at most 3 G + 1 ints.
+  const int B = P.node_groups < G ? P.node_groups : G, NN = (G + B - 1) / B;
+  int* rn = sh;
+  int* nodes = sh + NN;
+  int* rm = sh + 2 * NN;
+  int* mem = rm + G;
+  for (int j = lane; j < NN; j += 32) {
+    uint32_t r = 0;
+    if (j >= 1 && !draw_bounded(P.key0, P.key1, P.tag | 1u, ST_RING, (uint32_t)j, k, (uint32_t)j + 1u, r))
+      set_error(ds, ERR_DRAW, 4u, (uint32_t)track, (uint32_t)j);
+    rn[j] = (int)r;
+  }
+  for (int gi = lane; gi < G; gi += 32) {
+    const int j = gi % B;  // position within its node
+    uint32_t r = 0;
+    if (j >= 1 && !draw_bounded(P.key0, P.key1, P.tag | 2u, ST_RING, (uint32_t)gi, k, (uint32_t)j + 1u, r))
+      set_error(ds, ERR_DRAW, 5u, (uint32_t)track, (uint32_t)gi);
+    rm[gi] = (int)r;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    for (int n = 0; n < NN; ++n) nodes[n] = n;
+    for (int j = NN - 1; j >= 1; --j) {
+      const int r = rn[j], t = nodes[j];
+      nodes[j] = nodes[r];
+      nodes[r] = t;
+    }
+    int pos = 0;
+    for (int q = 0; q < NN; ++q) {
+      const int base = nodes[q] * B, sz = G - base < B ? G - base : B;
+      for (int i = 0; i < sz; ++i) mem[i] = base + i;
+      for (int j = sz - 1; j >= 1; --j) {
+        const int r = rm[base + j], t = mem[j];
+        mem[j] = mem[r];
+        mem[r] = t;
+      }
+      for (int i = 0; i < sz; ++i) out[pos++] = mem[i];
     }
   }
   __syncwarp();
@@ -714,7 +789,12 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
         if (P.send_rule == 1 && P.G > 1)
           keys_out[m] = philox(P.key0, P.key1, make_uint4((uint32_t)m, 0u, (uint32_t)(k + 1), P.tag | (ST_EXCH << 4) | 1u));
       }
-      if (warp == 0 && P.mode == MODE_ARNA && P.G > 1 && P.G <= RING_SMEM_G) {
+      if (warp == 0 && P.G > 1 && P.G <= RING_SMEM_G &&
+          (P.topology == TOPO_HYPERCUBE || (P.mode == MODE_ARNA && P.topology == TOPO_NODE_RING))) {
+        topology_for_step(P, t, (uint32_t)(k + 1), perm, rr, a.ds);
+        for (int p = lane; p < P.G; p += 32)
+          a.ring_next[(size_t)((k + 1) & 1) * a.ring_stride + P.group_off + p] = perm[p];
+      } else if (warp == 0 && P.mode == MODE_ARNA && P.G > 1 && P.G <= RING_SMEM_G) {
         ring_for_step(P, t, (uint32_t)(k + 1), perm, rr, a.ds);
         for (int p = lane; p < P.G; p += 32)
           a.ring_next[(size_t)((k + 1) & 1) * a.ring_stride + P.group_off + p] = perm[p];

@@ -42,6 +42,8 @@ def config_from_workload(wl: Workload, truth0=None, track_id: int = 0, record_an
     c.resample_rule = getattr(wl, "resample_rule", 0)
     c.ess_fraction = getattr(wl, "ess_fraction", 0.5)
     c.send_rule = getattr(wl, "send_rule", 0)
+    c.topology = getattr(wl, "topology", 0)
+    c.node_groups = max(1, getattr(wl, "node_groups", 1))
     return c
 
 

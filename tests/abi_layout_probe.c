@@ -17,7 +17,7 @@ int main(void) {
   F(pf_track_config, init_lo); F(pf_track_config, init_hi); F(pf_track_config, init_radius);
   F(pf_track_config, obs_model); F(pf_track_config, seed); F(pf_track_config, track_id);
   F(pf_track_config, record_ancestors); F(pf_track_config, resample_rule); F(pf_track_config, ess_fraction);
-  F(pf_track_config, send_rule);
+  F(pf_track_config, send_rule); F(pf_track_config, topology); F(pf_track_config, node_groups);
   printf("pf_step_stats sizeof %zu\n", sizeof(pf_step_stats));
   F(pf_step_stats, step); F(pf_step_stats, n_ex); F(pf_step_stats, pe_eff); F(pf_step_stats, log_c);
   F(pf_step_stats, log_Z); F(pf_step_stats, xhat); F(pf_step_stats, degenerate_groups);

@@ -76,6 +76,7 @@ def test_query_workspace_scales_with_particles(lib):
     ("track_id", 1 << 24, "track_id"), ("obs_model", 2, "obs_model"), ("G", 1025, "G must be"),
     ("Np", (1 << 20) + 1, "Np must be"), ("resample_rule", 2, "resample_rule"), ("ess_fraction", 1.5, "ess_fraction"),
     ("ess_fraction", float("nan"), "ess_fraction"), ("send_rule", 2, "send_rule"),
+    ("topology", 3, "topology"),
 ])
 def test_invalid_configs_are_rejected_on_the_host(lib, field, value, msg):
     with pytest.raises(B.PFError) as e:
@@ -83,6 +84,14 @@ def test_invalid_configs_are_rejected_on_the_host(lib, field, value, msg):
     assert e.value.status == B.PF_ERR_ARG
     assert msg in str(e.value)
     assert msg in B.pf_last_error(None)
+
+
+def test_node_ring_needs_node_groups(lib):
+    with pytest.raises(B.PFError) as e:
+        B.pf_query_workspace([_cfg(topology=B.PF_TOPO_NODE_RING, node_groups=0)], 4)
+    assert e.value.status == B.PF_ERR_ARG and "node_groups" in str(e.value)
+    assert B.pf_query_workspace([_cfg(topology=B.PF_TOPO_NODE_RING, node_groups=3)], 4) > 0
+    assert B.pf_query_workspace([_cfg(node_groups=0)], 4) > 0  # ignored by the other topologies
 
 
 def test_mixed_patch_radius_and_bad_history_rejected(lib):

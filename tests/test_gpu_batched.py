@@ -59,6 +59,8 @@ def test_batch_equals_tracks_run_alone(dev, mixed):
         wls[1] = wls[1].replace(resample_rule=1, ess_fraction=0.5)
         wls[4] = wls[4].replace(resample_rule=1, ess_fraction=0.8)
         wls[2] = wls[2].replace(send_rule=1)
+        wls[0] = wls[0].replace(topology=2)
+        wls[1] = wls[1].replace(topology=1, node_groups=2)
     seqs = [synth.make_sequence(wl) for wl in wls]
     frs = [torch.from_numpy(f).to(dev) for f, _ in seqs]
     cfgs = _configs(wls, seqs)

@@ -54,6 +54,10 @@ SMALL = [
     ("keyed_arna_ragged", synth.small_rna(G=5, Np=300, H=40, W=40, mode=synth.ARNA, ex_ratio=0.3, send_rule=1)),
     ("keyed_sharing_ess", synth.sharing(G=8, Np=700, H=64, W=64, mode=synth.ARNA, send_rule=1, resample_rule=1,
                                         ess_fraction=0.5)),
+    # exchange topologies of Sec. VI: node-aware random ring, hypercube dimension exchange
+    ("node_ring_arna", synth.sharing(G=10, Np=256, H=64, W=64, mode=synth.ARNA, topology=1, node_groups=3)),
+    ("hypercube_rna", synth.small_rna(G=8, Np=256, ex_ratio=0.25, topology=2)),
+    ("hypercube_arna_ragged", synth.sharing(G=6, Np=300, H=64, W=64, mode=synth.ARNA, topology=2, send_rule=1)),
 ]
 
 
