@@ -67,6 +67,9 @@ class Workload:
     send_rule: int = 0            # 0: systematic slot subsample, 1: keyed random permutation (Sec. III-C)
     topology: int = 0             # 0: ring (Sec. IV-B), 1: node-aware ring, 2: hypercube (Sec. VI)
     node_groups: int = 1          # topology 1: groups per node
+    cell: float = 0.0             # multi-object sequences: the spot's grid cell (size, origin)
+    cell_x: float = 0.0
+    cell_y: float = 0.0
 
     @property
     def N(self) -> int:
@@ -164,6 +167,54 @@ def render(wl: Workload, truth: np.ndarray, rng: np.random.Generator, noise: boo
         lam = wl.background + truth[k, 4] * np.outer(gy, gx)
         frames[k] = rng.poisson(lam).astype(np.float32) if noise else lam.astype(np.float32)
     return frames
+
+
+def multi_object(n_obj: int = 16, G: int = 16, Np: int = 4096, H: int = 256, W: int = 256, T: int = 30,
+                 mode: int = ARNA, seed: int = 0, data_seed: int = 0, cell: int = 64, vmax: float = 0.25,
+                 **kw) -> List[Workload]:
+    """Several spots in one sequence, one filter (track) per spot: spot i
+    starts at a seeded point of cell i of a grid of cell x cell pixel cells
+    (at least 14 px from the cell's edges) and drifts at constant velocity
+    of at most vmax px per frame, so patches of different spots stay apart
+    over T frames.  Every workload shares the frames (make_multi_sequence)."""
+    cols = W // cell
+    assert n_obj <= cols * (H // cell), "the frame holds fewer cells than spots"
+    return [Workload(name="multi_object_%dx%d_%dspots_G%dx%d" % (H, W, n_obj, G, Np), G=G, Np=Np, H=H, W=W, T=T,
+                     mode=mode, seed=seed, data_seed=data_seed * 1000 + i, vmax=vmax, cell=float(cell),
+                     cell_x=float(cell * (i % cols)), cell_y=float(cell * (i // cols))).replace(**kw)
+            for i in range(n_obj)]
+
+
+def make_multi_sequence(wls: List[Workload], noise: bool = True):
+    """(frames (T, H, W) float32 holding every spot, truths (n, T, 5)) for
+    multi_object workloads: each spot starts uniformly in its cell, at least
+    (14 + vmax T) px from the cell's edges."""
+    wl0 = wls[0]
+    truths = []
+    for wl in wls:
+        rng = np.random.default_rng(wl.data_seed)
+        m = 14.0 + wl.vmax * wl.T
+        assert wl.cell > 2 * m, "cells too small for the drift"
+        x0 = wl.cell_x + rng.uniform(m, wl.cell - m)
+        y0 = wl.cell_y + rng.uniform(m, wl.cell - m)
+        vx, vy = rng.uniform(-wl.vmax, wl.vmax, size=2)
+        tr = np.zeros((wl.T, 5))
+        tr[:, 0] = x0 + vx * np.arange(wl.T)
+        tr[:, 1] = y0 + vy * np.arange(wl.T)
+        tr[:, 2], tr[:, 3], tr[:, 4] = vx, vy, wl.amplitude
+        truths.append(tr)
+    truths = np.array(truths)
+    u = np.arange(wl0.W, dtype=np.float64)
+    v = np.arange(wl0.H, dtype=np.float64)
+    s2 = 2.0 * wl0.sigma_psf ** 2
+    rng = np.random.default_rng([wl0.data_seed, 7])
+    frames = np.empty((wl0.T, wl0.H, wl0.W), np.float32)
+    for k in range(wl0.T):
+        lam = np.full((wl0.H, wl0.W), wl0.background)
+        for tr in truths:
+            lam += tr[k, 4] * np.outer(np.exp(-(v - tr[k, 1]) ** 2 / s2), np.exp(-(u - tr[k, 0]) ** 2 / s2))
+        frames[k] = rng.poisson(lam).astype(np.float32) if noise else lam.astype(np.float32)
+    return frames, truths
 
 
 def make_sequence(wl: Workload, noise: bool = True, T: Optional[int] = None):

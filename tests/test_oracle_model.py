@@ -371,6 +371,21 @@ def test_small_workload_tracks_the_spot(ora):
     assert np.all(run.n_ex[1:] == 102) and run.n_ex[0] == 0
 
 
+def test_multi_object_track_follows_its_own_spot(ora):
+    """Several spots in one frame, one filter per spot: the oracle filter
+    started at a spot follows it (the other spots lie outside its patches)."""
+    wls = synth.multi_object(n_obj=4, G=2, Np=400, H=128, W=128, T=8, cell=64)
+    frames, truths = synth.make_multi_sequence(wls)
+    for t in (0, 3):
+        cfg = ora.cfg_from_workload(wls[t])
+        pop0 = ora.init_population(cfg, ora.INIT_POINT, truths[t][0])
+        run = ora.run(cfg, pop0, frames, wls[t].T)
+        err = np.sqrt(((run.xhat[:, :2] - truths[t][:, :2]) ** 2).sum(1).mean())
+        assert err < 0.6, (t, err)
+    d = min(np.hypot(*(truths[i, k, :2] - truths[j, k, :2])) for i in range(4) for j in range(i) for k in range(8))
+    assert d > 2 * (2 * 5 + 1)
+
+
 def test_init_samplers_ranges(ora):
     wl = synth.sharing(G=4, Np=2000, H=64, W=64)
     cfg = ora.cfg_from_workload(wl)
