@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <unordered_map>
 #include <mutex>
 #include <string>
 #include <tuple>
@@ -39,6 +40,7 @@ struct pf_handle {
   GroupState* gs = nullptr;
   GroupDesc* gd = nullptr;
   int4* tiles = nullptr;
+  int* frame_of = nullptr;  // per track: whose padded frame the step reads (tracks given the same frame share one)
   float4* pv[2] = {nullptr, nullptr};
   float* In[2] = {nullptr, nullptr};
   uint32_t* anc = nullptr;
@@ -140,7 +142,7 @@ QuantCoeffs make_qc() {
 }
 
 struct Layout {
-  size_t trk, ts, gs, gd, tiles, pv0, pv1, I0, I1, anc, lw, tp, ypad, hist, ghist, ring, ring_next, exo_next, keys_next,
+  size_t trk, ts, gs, gd, tiles, frame_of, pv0, pv1, I0, I1, anc, lw, tp, ypad, hist, ghist, ring, ring_next, exo_next, keys_next,
       tile_ctr, parent, ds,
       tmap, total;
   size_t rp_pv, rp_I, ck_pv, ck_I, ca_pv0, ca_pv1, ca_I0, ca_I1, lam_hist, lbar_hist, dlam, Dacc, grad, logz, seed;
@@ -253,6 +255,7 @@ Layout plan(const pf_track_config* c, int n, int history) {
   L.keys_next = take(sizeof(uint4) * 2 * (size_t)L.G_total);
   L.tile_ctr = take(sizeof(int));
   L.tiles = take(sizeof(int4) * L.n_tiles);
+  L.frame_of = take(sizeof(int) * (size_t)n);
   L.pv0 = take(sizeof(float4) * L.N_total);
   L.pv1 = take(sizeof(float4) * L.N_total);
   L.I0 = take(sizeof(float) * L.N_total);
@@ -330,20 +333,38 @@ cudaError_t mark(pf_handle* h, int kernel, cudaStream_t s) {
 
 // y = z - b into the padded frames, up to MAX_FRAMES_PER_LAUNCH tracks per
 // launch.  frames: n_tracks device pointers.
-cudaError_t prep_frames(pf_handle* h, const float* const* frames, cudaStream_t s) {
+// Tracks of one launch given the same frame (pointer, size and background)
+// share one padded copy, prepared once (several objects tracked in one
+// sequence); frame_of tells the propagate kernel which copy each reads.
+cudaError_t prep_frames(pf_handle* h, const float* const* frames, cudaStream_t s, bool share = true) {
   for (int t0 = 0; t0 < h->n_tracks; t0 += MAX_FRAMES_PER_LAUNCH) {
     const int nt = h->n_tracks - t0 < MAX_FRAMES_PER_LAUNCH ? h->n_tracks - t0 : MAX_FRAMES_PER_LAUNCH;
     FrameArgs a;
     a.trk = h->trk;
     a.ypad = h->ypad;
+    a.frame_of = h->frame_of;
     a.t0 = t0;
+    a.nt = nt;
     a.R = h->R;
-    int maxH = 1;
+    int maxH = 1, n_rep = 0;
+    std::unordered_map<const float*, int> first;
     for (int i = 0; i < nt; ++i) {
-      a.frames[i] = frames[t0 + i];
-      if (h->cfg[t0 + i].H > maxH) maxH = h->cfg[t0 + i].H;
+      const int t = t0 + i;
+      a.frames[i] = frames[t];
+      const pf_track_config& c = h->cfg[t];
+      auto it = first.find(frames[t]);
+      const bool same = it != first.end() && h->cfg[it->second].H == c.H && h->cfg[it->second].W == c.W &&
+                        h->tp[it->second].bg == h->tp[t].bg;
+      if (same && share) {
+        a.share[i] = it->second;
+      } else {
+        first[frames[t]] = t;
+        a.share[i] = t;
+        a.rep[n_rep++] = (short)i;
+        if (c.H > maxH) maxH = c.H;
+      }
     }
-    cudaError_t e = launch_frame_prep(a, nt, maxH > 4096 ? 4096 : maxH, h->pdl, s);
+    cudaError_t e = launch_frame_prep(a, n_rep, maxH > 4096 ? 4096 : maxH, h->pdl, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -368,7 +389,7 @@ K1Args k1_args(const pf_handle* h) {
   K1Args a{h->trk, h->tiles, h->n_tiles, h->gs, h->ts, h->ds, h->pv[0], h->pv[1], h->In[0], h->In[1],
            h->anc, h->parent, h->history, h->lw, h->carry_any ? h->lw + lw_stride(h->N_total) : h->lw, h->tile_part, h->ypad, h->tmaps, h->ring_next,
            h->G_total, h->exo_next, h->hist, h->ghist, h->tile_ctr, h->n_ring_blocks, h->n_tracks, TrackParams{}, 0,
-           nullptr, h->test_withhold_copy ? 1 : 0, h->variants ? 1 : 0, h->keys_next, CUtensorMap{}};
+           nullptr, h->test_withhold_copy ? 1 : 0, h->variants ? 1 : 0, h->keys_next, h->frame_of, CUtensorMap{}};
   a.p0 = h->tp[0];
   return a;
 }
@@ -476,6 +497,7 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
   h->keys_next = (uint4*)(w + L.keys_next);
   h->tile_ctr = (int*)(w + L.tile_ctr);
   h->tiles = (int4*)(w + L.tiles);
+  h->frame_of = (int*)(w + L.frame_of);
   h->pv[0] = (float4*)(w + L.pv0);
   h->pv[1] = (float4*)(w + L.pv1);
   h->In[0] = (float*)(w + L.I0);
@@ -607,11 +629,14 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
     if (!ok) h->tmaps = nullptr;
     if (ok) h->encode = fn;
   }
+  std::vector<int> ident(n_tracks);  // every track reads its own padded frame until a step shares one
+  for (int t = 0; t < n_tracks; ++t) ident[t] = t;
   cudaError_t e;
   if ((e = cudaMemsetAsync(w, 0, L.total, s)) != cudaSuccess) { pf_destroy(h); return cuda_fail(nullptr, e, "cudaMemsetAsync"); }
   if ((e = cudaMemcpyAsync(h->trk, tp.data(), sizeof(TrackParams) * n_tracks, cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemcpyAsync(h->gd, gd.data(), sizeof(GroupDesc) * gd.size(), cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemcpyAsync(h->tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(h->frame_of, ident.data(), sizeof(int) * ident.size(), cudaMemcpyHostToDevice, s)) ||
       (h->tmaps && (e = cudaMemcpyAsync(h->tmaps, maps.data(), sizeof(CUtensorMap) * n_tracks,
                                         cudaMemcpyHostToDevice, s)))) {
     pf_destroy(h);
@@ -703,7 +728,7 @@ pf_status pf_step(pf_handle* h, const float* const* frames, void* stream) {
 static cudaError_t launch_frames_table(pf_handle* h, const float* const* table, int T_table, cudaStream_t s) {
   int maxH = 1;
   for (int t = 0; t < h->n_tracks; ++t) maxH = h->cfg[t].H > maxH ? h->cfg[t].H : maxH;
-  FrameTableArgs fa{h->trk, h->ypad, h->R, table, T_table, h->n_tracks, h->ts, h->ds};
+  FrameTableArgs fa{h->trk, h->ypad, h->R, table, T_table, h->n_tracks, h->ts, h->ds, h->frame_of};
   return launch_frame_prep_table(fa, maxH > 4096 ? 4096 : maxH, h->pdl, s);
 }
 
@@ -1102,7 +1127,7 @@ pf_status pf_backward(pf_handle* h, const float* const* frames_host, int32_t T, 
   InitArgs ia{h->trk, h->tiles, h->n_tiles, N, nullptr, slot_pv(0), slot_I(0)};
   if ((e = launch_init(ia, grid, s)) != cudaSuccess) return cuda_fail(h, e, "k_init");
   for (int k = 0; k < T; ++k) {
-    if ((e = prep_frames(h, frames_host + (long long)k * h->n_tracks, s)) != cudaSuccess)
+    if ((e = prep_frames(h, frames_host + (long long)k * h->n_tracks, s, false)) != cudaSuccess)
       return cuda_fail(h, e, "k_frame_prep");
     ReplayArgs ra{};
     ra.trk = h->trk; ra.tiles = h->tiles; ra.n_tiles = h->n_tiles; ra.parent = h->parent; ra.history = h->history;
@@ -1140,7 +1165,7 @@ pf_status pf_backward(pf_handle* h, const float* const* frames_host, int32_t T, 
       if ((e = launch_replay(ra, h->R, grid, s)) != cudaSuccess) return cuda_fail(h, e, "k_replay");
     }
     for (int k = k1 - 1; k >= k0; --k) {
-      if ((e = prep_frames(h, frames_host + (long long)k * h->n_tracks, s)) != cudaSuccess)
+      if ((e = prep_frames(h, frames_host + (long long)k * h->n_tracks, s, false)) != cudaSuccess)
         return cuda_fail(h, e, "k_frame_prep");
       AdjointArgs aa{};
       aa.trk = h->trk; aa.tiles = h->tiles; aa.n_tiles = h->n_tiles; aa.parent = h->parent;

@@ -87,7 +87,9 @@ __global__ void __launch_bounds__(K1_THREADS) k_init(InitArgs a) {
 __global__ void k_frame_prep(FrameArgs a) {
   grid_dep_wait();
   grid_dep_launch();
-  const int tt = blockIdx.y;
+  if (blockIdx.x == 0 && blockIdx.y == 0)
+    for (int i = threadIdx.x; i < a.nt; i += blockDim.x) a.frame_of[a.t0 + i] = a.share[i];
+  const int tt = a.rep[blockIdx.y];
   const TrackParams& P = a.trk[a.t0 + tt];
   const float* __restrict__ z = a.frames[tt];
   float* __restrict__ yp = a.ypad + P.ypad_off;
@@ -111,6 +113,7 @@ __global__ void k_frame_prep_table(FrameTableArgs a) {
     if (t == 0 && blockIdx.x == 0 && threadIdx.x == 0) set_error(a.ds, ERR_INDEX, 5u, (uint32_t)k, 0u);
     return;
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.frame_of[t] = t;
   const TrackParams& P = a.trk[t];
   const float* __restrict__ z = a.table[(long long)k * a.n_tracks + t];
   float* __restrict__ yp = a.ypad + P.ypad_off;
@@ -817,6 +820,10 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
 
   auto run_tile = [&](const TrackParams& P, const int4 td) {
     const int g = td.y, Np = P.Np;
+    // the padded frame to read: the track's own, or the copy of a track
+    // given the same frame this step
+    const int ft = SINGLE ? 0 : (a.frame_of ? __ldg(&a.frame_of[td.x]) : td.x);
+    const long long ypad_off = (SINGLE || ft == td.x) ? P.ypad_off : a.trk[ft].ypad_off;
     const GroupState* __restrict__ gs = a.grp + P.group_off;
     const int nex = SINGLE ? nex1 : (k > 0 ? a.ts[td.x].n_ex : 0);
     // the group's exchange partners and weight offsets, once per tile
@@ -939,7 +946,7 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
           if (raw)
             tma_load_2d(&s_roi[0][b * ROI_W * ROI_BOX_H], &a.zmap, u0 - PAD, vmin - PAD + b * ROI_BOX_H, &s_bar);
           else
-            tma_load_2d(&s_roi[0][b * ROI_W * ROI_BOX_H], a.tmaps + td.x, u0, vmin + b * ROI_BOX_H, &s_bar);
+            tma_load_2d(&s_roi[0][b * ROI_W * ROI_BOX_H], a.tmaps + ft, u0, vmin + b * ROI_BOX_H, &s_bar);
         }
       }
       const bool ok = mbar_wait(&s_bar, phase);
@@ -1008,7 +1015,7 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
                    : patch_ss_raw<R, false>(a.zraw, P.W, P.H, P.bg, pu[q] - PAD, pv[q] - PAD, gxI, dy, P.c_psf,
                                             P.kappa);
         } else {
-          const float* base = a.ypad + P.ypad_off + (long long)pv[q] * P.pitch + pu[q];
+          const float* base = a.ypad + ypad_off + (long long)pv[q] * P.pitch + pu[q];
           ss = frame_model ? patch_ss<R, true, false>(base, P.pitch, gxI, dy, P.c_psf, P.kappa)
                            : patch_ss<R, false, false>(base, P.pitch, gxI, dy, P.c_psf, P.kappa);
         }

@@ -21,9 +21,16 @@ struct InitArgs {
 struct FrameArgs {
   const TrackParams* trk;
   float* ypad;
+  int* frame_of;       // per track: the track whose padded frame holds its frame this step
   int t0;              // first track of this launch
+  int nt;              // tracks of this launch
   int R;
   const float* frames[MAX_FRAMES_PER_LAUNCH];
+  // tracks given the same frame (same pointer, size and background) share
+  // one padded copy: rep[y] is the track that blockIdx.y prepares, and
+  // share[i] the track (absolute) whose copy track t0 + i reads
+  short rep[MAX_FRAMES_PER_LAUNCH];
+  int share[MAX_FRAMES_PER_LAUNCH];
 };
 
 struct FrameTableArgs {
@@ -35,6 +42,7 @@ struct FrameTableArgs {
   int n_tracks;
   const TrackState* ts;
   DevState* ds;
+  int* frame_of;              // set to the identity: every track reads its own copy
 };
 
 struct K1Args {
@@ -75,6 +83,7 @@ struct K1Args {
   int variants;              // 1: some track resamples by Alg. 1's test (groups may carry weights) or
                              // uses keyed send sets: launches the variants instance (frames prepared)
   uint4* keys_next;          // two buffers (by step parity) of G_total: keyed send-permutation keys of step k+1
+  const int* frame_of;       // per track: the track whose padded frame to read this step, or nullptr (its own)
   CUtensorMap zmap;
 };
 
