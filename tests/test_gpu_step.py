@@ -54,6 +54,15 @@ SMALL = [
     ("keyed_arna_ragged", synth.small_rna(G=5, Np=300, H=40, W=40, mode=synth.ARNA, ex_ratio=0.3, send_rule=1)),
     ("keyed_sharing_ess", synth.sharing(G=8, Np=700, H=64, W=64, mode=synth.ARNA, send_rule=1, resample_rule=1,
                                         ess_fraction=0.5)),
+    # limits: the most groups per track, the patch radii 1 and 7, frames narrower than a staging
+    # box or with rows off the 16-byte grid (no TMA descriptor over the caller's frame), one
+    # particle per group
+    ("max_groups", synth.small_rna(G=1024, Np=16, H=64, W=64, mode=synth.ARNA, ex_ratio=0.5)),
+    ("patch_r7", synth.small_rna(G=2, Np=200, patch_radius=7)),
+    ("patch_r1", synth.small_rna(G=3, Np=150, patch_radius=1, mode=synth.ARNA)),
+    ("tiny_frame", synth.small_rna(G=2, Np=128, H=12, W=12, margin=3.0, vmax=0.2)),
+    ("odd_width", synth.small_rna(G=3, Np=200, H=40, W=61)),
+    ("one_particle_groups", synth.small_rna(G=5, Np=1, mode=synth.ARNA)),
     # exchange topologies of Sec. VI: node-aware random ring, hypercube dimension exchange
     ("node_ring_arna", synth.sharing(G=10, Np=256, H=64, W=64, mode=synth.ARNA, topology=1, node_groups=3)),
     ("hypercube_rna", synth.small_rna(G=8, Np=256, ex_ratio=0.25, topology=2)),
@@ -70,6 +79,13 @@ def test_small_configs_match_oracle(dev, name, wl):
     elif name in ("ess_rna", "ess_arna_sharing"):
         # the test decided both ways over the run
         assert any(r["resampled"] < wl.G for r in rep) and any(r["resampled"] > 0 for r in rep), rep
+
+
+def test_largest_group_matches_oracle(dev):
+    """One group of 2^20 particles (the largest N_p): resampling across an
+    8-CTA cluster with streamed sub-chunks."""
+    rep = _run(dev, synth.small_rna(G=1, Np=1 << 20, H=128, W=128, mode=synth.ARNA), 2)
+    assert len(rep) == 2
 
 
 @pytest.mark.parametrize("mode", [synth.RNA, synth.ARNA])
