@@ -502,13 +502,14 @@ __device__ void ring_for_step(const TrackParams& P, int track, uint32_t k, int* 
 }
 
 // The exchange pattern of step k for the other topologies (Sec. VI), by one
-// warp, into out[0 .. G): TOPO_NODE_RING (ARNA): nodes of node_groups
+// warp, into out[0 .. G) (not inlined: leading blocks only, and inlining it
+// slowed the propagate kernel's tiles by ~1 us through code size): TOPO_NODE_RING (ARNA): nodes of node_groups
 // consecutive groups, the ring visiting the nodes in a Fisher-Yates order
 // (draw j from RING call 1, index j) and each node's groups in a
 // Fisher-Yates order (draw j from RING call 2, index n node_groups + j);
 // TOPO_HYPERCUBE: out[g] = g's partner g xor 2^d (g itself when that is
 // >= G), d = (k - 1) mod D (RNA) or drawn from RING call 3, index 0 (ARNA).
-__device__ void topology_for_step(const TrackParams& P, int track, uint32_t k, int* __restrict__ out,
+__device__ __noinline__ void topology_for_step(const TrackParams& P, int track, uint32_t k, int* __restrict__ out,
                                   int* __restrict__ sh, DevState* ds) {
   const int lane = threadIdx.x & 31;
   const int G = P.G;
