@@ -25,7 +25,8 @@
  *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
  *     default stream.  Calls enqueue work and return without synchronising,
  *     except pf_estimate, pf_exchange_stats and pf_history, which copy to the
- *     host and wait for the handle's last stream.
+ *     host and wait for the handle's last stream (pf_estimate_async only
+ *     enqueues its copies).
  *   - Every call returns a pf_status; nothing is thrown across the ABI.  On
  *     failure the text of the error is available from pf_last_error.
  *   - The caller owns all device memory (workspace, frames, outputs); the
@@ -245,6 +246,17 @@ pf_status pf_autotune(pf_handle* h, const float* const* frames_host, int32_t* k1
  * weight: its values are NaN / -inf), PF_ERR_DEVICE / PF_ERR_TIMEOUT (the
  * kernels reported an error), PF_ERR_CUDA. */
 pf_status pf_estimate(pf_handle* h, float* xhat_host, double* log_Z_host);
+
+/* pf_estimate without waiting: enqueue on `stream` (the stream the steps
+ * run on) the completion of the last step's statistics and copies of x^
+ * (n_tracks x 5 floats) and log Z (n_tracks doubles) into the caller's host
+ * buffers, and return.  The values are there once the stream has passed
+ * this point (the caller's event or synchronisation); with page-locked host
+ * buffers the copies overlap later work, so a stream of frames can be
+ * filtered with the next frame's upload and the last estimate's read-back
+ * in flight.  Degenerate tracks and device errors are reported by the next
+ * synchronising call.  Errors: PF_ERR_ARG, PF_ERR_STATE, PF_ERR_CUDA. */
+pf_status pf_estimate_async(pf_handle* h, float* xhat_host, double* log_Z_host, void* stream);
 
 /* Statistics of step `step` (< steps run, and among the last `history`) of
  * track `track`; optional per-group arrays (length G, may be NULL):

@@ -23,7 +23,8 @@ STATUS_NAMES = {0: "PF_OK", 1: "PF_ERR_ARG", 2: "PF_ERR_STATE", 3: "PF_ERR_CUDA"
                 5: "PF_ERR_DEGENERATE", 6: "PF_ERR_TIMEOUT", 7: "PF_ERR_DEVICE"}
 
 # Every symbol include/pfarna.h declares.
-EXPORTS = ("pf_abi_version", "pf_query_workspace", "pf_init", "pf_step", "pf_estimate", "pf_exchange_stats",
+EXPORTS = ("pf_abi_version", "pf_query_workspace", "pf_init", "pf_step", "pf_estimate", "pf_estimate_async",
+           "pf_exchange_stats",
            "pf_history", "pf_particles", "pf_resample_workspace", "pf_resample", "pf_resample_noalloc",
            "pf_profile_enable", "pf_profile_read", "pf_set_theta", "pf_reset", "pf_backward", "pf_step_table",
            "pf_graph_step", "pf_autotune", "pf_checkpoint_bytes", "pf_save", "pf_load", "pf_destroy",
@@ -86,6 +87,7 @@ def load():
                           C.POINTER(_P)]
     L.pf_step.argtypes = [_P, C.POINTER(_P), _P]
     L.pf_estimate.argtypes = [_P, _P, _P]
+    L.pf_estimate_async.argtypes = [_P, _P, _P, _P]
     L.pf_exchange_stats.argtypes = [_P, C.c_int32, C.c_int32, C.POINTER(pf_step_stats), _P, _P, _P, _P]
     L.pf_history.argtypes = [_P, C.c_int32, C.c_int32, C.c_int32, C.POINTER(pf_step_stats)]
     L.pf_particles.argtypes = [_P, C.c_int32, _P, _P, _P, _P, _P]
@@ -149,6 +151,10 @@ def pf_estimate(handle: int, xhat_host_ptr, logZ_host_ptr) -> int:
     if st not in (PF_OK, PF_ERR_DEGENERATE):
         _check(st, "pf_estimate", handle)
     return st
+
+
+def pf_estimate_async(handle: int, xhat_host_ptr, logZ_host_ptr, stream) -> None:
+    _check(load().pf_estimate_async(handle, xhat_host_ptr, logZ_host_ptr, stream), "pf_estimate_async", handle)
 
 
 def pf_exchange_stats(handle: int, track: int, step: int, ring_ptr=None, logW_ptr=None, xhat_ptr=None,

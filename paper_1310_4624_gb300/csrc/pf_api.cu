@@ -919,6 +919,29 @@ pf_status pf_estimate(pf_handle* h, float* xhat, double* logZ) {
   return PF_OK;
 }
 
+pf_status pf_estimate_async(pf_handle* h, float* xhat, double* logZ, void* stream) {
+  NvtxRange nvtx_range("pf_estimate_async");
+  if (!h) return fail(nullptr, PF_ERR_ARG, "handle is NULL");
+  if (!xhat && !logZ) return fail(h, PF_ERR_ARG, "no output buffer");
+  if (h->steps_run == 0) return fail(h, PF_ERR_STATE, "no step has run");
+  if (h->failed) return fail(h, PF_ERR_STATE, "handle failed earlier: " + h->err);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (h->finish_pending) {
+    if ((e = launch_finish(global_args(h, 1), h->n_tracks, s)) != cudaSuccess) return cuda_fail(h, e, "k_finish");
+    h->finish_pending = false;
+  }
+  // one strided copy per field across the tracks' states
+  if (xhat && (e = cudaMemcpy2DAsync(xhat, 5 * sizeof(float), &h->ts[0].xhat[0], sizeof(TrackState), 5 * sizeof(float),
+                                     h->n_tracks, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(h, e, "copying estimates");
+  if (logZ && (e = cudaMemcpy2DAsync(logZ, sizeof(double), &h->ts[0].log_Z, sizeof(TrackState), sizeof(double),
+                                     h->n_tracks, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(h, e, "copying log Z");
+  h->last_stream = s;
+  return PF_OK;
+}
+
 static pf_status check_step(pf_handle* h, int track, int step) {
   if (track < 0 || track >= h->n_tracks) return fail(h, PF_ERR_ARG, "track out of range");
   if (step < 0 || step >= h->steps_run) return fail(h, PF_ERR_STATE, "step has not run");
