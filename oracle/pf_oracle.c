@@ -27,8 +27,8 @@
  *
  * Parity status: every exported function is pinned by a test against a
  * closed form, an invariant, an installed library routine or brute force,
- * except the initial-population samplers (ora_init), which are pinned only
- * by range and moment checks ("parity partially pinned").
+ * except the initial-population samplers (ora_init), which are pinned by
+ * Kolmogorov-Smirnov tests against their laws (statistically).
  *
  * Build: plain C11, no contraction of a*b+c into fma (-ffp-contract=off) so
  * that x86-64 and AArch64 hosts give identical results.

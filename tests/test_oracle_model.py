@@ -402,6 +402,32 @@ def test_init_samplers_ranges(ora):
         assert abs(rest[d].mean() - (lo[d] + hi[d]) / 2) < 0.05 * (hi[d] - lo[d])
 
 
+def test_init_samplers_follow_their_distributions(ora):
+    """Kolmogorov-Smirnov against the exact laws: uniform components in the
+    box (INIT_UNIFORM, and the groups >= 1 of INIT_SHARING); in group 0's
+    disc, (r / R)^2 and the angle uniform on [0, 1) and [0, 2 pi), r and the
+    angle independent; POINT puts every particle at x0."""
+    stats = pytest.importorskip("scipy.stats")
+    wl = synth.sharing(G=3, Np=20000, H=64, W=64, seed=17)
+    cfg = ora.cfg_from_workload(wl)
+    x0 = np.array([30.0, 20.0, 0.5, -0.5, 10.0])
+    kind, _, lo, hi, rad = synth.init_arrays(wl, x0)
+    pop = ora.init_population(cfg, kind, x0, lo, hi, rad)
+    g0 = pop[:, :20000]
+    r2 = ((g0[0] - 30) ** 2 + (g0[1] - 20) ** 2) / rad ** 2
+    th = np.mod(np.arctan2(g0[1] - 20, g0[0] - 30), 2 * np.pi) / (2 * np.pi)
+    assert stats.kstest(r2, "uniform").pvalue > 1e-3
+    assert stats.kstest(th, "uniform").pvalue > 1e-3
+    assert abs(np.corrcoef(r2, th)[0, 1]) < 0.03
+    rest = pop[:, 20000:]
+    for d in range(5):
+        assert stats.kstest((rest[d] - lo[d]) / (hi[d] - lo[d]), "uniform").pvalue > 1e-3, d
+    c = np.corrcoef(rest)
+    assert np.all(np.abs(c - np.eye(5)) < 0.03)
+    pt = ora.init_population(cfg, ora.INIT_POINT, x0)
+    assert np.array_equal(pt, np.repeat(x0[:, None], pt.shape[1], axis=1))
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_exchange_preserves_the_weighted_population(ora, mode):
     """Exchanged particles carry their origin group's weight (Alg. 2/3 steps
