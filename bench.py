@@ -52,12 +52,19 @@ ALG_BYTES = 48          # HBM bytes of the whole step per particle
 
 
 def kernel_source_hash() -> str:
-    """sha256 of the kernel sources; ncu figures in profiles/ are tied to it."""
+    """sha256 of the kernel sources' code (comments and blank lines left
+    out, so that editing a comment keeps a profile valid); ncu figures in
+    profiles/ are tied to it."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ("pf_kernels.cu", "pf_device.cuh", "pf_math.cuh", "pf_launch.h"):
-        with open(os.path.join(ROOT, "paper_1310_4624_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1310_4624_gb300", "csrc", f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        code = "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+        h.update(code.encode())
     return h.hexdigest()[:16]
 
 

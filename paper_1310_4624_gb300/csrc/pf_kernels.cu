@@ -38,7 +38,7 @@ namespace cg = cooperative_groups;
 
 namespace pf {
 
-// ===================================================================== K0
+// ========================================================= initial population
 // Initial population (Sec. V tracking / information-sharing modes), drawn
 // from Philox stream INIT into the buffer step 0 reads.
 __global__ void __launch_bounds__(K1_THREADS) k_init(InitArgs a) {
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(K1_THREADS) k_init(InitArgs a) {
   }
 }
 
-// ===================================================================== K8
+// ========================================================= frame preparation
 // y = z - b into the interior of the zero-padded frame; the padding (2R+1
 // pixels on each side, zeroed once at init) stands for "outside the image
 // counts as background".
@@ -126,7 +126,7 @@ __global__ void k_frame_prep_table(FrameTableArgs a) {
   }
 }
 
-// ===================================================================== K5
+// ================================================================ global step
 // Per track: the master PE's reduction (Alg. 3 steps 9-10) and weight carry
 // (step 8) for step k, then ring order (step 1) and exchange count (step 2)
 // for step k+1.  G-sized; the exchange count is decided in FP64.
@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(K1_THREADS) k_finish(GlobalArgs a) {
   finish_step<K1_THREADS>(a, blockIdx.x, sc);
 }
 
-// ===================================================================== K1
+// ============================================================ propagate + weight
 // Fisher-Yates ring order of step k (Sec. IV-B, Alg. 3 step 1) for one
 // track, by one warp: the bounded draws r_j in [0, j] in parallel, the
 // descending swaps by lane 0 in shared memory.
@@ -1095,7 +1095,7 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
   }
 }
 
-// ===================================================================== K3
+// ==================================================================== resample
 // Number of outputs j in [0, Np) with (j 2^32 + u) Q < S Np 2^32: an FP32
 // estimate, then exact 128-bit corrections (the estimate is within 1).
 // #{j in [0, Np) : T_j < S}: an FP32 estimate, then exact corrections.
