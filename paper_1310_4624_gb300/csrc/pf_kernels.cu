@@ -613,9 +613,12 @@ __device__ __forceinline__ void tma_load_2d(float* dst, const CUtensorMap* map, 
       : "memory");
 }
 
-// Slot j of group g takes particle src_j of the predecessor group (true) or
-// its own slot j (false); exchange_source with the group's exchange offsets
-// o_r (receiver) and o_s (sender) hoisted out of the particle loop.
+// Systematic send sets (Sec. III-C): slot j of group g takes the
+// predecessor's slot src_j (true) when j is the t-th send slot
+// floor((t Np + o_r) / N_ex) of the receiver, src_j = floor((t Np + o_s) /
+// N_ex) being the sender's t-th; else it keeps its own slot j (false).  The
+// group's exchange offsets o_r (receiver) and o_s (sender) are hoisted out
+// of the particle loop.
 __device__ __forceinline__ bool exchange_from_pred(int j, int Np, int nex, uint32_t o_r, uint32_t o_s,
                                                    unsigned long long mNp, int& src_j) {
   src_j = j;
