@@ -192,6 +192,8 @@ pf_status pf_query_workspace(const pf_track_config* cfg, int32_t n_tracks, int32
  * may start while the previous kernel in the stream drains, and waits for
  * its completion before touching memory); the environment variable
  * PFARNA_PDL=0 at pf_init selects plain stream serialisation instead.
+ * PFARNA_RS_THREADS=128 or 512 at pf_init forces the resampler's CTA size
+ * (by default 128 when every group has at most 1024 particles, else 512).
  * Results are identical either way.  PFARNA_TEST_WITHHOLD_COPY=1 at pf_init
  * (failure-detection tests only) makes the propagate kernel issue no
  * frame-staging copy, so its bounded wait (0.2 s) runs out: the step ends
@@ -230,7 +232,7 @@ pf_status pf_graph_step(pf_handle* h, const float* const* table_dev, int32_t T_t
 /* One pf_step that also chooses the launch shapes of the handle's later
  * steps: the propagate kernel's grid (SM count x resident CTAs per SM, 1 ..
  * the occupancy limit) and the resampler's thread-block cluster size
- * (1, 2, 4, 8), each the fastest of the candidates timed with CUDA events
+ * (1, 2, 4, 8) and CTA size (512 or 128 threads), each the fastest of the candidates timed with CUDA events
  * on this step's data (the propagate candidates first: it is idempotent
  * until a resampler replaces the ancestors it reads).  Results
  * are cached per problem shape for the process.  Synchronises the stream.

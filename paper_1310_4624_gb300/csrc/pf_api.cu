@@ -29,6 +29,7 @@ struct pf_handle {
   long long N_total = 0;
   int G_total = 0, n_tiles = 0;
   int k1_grid = 1, rs_cluster = 1;
+  int rs_threads = RS_THREADS;  // resampler CTA: RS_THREADS, or RS_THREADS_SMALL for small groups
   int steps_run = 0;
   int failed = 0;
   cudaStream_t last_stream = nullptr;
@@ -676,7 +677,26 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
     if (cfg[t].resample_rule == PF_RESAMPLE_ESS) h->carry_any = true;
     if (cfg[t].resample_rule == PF_RESAMPLE_ESS || cfg[t].send_rule == PF_SEND_KEYED) h->variants = true;
   }
-  h->rs_cluster = resample_cluster(cfg[0].Np, n_tracks == 1);
+  {
+    // resampler shape: small CTAs (eight per SM) when every group fits one
+    // of their sub-chunks; clusters sized to the largest group, as long as
+    // the launch stays within about two waves of two CTAs per SM
+    int maxNp = 1;
+    for (int t = 0; t < n_tracks; ++t) maxNp = cfg[t].Np > maxNp ? cfg[t].Np : maxNp;
+    h->rs_threads = maxNp <= RS_THREADS_SMALL * RS_ITEMS ? RS_THREADS_SMALL : RS_THREADS;
+    if (n_tracks == 1) {
+      h->rs_cluster = resample_cluster(cfg[0].Np, true);
+    } else {
+      const int sub = h->rs_threads * RS_ITEMS;
+      int c = (maxNp + sub - 1) / sub;
+      c = c < 1 ? 1 : (c > 8 ? 8 : c);
+      while (c > 1 && (long long)h->G_total * c > 4LL * h->sms) c >>= 1;
+      h->rs_cluster = c;
+    }
+    const char* rt = std::getenv("PFARNA_RS_THREADS");  // "128" / "512": force the resampler's CTA size
+    if (rt && std::atoi(rt) == RS_THREADS_SMALL) h->rs_threads = RS_THREADS_SMALL;
+    if (rt && std::atoi(rt) == RS_THREADS) h->rs_threads = RS_THREADS;
+  }
 
   InitArgs ia{h->trk, h->tiles, h->n_tiles, h->N_total, user_state, h->pv[1], h->In[1]};
   if ((e = launch_init(ia, h->k1_grid, s)) != cudaSuccess) { pf_destroy(h); return cuda_fail(nullptr, e, "k_init"); }
@@ -693,7 +713,7 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
 static cudaError_t launch_step_kernels(pf_handle* h, cudaStream_t s) {
   cudaError_t e = launch_propagate(k1_args(h), h->R, h->k1_grid + h->n_ring_blocks, h->pdl, s);
   if (e != cudaSuccess) return e;
-  return launch_resample(resample_args(h, 1), h->G_total, h->rs_cluster, h->pdl, s);
+  return launch_resample(resample_args(h, 1), h->G_total, h->rs_cluster, h->pdl, s, h->rs_threads);
 }
 
 pf_status pf_step(pf_handle* h, const float* const* frames, void* stream) {
@@ -716,7 +736,7 @@ pf_status pf_step(pf_handle* h, const float* const* frames, void* stream) {
     return cuda_fail(h, e, "k_propagate_weight");
   if ((e = mark(h, PF_KERNEL_PROPAGATE_WEIGHT, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
   if ((e = mark(h, PF_KERNEL_RESAMPLE, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
-  if ((e = launch_resample(resample_args(h, 1), h->G_total, h->rs_cluster, h->pdl, s)) != cudaSuccess)
+  if ((e = launch_resample(resample_args(h, 1), h->G_total, h->rs_cluster, h->pdl, s, h->rs_threads)) != cudaSuccess)
     return cuda_fail(h, e, "k_resample");
   if ((e = mark(h, PF_KERNEL_RESAMPLE, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
   h->steps_run += 1;
@@ -793,7 +813,7 @@ pf_status pf_graph_step(pf_handle* h, const float* const* table_dev, int32_t T_t
 // Autotuner results by problem shape (tracks, particles, groups, largest
 // group, SMs): propagate grid and resampler cluster size.
 static std::mutex g_tune_mutex;
-static std::map<std::tuple<int, long long, int, int, int>, std::pair<int, int>> g_tune_cache;
+static std::map<std::tuple<int, long long, int, int, int>, std::tuple<int, int, int>> g_tune_cache;
 
 pf_status pf_autotune(pf_handle* h, const float* const* frames, int32_t* k1_grid_out, int32_t* cluster_out,
                       void* stream) {
@@ -814,8 +834,9 @@ pf_status pf_autotune(pf_handle* h, const float* const* frames, int32_t* k1_grid
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      h->k1_grid = it->second.first;
-      h->rs_cluster = it->second.second;
+      h->k1_grid = std::get<0>(it->second);
+      h->rs_cluster = std::get<1>(it->second);
+      h->rs_threads = std::get<2>(it->second);
       cached = true;
     }
   }
@@ -857,18 +878,19 @@ pf_status pf_autotune(pf_handle* h, const float* const* frames, int32_t* k1_grid
       }
       if (grid == h->n_tiles) break;
     }
-    int best_c = h->rs_cluster;
+    int best_c = h->rs_cluster, best_t = h->rs_threads;
     best = 1e30f;
-    if (e == cudaSuccess)
-      for (int c = 1; c <= 8; c *= 2) {
+    for (int nt : {RS_THREADS, RS_THREADS_SMALL})
+      for (int c = 1; c <= 8 && e == cudaSuccess; c *= 2) {
         const ResampleArgs ra = resample_args(h, 0);
         float ms = 0.0f;
         for (int rep = 0; rep < 2; ++rep)
-          if ((e = time_it([&] { return launch_resample(ra, h->G_total, c, false, s); }, ms)) != cudaSuccess) break;
+          if ((e = time_it([&] { return launch_resample(ra, h->G_total, c, false, s, nt); }, ms)) != cudaSuccess) break;
         if (e != cudaSuccess) break;
         if (ms < best) {
           best = ms;
           best_c = c;
+          best_t = nt;
         }
       }
     cudaEventDestroy(e0);
@@ -876,8 +898,9 @@ pf_status pf_autotune(pf_handle* h, const float* const* frames, int32_t* k1_grid
     if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
     h->k1_grid = best_grid;
     h->rs_cluster = best_c;
+    h->rs_threads = best_t;
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tune_cache[key] = {best_grid, best_c};
+    g_tune_cache[key] = std::make_tuple(best_grid, best_c, best_t);
   }
   // Complete the step with the chosen shapes.  When candidates were timed,
   // the propagate candidates (which run first) have left this step's states
@@ -885,7 +908,7 @@ pf_status pf_autotune(pf_handle* h, const float* const* frames, int32_t* k1_grid
   // the propagate kernel reads, so only the resampler runs again, now with
   // the global step.
   e = cached ? launch_step_kernels(h, s)
-             : launch_resample(resample_args(h, 1), h->G_total, h->rs_cluster, false, s);
+             : launch_resample(resample_args(h, 1), h->G_total, h->rs_cluster, false, s, h->rs_threads);
   if (e != cudaSuccess) return cuda_fail(h, e, "step kernels");
   h->steps_run += 1;
   h->finish_pending = true;
@@ -1249,7 +1272,7 @@ pf_status pf_profile_read(pf_handle* h, int32_t n, int64_t* launches, double* to
 // Checkpoint: a header, then the workspace except the TMA descriptors.
 struct CheckpointHeader {
   unsigned long long magic, sig, ws_total;
-  int32_t abi, steps_run, finish_pending, k1_grid, rs_cluster, pad;
+  int32_t abi, steps_run, finish_pending, k1_grid, rs_cluster, rs_threads;
 };
 static const unsigned long long kCheckpointMagic = 0x6b70635f666e7270ull;  // "prnf_cpk"
 
@@ -1266,7 +1289,7 @@ pf_status pf_save(pf_handle* h, void* host, size_t bytes, void* stream) {
   if (bytes < need) return fail(h, PF_ERR_ARG, "checkpoint buffer too small");
   cudaStream_t s = (cudaStream_t)stream;
   CheckpointHeader hd{kCheckpointMagic, h->cfg_sig, h->ws_total, PF_ABI_VERSION, h->steps_run,
-                      h->finish_pending ? 1 : 0, h->k1_grid, h->rs_cluster, 0};
+                      h->finish_pending ? 1 : 0, h->k1_grid, h->rs_cluster, h->rs_threads};
   std::memcpy(host, &hd, sizeof hd);
   char* dst = (char*)host + sizeof hd;
   cudaError_t e;
@@ -1300,6 +1323,7 @@ pf_status pf_load(pf_handle* h, const void* host, size_t bytes, void* stream) {
   h->finish_pending = hd.finish_pending != 0;
   h->k1_grid = hd.k1_grid;
   h->rs_cluster = hd.rs_cluster;
+  h->rs_threads = hd.rs_threads == RS_THREADS_SMALL ? RS_THREADS_SMALL : RS_THREADS;
   h->failed = 0;
   h->last_stream = s;
   if (h->graph) {  // a captured step may hold other launch shapes

@@ -29,6 +29,7 @@ constexpr int ROI_ROWS = ROI_BOX_H * ROI_MAX_BOXES;  // staged rows at most (64)
 constexpr int ROI_FLOATS = ROI_W * ROI_ROWS;
 constexpr int RING_SMEM_G = ROI_FLOATS / 2;  // ring orders drawn ahead up to this G
 constexpr int RS_THREADS = 512;       // resampler CTA
+constexpr int RS_THREADS_SMALL = 128; // resampler CTA for groups of at most RS_THREADS_SMALL x RS_ITEMS slots
 constexpr int RS_ITEMS = 8;           // items per thread per resampler sub-chunk
 constexpr int RS_SUB = RS_THREADS * RS_ITEMS;
 constexpr int RS_WIN = 2 * RS_SUB;    // resampler merge window: items and outputs merged at once (ancestors staged)

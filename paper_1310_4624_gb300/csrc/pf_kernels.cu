@@ -1118,21 +1118,22 @@ __device__ __forceinline__ int count_below(const Thresholds& th, unsigned long l
 // first p positions, for items i < n with boundaries X_i = s_incl[pad8(i)]
 // and outputs j0 + b, b < no, with thresholds T: the largest i in
 // [max(0, p - no), min(p, n)] with X_{i-1} <= T_{j0+p-i}.  A
-// RS_THREADS-ary search that every thread of the block enters.
+// NTR-ary search that every thread of the block (NTR threads) enters.
+template <int NTR>
 __device__ __noinline__ int merge_split(const unsigned long long* s_incl, const Thresholds& th, int j0, int n, int no, int p) {
   int lo = max(0, p - no), hi = min(p, n);
   while (lo < hi) {
     const int m = hi - lo;
-    const bool fine = m <= RS_THREADS;  // then candidates lo + 1 .. hi, else RS_THREADS evenly spaced
-    const int c = fine ? lo + 1 + (int)threadIdx.x : lo + (int)(((long long)(threadIdx.x + 1) * m) / RS_THREADS);
+    const bool fine = m <= NTR;  // then candidates lo + 1 .. hi, else NTR evenly spaced
+    const int c = fine ? lo + 1 + (int)threadIdx.x : lo + (int)(((long long)(threadIdx.x + 1) * m) / NTR);
     const bool ok = (!fine || (int)threadIdx.x < m) && s_incl[pad8(c - 1)] <= th.T((uint32_t)(j0 + p - c));
     const int cnt = __syncthreads_count(ok);  // the predicate holds for a prefix of the candidates
     if (fine) {
       lo += cnt;
       hi = lo;
     } else {
-      const int nlo = cnt == 0 ? lo : lo + (int)(((long long)cnt * m) / RS_THREADS);
-      const int nhi = cnt == RS_THREADS ? hi : lo + (int)(((long long)(cnt + 1) * m) / RS_THREADS) - 1;
+      const int nlo = cnt == 0 ? lo : lo + (int)(((long long)cnt * m) / NTR);
+      const int nhi = cnt == NTR ? hi : lo + (int)(((long long)(cnt + 1) * m) / NTR) - 1;
       lo = nlo;
       hi = nhi;
     }
@@ -1144,14 +1145,16 @@ __device__ __noinline__ int merge_split(const unsigned long long* s_incl, const 
 // X_i = s_incl[pad8(i)] against outputs j in [jlo, jhi); ancestors
 // obase_sub + item, stored to anc[j].  Every thread of the block enters.
 // (Not inlined: it runs with registers of its own.)
+template <int NTR>
 __device__ __noinline__ void merge_windows(const unsigned long long* __restrict__ s_incl, uint32_t* __restrict__ s_out,
                                            const Thresholds& th_s, int jlo, int jhi, int n,
                                            unsigned long long obase_sub, uint32_t* __restrict__ anc) {
+  constexpr int WIN = 2 * NTR * RS_ITEMS;
   const Thresholds th = th_s;
   // Merge path over the item boundaries X_i = S_{i+1} (s_incl) and the
   // thresholds Y_j = T_j of this sub-chunk's outputs j in [jlo, jhi):
   // output j takes the first item i with T_j < S_{i+1}.  The merged
-  // sequence (n items, no outputs) is cut into windows of at most RS_WIN
+  // sequence (n items, no outputs) is cut into windows of at most WIN
   // positions, each split at its diagonal by a block-wide search, so that
   // every item and output is merged once however the weight is spread
   // over the CTAs; within a window each thread merges an equal slice.  A
@@ -1159,13 +1162,13 @@ __device__ __noinline__ void merge_windows(const unsigned long long* __restrict_
   // consecutive threads writing consecutive outputs.
   const int no = jhi - jlo, Lt = n + no;
   int ia0 = 0, ib0 = 0;  // items and outputs merged before the window
-  for (int p0 = 0; p0 < Lt; p0 += RS_WIN) {
-    const int p1 = min(Lt, p0 + RS_WIN);
-    const int ia1 = p1 == Lt ? n : merge_split(s_incl, th, jlo, n, no, p1);
+  for (int p0 = 0; p0 < Lt; p0 += WIN) {
+    const int p1 = min(Lt, p0 + WIN);
+    const int ia1 = p1 == Lt ? n : merge_split<NTR>(s_incl, th, jlo, n, no, p1);
     const int nw = ia1 - ia0, mw = (p1 - ia1) - ib0, L = p1 - p0;
     const int jw = jlo + ib0;
-    const int d0 = (int)(((long long)L * threadIdx.x) / RS_THREADS);
-    const int d1 = (int)(((long long)L * (threadIdx.x + 1)) / RS_THREADS);
+    const int d0 = (int)(((long long)L * threadIdx.x) / NTR);
+    const int d1 = (int)(((long long)L * (threadIdx.x + 1)) / NTR);
     // largest ia in [max(0, d0 - mw), min(d0, nw)] whose items all precede
     // output d0 - ia of the window in the merge (X_{ia0+ia-1} <= Y_{jw+d0-ia})
     int lo2 = max(0, d0 - mw), hi2 = min(d0, nw);
@@ -1198,7 +1201,7 @@ __device__ __noinline__ void merge_windows(const unsigned long long* __restrict_
       }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < mw; e += RS_THREADS) anc[jw + e] = s_out[pad8(e)];
+    for (int e = threadIdx.x; e < mw; e += NTR) anc[jw + e] = s_out[pad8(e)];
     __syncthreads();
     ia0 = ia1;
     ib0 += mw;
@@ -1206,10 +1209,14 @@ __device__ __noinline__ void merge_windows(const unsigned long long* __restrict_
 }
 
 // Resampler: one thread-block cluster per group, each CTA a contiguous chunk
-// of the group's slots (a multiple of 8), processed in sub-chunks of RS_SUB
+// of the group's slots (a multiple of 8), processed in sub-chunks of SUB
 // items; thread t owns the RS_ITEMS consecutive items [t*RS_ITEMS, ...).
 
-__global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
+template <int NTR>
+__global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(ResampleArgs a) {
+  constexpr int SUB = NTR * RS_ITEMS;  // items per sub-chunk
+  constexpr int SUB_PAD = pad8(SUB);
+  constexpr int WIN = 2 * SUB;         // merge window: items and outputs merged at once
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -1218,7 +1225,7 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
   const int Np = d.Np;
   const int chunk = ((Np + C - 1) / C + 7) & ~7;
   const int lo = min(rank * chunk, Np), hi = min(lo + chunk, Np);
-  const bool single = (hi - lo) <= RS_SUB;  // the whole chunk stays in registers
+  const bool single = (hi - lo) <= SUB;  // the whole chunk stays in registers
   // In a filter step: the track's step index (read before the cluster
   // barrier that precedes every ticket below, since the track's global step,
   // run by the last ticket holder, advances it), which picks the log-weight
@@ -1233,9 +1240,9 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
   __shared__ float s_pub_max;
   __shared__ unsigned long long s_pub_q;
   __shared__ unsigned long long s_pub_e[2];
-  __shared__ float s_f[RS_THREADS / 32];
-  __shared__ unsigned long long s_w[RS_THREADS / 32];
-  __shared__ float s_stat[RS_THREADS / 32][8];
+  __shared__ float s_f[NTR / 32];
+  __shared__ unsigned long long s_w[NTR / 32];
+  __shared__ float s_stat[NTR / 32][8];
   __shared__ int s_jlo, s_jhi;
   __shared__ Thresholds s_th;
   // dynamic: inclusive prefixes of a sub-chunk's items, then a window of
@@ -1244,7 +1251,7 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
   // elements after its neighbour's, spreading a warp over the banks.
   extern __shared__ unsigned long long s_dyn_rs[];
   unsigned long long* s_incl = s_dyn_rs;
-  uint32_t* s_out = reinterpret_cast<uint32_t*>(s_dyn_rs + RS_SUB_PAD);
+  uint32_t* s_out = reinterpret_cast<uint32_t*>(s_dyn_rs + SUB_PAD);
 
   float v[RS_ITEMS];
   auto load_sub = [&](int sub) {
@@ -1281,17 +1288,17 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
   if (single) load_sub(lo);  // the CTA's items, for the quantisation below
   if (a.tile_part != nullptr) {
     float m = -INFINITY;
-    for (int t = threadIdx.x; t < d.tile_count; t += RS_THREADS)
+    for (int t = threadIdx.x; t < d.tile_count; t += NTR)
       m = fmaxf(m, a.tile_part[(long long)(d.tile_begin + t) * 8]);
-    M = block_max<RS_THREADS>(m, s_f);
+    M = block_max<NTR>(m, s_f);
   } else {
     float m = -INFINITY;
-    for (int sub = lo; sub < hi; sub += RS_SUB) {
+    for (int sub = lo; sub < hi; sub += SUB) {
       if (!single) load_sub(sub);
 #pragma unroll
       for (int r = 0; r < RS_ITEMS; ++r) m = fmaxf(m, v[r]);
     }
-    m = block_max<RS_THREADS>(m, s_f);
+    m = block_max<NTR>(m, s_f);
     if (threadIdx.x == 0) s_pub_max = m;
     cl.sync();
     for (int r = 0; r < C; ++r) M = fmaxf(M, *cl.map_shared_rank(&s_pub_max, r));
@@ -1301,7 +1308,7 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
   // under Alg. 1's test also the sums of c = q >> 20 and c^2
   unsigned long long qs = 0, e1 = 0, e2 = 0;
   unsigned long long qv[RS_ITEMS];
-  for (int sub = lo; sub < hi; sub += RS_SUB) {
+  for (int sub = lo; sub < hi; sub += SUB) {
     if (!single) load_sub(sub);
 #pragma unroll
     for (int r = 0; r < RS_ITEMS; ++r) {
@@ -1314,10 +1321,10 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
       }
     }
   }
-  qs = block_sum_u64<RS_THREADS>(qs, s_w);
+  qs = block_sum_u64<NTR>(qs, s_w);
   if (ess_rule) {
-    e1 = block_sum_u64<RS_THREADS>(e1, s_w);
-    e2 = block_sum_u64<RS_THREADS>(e2, s_w);
+    e1 = block_sum_u64<NTR>(e1, s_w);
+    e2 = block_sum_u64<NTR>(e2, s_w);
   }
   if (threadIdx.x == 0) {
     s_pub_q = qs;
@@ -1349,7 +1356,7 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
     if (a.tile_part != nullptr) {
       float acc[7] = {0, 0, 0, 0, 0, 0, 0};
       if (Q != 0) {
-        for (int t = threadIdx.x; t < d.tile_count; t += RS_THREADS) {
+        for (int t = threadIdx.x; t < d.tile_count; t += NTR) {
           const float* tp = a.tile_part + (long long)(d.tile_begin + t) * 8;
           const float Mt = tp[0];
           if (!(Mt - M >= -87.0f)) continue;
@@ -1367,7 +1374,7 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
       __syncthreads();
       if (threadIdx.x == 0) {
         float t7[7] = {0, 0, 0, 0, 0, 0, 0};
-        for (int w = 0; w < RS_THREADS / 32; ++w)
+        for (int w = 0; w < NTR / 32; ++w)
           for (int q = 0; q < 7; ++q) t7[q] += s_stat[w][q];
         const bool ok = (Q != 0) && t7[0] > 0.0f;
         for (int q = 0; q < 5; ++q) G.xs[q] = ok ? t7[1 + q] / t7[0] : 0.0f;
@@ -1396,7 +1403,7 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
     }
     __syncthreads();
     if (s_last) {
-      global_step<RS_THREADS>(a.glob, d.track, *reinterpret_cast<GlobalScratch*>(s_dyn_rs));
+      global_step<NTR>(a.glob, d.track, *reinterpret_cast<GlobalScratch*>(s_dyn_rs));
       if (threadIdx.x == 0) a.glob.ts[d.track].ticket = 0u;
       __syncthreads();  // the scratch is the prefix array below
     }
@@ -1407,7 +1414,7 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
   uint32_t* __restrict__ anc = a.anc + d.base;
   if (Q == 0 || !resample) {
     // no finite weight, or Alg. 1's test keeps the particles: identity
-    for (int i = lo + threadIdx.x; i < hi; i += RS_THREADS) {
+    for (int i = lo + threadIdx.x; i < hi; i += NTR) {
       anc[i] = (uint32_t)(obase + i);
       if (a.q_out) a.q_out[d.base + i] = 0ull;
     }
@@ -1424,8 +1431,8 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
     const Thresholds th = s_th;
     const float inv_Q = 1.0f / u64_to_float_approx(Q);
     unsigned long long carry = Sb;
-    for (int sub = lo; sub < hi; sub += RS_SUB) {
-      const int n = min(RS_SUB, hi - sub);
+    for (int sub = lo; sub < hi; sub += SUB) {
+      const int n = min(SUB, hi - sub);
       const int i0 = (int)threadIdx.x * RS_ITEMS;  // first item of this thread (sub-chunk relative)
       if (!single) {
         load_sub(sub);
@@ -1450,7 +1457,7 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
       __syncthreads();
       unsigned long long wpre = 0, tot = 0;
 #pragma unroll
-      for (int w = 0; w < RS_THREADS / 32; ++w) {
+      for (int w = 0; w < NTR / 32; ++w) {
         const unsigned long long y = s_w[w];
         if (w < warp) wpre += y;
         tot += y;
@@ -1469,7 +1476,7 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_resample(ResampleArgs a) {
         s_jhi = count_below(th, carry + tot, inv_Q, Np, u, a.ds);
       }
       __syncthreads();
-      merge_windows(s_incl, s_out, s_th, s_jlo, s_jhi, n, obase + sub, anc);
+      merge_windows<NTR>(s_incl, s_out, s_th, s_jlo, s_jhi, n, obase + sub, anc);
       carry += tot;
       __syncthreads();
     }
@@ -1586,16 +1593,22 @@ cudaError_t launch_propagate(const K1Args& a, int R, int grid, bool pdl, cudaStr
   }
 }
 
-cudaError_t launch_resample(const ResampleArgs& a, int n_groups, int cluster, bool pdl, cudaStream_t s) {
-  constexpr size_t smem = RS_SUB_PAD * sizeof(unsigned long long) + pad8(RS_WIN) * sizeof(uint32_t);
+template <int NTR>
+static cudaError_t launch_resample_t(const ResampleArgs& a, int n_groups, int cluster, bool pdl, cudaStream_t s) {
+  constexpr size_t smem = pad8(NTR * RS_ITEMS) * sizeof(unsigned long long) + pad8(2 * NTR * RS_ITEMS) * sizeof(uint32_t);
   static_assert(sizeof(GlobalScratch) <= smem, "the global step's scratch lives in the resampler's shared memory");
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_resample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_err = cudaFuncSetAttribute(k_resample<NTR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
   if (attr_err != cudaSuccess) return attr_err;
-  return launch_ex(k_resample, dim3((unsigned)(n_groups * cluster)), dim3(RS_THREADS), cluster, pdl, s, a, smem);
+  return launch_ex(k_resample<NTR>, dim3((unsigned)(n_groups * cluster)), dim3(NTR), cluster, pdl, s, a, smem);
+}
+
+cudaError_t launch_resample(const ResampleArgs& a, int n_groups, int cluster, bool pdl, cudaStream_t s, int threads) {
+  if (threads == RS_THREADS_SMALL) return launch_resample_t<RS_THREADS_SMALL>(a, n_groups, cluster, pdl, s);
+  return launch_resample_t<RS_THREADS>(a, n_groups, cluster, pdl, s);
 }
 
 cudaError_t launch_global(const GlobalArgs& a, int n_tracks, cudaStream_t s) {

@@ -188,7 +188,9 @@ cudaError_t launch_init(const InitArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_frame_prep(const FrameArgs& a, int nt, int blocks_x, bool pdl, cudaStream_t s);
 cudaError_t launch_frame_prep_table(const FrameTableArgs& a, int blocks_x, bool pdl, cudaStream_t s);
 cudaError_t launch_propagate(const K1Args& a, int R, int grid, bool pdl, cudaStream_t s);
-cudaError_t launch_resample(const ResampleArgs& a, int n_groups, int cluster, bool pdl, cudaStream_t s);
+// threads: RS_THREADS, or RS_THREADS_SMALL (eight CTAs per SM, for batches of small groups)
+cudaError_t launch_resample(const ResampleArgs& a, int n_groups, int cluster, bool pdl, cudaStream_t s,
+                            int threads = RS_THREADS);
 cudaError_t launch_global(const GlobalArgs& a, int n_tracks, cudaStream_t s);
 cudaError_t launch_finish(const GlobalArgs& a, int n_tracks, cudaStream_t s);
 cudaError_t launch_export_states(const float4* pv, const float* In, long long n, float* out, cudaStream_t s);

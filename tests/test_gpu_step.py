@@ -81,6 +81,16 @@ def test_small_configs_match_oracle(dev, name, wl):
         assert any(r["resampled"] < wl.G for r in rep) and any(r["resampled"] > 0 for r in rep), rep
 
 
+@pytest.mark.parametrize("name", ["cfg1_rna", "two_groups_multi_tile", "max_groups", "ess_rna", "odd_width"])
+def test_small_resampler_ctas_match_oracle(dev, name, monkeypatch):
+    """The 128-thread resampler CTAs (forced), including groups larger than
+    one of their sub-chunks (streamed)."""
+    monkeypatch.setenv("PFARNA_RS_THREADS", "128")
+    wl = dict(SMALL)[name]
+    rep = _run(dev, wl, 5)
+    assert len(rep) == 5
+
+
 def test_largest_group_matches_oracle(dev):
     """One group of 2^20 particles (the largest N_p): resampling across an
     8-CTA cluster with streamed sub-chunks."""
