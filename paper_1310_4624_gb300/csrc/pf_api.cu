@@ -334,6 +334,15 @@ cudaError_t mark(pf_handle* h, int kernel, cudaStream_t s) {
 
 // y = z - b into the padded frames, up to MAX_FRAMES_PER_LAUNCH tracks per
 // launch.  frames: n_tracks device pointers.
+// Blocks per frame of the frame preparation: enough for about sixteen
+// 256-thread blocks per SM over the launch, each looping over rows, so that
+// a batch of many small frames does not pay a block's start-up per row.
+int prep_blocks(const pf_handle* h, int n_frames, int maxH) {
+  const long long want = (16LL * h->sms + n_frames - 1) / n_frames;
+  const int cap = maxH > 4096 ? 4096 : maxH;
+  return (int)(want < 1 ? 1 : (want > cap ? cap : want));
+}
+
 // Tracks of one launch given the same frame (pointer, size and background)
 // share one padded copy, prepared once (several objects tracked in one
 // sequence); frame_of tells the propagate kernel which copy each reads.
@@ -365,7 +374,7 @@ cudaError_t prep_frames(pf_handle* h, const float* const* frames, cudaStream_t s
         if (c.H > maxH) maxH = c.H;
       }
     }
-    cudaError_t e = launch_frame_prep(a, n_rep, maxH > 4096 ? 4096 : maxH, h->pdl, s);
+    cudaError_t e = launch_frame_prep(a, n_rep, prep_blocks(h, n_rep, maxH), h->pdl, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -749,7 +758,7 @@ static cudaError_t launch_frames_table(pf_handle* h, const float* const* table, 
   int maxH = 1;
   for (int t = 0; t < h->n_tracks; ++t) maxH = h->cfg[t].H > maxH ? h->cfg[t].H : maxH;
   FrameTableArgs fa{h->trk, h->ypad, h->R, table, T_table, h->n_tracks, h->ts, h->ds, h->frame_of};
-  return launch_frame_prep_table(fa, maxH > 4096 ? 4096 : maxH, h->pdl, s);
+  return launch_frame_prep_table(fa, prep_blocks(h, h->n_tracks, maxH), h->pdl, s);
 }
 
 pf_status pf_step_table(pf_handle* h, const float* const* table_dev, int32_t T_table, void* stream) {
