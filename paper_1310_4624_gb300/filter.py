@@ -2,6 +2,25 @@
 
 PyTorch supplies device memory (the workspace, frames, outputs) and the CUDA
 stream; every step of the filter runs in the library's kernels.
+
+Typical use (one track; a list of configurations makes a batch)::
+
+    from paper_1310_4624_gb300 import synth
+    from paper_1310_4624_gb300.filter import ParticleFilter, config_from_workload
+    wl = synth.tracking()                       # G = 64 x 16384, ARNA, 512 x 512
+    frames, truth = synth.make_sequence(wl)
+    fr = torch.from_numpy(frames).cuda()
+    pf = ParticleFilter([config_from_workload(wl, truth[0])])
+    for k in range(wl.T):
+        pf.step(fr[k])                          # Alg. 3 for every track
+    xhat, log_z, status = pf.estimate()         # x^ and log Z of the last step
+    stats = pf.stats(wl.T - 1)                  # N_ex, PE_eff, ring, group weights
+    pf.close()
+
+Method variants are fields of the configuration: ``resample_rule`` /
+``ess_fraction`` (Alg. 1's N_eff test per group), ``send_rule`` (keyed random
+send sets), ``topology`` / ``node_groups`` (Sec. VI's node-aware ring and
+hypercube), ``obs_model`` (the frame likelihood ratio).
 """
 from __future__ import annotations
 
