@@ -84,6 +84,39 @@ __global__ void __launch_bounds__(K1_THREADS) k_init(InitArgs a) {
 // y = z - b into the interior of the zero-padded frame; the padding (2R+1
 // pixels on each side, zeroed once at init) stands for "outside the image
 // counts as background".
+// y = z - b of one frame into its padded copy (rows offset by pad, pitch
+// P.pitch), by the rows blockIdx.x, blockIdx.x + gridDim.x, ...  Frames
+// with rows of whole float4 (and 16-byte aligned) are read four pixels per
+// thread, several rows per block pass; the padded rows start off the 16-byte
+// grid, so the stores stay scalar.
+__device__ __forceinline__ void prep_rows(const float* __restrict__ z, float* __restrict__ yp, const TrackParams& P,
+                                          int pad, float bg) {
+  if ((P.W & 3) == 0 && (reinterpret_cast<uintptr_t>(z) & 15) == 0) {
+    const int cols4 = P.W >> 2, nt = (int)blockDim.x;
+    const int rpi = cols4 >= nt ? 1 : nt / cols4;  // rows per pass
+    const int span = rpi == 1 ? nt : cols4;        // threads per row
+    const int tr = (int)threadIdx.x / span, tc = (int)threadIdx.x - tr * span;
+    if (tr < rpi)
+      for (int v = (int)blockIdx.x * rpi + tr; v < P.H; v += (int)gridDim.x * rpi) {
+        const float4* __restrict__ zr = reinterpret_cast<const float4*>(z + (long long)v * P.W);
+        float* __restrict__ yr = yp + (long long)(v + pad) * P.pitch + pad;
+        for (int c = tc; c < cols4; c += span) {
+          const float4 q = __ldg(zr + c);
+          yr[4 * c] = __fsub_rn(q.x, bg);
+          yr[4 * c + 1] = __fsub_rn(q.y, bg);
+          yr[4 * c + 2] = __fsub_rn(q.z, bg);
+          yr[4 * c + 3] = __fsub_rn(q.w, bg);
+        }
+      }
+    return;
+  }
+  for (int v = blockIdx.x; v < P.H; v += gridDim.x) {
+    const float* __restrict__ zr = z + (long long)v * P.W;
+    float* __restrict__ yr = yp + (long long)(v + pad) * P.pitch + pad;
+    for (int u = threadIdx.x; u < P.W; u += blockDim.x) yr[u] = __fsub_rn(__ldg(zr + u), bg);
+  }
+}
+
 __global__ void k_frame_prep(FrameArgs a) {
   grid_dep_wait();
   grid_dep_launch();
@@ -95,11 +128,7 @@ __global__ void k_frame_prep(FrameArgs a) {
   float* __restrict__ yp = a.ypad + P.ypad_off;
   const int pad = 2 * a.R + 1;
   const float bg = P.bg;
-  for (int v = blockIdx.x; v < P.H; v += gridDim.x) {
-    const float* __restrict__ zr = z + (long long)v * P.W;
-    float* __restrict__ yr = yp + (long long)(v + pad) * P.pitch + pad;
-    for (int u = threadIdx.x; u < P.W; u += blockDim.x) yr[u] = __fsub_rn(__ldg(zr + u), bg);
-  }
+  prep_rows(z, yp, P, pad, bg);
 }
 
 // Same, frame pointers from a device table indexed by the device-side step
@@ -119,11 +148,7 @@ __global__ void k_frame_prep_table(FrameTableArgs a) {
   float* __restrict__ yp = a.ypad + P.ypad_off;
   const int pad = 2 * a.R + 1;
   const float bg = P.bg;
-  for (int v = blockIdx.x; v < P.H; v += gridDim.x) {
-    const float* __restrict__ zr = z + (long long)v * P.W;
-    float* __restrict__ yr = yp + (long long)(v + pad) * P.pitch + pad;
-    for (int u = threadIdx.x; u < P.W; u += blockDim.x) yr[u] = __fsub_rn(__ldg(zr + u), bg);
-  }
+  prep_rows(z, yp, P, pad, bg);
 }
 
 // ================================================================ global step
