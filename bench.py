@@ -721,7 +721,8 @@ def main():
             "e2e": {"value": n_all * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": wl.H * wl.W * 4,
                     "d2h_bytes_per_step": 5 * 4 + 8,
                     "form": "wall clock; per step a page-locked frame upload (copy stream, overlapping the "
-                            "previous step), pf_step, pf_estimate_async into page-locked memory, the "
+                            "previous step), pf_step, pf_estimate_async into page-locked memory (stored by the "
+                            "finishing kernel), the "
                             "estimate consumed on the host one step later"},
             "gpu_launches": int(round(prof_launches / KP * K)),
             "roofline": roofline,

@@ -253,11 +253,14 @@ pf_status pf_estimate(pf_handle* h, float* xhat_host, double* log_Z_host);
  * run on) the completion of the last step's statistics and copies of x^
  * (n_tracks x 5 floats) and log Z (n_tracks doubles) into the caller's host
  * buffers, and return.  The values are there once the stream has passed
- * this point (the caller's event or synchronisation); with page-locked host
- * buffers the copies overlap later work, so a stream of frames can be
- * filtered with the next frame's upload and the last estimate's read-back
- * in flight.  Degenerate tracks and device errors are reported by the next
- * synchronising call.  Errors: PF_ERR_ARG, PF_ERR_STATE, PF_ERR_CUDA. */
+ * this point (the caller's event or synchronisation).  Page-locked host
+ * buffers (cudaHostAlloc, cudaHostRegister) are written by the finishing
+ * kernel itself through their device addresses, so no copy follows it on
+ * the stream; pageable buffers are filled by copies.  Either way a stream
+ * of frames can be filtered with the next frame's upload and the last
+ * estimate's read-back in flight.  Degenerate tracks and device errors are
+ * reported by the next synchronising call.  Errors: PF_ERR_ARG,
+ * PF_ERR_STATE, PF_ERR_CUDA. */
 pf_status pf_estimate_async(pf_handle* h, float* xhat_host, double* log_Z_host, void* stream);
 
 /* Statistics of step `step` (< steps run, and among the last `history`) of

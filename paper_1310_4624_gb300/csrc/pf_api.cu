@@ -951,6 +951,22 @@ pf_status pf_estimate(pf_handle* h, float* xhat, double* logZ) {
   return PF_OK;
 }
 
+// p is null, or page-locked host memory the device can address (cudaHostAlloc
+// or cudaHostRegister on a unified address space): *dev = its device address.
+// Pageable memory (or a failed query, whose error is cleared) gives false.
+static bool host_mapped(void* p, void** dev) {
+  *dev = nullptr;
+  if (!p) return true;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type != cudaMemoryTypeHost || !at.devicePointer) return false;
+  *dev = at.devicePointer;
+  return true;
+}
+
 pf_status pf_estimate_async(pf_handle* h, float* xhat, double* logZ, void* stream) {
   NvtxRange nvtx_range("pf_estimate_async");
   if (!h) return fail(nullptr, PF_ERR_ARG, "handle is NULL");
@@ -959,6 +975,17 @@ pf_status pf_estimate_async(pf_handle* h, float* xhat, double* logZ, void* strea
   if (h->failed) return fail(h, PF_ERR_STATE, "handle failed earlier: " + h->err);
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
+  // page-locked host buffers: the finishing kernel stores the values itself
+  float* xhat_dev = nullptr;
+  double* logZ_dev = nullptr;
+  if (host_mapped(xhat, reinterpret_cast<void**>(&xhat_dev)) &&
+      host_mapped(logZ, reinterpret_cast<void**>(&logZ_dev))) {
+    if ((e = launch_finish_out(global_args(h, 1), h->n_tracks, xhat_dev, logZ_dev, s)) != cudaSuccess)
+      return cuda_fail(h, e, "k_finish_out");
+    h->finish_pending = false;
+    h->last_stream = s;
+    return PF_OK;
+  }
   if (h->finish_pending) {
     if ((e = launch_finish(global_args(h, 1), h->n_tracks, s)) != cudaSuccess) return cuda_fail(h, e, "k_finish");
     h->finish_pending = false;

@@ -499,6 +499,20 @@ __global__ void __launch_bounds__(K1_THREADS) k_finish(GlobalArgs a) {
   finish_step<K1_THREADS>(a, blockIdx.x, sc);
 }
 
+// k_finish, then the track's x^ and log Z stored straight into the caller's
+// page-locked host buffers (their device addresses; either may be null), so
+// that reading the estimate back takes no copy on the stream.
+__global__ void __launch_bounds__(K1_THREADS) k_finish_out(GlobalArgs a, float* xhat, double* logZ) {
+  __shared__ GlobalScratch sc;
+  finish_step<K1_THREADS>(a, blockIdx.x, sc);
+  if (threadIdx.x == 0) {  // the thread that wrote the track state, if finish_step ran here
+    const TrackState* T = a.ts + blockIdx.x;
+    if (xhat)
+      for (int q = 0; q < 5; ++q) xhat[blockIdx.x * 5 + q] = __ldcg(&T->xhat[q]);
+    if (logZ) logZ[blockIdx.x] = __ldcg(&T->log_Z);
+  }
+}
+
 // ============================================================ propagate + weight
 // Fisher-Yates ring order of step k (Sec. IV-B, Alg. 3 step 1) for one
 // track, by one warp: the bounded draws r_j in [0, j] in parallel, the
@@ -1643,6 +1657,11 @@ cudaError_t launch_global(const GlobalArgs& a, int n_tracks, cudaStream_t s) {
 
 cudaError_t launch_finish(const GlobalArgs& a, int n_tracks, cudaStream_t s) {
   k_finish<<<n_tracks, K1_THREADS, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish_out(const GlobalArgs& a, int n_tracks, float* xhat, double* logZ, cudaStream_t s) {
+  k_finish_out<<<n_tracks, K1_THREADS, 0, s>>>(a, xhat, logZ);
   return cudaGetLastError();
 }
 

@@ -154,8 +154,10 @@ class ParticleFilter:
 
     def estimate_async(self, xhat: torch.Tensor, log_z: torch.Tensor) -> None:
         """Enqueue the read-back of x^ ((n_tracks, 5) float32) and log Z
-        ((n_tracks,) float64) into page-locked host tensors on the filter's
-        stream; they hold the values once the stream has passed this point."""
+        ((n_tracks,) float64) into host tensors on the filter's stream; they
+        hold the values once the stream has passed this point.  Page-locked
+        tensors are written by the finishing kernel itself (no copy on the
+        stream), pageable ones by copies."""
         assert xhat.dtype == torch.float32 and xhat.numel() == 5 * self.n_tracks and not xhat.is_cuda
         assert log_z.dtype == torch.float64 and log_z.numel() == self.n_tracks and not log_z.is_cuda
         B.pf_estimate_async(self.handle, C.c_void_p(xhat.data_ptr()), C.c_void_p(log_z.data_ptr()),
