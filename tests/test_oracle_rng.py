@@ -39,6 +39,19 @@ def test_philox_matches_torch_engine(ora, torch_philox):
         assert [int(v) for v in ours] == [int(v) for v in line.split()]
 
 
+def test_philox_known_answer_vectors(ora):
+    """The generator's published known-answer vectors (tests/golden, cited
+    there): counter, key and the 10-round output."""
+    rows = [line.split() for line in open(os.path.join(HERE, "golden", "philox4x32_10_kat.txt"))
+            if line.strip() and not line.startswith("#")]
+    assert len(rows) == 3
+    for row in rows:
+        v = [int(x, 16) for x in row]
+        ctr, (k0, k1), want = v[0:4], v[4:6], v[6:10]
+        ours = ora.philox(k0 | (k1 << 32), np.array(ctr, dtype=np.uint32))
+        assert [int(x) for x in ours] == want
+
+
 def test_uniform_map_open_interval_and_fp32_exact(ora):
     for w in [0, 1, 255, 256, 2 ** 31, 2 ** 32 - 257, 2 ** 32 - 1]:
         u = ora.uniform(w)
