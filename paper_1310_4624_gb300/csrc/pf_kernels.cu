@@ -1114,7 +1114,9 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
       }
       a.tile_part[(long long)tile * 8 + threadIdx.x] = r;
     }
-    __syncthreads();
+    // No barrier here: every shared buffer the next tile writes first (s_box,
+    // then s_roi by TMA, s_red / s_key) is written only after that tile's
+    // box barrier, which warp 0 reaches after its reads of s_red above.
     return true;
   };
 
