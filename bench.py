@@ -638,20 +638,19 @@ def main():
         pf.close()
         del flush
 
-    # end to end through the public API, every step: the frame copied from
-    # page-locked host memory to the device (on a copy stream, so frame k+1
-    # uploads while step k runs), the step, and the estimate read back to
-    # page-locked host memory (pf_estimate_async); the host consumes step k's
-    # estimate after enqueueing step k+1, and the clock stops once the last
-    # estimate is on the host
+    # end to end through the public API, every step: pf_step_host on the
+    # frame in page-locked host memory (the library uploads it on its own
+    # stream into a device staging slot, so frame k+1 uploads while step k
+    # runs), and the estimate read back to page-locked host memory
+    # (pf_estimate_async: the finishing kernel stores it there); the host
+    # consumes step k's estimate after enqueueing step k+1, and the clock
+    # stops once the last estimate is on the host
     wl = res[synth.ARNA]["wl"]
     frames = res[synth.ARNA]["frames"]
     truth = res[synth.ARNA]["truth"]
     host = torch.from_numpy(frames).pin_memory()
-    dbuf = torch.empty((2, wl.H, wl.W), dtype=torch.float32, device=dev)
+    host_k = [host[k] for k in range(host.shape[0])]
     pf = ParticleFilter([config_from_workload(wl, truth[0])], history=T + 1, device=dev)
-    copy_stream = torch.cuda.Stream(dev)
-    ev_copy = [torch.cuda.Event() for _ in range(2)]
     ev_done = [torch.cuda.Event() for _ in range(2)]
     x_out = [torch.zeros((1, 5), dtype=torch.float32).pin_memory() for _ in range(2)]
     z_out = [torch.zeros(1, dtype=torch.float64).pin_memory() for _ in range(2)]
@@ -659,12 +658,7 @@ def main():
 
     def enqueue(k):
         b = k & 1
-        with torch.cuda.stream(copy_stream):
-            copy_stream.wait_event(ev_done[b])       # step k-2 no longer reads dbuf[b]
-            dbuf[b].copy_(host[k], non_blocking=True)
-            ev_copy[b].record(copy_stream)
-        pf.stream.wait_event(ev_copy[b])
-        pf.step(dbuf[b])
+        pf.step_host(host_k[k])
         pf.estimate_async(x_out[b], z_out[b])
         ev_done[b].record(pf.stream)
 
@@ -720,10 +714,10 @@ def main():
                        "l2": "flushed (256 MB write) before every timed step, outside the timed interval"},
             "e2e": {"value": n_all * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": wl.H * wl.W * 4,
                     "d2h_bytes_per_step": 5 * 4 + 8,
-                    "form": "wall clock; per step a page-locked frame upload (copy stream, overlapping the "
-                            "previous step), pf_step, pf_estimate_async into page-locked memory (stored by the "
-                            "finishing kernel), the "
-                            "estimate consumed on the host one step later"},
+                    "form": "wall clock; per step pf_step_host on a page-locked host frame (uploaded by the "
+                            "library on its own stream, overlapping the previous step), pf_estimate_async into "
+                            "page-locked memory (stored by the finishing kernel), the estimate consumed on the "
+                            "host one step later"},
             "gpu_launches": int(round(prof_launches / KP * K)),
             "roofline": roofline,
             "kernels": kernels,

@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define PF_ABI_VERSION 3
+#define PF_ABI_VERSION 4
 
 typedef enum pf_status {
   PF_OK = 0,
@@ -214,6 +214,28 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
  * Errors: PF_ERR_ARG (NULL frame), PF_ERR_STATE (handle failed before),
  * PF_ERR_CUDA. */
 pf_status pf_step(pf_handle* h, const float* const* frames_host, void* stream);
+
+/* Bytes of the device staging buffer pf_step_host needs: two slots (by step
+ * parity), each with every track's H x W float32 frame at a 256-byte
+ * aligned offset.  Errors: PF_ERR_ARG. */
+pf_status pf_host_staging_bytes(const pf_handle* h, size_t* bytes);
+
+/* pf_step with the frames in HOST memory: frames_host holds n_tracks host
+ * pointers (frame k of each track, H x W float32, row-major).  The frames
+ * are uploaded on a stream of the handle's own into the caller's device
+ * staging buffer (staging_dev: 256-byte aligned, at least
+ * pf_host_staging_bytes; the caller owns it and keeps it for the handle's
+ * life), slot k & 1, after the step two back has finished reading that
+ * slot; `stream` waits for the upload, then runs pf_step on the staged
+ * frames.  A host pointer given to several tracks of the same frame size is
+ * uploaded once.  With page-locked host frames (cudaHostAlloc,
+ * cudaHostRegister) the call returns at once and frame k + 1 uploads while
+ * step k runs; the host frame must then stay unchanged until the upload has
+ * run (the step's completion on `stream` implies it).  Pageable frames are
+ * copied before the call returns.  Errors: PF_ERR_ARG (NULL frame, staging
+ * buffer NULL, misaligned or too small), PF_ERR_STATE, PF_ERR_CUDA. */
+pf_status pf_step_host(pf_handle* h, const float* const* frames_host, void* staging_dev, size_t staging_bytes,
+                       void* stream);
 
 /* pf_step with the frames taken from a device table: table_dev holds
  * T_table x n_tracks device pointers, frame k of track t at index

@@ -23,7 +23,8 @@ STATUS_NAMES = {0: "PF_OK", 1: "PF_ERR_ARG", 2: "PF_ERR_STATE", 3: "PF_ERR_CUDA"
                 5: "PF_ERR_DEGENERATE", 6: "PF_ERR_TIMEOUT", 7: "PF_ERR_DEVICE"}
 
 # Every symbol include/pfarna.h declares.
-EXPORTS = ("pf_abi_version", "pf_query_workspace", "pf_init", "pf_step", "pf_estimate", "pf_estimate_async",
+EXPORTS = ("pf_abi_version", "pf_query_workspace", "pf_init", "pf_step", "pf_host_staging_bytes", "pf_step_host",
+           "pf_estimate", "pf_estimate_async",
            "pf_exchange_stats",
            "pf_history", "pf_particles", "pf_resample_workspace", "pf_resample", "pf_resample_noalloc",
            "pf_profile_enable", "pf_profile_read", "pf_set_theta", "pf_reset", "pf_backward", "pf_step_table",
@@ -86,6 +87,8 @@ def load():
     L.pf_init.argtypes = [C.POINTER(pf_track_config), C.c_int32, C.c_int32, _P, C.c_size_t, _P, _P,
                           C.POINTER(_P)]
     L.pf_step.argtypes = [_P, C.POINTER(_P), _P]
+    L.pf_host_staging_bytes.argtypes = [_P, C.POINTER(C.c_size_t)]
+    L.pf_step_host.argtypes = [_P, C.POINTER(_P), _P, C.c_size_t, _P]
     L.pf_estimate.argtypes = [_P, _P, _P]
     L.pf_estimate_async.argtypes = [_P, _P, _P, _P]
     L.pf_exchange_stats.argtypes = [_P, C.c_int32, C.c_int32, C.POINTER(pf_step_stats), _P, _P, _P, _P]
@@ -143,6 +146,17 @@ def pf_init(cfgs, history: int, workspace_ptr: int, nbytes: int, user_state_ptr,
 def pf_step(handle: int, frame_ptrs, stream_ptr) -> None:
     arr = (_P * len(frame_ptrs))(*frame_ptrs)
     _check(load().pf_step(handle, arr, stream_ptr), "pf_step", handle)
+
+
+def pf_host_staging_bytes(handle: int) -> int:
+    n = C.c_size_t(0)
+    _check(load().pf_host_staging_bytes(handle, C.byref(n)), "pf_host_staging_bytes", handle)
+    return n.value
+
+
+def pf_step_host(handle: int, frame_ptrs, staging_ptr, staging_bytes: int, stream_ptr) -> None:
+    arr = (_P * len(frame_ptrs))(*frame_ptrs)
+    _check(load().pf_step_host(handle, arr, staging_ptr, staging_bytes, stream_ptr), "pf_step_host", handle)
 
 
 def pf_estimate(handle: int, xhat_host_ptr, logZ_host_ptr) -> int:

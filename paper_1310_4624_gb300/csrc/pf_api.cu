@@ -33,6 +33,10 @@ struct pf_handle {
   int steps_run = 0;
   int failed = 0;
   cudaStream_t last_stream = nullptr;
+  // pf_step_host: the upload stream and, per staging slot, "copied" and
+  // "read by its step" events (created on first use)
+  cudaStream_t up_stream = nullptr;
+  cudaEvent_t up_copied[2] = {nullptr, nullptr}, up_used[2] = {nullptr, nullptr};
   std::string err;
   QuantCoeffs qc{};
   // device pointers into the caller's workspace
@@ -98,6 +102,11 @@ struct pf_handle {
     for (auto& v : ev)
       for (cudaEvent_t e : v) cudaEventDestroy(e);
     if (graph) cudaGraphExecDestroy(graph);
+    for (int i = 0; i < 2; ++i) {
+      if (up_copied[i]) cudaEventDestroy(up_copied[i]);
+      if (up_used[i]) cudaEventDestroy(up_used[i]);
+    }
+    if (up_stream) cudaStreamDestroy(up_stream);
   }
 };
 
@@ -751,6 +760,74 @@ pf_status pf_step(pf_handle* h, const float* const* frames, void* stream) {
   h->steps_run += 1;
   h->finish_pending = true;
   h->last_stream = s;
+  return PF_OK;
+}
+
+// pf_step_host's staging: two slots (by step parity), each holding every
+// track's frame at a 256-byte aligned offset.
+static size_t staging_slot_bytes(const pf_handle* h, std::vector<size_t>* off) {
+  size_t n = 0;
+  for (int t = 0; t < h->n_tracks; ++t) {
+    if (off) off->push_back(n);
+    n += ((size_t)h->cfg[t].H * h->cfg[t].W * sizeof(float) + 255) & ~(size_t)255;
+  }
+  return n;
+}
+
+pf_status pf_host_staging_bytes(const pf_handle* h, size_t* bytes) {
+  if (!h || !bytes) return fail(nullptr, PF_ERR_ARG, "handle or output is NULL");
+  *bytes = 2 * staging_slot_bytes(h, nullptr);
+  return PF_OK;
+}
+
+pf_status pf_step_host(pf_handle* h, const float* const* frames_host, void* staging_dev, size_t staging_bytes,
+                       void* stream) {
+  NvtxRange nvtx_range("pf_step_host");
+  if (!h) return fail(nullptr, PF_ERR_ARG, "handle is NULL");
+  if (h->failed) return fail(h, PF_ERR_STATE, "handle failed earlier: " + h->err);
+  if (!frames_host) return fail(h, PF_ERR_ARG, "frames is NULL");
+  for (int t = 0; t < h->n_tracks; ++t)
+    if (!frames_host[t]) return fail(h, PF_ERR_ARG, "frame pointer of track " + std::to_string(t) + " is NULL");
+  std::vector<size_t> off;
+  const size_t slot_bytes = staging_slot_bytes(h, &off);
+  if (!staging_dev || ((uintptr_t)staging_dev & 255) != 0)
+    return fail(h, PF_ERR_ARG, "staging buffer is NULL or not 256-byte aligned");
+  if (staging_bytes < 2 * slot_bytes) return fail(h, PF_ERR_ARG, "staging buffer is smaller than pf_host_staging_bytes");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (!h->up_stream) {
+    if ((e = cudaStreamCreateWithFlags(&h->up_stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(h, e, "creating the upload stream");
+    for (int i = 0; i < 2; ++i)
+      if ((e = cudaEventCreateWithFlags(&h->up_copied[i], cudaEventDisableTiming)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&h->up_used[i], cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(h, e, "creating upload events");
+  }
+  const int slot = h->steps_run & 1;
+  char* base = (char*)staging_dev + (size_t)slot * slot_bytes;
+  // the step two back read this slot (an event never recorded waits for nothing)
+  if ((e = cudaStreamWaitEvent(h->up_stream, h->up_used[slot], 0)) != cudaSuccess)
+    return cuda_fail(h, e, "upload stream wait");
+  std::vector<const float*> dev(h->n_tracks);
+  std::unordered_map<const float*, int> first;  // a host frame given to several tracks is uploaded once
+  for (int t = 0; t < h->n_tracks; ++t) {
+    const size_t n = (size_t)h->cfg[t].H * h->cfg[t].W * sizeof(float);
+    auto it = first.find(frames_host[t]);
+    if (it != first.end() && (size_t)h->cfg[it->second].H * h->cfg[it->second].W * sizeof(float) == n) {
+      dev[t] = dev[it->second];
+      continue;
+    }
+    first.emplace(frames_host[t], t);
+    dev[t] = reinterpret_cast<const float*>(base + off[t]);
+    if ((e = cudaMemcpyAsync(base + off[t], frames_host[t], n, cudaMemcpyHostToDevice, h->up_stream)) != cudaSuccess)
+      return cuda_fail(h, e, "frame upload");
+  }
+  if ((e = cudaEventRecord(h->up_copied[slot], h->up_stream)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(s, h->up_copied[slot], 0)) != cudaSuccess)
+    return cuda_fail(h, e, "upload event");
+  const pf_status st = pf_step(h, dev.data(), stream);
+  if (st != PF_OK) return st;
+  if ((e = cudaEventRecord(h->up_used[slot], s)) != cudaSuccess) return cuda_fail(h, e, "upload event");
   return PF_OK;
 }
 

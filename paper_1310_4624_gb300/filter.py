@@ -92,6 +92,7 @@ class ParticleFilter:
         self.handle = B.pf_init(self.configs, history, self._ws_ptr, nbytes, _ptr(user_state),
                                 C.c_void_p(self.stream.cuda_stream))
         self.steps = 0
+        self._staging = None  # device staging of step_host (allocated on first use)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -114,6 +115,26 @@ class ParticleFilter:
                 raise ValueError("frames must be contiguous float32 CUDA tensors")
             ptrs.append(f.data_ptr())
         B.pf_step(self.handle, ptrs, C.c_void_p(self.stream.cuda_stream))
+        self.steps += 1
+
+    def step_host(self, frames) -> None:
+        """Advance every track by one step with frames in host memory: one
+        (H, W) float32 CPU tensor per track, page-locked for the upload to
+        overlap the previous step (pf_step_host; the device staging buffer
+        is allocated on the first call and kept)."""
+        if isinstance(frames, torch.Tensor) and frames.dim() == 2:
+            frames = [frames]
+        ptrs = []
+        for f in frames:
+            if f.dtype != torch.float32 or f.is_cuda or not f.is_contiguous():
+                raise ValueError("frames must be contiguous float32 host tensors")
+            ptrs.append(f.data_ptr())
+        if self._staging is None:
+            n = B.pf_host_staging_bytes(self.handle)
+            self._staging = torch.empty(n + 256, dtype=torch.uint8, device=self.device)
+            self._staging_ptr = C.c_void_p((self._staging.data_ptr() + 255) // 256 * 256)
+            self._staging_bytes = n
+        B.pf_step_host(self.handle, ptrs, self._staging_ptr, self._staging_bytes, C.c_void_p(self.stream.cuda_stream))
         self.steps += 1
 
     def frame_table(self, frames_per_track) -> torch.Tensor:

@@ -36,7 +36,7 @@ def test_header_declares_what_the_binding_wraps():
 def test_library_exports_every_declared_symbol(lib):
     for name in declared_functions():
         assert hasattr(lib, name), name
-    assert lib.pf_abi_version() == 3
+    assert lib.pf_abi_version() == 4
 
 
 def test_struct_layout_matches_ctypes(tmp_path):
@@ -120,6 +120,8 @@ def test_handle_less_calls_validate(lib):
     assert lib.pf_resample(None, None, 3, 5, None, None, None, 0, None) == B.PF_ERR_ARG
     assert lib.pf_step(None, None, None) == B.PF_ERR_ARG
     assert lib.pf_estimate(None, None, None) == B.PF_ERR_ARG
+    assert lib.pf_step_host(None, None, None, 0, None) == B.PF_ERR_ARG
+    assert lib.pf_host_staging_bytes(None, C.byref(n)) == B.PF_ERR_ARG
 
 
 def test_build_targets_sm103a_only():
