@@ -1057,7 +1057,7 @@ pf_status pf_estimate_async(pf_handle* h, float* xhat, double* logZ, void* strea
   double* logZ_dev = nullptr;
   if (host_mapped(xhat, reinterpret_cast<void**>(&xhat_dev)) &&
       host_mapped(logZ, reinterpret_cast<void**>(&logZ_dev))) {
-    if ((e = launch_finish_out(global_args(h, 1), h->n_tracks, xhat_dev, logZ_dev, s)) != cudaSuccess)
+    if ((e = launch_finish_out(global_args(h, 1), h->n_tracks, xhat_dev, logZ_dev, h->pdl, s)) != cudaSuccess)
       return cuda_fail(h, e, "k_finish_out");
     h->finish_pending = false;
     h->last_stream = s;

@@ -501,15 +501,24 @@ __global__ void __launch_bounds__(K1_THREADS) k_finish(GlobalArgs a) {
 
 // k_finish, then the track's x^ and log Z stored straight into the caller's
 // page-locked host buffers (their device addresses; either may be null), so
-// that reading the estimate back takes no copy on the stream.
-__global__ void __launch_bounds__(K1_THREADS) k_finish_out(GlobalArgs a, float* xhat, double* logZ) {
+// that reading the estimate back takes no copy on the stream.  It may be
+// launched while the resampler drains (programmatic dependent launch) and
+// waits for it before reading anything.
+struct FinishOutArgs {
+  GlobalArgs g;
+  float* xhat;
+  double* logZ;
+};
+
+__global__ void __launch_bounds__(K1_THREADS) k_finish_out(FinishOutArgs a) {
   __shared__ GlobalScratch sc;
-  finish_step<K1_THREADS>(a, blockIdx.x, sc);
+  grid_dep_wait();
+  finish_step<K1_THREADS>(a.g, blockIdx.x, sc);
   if (threadIdx.x == 0) {  // the thread that wrote the track state, if finish_step ran here
-    const TrackState* T = a.ts + blockIdx.x;
-    if (xhat)
-      for (int q = 0; q < 5; ++q) xhat[blockIdx.x * 5 + q] = __ldcg(&T->xhat[q]);
-    if (logZ) logZ[blockIdx.x] = __ldcg(&T->log_Z);
+    const TrackState* T = a.g.ts + blockIdx.x;
+    if (a.xhat)
+      for (int q = 0; q < 5; ++q) a.xhat[blockIdx.x * 5 + q] = __ldcg(&T->xhat[q]);
+    if (a.logZ) a.logZ[blockIdx.x] = __ldcg(&T->log_Z);
   }
 }
 
@@ -1662,9 +1671,9 @@ cudaError_t launch_finish(const GlobalArgs& a, int n_tracks, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_finish_out(const GlobalArgs& a, int n_tracks, float* xhat, double* logZ, cudaStream_t s) {
-  k_finish_out<<<n_tracks, K1_THREADS, 0, s>>>(a, xhat, logZ);
-  return cudaGetLastError();
+cudaError_t launch_finish_out(const GlobalArgs& a, int n_tracks, float* xhat, double* logZ, bool pdl,
+                              cudaStream_t s) {
+  return launch_ex(k_finish_out, dim3(n_tracks), dim3(K1_THREADS), 0, pdl, s, FinishOutArgs{a, xhat, logZ});
 }
 
 cudaError_t launch_export_states(const float4* pv, const float* In, long long n, float* out, cudaStream_t s) {

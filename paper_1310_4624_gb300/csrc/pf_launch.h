@@ -194,8 +194,10 @@ cudaError_t launch_resample(const ResampleArgs& a, int n_groups, int cluster, bo
 cudaError_t launch_global(const GlobalArgs& a, int n_tracks, cudaStream_t s);
 cudaError_t launch_finish(const GlobalArgs& a, int n_tracks, cudaStream_t s);
 // launch_finish, then x^ (n_tracks x 5) and log Z (n_tracks) stored through
-// device addresses of page-locked host memory (either may be null)
-cudaError_t launch_finish_out(const GlobalArgs& a, int n_tracks, float* xhat, double* logZ, cudaStream_t s);
+// device addresses of page-locked host memory (either may be null); pdl:
+// programmatic dependent launch behind the previous kernel
+cudaError_t launch_finish_out(const GlobalArgs& a, int n_tracks, float* xhat, double* logZ, bool pdl,
+                              cudaStream_t s);
 cudaError_t launch_export_states(const float4* pv, const float* In, long long n, float* out, cudaStream_t s);
 cudaError_t k1_occupancy(int R, int* blocks_per_sm);
 const void* propagate_kernel(int R);
