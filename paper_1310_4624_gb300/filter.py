@@ -17,6 +17,22 @@ Typical use (one track; a list of configurations makes a batch)::
     stats = pf.stats(wl.T - 1)                  # N_ex, PE_eff, ring, group weights
     pf.close()
 
+Frames streamed from host memory, with the estimate read back every step and
+nothing waiting on the device (the library uploads frame k+1 while step k
+runs; page-locked buffers make both directions asynchronous)::
+
+    host = torch.from_numpy(frames).pin_memory()
+    outs = [(torch.zeros(1, 5).pin_memory(), torch.zeros(1, dtype=torch.float64).pin_memory())
+            for _ in range(2)]
+    done = [torch.cuda.Event() for _ in range(2)]
+    for k in range(wl.T):
+        pf.step_host(host[k])
+        pf.estimate_async(*outs[k & 1])
+        done[k & 1].record(pf.stream)
+        if k > 0:
+            done[(k - 1) & 1].synchronize()     # step k-1's estimate is on the host
+            use(outs[(k - 1) & 1][0])
+
 Method variants are fields of the configuration: ``resample_rule`` /
 ``ess_fraction`` (Alg. 1's N_eff test per group), ``send_rule`` (keyed random
 send sets), ``topology`` / ``node_groups`` (Sec. VI's node-aware ring and
