@@ -42,3 +42,23 @@ def test_replicas_barrier_and_max_over_ranks():
         got = dict(out)
     assert got[0] == (2, 0, 0, 2.5)
     assert got[1] == (2, 1, 1, 2.5)
+
+
+def test_reference_arm_prints_one_oracle_line():
+    """bench.py --impl reference (the oracle on the host cores) prints one
+    JSON line with the headline metric, unit and config, and the fields the
+    reference arm carries."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], capture_output=True, text=True, check=True, cwd=root, timeout=600)
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["unit"] == "particle-steps/s" and d["metric"].startswith("particle-steps/s")
+    assert d["config"]["workload"] == "tracking_512x512_G64x16384_arna"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
