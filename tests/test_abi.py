@@ -126,3 +126,25 @@ def test_handle_less_calls_validate(lib):
 
 def test_build_targets_sm103a_only():
     assert cuda_build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built library every call raises (no CPU fallback)."""
+    monkeypatch.setattr(B, "_lib", None)
+    monkeypatch.setattr(B._build, "LIB", str(tmp_path / "libpfarna.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        B.load()
+    with pytest.raises(RuntimeError, match="not built"):
+        B.pf_query_workspace([_cfg()], 4)
+
+
+def test_product_package_does_not_use_the_oracle():
+    """The package (binding, wrapper, kernels) never imports, loads or runs
+    anything under oracle/: the oracle is test infrastructure."""
+    pkg = os.path.join(ROOT, "paper_1310_4624_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".c", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", text, flags=re.M), f
+                assert "pf_oracle" not in text and "liboracle" not in text, f
