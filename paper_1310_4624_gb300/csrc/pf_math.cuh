@@ -128,20 +128,23 @@ __device__ __forceinline__ void gauss_row(float cf, float x, float c, float kapp
 }
 
 // gauss_row scaled by `scale` (the spot intensity I): the centre value is
-// scale 2^(-c d^2) and the recurrence carries the factor.
+// scale 2^(-c d^2) and the recurrence carries the factor.  The two sides of
+// the recurrence advance together in packed FP32 pairs (one FMUL2 per pair
+// of products, each lane rounded as its scalar product would be).
 template <int R>
 __device__ __forceinline__ void gauss_row_scaled(float cf, float x, float c, float kappa, float scale,
                                                  float (&g)[2 * R + 1]) {
   const float d = cf - x;
   g[R] = scale * ex2(-c * d * d);
-  float up = ex2(-c * fmaf(2.0f, d, 1.0f));
-  float dn = ex2(c * fmaf(2.0f, d, -1.0f));
+  float2 ud = make_float2(ex2(-c * fmaf(2.0f, d, 1.0f)), ex2(c * fmaf(2.0f, d, -1.0f)));  // (up, dn)
+  const float2 kk = make_float2(kappa, kappa);
+  float2 gv = make_float2(g[R], g[R]);
 #pragma unroll
   for (int a = 1; a <= R; ++a) {
-    g[R + a] = g[R + a - 1] * up;
-    g[R - a] = g[R - a + 1] * dn;
-    up *= kappa;
-    dn *= kappa;
+    gv = __fmul2_rn(gv, ud);
+    g[R + a] = gv.x;
+    g[R - a] = gv.y;
+    ud = __fmul2_rn(ud, kk);
   }
 }
 
@@ -213,16 +216,58 @@ __device__ __forceinline__ float patch_ss(const float* __restrict__ base, int pi
 
 // Shared-memory rows read as float pairs: `base` is 8-byte aligned and row
 // b's pixels are base[b ROI_W + 0 .. 2R] (the pair loads also fetch
-// base[.. + 2R + 1], unused).
+// base[.. + 2R + 1], unused).  Columns 2p and 2p + 1 are processed as one
+// packed FP32 pair (FFMA2 / FMUL2): lane x is the even column, lane y the
+// odd one, so the even and odd accumulators of patch_sum become the two
+// lanes of one pair and every lane rounds as the scalar form does; the
+// last (even) column goes through the scalar path.  The result is therefore
+// bit-identical to patch_sum over the same pixels, in about half the
+// instructions.
 template <int R, bool FRAME>
 __device__ __forceinline__ float patch_ss_pairs(const float* __restrict__ base, const float (&gxI)[2 * R + 1],
                                                 float dy, float c, float kappa) {
-  return patch_sum<R, FRAME>(
-      [&](int b, int a) {
-        const float2 v = reinterpret_cast<const float2*>(base + b * ROI_W)[a >> 1];
-        return (a & 1) ? v.y : v.x;
-      },
-      gxI, dy, c, kappa);
+  float2 gp[R];  // (gx(2p), gx(2p+1)), negated for the residual form
+#pragma unroll
+  for (int p = 0; p < R; ++p)
+    gp[p] = FRAME ? make_float2(gxI[2 * p], gxI[2 * p + 1]) : make_float2(-gxI[2 * p], -gxI[2 * p + 1]);
+  float2 acc = make_float2(0.0f, 0.0f);  // (even columns, odd columns)
+  auto row = [&](int b, float gy) {
+    const float2* __restrict__ r2 = reinterpret_cast<const float2*>(base + b * ROI_W);
+    const float2 gy2 = make_float2(gy, gy);
+#pragma unroll
+    for (int p = 0; p < R; ++p) {
+      const float2 y = r2[p];
+      if constexpr (FRAME) {
+        const float2 m = __fmul2_rn(gp[p], gy2);
+        const float2 t = __ffma2_rn(make_float2(-2.0f, -2.0f), y, m);
+        acc = __ffma2_rn(m, t, acc);
+      } else {
+        const float2 r = __ffma2_rn(gp[p], gy2, y);
+        acc = __ffma2_rn(r, r, acc);
+      }
+    }
+    const float y = r2[R].x;  // column 2R
+    if constexpr (FRAME) {
+      const float m = gxI[2 * R] * gy;
+      acc.x = fmaf(m, fmaf(-2.0f, y, m), acc.x);
+    } else {
+      const float r = fmaf(-gxI[2 * R], gy, y);
+      acc.x = fmaf(r, r, acc.x);
+    }
+  };
+  const float g = ex2(-c * dy * dy);
+  float2 ud = make_float2(ex2(-c * fmaf(2.0f, dy, 1.0f)), ex2(c * fmaf(2.0f, dy, -1.0f)));  // (up, dn)
+  const float2 kk = make_float2(kappa, kappa);
+  row(R, g);
+  float2 gv = make_float2(g, g);  // (rows below the centre, rows above)
+#pragma unroll
+  for (int a = 1; a <= R; ++a) {
+    gv = __fmul2_rn(gv, ud);
+    ud = __fmul2_rn(ud, kk);
+    row(R + a, gv.x);
+    row(R - a, gv.y);
+  }
+  return acc.x + acc.y;
 }
 
 // The caller's frame z (W x H, pitch W) instead of the padded frame: pixel
