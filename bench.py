@@ -44,11 +44,20 @@ if ROOT not in sys.path:
 METRIC = "particle-steps/s (propagate+weight+ARNA)"
 UNIT = "particle-steps/s"
 
-# Algorithmic work of the dominant kernel (propagate_weight) per particle and
-# step; derivation in DESIGN.md ("Roofline").
-ALG_LANE_OPS = 540      # FP32 + INT32 lane operations
-ALG_SFU_OPS = 35        # MUFU operations
-ALG_BYTES = 48          # HBM bytes of the whole step per particle
+# Algorithmic work per particle-step, fixed for the roofline: FP32 / INT32
+# lane operations (likelihood 121 pixels x 3 + 44 Gaussian arguments + 11
+# hoisted products, propagation 10, Box-Muller ~15, uniform maps 6, Philox 2
+# calls x 10 rounds x ~8), MUFU operations (22 ex2, 3 lg2, 3 sqrt, 6
+# sin/cos), and HBM bytes (parent state 20 + new state 20 + ancestor written
+# 4 + ancestor read 4).  These are counts of the method, not of the kernels:
+# arithmetic the kernels save (fused multiply-adds, recurrences) raises the
+# reported fraction and does not lower the work credited.
+ALG_LANE_OPS = 610
+ALG_SFU_OPS = 34
+ALG_BYTES = 48
+# The same lane count with two fused multiply-adds per pixel, a tighter
+# reading of the likelihood (reported beside the fixed one, labelled).
+ALG_LANE_OPS_FMA = 540
 
 
 def kernel_source_hash() -> str:
@@ -192,56 +201,112 @@ def time_filter(pf, fr, first: int, K: int, flush, profile: bool):
     return sum(a.elapsed_time(b) for a, b in evs)
 
 
-def cpu_baseline(wl, frames, truth, steps: int = 8):
-    """The FP64 oracle as it stands, single-threaded, on the full workload
-    population for `steps` steps after an untimed step 0."""
+def _oracle_rate(wl, frames, truth, steps: int, threads: int, first: int = 1):
+    """particle-steps/s of the FP64 oracle (as it stands) over steps
+    first .. first+steps-1 of `wl` after untimed steps 0 .. first-1, on
+    `threads` host threads; returns (rate, seconds, threads used)."""
     import oracle as ora
+    from paper_1310_4624_gb300 import synth
     ocfg = ora.cfg_from_workload(wl)
-    pop = ora.init_population(ocfg, ora.INIT_POINT, np.float32(truth[0]).astype(np.float64))
-    r = ora.step(ocfg, 0, frames[0], pop)
-    t0 = time.perf_counter()
-    for k in range(1, steps + 1):
-        r = ora.step(ocfg, k, frames[k], r.pop_out, r.Lambda)
-    dt = time.perf_counter() - t0
-    return {"value": wl.N * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d oracle steps (k=1..%d) of the full %d-particle workload, FP64, 1 thread, %.1f s"
-                      % (steps, steps, wl.N, dt)}
+    kind, x0, lo, hi, rad = synth.init_arrays(wl, np.float32(truth[0]).astype(np.float64))
+    f = lambda a: np.float32(a).astype(np.float64)  # noqa: E731
+    pop = ora.init_population(ocfg, kind, f(x0), f(lo), f(hi), float(np.float32(rad)))
+    used = ora.set_threads(threads)
+    try:
+        lam = None
+        for k in range(first):
+            r = ora.step(ocfg, k, frames[k], pop, lam)
+            pop, lam = r.pop_out, r.Lambda
+        t0 = time.perf_counter()
+        for k in range(first, first + steps):
+            r = ora.step(ocfg, k, frames[k], pop, lam)
+            pop, lam = r.pop_out, r.Lambda
+        dt = time.perf_counter() - t0
+    finally:
+        ora.set_threads(1)
+    return wl.N * steps / dt, dt, used
+
+
+def cpu_baseline(wl, frames, truth, steps: int = 8, steps_single: int = 4):
+    """The FP64 oracle as it stands on the full workload population: `steps`
+    steps with its loops on every host core (OpenMP over particles and
+    groups), and `steps_single` steps on one thread, each after an untimed
+    step 0."""
+    cores = os.cpu_count() or 1
+    v, dt, used = _oracle_rate(wl, frames, truth, steps, cores)
+    v1, dt1, _ = _oracle_rate(wl, frames, truth, steps_single, 1)
+    return {"value": v, "unit": UNIT, "cores": used, "kind": "oracle", "host_cpu_count": cores,
+            "sample": "%d oracle steps (k=1..%d) of the full %d-particle workload, FP64, %d threads, %.1f s"
+                      % (steps, steps, wl.N, used, dt),
+            "single_thread": {"value": v1, "cores": 1,
+                              "sample": "%d steps (k=1..%d), 1 thread, %.1f s" % (steps_single, steps_single, dt1)}}
+
+
+def bench_oracle_configs():
+    """The oracle timed on the host cores (all of them, OpenMP; and one
+    thread) per workload: the small RNA run and the information-sharing run
+    in full, the tracking and differentiable runs on their first 5 frames,
+    and 8 tracks drawn from the batched workload."""
+    from paper_1310_4624_gb300 import synth
+    cores = os.cpu_count() or 1
+    out = {"host_cpu_count": cores}
+    jobs = [("small_rna", synth.small_rna(), None, 0),
+            ("sharing_arna", synth.sharing(mode=synth.ARNA), None, 0),
+            ("tracking_arna", synth.tracking(mode=synth.ARNA), 5, 0),
+            ("differentiable", synth.differentiable(), 5, 0)]
+    for name, wl, T, _ in jobs:
+        T = wl.T if T is None else T
+        frames, truth = synth.make_sequence(wl, T=T)
+        v, dt, used = _oracle_rate(wl, frames, truth, T, cores, first=0)
+        row = {"value": v, "unit": UNIT, "threads": used, "steps": T, "particles": wl.N, "seconds": dt}
+        if name == "small_rna":
+            v1, dt1, _ = _oracle_rate(wl, frames, truth, T, 1, first=0)
+            row["single_thread"] = {"value": v1, "seconds": dt1}
+        out[name] = row
+    # batched: 8 of the 512 tracks (every 64th), 50 frames each
+    wls = synth.batched_tracks(512)[::64]
+    n, secs = 0, 0.0
+    for wl in wls:
+        frames, truth = synth.make_sequence(wl)
+        v, dt, used = _oracle_rate(wl, frames, truth, wl.T, cores, first=0)
+        n += wl.N * wl.T
+        secs += dt
+    out["batched_8_tracks"] = {"value": n / secs, "unit": UNIT, "threads": used, "tracks": len(wls),
+                               "particle_steps": n, "seconds": secs}
+    return out
 
 
 def run_reference(args, ws, rank):
-    """The reference arm: the CPU oracle, timed as it stands, on a bounded
-    sample of the same workload (all 64 groups, 1024 particles each)."""
+    """The reference arm: the FP64 CPU oracle, timed as it stands, on the
+    same workload (all 64 x 16384 particles of the tracking run, ARNA), its
+    per-particle and per-group loops on every host core; W untimed steps,
+    then K timed steps."""
     if rank != 0:
         return
-    import oracle as ora
     from paper_1310_4624_gb300 import synth
     K, W = args.steps, args.warmup
-    full = synth.tracking(mode=synth.ARNA, T=max(K + W + 1, 8))
-    wl = full.replace(Np=1024)
+    wl = synth.tracking(mode=synth.ARNA, T=K + W + 1)
     frames, truth = synth.make_sequence(wl)
-    ocfg = ora.cfg_from_workload(wl)
-    pop = ora.init_population(ocfg, ora.INIT_POINT, np.float32(truth[0]).astype(np.float64))
-    lam = None
-    for k in range(W):
-        r = ora.step(ocfg, k, frames[k], pop, lam)
-        pop, lam = r.pop_out, r.Lambda
-    t0 = time.perf_counter()
-    for k in range(W, W + K):
-        r = ora.step(ocfg, k, frames[k], pop, lam)
-        pop, lam = r.pop_out, r.Lambda
-    dt = time.perf_counter() - t0
-    value = wl.N * K / dt
+    cores = os.cpu_count() or 1
+    value, dt, used = _oracle_rate(wl, frames, truth, K, cores, first=W)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
             "warmup": W, "ms_per_step": dt / K * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": full.name, "particles": full.N, "G": full.G, "Np": full.Np,
-                       "frame": "%dx%d" % (full.H, full.W), "mode": "ARNA",
-                       "sample": "G=64 x 1024 particles per step"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "each step: all 64 groups x 1024 particles of the workload, FP64 oracle, "
-                                       "1 thread"},
+            "config": {"workload": wl.name, "particles": wl.N, "G": wl.G, "Np": wl.Np,
+                       "frame": "%dx%d" % (wl.H, wl.W), "mode": "ARNA", "init": "all particles at the truth"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
+                             "sample": "steps %d..%d of the full %d-particle workload, FP64 oracle, %d threads, %.1f s"
+                                       % (W, W + K - 1, wl.N, used, dt)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def _lane_peak(dev):
+    """SMs x 128 lanes x the maximum SM clock (per second)."""
+    import torch
+    peaks, _ = _peaks()
+    return torch.cuda.get_device_properties(dev).multi_processor_count * 128 * float(
+        peaks.get("sm_max_mhz", 2070.0)) * 1e6
 
 
 def _events(stream, fn):
@@ -256,6 +321,51 @@ def _events(stream, fn):
     return a.elapsed_time(b)
 
 
+def bench_configs(dev, reps: int = 3):
+    """GPU particle-steps/s of the other single-track workloads, whole
+    sequences timed with CUDA events (best of `reps`; L2 not flushed inside a
+    sequence): the small RNA run (20 frames 64 x 64, G = 4 x 1024, RNA 10 %)
+    through pf_step and through the CUDA-graph step (pf_graph_step, frames
+    from a device table), and the information-sharing run (100 frames 512 x
+    512, G = 256 x 4096, sharing start) for ARNA and RNA 10 %."""
+    import torch
+    from paper_1310_4624_gb300 import synth
+    from paper_1310_4624_gb300.filter import ParticleFilter, config_from_workload
+    out = {}
+    wl = synth.small_rna()
+    frames, truth = synth.make_sequence(wl)
+    fr = torch.from_numpy(frames).to(dev)
+    pf = ParticleFilter([config_from_workload(wl, truth[0])], history=wl.T + 1, device=dev)
+    table = pf.frame_table([fr])
+    best_step, best_graph = 1e30, 1e30
+    for _ in range(reps):
+        pf.reset()
+        best_step = min(best_step, _events(pf.stream, lambda: [pf.step(fr[k]) for k in range(wl.T)]))
+        pf.reset()
+        best_graph = min(best_graph, _events(pf.stream, lambda: [pf.step_table(table, graph=True)
+                                                                  for _ in range(wl.T)]))
+    pf.close()
+    n = wl.N * wl.T
+    out["small_rna"] = {"workload": wl.name, "particles": wl.N, "steps": wl.T, "unit": UNIT,
+                        "pf_step": {"value": n / (best_step / 1e3), "ms_per_step": best_step / wl.T},
+                        "graph": {"value": n / (best_graph / 1e3), "ms_per_step": best_graph / wl.T}}
+    frames = fr = None
+    for mode, name in ((synth.ARNA, "sharing_arna"), (synth.RNA, "sharing_rna10")):
+        wl = synth.sharing(mode=mode)
+        if frames is None:
+            frames, truth = synth.make_sequence(wl)
+            fr = torch.from_numpy(frames).to(dev)
+        pf = ParticleFilter([config_from_workload(wl, truth[0])], history=wl.T + 1, device=dev)
+        best = 1e30
+        for _ in range(reps):
+            pf.reset()
+            best = min(best, _events(pf.stream, lambda: [pf.step(fr[k]) for k in range(wl.T)]))
+        pf.close()
+        out[name] = {"workload": wl.name, "particles": wl.N, "steps": wl.T, "unit": UNIT,
+                     "value": wl.N * wl.T / (best / 1e3), "ms_per_step": best / wl.T}
+    return out
+
+
 def bench_batched(dev, K: int, W: int, flush, n_tracks: int = 512, k_alone: int = 8):
     """512 independent tracks (256 x 256 frames, 50-frame sequences; particle
     counts log-uniform in [4096, 262144], groups log-uniform in [4, 128],
@@ -266,7 +376,7 @@ def bench_batched(dev, K: int, W: int, flush, n_tracks: int = 512, k_alone: int 
     import torch
     from paper_1310_4624_gb300 import synth
     from paper_1310_4624_gb300.filter import ParticleFilter, config_from_workload
-    T = max(50, W + K + 2)
+    T = max(50, W + K + 6)  # autotuned step, warm-up, timed steps, three profiled steps
     wls = synth.batched_tracks(n_tracks, T=T)
     frames, truths = synth.render_batched_torch(wls, dev, seed=0)
     cfgs = [config_from_workload(wl, truths[t][0], track_id=t) for t, wl in enumerate(wls)]
@@ -280,8 +390,16 @@ def bench_batched(dev, K: int, W: int, flush, n_tracks: int = 512, k_alone: int 
     for _ in range(K):
         flush.zero_()
         ms += _events(pf.stream, lambda: pf.step_table(table, graph=True))
+    # the kernels of a step (per-kernel events serialise them; not the timed steps)
+    pf.profile(True)
+    for _ in range(3):
+        flush.zero_()
+        pf.step_table(table, graph=False)
+    prof = pf.profile_read()
+    pf.profile(False)
     _, logz, st = pf.estimate()
     pf.close()
+    pixels = sum(wl.H * wl.W for wl in wls)
     # the same tracks one by one through the plain entry point
     alone = [ParticleFilter([c], history=4, device=dev) for c in cfgs]
     for k in range(W):
@@ -307,7 +425,10 @@ def bench_batched(dev, K: int, W: int, flush, n_tracks: int = 512, k_alone: int 
                     % (grid, cluster),
             "one_by_one": {"value": n_total * Ka / (ms_alone / 1e3), "ms_per_step": ms_alone / Ka,
                            "steps": Ka, "form": "512 handles, pf_step each, same stream"},
-            "speedup": (ms_alone / Ka) / (ms / K), "degenerate_status": int(st)}
+            "speedup": (ms_alone / Ka) / (ms / K), "degenerate_status": int(st),
+            "roofline_frac": ALG_LANE_OPS * n_total / (ms / K / 1e3) / _lane_peak(dev),
+            "kernels": {n: {"launches": c, "ms_per_launch": t / max(1, c)} for n, (c, t) in prof.items() if c > 0},
+            "frame_prep_hbm_bound_ms": 8.0 * pixels / (float(_peaks()[0]["hbm_gbs"]) * 1e9) * 1e3}
 
 
 def bench_adjoint(dev, flush, reps: int = 3):
@@ -351,9 +472,13 @@ def bench_adjoint(dev, flush, reps: int = 3):
             out["log_Z"] = float(lz[0])
         if rec:
             out["fit"] = adam_fit(pf, wl, fr, truth)
+            out["fit_observation"] = adam_fit(pf, wl, fr, truth, fit=(0, 1, 2))
         pf.close()
     n = wl.N * wl.T
-    return {"fit": out["fit"], "workload": wl.name, "particles": wl.N, "steps": wl.T, "unit": UNIT,
+    lane = _lane_peak(dev)
+    return {"fit": out["fit"], "fit_observation_only": out["fit_observation"], "workload": wl.name,
+            "fwd_roofline_frac": ALG_LANE_OPS * n / (out["fwd"] / 1e3) / lane,
+            "fwd_bwd_rate_over_fwd_roofline": ALG_LANE_OPS * n / ((out["fwd_rec"] + out["bwd"]) / 1e3) / lane, "particles": wl.N, "steps": wl.T, "unit": UNIT,
             "fwd": {"value": n / (out["fwd"] / 1e3), "ms": out["fwd"]},
             "fwd_recording": {"value": n / (out["fwd_rec"] / 1e3), "ms": out["fwd_rec"]},
             "fwd_bwd": {"value": n / ((out["fwd_rec"] + out["bwd"]) / 1e3), "ms": out["fwd_rec"] + out["bwd"]},
@@ -362,16 +487,21 @@ def bench_adjoint(dev, flush, reps: int = 3):
             "log_Z": out["log_Z"], "timing": "best of %d passes, CUDA events" % reps}
 
 
-def adam_fit(pf, wl, fr, truth, iters: int = 200, lr: float = 0.02):
+def adam_fit(pf, wl, fr, truth, iters: int = 200, lr: float = 0.02, fit=(0, 1, 2, 3, 4)):
     """Maximum-likelihood fit of theta = (sigma_psf, A, b, sigma_pos, sigma_v)
-    by Adam on log theta, from theta_true x 1.3, each iteration one forward
-    run (ancestry recorded) and one pf_backward (common random numbers: the
-    filter's seed is fixed)."""
+    by Adam on log theta, from theta_true x 1.3 on the components in `fit`
+    (the others held at the truth), each iteration one forward run
+    (ancestry recorded) and one pf_backward (common random numbers: the
+    filter's seed is fixed).  The gradient holds the resampling ancestry
+    fixed, so it is biased for sigma_pos and sigma_v, which move particles
+    across the resampling decisions; sigma_psf, A and b do not."""
     import torch
     from paper_1310_4624_gb300.filter import LogLikelihood
     names = ("sigma_psf", "A", "b", "sigma_pos", "sigma_v")
     true = np.array([wl.sigma_psf, float(np.float32(truth[0][4])), wl.background, wl.sigma_pos, wl.sigma_v])
-    logt = torch.tensor(np.log(true * 1.3), dtype=torch.float64, requires_grad=True)
+    mask = torch.tensor([1.0 if q in fit else 0.0 for q in range(5)], dtype=torch.float64)
+    start = np.where(mask.numpy() > 0, true * 1.3, true)
+    logt = torch.tensor(np.log(start), dtype=torch.float64, requires_grad=True)
     opt = torch.optim.Adam([logt], lr=lr)
     first = last = None
     t0 = time.perf_counter()
@@ -379,6 +509,7 @@ def adam_fit(pf, wl, fr, truth, iters: int = 200, lr: float = 0.02):
         opt.zero_grad()
         lz = LogLikelihood.apply(torch.exp(logt), pf, fr)
         (-lz).backward()
+        logt.grad.mul_(mask)
         opt.step()
         v = float(lz)
         first = v if first is None else first
@@ -388,7 +519,8 @@ def adam_fit(pf, wl, fr, truth, iters: int = 200, lr: float = 0.02):
     lz_true = float(LogLikelihood.apply(torch.tensor(true), pf, fr))
     end = np.exp(logt.detach().numpy())
     return {"iters": iters, "lr_log_theta": lr, "theta_true": dict(zip(names, true.round(4).tolist())),
-            "theta_start": dict(zip(names, (true * 1.3).round(4).tolist())),
+            "fitted": [names[q] for q in fit],
+            "theta_start": dict(zip(names, start.round(4).tolist())),
             "theta_end": dict(zip(names, end.round(4).tolist())),
             "log_Z_start": first, "log_Z_end": last, "log_Z_at_true": lz_true, "seconds": dt}
 
@@ -694,15 +826,29 @@ def main():
     k1_avg_s = k1_ms / 1e3 / max(1, k1_launches)
     achieved = ALG_LANE_OPS * wl.N / k1_avg_s
     traffic, traffic_src = profiled_traffic("k_propagate_weight")
+    step_s = a["ms"] / K / 1e3
+    hbm = float(peaks["hbm_gbs"]) * 1e9
+    sfu_peak = sms * 16 * f_max
+    sm_mhz = a["clocks"]["sm_mhz"] if a["clocks"] and a["clocks"].get("sm_mhz") else None
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": lane_peak / 1e12, "unit": "Tops/s",
                 "frac": achieved / lane_peak, "traffic": traffic, "traffic_source": traffic_src,
                 "kernel": "k_propagate_weight", "peak_source": "%d SMs x 128 lanes x %.0f MHz (%s sm_max_mhz)"
                 % (sms, f_max / 1e6, src),
+                "work_per_particle": {"lane_ops": ALG_LANE_OPS, "mufu": ALG_SFU_OPS, "hbm_bytes": ALG_BYTES},
                 "kernel_ms": k1_avg_s * 1e3,
-                "frac_at_sampled_clock": (achieved / (sms * 128 * a["clocks"]["sm_mhz"] * 1e6)
-                                          if a["clocks"] and a["clocks"].get("sm_mhz") else None),
-                "hbm_frac": ALG_BYTES * wl.N / k1_avg_s / (float(peaks["hbm_gbs"]) * 1e9),
-                "sfu_frac": ALG_SFU_OPS * wl.N / k1_avg_s / (sms * 16 * f_max)}
+                "frac_at_sampled_clock": achieved / (sms * 128 * sm_mhz * 1e6) if sm_mhz else None,
+                "frac_fma_count": ALG_LANE_OPS_FMA * wl.N / k1_avg_s / lane_peak,
+                "hbm_frac": ALG_BYTES * wl.N / k1_avg_s / hbm,
+                "sfu_frac": ALG_SFU_OPS * wl.N / k1_avg_s / sfu_peak,
+                # the whole step (every kernel of pf_step, device-timed), against
+                # the step's bound: the slowest of lane ops, MUFU and HBM bytes
+                "step": {"ms": step_s * 1e3, "achieved": ALG_LANE_OPS * wl.N / step_s / 1e12,
+                         "frac": ALG_LANE_OPS * wl.N / step_s / lane_peak,
+                         "frac_at_sampled_clock": (ALG_LANE_OPS * wl.N / step_s / (sms * 128 * sm_mhz * 1e6)
+                                                   if sm_mhz else None),
+                         "bound_ms": 1e3 * wl.N * max(ALG_LANE_OPS / lane_peak, ALG_SFU_OPS / sfu_peak,
+                                                       ALG_BYTES / hbm),
+                         "hbm_frac": ALG_BYTES * wl.N / step_s / hbm}}
     kernels = {n: {"launches": c, "ms_per_launch": ms / max(1, c), "share": ms / max(1e-12, sum(
         v[1] for v in a["prof"].values()))} for n, (c, ms) in a["prof"].items() if c > 0}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
@@ -728,6 +874,7 @@ def main():
             "arna_n_ex": a["n_ex"][:12]}
     if not args.no_extras:
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+        line["configs"] = bench_configs(dev)
         line["batched"] = bench_batched(dev, K, W, flush)
         line["adjoint"] = bench_adjoint(dev, flush)
         line["sharing"] = bench_sharing(dev)
@@ -738,6 +885,8 @@ def main():
         del flush
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, frames, truth)
+        if not args.no_extras:
+            line["oracle_by_config"] = bench_oracle_configs()
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:

@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define PF_ABI_VERSION 4
+#define PF_ABI_VERSION 5
 
 typedef enum pf_status {
   PF_OK = 0,
@@ -172,8 +172,12 @@ typedef struct pf_handle pf_handle;
 /* ABI version of the loaded library (PF_ABI_VERSION it was built with). */
 int32_t pf_abi_version(void);
 
-/* Workspace bytes needed by pf_init for `n_tracks` configs (cfg[0..n-1])
- * keeping `history` steps of statistics (>= 1; the last `history` steps stay
+/* Workspace bytes needed by pf_init for `n_tracks` configs (cfg[0..n-1]).
+ * The paper's problem (Sec. II) is the filtering density of the state given
+ * the frames so far, carried by N = G * Np weighted particles split over
+ * the G PEs (Sec. III); the workspace holds those particles, their weights
+ * and the per-group and per-step quantities of Alg. 3, sized here
+ * for `history` steps of statistics (>= 1; the last `history` steps stay
  * readable through pf_exchange_stats / pf_history).  With record_ancestors
  * set, `history` is also the longest sequence pf_backward can differentiate.
  * Errors: PF_ERR_ARG for invalid configs or NULL pointers. */
@@ -265,7 +269,10 @@ pf_status pf_autotune(pf_handle* h, const float* const* frames_host, int32_t* k1
 
 /* Wait for the handle's last stream and copy the latest global estimate
  * (n_tracks x 5 floats, may be NULL) and log marginal-likelihood estimate
- * log Z = sum_k log c_k (n_tracks doubles, may be NULL) to the host.
+ * log Z = sum_k log c_k (n_tracks doubles, may be NULL) to the host.  These
+ * are the master PE's outputs of Alg. 3 steps 9-10: the estimate combines
+ * the group estimates x^^m (step 6) with the normalised group weights, and
+ * c_k is the sum of the group weights W^(m) (the normaliser of step 9).
  * Errors: PF_ERR_STATE (no step run), PF_ERR_DEGENERATE (some track lost all
  * weight: its values are NaN / -inf), PF_ERR_DEVICE / PF_ERR_TIMEOUT (the
  * kernels reported an error), PF_ERR_CUDA. */
@@ -286,7 +293,11 @@ pf_status pf_estimate(pf_handle* h, float* xhat_host, double* log_Z_host);
 pf_status pf_estimate_async(pf_handle* h, float* xhat_host, double* log_Z_host, void* stream);
 
 /* Statistics of step `step` (< steps run, and among the last `history`) of
- * track `track`; optional per-group arrays (length G, may be NULL):
+ * track `track`: the exchange count N_ex of Eq. 3 (the fixed ratio for
+ * PF_RNA) and the PE_eff of Eq. 4 it was decided from, the ring of Sec.
+ * IV-B, the group weights and estimates of Alg. 3 steps 6 and 8, and the
+ * step's incremental likelihood (steps 9-10).  Optional per-group arrays
+ * (length G, may be NULL):
  * ring_host[p] = group at ring position p (group ring[p] sends to
  * ring[(p+1) mod G]) used at that step; group_logW_host = log W^(m) after
  * the step; group_xhat_host = group estimates x^^m, 5 x G SoA;
@@ -329,7 +340,10 @@ pf_status pf_resample_workspace(int32_t G, int32_t Np, size_t* bytes);
  * Output j takes the particle i with S_i <= (j + u/2^32) Q / Np < S_{i+1},
  * S the prefix sums of q and Q their total, compared exactly in 128-bit
  * integers; a group with Q = 0 resamples as the identity.
- * G >= 1, 1 <= Np <= 2^20, G*Np < 2^31.
+ * G >= 1, 1 <= Np <= 2^20, G*Np < 2^31.  The call only enqueues: a
+ * device-side error of the kernel (an internal bound exhausted, reported in
+ * the error word at the start of the workspace) is not returned here but by
+ * pf_resample_check(workspace_dev, stream).
  * Errors: PF_ERR_ARG, PF_ERR_WORKSPACE, PF_ERR_CUDA. */
 pf_status pf_resample(const float* logw_dev, const uint32_t* u_dev, int32_t G, int32_t Np,
                       uint32_t* anc_dev, uint64_t* q_dev, void* workspace_dev, size_t bytes,
@@ -349,14 +363,27 @@ pf_status pf_resample(const float* logw_dev, const uint32_t* u_dev, int32_t G, i
  * every GPU that loads the library holds until the process exits.  The
  * first call on a device looks up that array's device address
  * (cudaGetSymbolAddress, with the device current) and should come before
- * any stream capture.  The call allocates nothing and frees nothing.  All
- * calls share the array, which keeps the last call's contents; each call
- * clears what must start at zero, and calls that overlap on the GPU race.
+ * any stream capture.  The cached address belongs to the CUDA context it was
+ * looked up in; after cudaDeviceReset the next call looks it up again.  The
+ * call allocates nothing and frees nothing.  All calls share the array,
+ * which keeps the last call's contents; each call clears what must start at
+ * zero, and calls that overlap on the GPU race.  As with pf_resample, a
+ * device-side error of the kernel is not returned by this call but by
+ * pf_resample_check(NULL, stream), until the next call clears it.
  * G >= 1 and G <= PF_NOALLOC_MAX_GROUPS, 1 <= Np <= 2^20, G*Np < 2^31;
  * larger G is rejected with PF_ERR_ARG.  Errors are reported through
  * pf_last_error(NULL).  Errors: PF_ERR_ARG, PF_ERR_CUDA. */
 pf_status pf_resample_noalloc(const float* logw_dev, const uint32_t* u_dev, int32_t G, int32_t Np,
                               uint32_t* anc_dev, uint64_t* q_dev, void* stream);
+
+/* Wait for `stream` and report the device-side error word of the last
+ * pf_resample run in `workspace_dev` (its workspace), or, with workspace_dev
+ * NULL, of the last pf_resample_noalloc on the current device: PF_OK, or
+ * PF_ERR_DEVICE / PF_ERR_TIMEOUT with the error bits in pf_last_error(NULL).
+ * The resampler itself is Alg. 1 step 6; this call only reads back what its
+ * kernel recorded.  Errors: PF_ERR_WORKSPACE (misaligned), PF_ERR_CUDA,
+ * PF_ERR_DEVICE, PF_ERR_TIMEOUT. */
+pf_status pf_resample_check(const void* workspace_dev, void* stream);
 
 /* Kernel timing.  With enable = 1, every later pf_step records a pair of
  * CUDA events around each of its kernels, on the stream it launches them
@@ -419,6 +446,24 @@ pf_status pf_reset(pf_handle* h, void* stream);
  * every step).  Errors: PF_ERR_ARG, PF_ERR_STATE, PF_ERR_CUDA. */
 pf_status pf_backward(pf_handle* h, const float* const* frames_host, int32_t T, const float* dlogZ_host,
                       float* grad_dev, double* logZ_dev, void* stream);
+
+/* Replace the recorded ancestry of the T steps run (T must equal the steps
+ * run since pf_init / pf_reset, and T <= history) by the caller's, so that
+ * pf_backward differentiates log Z along an externally supplied ancestry
+ * (for instance another implementation's run, for verification): the
+ * replay of Alg. 3 with steps 3 and 7 (exchange and resampling) held fixed
+ * at the given choices.  parents_dev: device array of T x N_total uint32,
+ * row k (k = 1 .. T-1; row 0 is ignored) holding, for every track in handle
+ * order, the track-local slot of X_{k-1} that each slot of step k was
+ * propagated from (the exchange composed with the previous step's
+ * resampling, as pf_particles' parent_dev reports it); the particle's
+ * carried weight is that of the slot's group, slot / Np.  The exchange
+ * count and ring of each step are implied by these parents.  Every track
+ * needs record_ancestors.  Synchronises `stream`.  An index outside its
+ * track is rejected: PF_ERR_ARG, and pf_backward refuses until a valid
+ * pf_set_replay or pf_reset.  The forward filter's states are untouched.
+ * Errors: PF_ERR_ARG, PF_ERR_STATE, PF_ERR_CUDA. */
+pf_status pf_set_replay(pf_handle* h, const uint32_t* parents_dev, int32_t T, void* stream);
 
 /* Checkpoint and resume.  A filter's whole state lives in its workspace
  * and a few host counters, and every random draw is a counter-based Philox

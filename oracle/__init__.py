@@ -107,9 +107,21 @@ def lib():
         L.ora_loglik_image_grad.restype = C.c_double
         L.ora_replay_grad.argtypes = [C.POINTER(Cfg), C.c_int32, _P, _P, _P, C.c_double, _P, C.c_int32, _P, _P, _P]
         L.ora_replay_grad.restype = C.c_int
+        L.ora_replay_grad_ex.argtypes = [C.POINTER(Cfg), C.c_int32, _P, _P, _P, C.c_double, _P, C.c_int32, _P,
+                                         C.c_int32, _P, _P, _P]
+        L.ora_replay_grad_ex.restype = C.c_int
         L.ora_run.restype = C.c_int
+        L.ora_set_threads.argtypes = [C.c_int]
+        L.ora_set_threads.restype = C.c_int
         _lib = L
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the oracle step's per-particle and per-group loops
+    (1 by default); returns the count in effect (1 without OpenMP).  The
+    results do not depend on it."""
+    return int(lib().ora_set_threads(int(n)))
 
 
 def _ptr(a: Optional[np.ndarray]):
@@ -416,9 +428,15 @@ def loglik_image_grad(cfg: Cfg, frame, x: float, y: float, I: float):
     return l, d
 
 
-def replay_grad(cfg: Cfg, kind: int, x0, frames, T: int, parents, lo=None, hi=None, radius: float = 0.0):
+def replay_grad(cfg: Cfg, kind: int, x0, frames, T: int, parents, lo=None, hi=None, radius: float = 0.0,
+                fp32_states: bool = False, states=None):
     """(log Z, d log Z / d theta) of a replay with frozen ancestry; theta =
-    (sigma_psf, A = x0[4], background, sigma_pos, sigma_v)."""
+    (sigma_psf, A = x0[4], background, sigma_pos, sigma_v).  fp32_states:
+    the same replay with every state rounded to FP32 after each propagation
+    (the rest in FP64), to measure the estimator's sensitivity to FP32 state
+    storage.  states: optional (T, 5, N) states to evaluate the likelihood
+    at instead of the replay's own (its tangents still follow the ancestry
+    and the noise)."""
     N = cfg.G * cfg.Np
     x0 = _c(x0, np.float64)
     lo = _c(lo if lo is not None else np.zeros(5), np.float64)
@@ -428,8 +446,10 @@ def replay_grad(cfg: Cfg, kind: int, x0, frames, T: int, parents, lo=None, hi=No
     assert par.shape == (T, N)
     lz = np.zeros(1)
     g = np.zeros(5)
-    rc = lib().ora_replay_grad(C.byref(cfg), kind, _ptr(x0), _ptr(lo), _ptr(hi), radius, _ptr(fr), T, _ptr(par),
-                               _ptr(lz), _ptr(g))
+    st = None if states is None else _c(states, np.float64)
+    assert st is None or st.shape == (T, 5, N)
+    rc = lib().ora_replay_grad_ex(C.byref(cfg), kind, _ptr(x0), _ptr(lo), _ptr(hi), radius, _ptr(fr), T, _ptr(par),
+                                  1 if fp32_states else 0, _ptr(st), _ptr(lz), _ptr(g))
     if rc != 0:
         raise ValueError("replay_grad needs resample_rule = RESAMPLE_ALWAYS")
     return float(lz[0]), g

@@ -2,7 +2,9 @@
 
 Test infrastructure: the CUDA library never links or loads the result.
 Flags: C11, -O2, and no a*b+c -> fma contraction, so that x86-64 and AArch64
-hosts produce the same bits.
+hosts produce the same bits; OpenMP when the compiler has it (the oracle's
+parallel loops then honour ora_set_threads; their results do not depend on
+the thread count).
 """
 import os
 import subprocess
@@ -21,7 +23,9 @@ def build(force: bool = False) -> str:
     tmp = LIB + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
            "-Wall", "-Wextra", "-o", tmp, SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    r = subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True, text=True)
+    if r.returncode != 0:  # no OpenMP runtime: the same library, single-threaded
+        subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB
 

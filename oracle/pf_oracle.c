@@ -32,11 +32,36 @@
  *
  * Build: plain C11, no contraction of a*b+c into fma (-ffp-contract=off) so
  * that x86-64 and AArch64 hosts give identical results.
+ *
+ * Threads: with OpenMP (-fopenmp) the per-particle and per-group loops of
+ * ora_step can run on several host threads (ora_set_threads; 1 by default).
+ * Every such loop writes only its own item's outputs and sums within an
+ * item in the serial order, so the results do not depend on the thread
+ * count.  This exists to time the oracle on all host cores beside the GPU.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Host threads of ora_step's parallel loops (see "Threads" above). */
+static int ora_threads = 1;
+
+/* Set the thread count of the parallel loops (n >= 1); returns the count in
+ * effect, 1 when the library was built without OpenMP. */
+int ora_set_threads(int n) {
+#ifdef _OPENMP
+  ora_threads = n < 1 ? 1 : n;
+  return ora_threads;
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 #define ORA_STREAM_INIT 0u
 #define ORA_STREAM_PROP 1u
@@ -455,6 +480,7 @@ void ora_exchange(const ora_cfg* c, uint32_t k, const int32_t* sigma, int32_t n_
 void ora_propagate(const ora_cfg* c, uint32_t k, const double* pop, double* X) {
   int32_t G = c->G, Np = c->Np;
   int64_t N = (int64_t)G * Np;
+#pragma omp parallel for collapse(2) schedule(static) num_threads(ora_threads) if (ora_threads > 1)
   for (int32_t g = 0; g < G; ++g)
     for (int32_t j = 0; j < Np; ++j) {
       int64_t i = (int64_t)g * Np + j;
@@ -762,6 +788,7 @@ int ora_step(const ora_cfg* c, uint32_t k, const float* obs, const double* pop_i
     memcpy(o->X, pop, sizeof(double) * (size_t)(5 * N));
   else
     ora_propagate(c, k, pop, o->X);
+#pragma omp parallel for schedule(static) num_threads(ora_threads) if (ora_threads > 1)
   for (int64_t i = 0; i < N; ++i) {
     double x = o->X[i], y = o->X[N + i], I = o->X[4 * N + i];
     double l = (c->obs_kind == ORA_OBS_POINT)   ? ora_loglik_point(c, obs, x, y)
@@ -783,6 +810,7 @@ int ora_step(const ora_cfg* c, uint32_t k, const float* obs, const double* pop_i
 
   /* S7 (Alg. 3 step 6): group estimate and group weight, FP64 */
   int32_t degen = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : degen) num_threads(ora_threads) if (ora_threads > 1)
   for (int32_t m = 0; m < G; ++m) {
     const double* lwm = lwe + (int64_t)m * Np;
     double mx = -INFINITY;
@@ -822,8 +850,10 @@ int ora_step(const ora_cfg* c, uint32_t k, const float* obs, const double* pop_i
    * ORA_RESAMPLE_ESS only where Alg. 1's N_eff test asks for it.  S10: a
    * resampled group's particles weigh 1 / Np within it, the others keep
    * w_i = w~_i / W'_m. */
-  float* lwf = (float*)malloc(sizeof(float) * (size_t)Np);
+  ora_build_coeffs(); /* the weight-code table, before any thread uses it */
+#pragma omp parallel for schedule(dynamic, 1) num_threads(ora_threads) if (ora_threads > 1)
   for (int32_t m = 0; m < G; ++m) {
+    float* lwf = (float*)malloc(sizeof(float) * (size_t)Np);
     for (int32_t j = 0; j < Np; ++j)
       lwf[j] = lw_override ? lw_override[(int64_t)m * Np + j] : (float)o->lw[(int64_t)m * Np + j];
     uint64_t* qm = o->q + (int64_t)m * Np;
@@ -841,12 +871,13 @@ int ora_step(const ora_cfg* c, uint32_t k, const float* obs, const double* pop_i
         omm[j] = lwe[(int64_t)m * Np + j] - o->Lambda_out[m];
       }
     }
+    free(lwf);
   }
-  free(lwf);
   free(lwbuf);
   free(om);
 
   /* S10 (Alg. 3 step 8): the resampled population; group weights carried */
+#pragma omp parallel for collapse(2) schedule(static) num_threads(ora_threads) if (ora_threads > 1)
   for (int d = 0; d < 5; ++d)
     for (int32_t m = 0; m < G; ++m)
       for (int32_t j = 0; j < Np; ++j) {
@@ -980,9 +1011,23 @@ double ora_loglik_image_grad(const ora_cfg* c, const float* frame, double x, dou
  * d theta.  Per step (Alg. 3): X_k = NCV(X_{k-1}[parent]) (k >= 1),
  * lw = Lambda_bar_{k-1}[origin] - log Np + l, Lambda_k,m = LSE_{i in m} lw,
  * log c_k = LSE_m Lambda_k,m, Lambda_bar_k = Lambda_k - log c_k. */
-int ora_replay_grad(const ora_cfg* c, int32_t kind, const double* x0, const double* lo, const double* hi,
-                    double radius, const float* frames, int32_t T, const int32_t* parents, double* logZ,
-                    double* grad) {
+/* round_f32: 0 for the FP64 replay; 1 to hold the states in FP32 (each state
+ * component rounded to the nearest float after the initial draw and after
+ * every propagation, everything else in FP64).  The second form measures how
+ * far the estimator moves when only its states are stored in FP32, as a GPU
+ * filter with FP32 states stores them: the patch centre of a particle that
+ * sits within a rounding of a half-pixel boundary can change, and log Z is
+ * discontinuous there.
+ * states: NULL, or T x 5 x N given states (SoA per step); the replay then
+ * takes step k's states from states[k] instead of computing them (the
+ * tangents still follow the ancestry and the noise), so that the likelihood
+ * and its derivatives are evaluated at exactly those states -- for
+ * instance the states of an implementation under test, which removes the
+ * difference its own state arithmetic makes and leaves that of its
+ * gradient. */
+int ora_replay_grad_ex(const ora_cfg* c, int32_t kind, const double* x0, const double* lo, const double* hi,
+                       double radius, const float* frames, int32_t T, const int32_t* parents, int32_t round_f32,
+                       const double* states, double* logZ, double* grad) {
   /* every step resamples here: a replay does not carry per-particle weights */
   if (c->resample_rule != ORA_RESAMPLE_ALWAYS) return -1;
   int32_t G = c->G, Np = c->Np;
@@ -999,6 +1044,9 @@ int ora_replay_grad(const ora_cfg* c, int32_t kind, const double* x0, const doub
   double* Lam = (double*)malloc(sizeof(double) * (size_t)G);
   double* dLam = (double*)malloc(sizeof(double) * (size_t)(5 * G));
   ora_init(c, kind, x0, lo, hi, radius, X);
+  if (round_f32)
+    for (int64_t i = 0; i < 5 * N; ++i) X[i] = (double)(float)X[i];
+  if (states) memcpy(X, states, sizeof(double) * (size_t)(5 * N));
   if (kind == ORA_INIT_POINT || kind == ORA_INIT_SHARING)
     for (int64_t i = 0; i < N; ++i)
       if (kind == ORA_INIT_POINT || i < Np) dX[(i * 5 + 4) * 5 + 1] = 1.0; /* dI/dA */
@@ -1007,6 +1055,7 @@ int ora_replay_grad(const ora_cfg* c, int32_t kind, const double* x0, const doub
   for (int32_t k = 0; k < T; ++k) {
     if (k >= 1) {
       const int32_t* par = parents + (int64_t)k * N;
+#pragma omp parallel for collapse(2) schedule(static) num_threads(ora_threads) if (ora_threads > 1)
       for (int32_t g = 0; g < G; ++g)
         for (int32_t j = 0; j < Np; ++j) {
           int64_t i = (int64_t)g * Np + j, p = par[i];
@@ -1030,8 +1079,12 @@ int ora_replay_grad(const ora_cfg* c, int32_t kind, const double* x0, const doub
         }
       double* t = X; X = Xn; Xn = t;
       t = dX; dX = dXn; dXn = t;
+      if (round_f32)
+        for (int64_t i = 0; i < 5 * N; ++i) X[i] = (double)(float)X[i];
+      if (states) memcpy(X, states + (size_t)k * (size_t)(5 * N), sizeof(double) * (size_t)(5 * N));
     }
     /* weights and their tangents */
+#pragma omp parallel for schedule(static) num_threads(ora_threads) if (ora_threads > 1)
     for (int64_t i = 0; i < N; ++i) {
       int32_t o = (k == 0) ? (int32_t)(i / Np) : (int32_t)(parents[(int64_t)k * N + i] / Np);
       double dl[5];
@@ -1075,4 +1128,11 @@ int ora_replay_grad(const ora_cfg* c, int32_t kind, const double* x0, const doub
   for (int q = 0; q < 5; ++q) grad[q] = gz[q];
   free(X); free(Xn); free(dX); free(dXn); free(lw); free(dlw); free(lbar); free(dlbar); free(Lam); free(dLam);
   return 0;
+}
+
+/* The FP64 replay (ora_replay_grad_ex with round_f32 = 0). */
+int ora_replay_grad(const ora_cfg* c, int32_t kind, const double* x0, const double* lo, const double* hi,
+                    double radius, const float* frames, int32_t T, const int32_t* parents, double* logZ,
+                    double* grad) {
+  return ora_replay_grad_ex(c, kind, x0, lo, hi, radius, frames, T, parents, 0, NULL, logZ, grad);
 }

@@ -26,8 +26,8 @@ STATUS_NAMES = {0: "PF_OK", 1: "PF_ERR_ARG", 2: "PF_ERR_STATE", 3: "PF_ERR_CUDA"
 EXPORTS = ("pf_abi_version", "pf_query_workspace", "pf_init", "pf_step", "pf_host_staging_bytes", "pf_step_host",
            "pf_estimate", "pf_estimate_async",
            "pf_exchange_stats",
-           "pf_history", "pf_particles", "pf_resample_workspace", "pf_resample", "pf_resample_noalloc",
-           "pf_profile_enable", "pf_profile_read", "pf_set_theta", "pf_reset", "pf_backward", "pf_step_table",
+           "pf_history", "pf_particles", "pf_resample_workspace", "pf_resample", "pf_resample_noalloc", "pf_resample_check",
+           "pf_profile_enable", "pf_profile_read", "pf_set_theta", "pf_reset", "pf_backward", "pf_set_replay", "pf_step_table",
            "pf_graph_step", "pf_autotune", "pf_checkpoint_bytes", "pf_save", "pf_load", "pf_destroy",
            "pf_last_error")
 THETA_NAMES = ("sigma_psf", "amplitude", "background", "sigma_pos", "sigma_v")
@@ -97,6 +97,8 @@ def load():
     L.pf_resample_workspace.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]
     L.pf_resample.argtypes = [_P, _P, C.c_int32, C.c_int32, _P, _P, _P, C.c_size_t, _P]
     L.pf_resample_noalloc.argtypes = [_P, _P, C.c_int32, C.c_int32, _P, _P, _P]
+    L.pf_resample_check.argtypes = [_P, _P]
+    L.pf_set_replay.argtypes = [_P, _P, C.c_int32, _P]
     L.pf_profile_enable.argtypes = [_P, C.c_int32]
     L.pf_profile_read.argtypes = [_P, C.c_int32, _P, _P]
     L.pf_set_theta.argtypes = [_P, C.c_int32, _P]
@@ -202,6 +204,14 @@ def pf_resample(logw_ptr, u_ptr, G: int, Np: int, anc_ptr, q_ptr, ws_ptr, nbytes
 
 def pf_resample_noalloc(logw_ptr, u_ptr, G: int, Np: int, anc_ptr, q_ptr, stream_ptr) -> None:
     _check(load().pf_resample_noalloc(logw_ptr, u_ptr, G, Np, anc_ptr, q_ptr, stream_ptr), "pf_resample_noalloc")
+
+
+def pf_resample_check(ws_ptr, stream_ptr) -> None:
+    _check(load().pf_resample_check(ws_ptr, stream_ptr), "pf_resample_check")
+
+
+def pf_set_replay(handle: int, parents_ptr, T: int, stream_ptr) -> None:
+    _check(load().pf_set_replay(handle, parents_ptr, T, stream_ptr), "pf_set_replay", handle)
 
 
 def pf_profile_enable(handle: int, enable: bool) -> None:

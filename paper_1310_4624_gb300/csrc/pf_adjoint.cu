@@ -423,6 +423,41 @@ cudaError_t launch_adjoint(const AdjointArgs& a, int R, int grid, cudaStream_t s
   return cudaGetLastError();
 }
 
+// Caller-supplied ancestry for the replay (pf_set_replay): for steps k = 1 ..
+// T-1 (blockIdx.y + 1), parents[k * n_total + part_off + il] (track-local
+// slot of X_{k-1} that slot il of step k was propagated from) into the
+// ancestry record the replay reads.  An index outside the track is counted
+// in *bad and recorded as the slot itself, so that no later kernel reads
+// outside the track.
+__global__ void k_set_replay(const TrackParams* __restrict__ trk, const int4* __restrict__ tiles, int n_tiles,
+                             const uint32_t* __restrict__ parents, long long n_total, uint32_t* __restrict__ parent,
+                             int history, int* __restrict__ bad) {
+  const int k = (int)blockIdx.y + 1;
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int4 td = tiles[tile];
+    const TrackParams& P = trk[td.x];
+    if (!P.record) continue;
+    const long long Nt = (long long)P.G * P.Np;
+    for (int jj = threadIdx.x; jj < td.w; jj += blockDim.x) {
+      const long long il = (long long)td.y * P.Np + td.z + jj;
+      uint32_t v = parents[(long long)k * n_total + P.part_off + il];
+      if ((long long)v >= Nt) {
+        atomicAdd(bad, 1);
+        v = (uint32_t)il;
+      }
+      parent[P.parent_off + (long long)(k % history) * Nt + il] = v;
+    }
+  }
+}
+
+cudaError_t launch_set_replay(const TrackParams* trk, const int4* tiles, int n_tiles, const uint32_t* parents,
+                              long long n_total, uint32_t* parent, int history, int T, int* bad, int grid,
+                              cudaStream_t s) {
+  if (T < 2) return cudaSuccess;
+  k_set_replay<<<dim3(grid, T - 1), 256, 0, s>>>(trk, tiles, n_tiles, parents, n_total, parent, history, bad);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_adjoint_groups(double* dlam, double* D, int G_total, cudaStream_t s) {
   k_adjoint_groups<<<(G_total + 255) / 256, 256, 0, s>>>(dlam, D, G_total);
   return cudaGetLastError();

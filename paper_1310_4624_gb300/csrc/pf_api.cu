@@ -60,6 +60,15 @@ struct pf_handle {
   uint4* keys_next = nullptr;  // two buffers (by step parity) of G_total: send-permutation keys of step k+1
   int* tile_ctr = nullptr;
   int n_ring_blocks = 0;  // leading blocks of the propagate kernel
+  // fused step: task list, resampling chunks, their code sums, counters
+  int4* tasks = nullptr;
+  int n_tasks = 0;
+  int4* chunks = nullptr;
+  int n_chunks = 0;
+  unsigned long long* chunk_q = nullptr;
+  unsigned int* fsync = nullptr;
+  int fused_grid = 1;
+  bool fused = true;  // PFARNA_FUSED=0 at pf_init: propagate and resample as two launches
   bool finish_pending = false;  // the last step's estimate / history not yet written (k_finish)
   int max_G = 1;
   uint32_t* parent = nullptr;
@@ -81,6 +90,8 @@ struct pf_handle {
   double* grad = nullptr;       // n_tracks x 5
   double* logz_rp = nullptr;    // n_tracks
   float* seed = nullptr;        // n_tracks
+  int* replay_bad = nullptr;    // pf_set_replay's count of out-of-range parents
+  bool replay_invalid = false;  // a rejected pf_set_replay left the ancestry unusable
   // pf_graph_step: the captured step for one frame table
   cudaGraphExec_t graph = nullptr;
   const void* graph_table = nullptr;
@@ -153,13 +164,14 @@ QuantCoeffs make_qc() {
 
 struct Layout {
   size_t trk, ts, gs, gd, tiles, frame_of, pv0, pv1, I0, I1, anc, lw, tp, ypad, hist, ghist, ring, ring_next, exo_next, keys_next,
-      tile_ctr, parent, ds,
+      tile_ctr, parent, ds, tasks, chunks, chunk_q, fsync,
       tmap, total;
-  size_t rp_pv, rp_I, ck_pv, ck_I, ca_pv0, ca_pv1, ca_I0, ca_I1, lam_hist, lbar_hist, dlam, Dacc, grad, logz, seed;
+  size_t rp_pv, rp_I, ck_pv, ck_I, ca_pv0, ca_pv1, ca_I0, ca_I1, lam_hist, lbar_hist, dlam, Dacc, grad, logz, seed,
+      replay_bad;
   bool adjoint = false;
   int adj_slots = 0, adj_ckpts = 0;
   long long N_total = 0, ypad_total = 0, parent_total = 0, ghist_total = 0;
-  int G_total = 0, n_tiles = 0, hist_total = 0;
+  int G_total = 0, n_tiles = 0, hist_total = 0, n_chunks = 0;
   int R = 5;
 };
 
@@ -242,6 +254,7 @@ Layout plan(const pf_track_config* c, int n, int history) {
     L.N_total += Nt;
     L.G_total += c[t].G;
     L.n_tiles += c[t].G * ((c[t].Np + K1_TILE - 1) / K1_TILE);
+    L.n_chunks += c[t].G * ((c[t].Np + RS_CHUNK - 1) / RS_CHUNK);
     L.ypad_total += pad_pitch(c[t].W, L.R) * pad_rows(c[t].H, L.R);
     if (c[t].record_ancestors) L.parent_total += Nt * history;
     L.hist_total += history;
@@ -264,13 +277,17 @@ Layout plan(const pf_track_config* c, int n, int history) {
   L.exo_next = take(sizeof(uint32_t) * 2 * (size_t)L.G_total);
   L.keys_next = take(sizeof(uint4) * 2 * (size_t)L.G_total);
   L.tile_ctr = take(sizeof(int));
+  L.tasks = take(sizeof(int4) * (size_t)(L.n_tiles + 2 * L.n_chunks));
+  L.chunks = take(sizeof(int4) * (size_t)L.n_chunks);
+  L.chunk_q = take(3 * sizeof(unsigned long long) * (size_t)L.n_chunks);
+  L.fsync = take(sizeof(unsigned int) * (size_t)FusedSync{L.G_total}.count());
   L.tiles = take(sizeof(int4) * L.n_tiles);
   L.frame_of = take(sizeof(int) * (size_t)n);
   L.pv0 = take(sizeof(float4) * L.N_total);
   L.pv1 = take(sizeof(float4) * L.N_total);
   L.I0 = take(sizeof(float) * L.N_total);
   L.I1 = take(sizeof(float) * L.N_total);
-  L.anc = take(sizeof(uint32_t) * L.N_total);
+  L.anc = take(2 * sizeof(uint32_t) * L.N_total);  // by step parity
   L.lw = take(sizeof(float) * (size_t)lw_stride(L.N_total) * 2);
   L.tp = take(sizeof(float) * 8 * (size_t)L.n_tiles);
   L.ypad = take(sizeof(float) * (size_t)L.ypad_total);
@@ -299,6 +316,7 @@ Layout plan(const pf_track_config* c, int n, int history) {
     L.grad = take(sizeof(double) * 5 * (size_t)n);
     L.logz = take(sizeof(double) * (size_t)n);
     L.seed = take(sizeof(float) * (size_t)n);
+    L.replay_bad = take(sizeof(int));
   }
   L.total = o;
   return L;
@@ -405,11 +423,48 @@ pf_status sync(pf_handle* h) {
 }
 
 K1Args k1_args(const pf_handle* h) {
-  K1Args a{h->trk, h->tiles, h->n_tiles, h->gs, h->ts, h->ds, h->pv[0], h->pv[1], h->In[0], h->In[1],
-           h->anc, h->parent, h->history, h->lw, h->carry_any ? h->lw + lw_stride(h->N_total) : h->lw, h->tile_part, h->ypad, h->tmaps, h->ring_next,
-           h->G_total, h->exo_next, h->hist, h->ghist, h->tile_ctr, h->n_ring_blocks, h->n_tracks, TrackParams{}, 0,
-           nullptr, h->test_withhold_copy ? 1 : 0, h->variants ? 1 : 0, h->keys_next, h->frame_of, CUtensorMap{}};
+  K1Args a{};
+  a.trk = h->trk;
+  a.tiles = h->tiles;
+  a.n_tiles = h->n_tiles;
+  a.grp = h->gs;
+  a.ts = h->ts;
+  a.ds = h->ds;
+  a.pv0 = h->pv[0];
+  a.pv1 = h->pv[1];
+  a.I0 = h->In[0];
+  a.I1 = h->In[1];
+  a.anc = h->anc;
+  a.anc_stride = h->N_total;
+  a.parent = h->parent;
+  a.history = h->history;
+  a.lw = h->lw;
+  a.lw1 = h->carry_any ? h->lw + lw_stride(h->N_total) : h->lw;
+  a.tile_part = h->tile_part;
+  a.ypad = h->ypad;
+  a.tmaps = h->tmaps;
+  a.ring_next = h->ring_next;
+  a.ring_stride = h->G_total;
+  a.exo_next = h->exo_next;
+  a.hist = h->hist;
+  a.ghist = h->ghist;
+  a.tile_ctr = h->tile_ctr;
+  a.n_ring_blocks = h->n_ring_blocks;
+  a.n_tracks = h->n_tracks;
   a.p0 = h->tp[0];
+  a.raw_frame = 0;
+  a.zraw = nullptr;
+  a.test_withhold_copy = h->test_withhold_copy ? 1 : 0;
+  a.variants = h->variants ? 1 : 0;
+  a.keys_next = h->keys_next;
+  a.frame_of = h->frame_of;
+  a.tasks = h->tasks;
+  a.n_tasks = h->n_tasks;
+  a.chunks = h->chunks;
+  a.gd = h->gd;
+  a.chunk_q = h->chunk_q;
+  a.sync = h->fsync;
+  a.qc = h->qc;
   return a;
 }
 
@@ -446,7 +501,7 @@ GlobalArgs global_args(const pf_handle* h, int finalize) {
 // group of the track to finish); 0: resampling only (autotuner candidates).
 ResampleArgs resample_args(const pf_handle* h, int fuse) {
   ResampleArgs ra{h->gd,  h->gs,  h->tile_part, h->lw, h->carry_any ? h->lw + lw_stride(h->N_total) : nullptr,
-                  h->anc, nullptr, nullptr,      0,     h->qc, h->ds};
+                  h->anc, h->N_total, nullptr, nullptr, 0, h->qc, h->ds};
   ra.fuse_global = fuse;
   ra.tile_ctr = h->tile_ctr;
   ra.glob = global_args(h, 1);
@@ -515,6 +570,11 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
   h->exo_next = (uint32_t*)(w + L.exo_next);
   h->keys_next = (uint4*)(w + L.keys_next);
   h->tile_ctr = (int*)(w + L.tile_ctr);
+  h->tasks = (int4*)(w + L.tasks);
+  h->chunks = (int4*)(w + L.chunks);
+  h->n_chunks = L.n_chunks;
+  h->chunk_q = (unsigned long long*)(w + L.chunk_q);
+  h->fsync = (unsigned int*)(w + L.fsync);
   h->tiles = (int4*)(w + L.tiles);
   h->frame_of = (int*)(w + L.frame_of);
   h->pv[0] = (float4*)(w + L.pv0);
@@ -548,6 +608,7 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
     h->grad = (double*)(w + L.grad);
     h->logz_rp = (double*)(w + L.logz);
     h->seed = (float*)(w + L.seed);
+    h->replay_bad = (int*)(w + L.replay_bad);
   }
 
   // host tables
@@ -1146,7 +1207,8 @@ pf_status pf_particles(pf_handle* h, int32_t track, float* states, uint32_t* anc
   cudaError_t e;
   if (states && (e = launch_export_states(h->pv[k & 1] + P.part_off, h->In[k & 1] + P.part_off, Nt, states, s)))
     return cuda_fail(h, e, "export states");
-  if (anc && (e = cudaMemcpyAsync(anc, h->anc + P.part_off, sizeof(uint32_t) * Nt, cudaMemcpyDeviceToDevice, s)))
+  const uint32_t* anc_k = h->anc + (long long)(k & 1) * h->N_total;  // step k resampled into buffer k & 1
+  if (anc && (e = cudaMemcpyAsync(anc, anc_k + P.part_off, sizeof(uint32_t) * Nt, cudaMemcpyDeviceToDevice, s)))
     return cuda_fail(h, e, "copy ancestors");
   if (logw && (e = cudaMemcpyAsync(logw, h->lw + (h->carry_any ? (k & 1) * lw_stride(h->N_total) : 0) + P.part_off, sizeof(float) * Nt,
                                    cudaMemcpyDeviceToDevice, s)))
@@ -1194,9 +1256,31 @@ pf_status pf_resample(const float* logw, const uint32_t* u, int32_t G, int32_t N
   if ((e = cudaMemsetAsync(ds, 0, sizeof(DevState), s)) ||
       (e = cudaMemcpyAsync(gd, h.data(), sizeof(GroupDesc) * G, cudaMemcpyHostToDevice, s)))
     return cuda_fail(nullptr, e, "pf_resample setup");
-  ResampleArgs ra{gd, gs, nullptr, logw, nullptr, anc, (unsigned long long*)q, u, 1, make_qc(), ds};
+  ResampleArgs ra{gd, gs, nullptr, logw, nullptr, anc, 0, (unsigned long long*)q, u, 1, make_qc(), ds};
   if ((e = launch_resample(ra, G, resample_cluster(Np, true), false, s)) != cudaSuccess)
     return cuda_fail(nullptr, e, "k_resample");
+  return PF_OK;
+}
+
+pf_status pf_resample_check(const void* workspace, void* stream) {
+  const DevState* src = (const DevState*)workspace;
+  if (!src) {
+    const int st = noalloc_error_word(&src);
+    if (st != PF_OK) return (pf_status)st;
+  } else if ((uintptr_t)workspace % ALIGN) {
+    return fail(nullptr, PF_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  DevState ds{};
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(&ds, src, sizeof ds, cudaMemcpyDeviceToHost, s)) || (e = cudaStreamSynchronize(s)))
+    return cuda_fail(nullptr, e, "pf_resample_check");
+  if (ds.err) {
+    char b[200];
+    std::snprintf(b, sizeof b, "the resampler reported error bits 0x%x (info %u %u %u)", ds.err, ds.err_info[0],
+                  ds.err_info[1], ds.err_info[2]);
+    return fail(nullptr, (ds.err & ERR_TIMEOUT) ? PF_ERR_TIMEOUT : PF_ERR_DEVICE, b);
+  }
   return PF_OK;
 }
 
@@ -1245,7 +1329,33 @@ pf_status pf_reset(pf_handle* h, void* stream) {
   h->steps_run = 0;
   h->finish_pending = false;
   h->failed = 0;
+  h->replay_invalid = false;
   h->last_stream = s;
+  return PF_OK;
+}
+
+pf_status pf_set_replay(pf_handle* h, const uint32_t* parents_dev, int32_t T, void* stream) {
+  if (!h) return fail(nullptr, PF_ERR_ARG, "handle is NULL");
+  if (!h->adjoint) return fail(h, PF_ERR_STATE, "pf_set_replay needs record_ancestors on every track");
+  if (!parents_dev) return fail(h, PF_ERR_ARG, "parents_dev is NULL");
+  if (T < 1 || T != h->steps_run) return fail(h, PF_ERR_STATE, "T must equal the number of steps run");
+  if (T > h->history) return fail(h, PF_ERR_STATE, "T exceeds the kept history");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  int bad = 0;
+  if ((e = cudaMemsetAsync(h->replay_bad, 0, sizeof(int), s)) ||
+      (e = launch_set_replay(h->trk, h->tiles, h->n_tiles, parents_dev, h->N_total, h->parent, h->history, T,
+                             h->replay_bad, h->k1_grid, s)) ||
+      (e = cudaMemcpyAsync(&bad, h->replay_bad, sizeof(int), cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaStreamSynchronize(s)))
+    return cuda_fail(h, e, "pf_set_replay");
+  h->last_stream = s;
+  if (bad) {
+    h->replay_invalid = true;
+    return fail(h, PF_ERR_ARG, std::to_string(bad) + " parent indices outside their track; pf_backward refuses "
+                                                     "this ancestry until a valid pf_set_replay or pf_reset");
+  }
+  h->replay_invalid = false;
   return PF_OK;
 }
 
@@ -1260,6 +1370,7 @@ pf_status pf_backward(pf_handle* h, const float* const* frames_host, int32_t T, 
   if (!frames_host || !dlogZ_host || !grad_dev) return fail(h, PF_ERR_ARG, "NULL argument");
   if (T < 1 || T != h->steps_run) return fail(h, PF_ERR_STATE, "T must equal the number of steps run");
   if (T > h->history) return fail(h, PF_ERR_STATE, "T exceeds the kept history");
+  if (h->replay_invalid) return fail(h, PF_ERR_STATE, "the ancestry given to pf_set_replay was rejected");
   for (int i = 0; i < T * h->n_tracks; ++i)
     if (!frames_host[i]) return fail(h, PF_ERR_ARG, "NULL frame pointer");
   cudaStream_t s = (cudaStream_t)stream;

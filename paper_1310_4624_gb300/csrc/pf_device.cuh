@@ -35,6 +35,8 @@ constexpr int RS_SUB = RS_THREADS * RS_ITEMS;
 constexpr int RS_WIN = 2 * RS_SUB;    // resampler merge window: items and outputs merged at once (ancestors staged)
 __host__ __device__ constexpr int pad8(int i) { return i + (i >> 3); }  // shared index with one spare per 8
 constexpr int RS_SUB_PAD = pad8(RS_SUB);
+constexpr int RS_CHUNK = K1_THREADS * RS_ITEMS;  // fused step: items of one resampling chunk (A and B tasks)
+constexpr int TASK_P = 0, TASK_A = 1, TASK_B = 2;  // fused step task kinds
 constexpr int GL_THREADS = 1024;      // per-track global-step CTA, one thread per group
 constexpr int MAX_G = GL_THREADS;      // groups per track
 constexpr int MAX_FRAMES_PER_LAUNCH = 1024;
@@ -110,6 +112,8 @@ struct GroupState {
   float M;              // group max log-weight (step k)
   int carry;            // 1: the group skipped resampling at step k - 1, its
                         // particles carry their own log-weights into step k
+  int carry_next;       // the resampler's decision at step k (becomes carry at
+                        // the track's global step, once no step-k reader is left)
   unsigned long long Q; // group total weight code (step k)
   float xs[5];          // group estimate x^^m (step k)
   float ess;            // group ESS (step k)
@@ -123,7 +127,8 @@ struct GroupDesc {
   int g;            // track-local group index
   int tile_begin;   // first propagate tile
   int tile_count;
-  int pad;
+  int chunk_begin;  // first resampling chunk (fused step)
+  int chunk_count;
 };
 
 // One history record per (track, step).

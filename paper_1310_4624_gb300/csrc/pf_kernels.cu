@@ -221,7 +221,7 @@ __device__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
     if (m < G) {
       Q[i] = __ldcg(&gs[m].Q);
       Mg[i] = __ldcg(&gs[m].M);
-      if (a.finalize) cy[i] = __ldcg(&gs[m].carry);
+      if (a.finalize) cy[i] = __ldcg(&gs[m].carry_next);
       ring_m[i] = __ldcg(&ring[m]);
       rnext[i] = __ldcg(&rnext_buf[m]);
       exo[i] = __ldcg(&exo_buf[m]);
@@ -367,7 +367,9 @@ __device__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
       // S4: a resampled group's particles weigh W_m / Np, a group that kept
       // its particles passes their own log-weights on (log w~ - LSE)
       gs[m].off = cy[i] ? -lse : lam[i] - log_np - lse;
-      if (!a.finalize) gs[m].carry = 0;
+      // the resampler's decision of step k, read by step k1's propagation
+      gs[m].carry = cy[i];
+      if (!a.finalize) gs[m].carry_next = 0;
     }
   }
   if (threadIdx.x == 0) {
@@ -377,7 +379,7 @@ __device__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
     T->res_k = a.finalize ? res : 0;
     T->lse_k = lse;
     if (!a.finalize) T->fin_k = -1;
-    T->k = k1;
+    if (!a.keep_k) T->k = k1;
   }
 }
 
@@ -771,7 +773,7 @@ __device__ __forceinline__ void prefetch_tile(const K1Args& a, int4 td, int k, c
                                               const float* I_prev) {
   const TrackParams& P = a.trk[td.x];
   const long long i0 = P.part_off + (long long)td.y * P.Np + td.z;
-  if (k > 0) prefetch_l2(a.anc + i0, sizeof(uint32_t) * (size_t)td.w);
+  if (k > 0) prefetch_l2(a.anc + ((k + 1) & 1) * a.anc_stride + i0, sizeof(uint32_t) * (size_t)td.w);
   prefetch_l2(pv_prev + i0, sizeof(float4) * (size_t)td.w);
   prefetch_l2(I_prev + i0, sizeof(float) * (size_t)td.w);
 }
@@ -827,6 +829,21 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
     // depend only on the seed and the step index), then the previous step's
     // estimate, log c, log Z and history (finish_step).
     static_assert(sizeof(GlobalScratch) <= sizeof(s_roi), "the leading blocks' scratch lives in s_roi");
+    // the fused step's counters of the next step (this launch uses parity
+    // k & 1; the previous launch, which used the other parity, has ended)
+    if (a.sync) {
+      const FusedSync fs{a.ring_stride};
+      const int par1 = (k + 1) & 1;
+      for (int i = blockIdx.x * K1_THREADS + threadIdx.x; i < a.ring_stride; i += a.n_ring_blocks * K1_THREADS) {
+        a.sync[fs.pdone(par1, i)] = 0u;
+        a.sync[fs.adone(par1, i)] = 0u;
+      }
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.sync[fs.task_ctr(par1)] = 0u;
+        a.sync[fs.exit_ctr(par1)] = 0u;
+        a.sync[fs.ring_done(par1)] = 0u;
+      }
+    }
     const GlobalArgs ga{a.trk, a.ts, a.grp, nullptr, a.ring_next, a.ring_stride, a.exo_next, a.hist, a.ghist,
                         a.history, 1, a.ds};
     int* perm = reinterpret_cast<int*>(&s_roi[0][0]);
@@ -901,7 +918,7 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
     // sending group did; their particles pass their own log-weights on
     const int cmask = (VARIANTS && k > 0) ? (gs[g].carry | (gs[sg].carry << 1)) : 0;
     const uint32_t n_track = (uint32_t)(P.G * Np);
-    const uint32_t* __restrict__ anc_t = a.anc + P.part_off;
+    const uint32_t* __restrict__ anc_t = a.anc + ((k + 1) & 1) * a.anc_stride + P.part_off;  // step k - 1's
     const float4* __restrict__ pvp_t = pv_prev + P.part_off;
     const float* __restrict__ Ip_t = I_prev + P.part_off;
     float4* __restrict__ pvc_t = pv_cur + P.part_off;
@@ -1434,7 +1451,7 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(ResampleAr
     if (threadIdx.x == 0) {
       G.M = M;
       G.Q = Q;
-      G.carry = resample ? 0 : 1;
+      G.carry_next = resample ? 0 : 1;
     }
   }
   // The last group of a track to report its statistics runs the track's
@@ -1461,7 +1478,7 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(ResampleAr
 
 
   const unsigned long long obase = a.local_idx ? 0ull : (unsigned long long)(d.g) * (unsigned long long)Np;
-  uint32_t* __restrict__ anc = a.anc + d.base;
+  uint32_t* __restrict__ anc = a.anc + (kk & 1) * a.anc_stride + d.base;
   if (Q == 0 || !resample) {
     // no finite weight, or Alg. 1's test keeps the particles: identity
     for (int i = lo + threadIdx.x; i < hi; i += NTR) {

@@ -56,7 +56,9 @@ struct K1Args {
   float4* pv1;
   float* I0;
   float* I1;
-  const uint32_t* anc;  // previous step's ancestors (track-local slots)
+  uint32_t* anc;        // ancestors, two buffers of anc_stride by step parity: step k reads
+                        // buffer (k + 1) & 1 (the previous step's) and resamples into buffer k & 1
+  long long anc_stride;
   uint32_t* parent;     // ancestry records or nullptr
   int history;
   float* lw;            // log-weights; with carried weights, two buffers by step parity:
@@ -84,7 +86,28 @@ struct K1Args {
                              // uses keyed send sets: launches the variants instance (frames prepared)
   uint4* keys_next;          // two buffers (by step parity) of G_total: keyed send-permutation keys of step k+1
   const int* frame_of;       // per track: the track whose padded frame to read this step, or nullptr (its own)
+  // fused step (one persistent launch per step): the task list, the
+  // resampling chunks and the counters the tasks wait on
+  const int4* tasks;         // (kind, tile or chunk, global group, 0) in the order CTAs take them
+  int n_tasks;
+  const int4* chunks;        // (track, global group, first slot in the group, items)
+  const GroupDesc* gd;
+  unsigned long long* chunk_q;  // per chunk: sum of weight codes, and for Alg. 1's test sums of c and c^2
+  unsigned int* sync;        // [2][G_total] tiles done (per warp), [2][G_total] chunks done, then per
+                             // parity: task counter, CTAs exited, leading blocks done (see fused_sync)
+  QuantCoeffs qc;
   CUtensorMap zmap;
+};
+
+// Offsets of the fused step's counters in K1Args::sync (each by step parity).
+struct FusedSync {
+  int G_total;
+  __host__ __device__ int pdone(int par, int gi) const { return par * G_total + gi; }
+  __host__ __device__ int adone(int par, int gi) const { return 2 * G_total + par * G_total + gi; }
+  __host__ __device__ int task_ctr(int par) const { return 4 * G_total + par; }
+  __host__ __device__ int exit_ctr(int par) const { return 4 * G_total + 2 + par; }
+  __host__ __device__ int ring_done(int par) const { return 4 * G_total + 4 + par; }
+  __host__ __device__ int count() const { return 4 * G_total + 6; }
 };
 
 struct GlobalArgs {
@@ -100,6 +123,7 @@ struct GlobalArgs {
   int history;
   int finalize;  // 0: prepare step 0 only
   DevState* ds;
+  int keep_k;    // 1: leave the step index to the caller (fused step: advanced when its launch ends)
 };
 
 struct ResampleArgs {
@@ -108,7 +132,8 @@ struct ResampleArgs {
   const float* tile_part;      // nullptr: no group estimate
   const float* lw;
   const float* lw1;            // filter step with carry: the weights are lw1 at odd steps (nullptr: always lw)
-  uint32_t* anc;
+  uint32_t* anc;               // filter step: two buffers of anc_stride by step parity (step k writes k & 1)
+  long long anc_stride;        // 0: a single output array
   unsigned long long* q_out;   // nullptr: not stored
   const uint32_t* u_arr;       // nullptr: GroupState::u
   int local_idx;               // 1: ancestors within the group
@@ -179,6 +204,11 @@ cudaError_t launch_replay_groups(const ReplayGroupArgs& a, int n_tracks, int max
 cudaError_t launch_adjoint(const AdjointArgs& a, int R, int grid, cudaStream_t s);
 cudaError_t launch_adjoint_groups(double* dlam, double* D, int G_total, cudaStream_t s);
 cudaError_t launch_grad_out(const double* g, const double* lz, float* out, double* lz_out, int n, cudaStream_t s);
+// parents (T x n_total, row k = step k) into the replay's ancestry record;
+// out-of-range indices are counted in *bad (not read or written past)
+cudaError_t launch_set_replay(const TrackParams* trk, const int4* tiles, int n_tiles, const uint32_t* parents,
+                              long long n_total, uint32_t* parent, int history, int T, int* bad, int grid,
+                              cudaStream_t s);
 
 cudaError_t launch_init(const InitArgs& a, int grid, cudaStream_t s);
 // The step launchers take `pdl`: launch with programmatic stream
@@ -188,6 +218,10 @@ cudaError_t launch_init(const InitArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_frame_prep(const FrameArgs& a, int nt, int blocks_x, bool pdl, cudaStream_t s);
 cudaError_t launch_frame_prep_table(const FrameTableArgs& a, int blocks_x, bool pdl, cudaStream_t s);
 cudaError_t launch_propagate(const K1Args& a, int R, int grid, bool pdl, cudaStream_t s);
+// The fused step: propagate + weight tiles, the per-group resampling and the
+// global step in one persistent launch (a.tasks).
+cudaError_t launch_fused_step(const K1Args& a, int R, int grid, bool pdl, cudaStream_t s);
+cudaError_t fused_occupancy(int R, int* blocks_per_sm);
 // threads: RS_THREADS, or RS_THREADS_SMALL (eight CTAs per SM, for batches of small groups)
 cudaError_t launch_resample(const ResampleArgs& a, int n_groups, int cluster, bool pdl, cudaStream_t s,
                             int threads = RS_THREADS);
@@ -206,5 +240,8 @@ const void* propagate_kernel(int R);
 QuantCoeffs resample_coeffs();             // weight-code coefficients
 int resample_cluster_size(int Np);         // resampler cluster size for one group of Np
 void set_handleless_error(const char* msg);  // text for pf_last_error(NULL)
+// The no-allocation resampler's error word on the current device (defined
+// in pf_noalloc.cu); PF_OK and *out set, or an error status.
+int noalloc_error_word(const DevState** out);
 
 }  // namespace pf

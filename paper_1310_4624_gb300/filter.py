@@ -262,6 +262,14 @@ class ParticleFilter:
         self.stream.synchronize()
         return grad, logz
 
+    def set_replay(self, parents: torch.Tensor) -> None:
+        """Replace the recorded ancestry of the steps run by `parents`
+        ((T, N_total) int32 or uint32 CUDA tensor, row k the step-k parents
+        of every track; row 0 ignored), for the next backward()."""
+        assert parents.is_cuda and parents.dim() == 2 and parents.is_contiguous()
+        assert parents.dtype in (torch.int32, torch.uint32) and parents.shape[1] == sum(self.N)
+        B.pf_set_replay(self.handle, _ptr(parents), parents.shape[0], C.c_void_p(self.stream.cuda_stream))
+
     def particles(self, track: int = 0, parents: bool = False) -> dict:
         """Latest step's X_k (5, N), ancestors, log-weights (and parents)."""
         n = self.N[track]
@@ -290,7 +298,7 @@ def resample(logw: torch.Tensor, u: torch.Tensor, G: int, Np: int, want_q: bool 
     wp = (ws.data_ptr() + 255) // 256 * 256
     s = torch.cuda.current_stream(dev)
     B.pf_resample(_ptr(logw), _ptr(u), G, Np, _ptr(anc), _ptr(q), C.c_void_p(wp), nb, C.c_void_p(s.cuda_stream))
-    s.synchronize()
+    B.pf_resample_check(C.c_void_p(wp), C.c_void_p(s.cuda_stream))  # waits; raises on a device-side error
     return (anc, q) if want_q else anc
 
 

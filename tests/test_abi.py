@@ -36,7 +36,7 @@ def test_header_declares_what_the_binding_wraps():
 def test_library_exports_every_declared_symbol(lib):
     for name in declared_functions():
         assert hasattr(lib, name), name
-    assert lib.pf_abi_version() == 4
+    assert lib.pf_abi_version() == 5
 
 
 def test_struct_layout_matches_ctypes(tmp_path):

@@ -113,3 +113,28 @@ def test_table_graph_and_autotuned_steps_equal_plain_steps(dev, how):
             alt.step_table(table, graph=(how == "graph"))
     for t in range(len(wls)):
         _equal(_snapshot(ref, t), _snapshot(alt, t))
+
+
+def test_batched_workload_tracks_match_oracle(dev):
+    """Three tracks of the batched workload itself (256 x 256 frames, sizes
+    drawn log-uniformly as that workload draws them), one of them with
+    G >= 64 groups and more than 100 000 particles, in one handle: each
+    track against the oracle step by step."""
+    import os
+    import oracle as ora
+    from parity_util import run_and_compare
+    from paper_1310_4624_gb300.filter import ParticleFilter
+    drawn = synth.batched_tracks(512)
+    big = next(w for w in drawn if w.G >= 64 and w.N >= 100000)
+    wls = [w.replace(T=4) for w in (big, drawn[0], drawn[5])]
+    seqs = [synth.make_sequence(wl) for wl in wls]
+    frs = [torch.from_numpy(f).to(dev) for f, _ in seqs]
+    ora.set_threads(os.cpu_count() or 1)
+    try:
+        for t in range(len(wls)):
+            batch = ParticleFilter(_configs(wls, seqs), history=8, device=dev)
+            run_and_compare(batch, wls[t], seqs[t][0], seqs[t][1][0], wls[t].T, None, track=t,
+                            stepper=lambda k: batch.step([fr[k] for fr in frs]))
+            batch.close()
+    finally:
+        ora.set_threads(1)

@@ -118,14 +118,47 @@ def test_autograd_function(dev):
 
 
 def test_differentiable_workload_shape(dev):
-    """The differentiable workload's shape (G=16 x 65536, 512x512) on 3 frames."""
-    wl = synth.differentiable(T=3)
-    pf, frames, fr, truth, parents = _forward(dev, wl)
+    """The differentiable workload's shape (G=16 x 65536, 512x512) over its
+    first 10 frames: FP32 accumulation in the adjoint and the atomics of
+    the reverse sweep over a longer horizon.
+
+    Against the oracle evaluated at the GPU's own FP32 states (its tangents
+    in FP64 along the same ancestry and noise): every component within 1e-3
+    relative.  Against the oracle's own FP64 run the states differ by FP32
+    storage, and over this horizon that alone moves the gradient by ~2e-3
+    (a particle within a rounding of a half-pixel boundary changes its patch
+    centre, where log Z is discontinuous; the oracle with its states rounded
+    to FP32 moves as much): every component within 5e-3 relative there,
+    log Z within 1e-5."""
+    import os
+    wl = synth.differentiable(T=10)
+    from paper_1310_4624_gb300.filter import ParticleFilter, config_from_workload
+    frames, truth = synth.make_sequence(wl)
+    pf = ParticleFilter([config_from_workload(wl, truth[0], record_ancestors=True)], history=wl.T, device=dev)
+    fr = torch.from_numpy(frames).to(dev)
+    parents = np.zeros((wl.T, wl.N), np.int32)
+    parents[0] = np.arange(wl.N)
+    states = np.zeros((wl.T, 5, wl.N), np.float64)
+    for k in range(wl.T):
+        pf.step(fr[k])
+        p = pf.particles(parents=True)
+        states[k] = p["states"].double().cpu().numpy()
+        if k > 0:
+            parents[k] = p["parent"].cpu().numpy()
     grad, lz = pf.backward([fr[k] for k in range(wl.T)])
-    lz_o, g_o = _oracle(wl, frames, truth, parents)
     g = grad[0].double().cpu().numpy()
+    from parity_util import _init
+    kind, x0, lo, hi, rad = _init(wl, truth[0])
+    cfg = ora.cfg_from_workload(wl)
+    ora.set_threads(os.cpu_count() or 1)
+    try:
+        lz_o, g_o = ora.replay_grad(cfg, kind, x0, frames, wl.T, parents, lo, hi, rad)
+        lz_s, g_s = ora.replay_grad(cfg, kind, x0, frames, wl.T, parents, lo, hi, rad, states=states)
+    finally:
+        ora.set_threads(1)
+    assert abs(float(lz[0]) - lz_s) <= 1e-5 * abs(lz_s)
     assert abs(float(lz[0]) - lz_o) <= 1e-5 * abs(lz_o)
-    scale = np.abs(g_o).max()
     for q in range(5):
-        assert abs(g[q] - g_o[q]) <= 1e-3 * abs(g_o[q]) + 1e-5 * scale, (ora.THETA[q], g[q], g_o[q])
+        assert abs(g[q] - g_s[q]) <= 1e-3 * abs(g_s[q]) + 1e-5 * np.abs(g_s).max(), (ora.THETA[q], g[q], g_s[q])
+        assert abs(g[q] - g_o[q]) <= 5e-3 * abs(g_o[q]) + 1e-5 * np.abs(g_o).max(), (ora.THETA[q], g[q], g_o[q])
     pf.close()

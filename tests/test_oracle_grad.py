@@ -84,3 +84,46 @@ def test_likelihood_partials_match_differences(ora):
         fb = (ora.loglik_image(bp, frames[0], x, y, I) - ora.loglik_image(bm, frames[0], x, y, I)) / (2 * h)
         for got, want in zip(d, (fx, fy, fI, fs, fb)):
             assert abs(got - want) <= 1e-5 * max(1.0, abs(want))
+
+
+def test_fp32_state_replay(ora):
+    """The FP32-state form of the replay: a one-frame run from a point whose
+    components are floats already changes nothing (exactly); over a run it
+    stays within a small distance of the FP64 replay, and its own finite
+    differences in sigma_psf (which moves no particle) match its gradient."""
+    wl, cfg, frames, (kind, x0, lo, hi, rad), par, _ = _setup(ora, T=1)
+    x0f = np.float32(x0).astype(np.float64)
+    a = ora.replay_grad(cfg, kind, x0f, frames, 1, par[:1], lo, hi, rad)
+    b = ora.replay_grad(cfg, kind, x0f, frames, 1, par[:1], lo, hi, rad, fp32_states=True)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1])
+    wl, cfg, frames, (kind, x0, lo, hi, rad), par, _ = _setup(ora, T=6)
+    lz, g = ora.replay_grad(cfg, kind, x0, frames, wl.T, par, lo, hi, rad)
+    lz32, g32 = ora.replay_grad(cfg, kind, x0, frames, wl.T, par, lo, hi, rad, fp32_states=True)
+    assert lz32 != lz                       # the rounding is applied
+    assert abs(lz32 - lz) <= 1e-5 * abs(lz)
+    assert np.all(np.abs(g32 - g) <= 1e-2 * np.abs(g) + 1e-3 * np.abs(g).max())
+    h = 1e-5 * cfg.sigma_psf
+    vals = [ora.replay_grad(_with(cfg, ora, 0, cfg.sigma_psf + s * h), kind, x0, frames, wl.T, par, lo, hi, rad,
+                            fp32_states=True)[0] for s in (1, -1)]
+    fd = (vals[0] - vals[1]) / (2 * h)
+    assert abs(fd - g32[0]) <= 1e-5 * max(1.0, abs(g32[0]))
+
+
+def test_replay_at_given_states(ora):
+    """Given the replay's own states (rebuilt from the ancestry by the
+    oracle's propagation), the replay is unchanged bit for bit; given other
+    states it evaluates the likelihood there (log Z moves)."""
+    wl, cfg, frames, (kind, x0, lo, hi, rad), par, _ = _setup(ora, T=5)
+    N = wl.G * wl.Np
+    X = [ora.init_population(cfg, kind, x0, lo, hi, rad)]
+    for k in range(1, wl.T):
+        X.append(ora.propagate(cfg, k, X[-1][:, par[k]]))
+    states = np.stack(X)
+    assert states.shape == (wl.T, 5, N)
+    a = ora.replay_grad(cfg, kind, x0, frames, wl.T, par, lo, hi, rad)
+    b = ora.replay_grad(cfg, kind, x0, frames, wl.T, par, lo, hi, rad, states=states)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1])
+    moved = states.copy()
+    moved[2, 0] += 0.25
+    c = ora.replay_grad(cfg, kind, x0, frames, wl.T, par, lo, hi, rad, states=moved)
+    assert c[0] != a[0]

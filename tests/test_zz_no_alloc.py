@@ -38,19 +38,22 @@ def _inputs(G, Np, seed):
     return lw, u
 
 
-def _noalloc(lw_t, u_t, G, Np, dev):
+def _noalloc(lw_t, u_t, G, Np, dev, want_q=True):
     from paper_1310_4624_gb300 import binding as B
     anc = torch.full((G * Np,), -1, dtype=torch.int32, device=dev)
-    q = torch.full((G * Np,), -1, dtype=torch.int64, device=dev)
+    q = torch.full((G * Np,), -1, dtype=torch.int64, device=dev) if want_q else None
     s = torch.cuda.current_stream(dev)
     B.pf_resample_noalloc(C.c_void_p(lw_t.data_ptr()), C.c_void_p(u_t.data_ptr()), G, Np,
-                          C.c_void_p(anc.data_ptr()), C.c_void_p(q.data_ptr()), C.c_void_p(s.cuda_stream))
-    s.synchronize()
+                          C.c_void_p(anc.data_ptr()), C.c_void_p(q.data_ptr()) if want_q else None,
+                          C.c_void_p(s.cuda_stream))
+    # the kernel's device-side error word, read back after the stream
+    B.pf_resample_check(None, C.c_void_p(s.cuda_stream))
     return anc, q
 
 
-@pytest.mark.parametrize("G,Np", [(4, 1000), (64, 16384), (3, 70001)])
+@pytest.mark.parametrize("G,Np", [(4, 1000), (64, 16384), (3, 70001), (1024, 64)])
 def test_noalloc_equals_pf_resample_on_consecutive_calls(dev, G, Np):
+    """(1024, 64) fills the scratch: as many groups as it holds."""
     from paper_1310_4624_gb300.filter import resample
     first = _inputs(G, Np, 1)
     second = _inputs(G, Np, 2)
@@ -61,6 +64,19 @@ def test_noalloc_equals_pf_resample_on_consecutive_calls(dev, G, Np):
         anc, q = _noalloc(lw_t, u_t, G, Np, dev)
         assert torch.equal(anc, ref_anc)
         assert torch.equal(q, ref_q)
+
+
+def test_noalloc_without_weight_codes(dev):
+    """q_dev may be NULL: the same ancestors, twice in a row."""
+    from paper_1310_4624_gb300.filter import resample
+    G, Np = 5, 3001
+    lw, u = _inputs(G, Np, 3)
+    lw_t = torch.from_numpy(lw.ravel()).to(dev)
+    u_t = torch.from_numpy(u.view(np.int32)).to(dev)
+    ref = resample(lw_t, u_t, G, Np)
+    for _ in range(2):
+        anc, _ = _noalloc(lw_t, u_t, G, Np, dev, want_q=False)
+        assert torch.equal(anc, ref)
 
 
 def test_noalloc_rejects_more_groups_than_its_scratch(dev):
