@@ -198,7 +198,12 @@ pf_status pf_query_workspace(const pf_track_config* cfg, int32_t n_tracks, int32
  * PFARNA_PDL=0 at pf_init selects plain stream serialisation instead.
  * PFARNA_RS_THREADS=128 or 512 at pf_init forces the resampler's CTA size
  * (by default 128 when every group has at most 1024 particles, else 512).
- * Results are identical either way.  PFARNA_TEST_WITHHOLD_COPY=1 at pf_init
+ * Results are identical either way.  PFARNA_FUSED=1 at pf_init runs each step
+ * as one persistent launch instead (propagate + weight tiles, the per-group
+ * resampling split into chunk tasks that start as soon as their group's
+ * tiles are done, and the global step), with the same results; on the
+ * workloads measured it is slower than the two launches, so it is off by
+ * default.  PFARNA_TEST_WITHHOLD_COPY=1 at pf_init
  * (failure-detection tests only) makes the propagate kernel issue no
  * frame-staging copy, so its bounded wait (0.2 s) runs out: the step ends
  * early and the next synchronising call reports PF_ERR_TIMEOUT.
@@ -397,7 +402,8 @@ enum {
   PF_KERNEL_PROPAGATE_WEIGHT = 1,
   PF_KERNEL_RESAMPLE = 2,
   PF_KERNEL_GLOBAL = 3,
-  PF_KERNEL_COUNT = 4
+  PF_KERNEL_FUSED_STEP = 4, /* the one-launch step: propagate, weight, resample, global step */
+  PF_KERNEL_COUNT = 5
 };
 
 /* Wait for the recorded work, then write, for each of the first n (<=

@@ -31,7 +31,7 @@ EXPORTS = ("pf_abi_version", "pf_query_workspace", "pf_init", "pf_step", "pf_hos
            "pf_graph_step", "pf_autotune", "pf_checkpoint_bytes", "pf_save", "pf_load", "pf_destroy",
            "pf_last_error")
 THETA_NAMES = ("sigma_psf", "amplitude", "background", "sigma_pos", "sigma_v")
-KERNEL_NAMES = ("frame_prep", "propagate_weight", "resample", "global")
+KERNEL_NAMES = ("frame_prep", "propagate_weight", "resample", "global", "fused_step")
 
 
 class pf_track_config(C.Structure):

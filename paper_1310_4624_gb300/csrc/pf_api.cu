@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <unordered_map>
 #include <mutex>
@@ -61,14 +62,13 @@ struct pf_handle {
   int* tile_ctr = nullptr;
   int n_ring_blocks = 0;  // leading blocks of the propagate kernel
   // fused step: task list, resampling chunks, their code sums, counters
-  int4* tasks = nullptr;
-  int n_tasks = 0;
   int4* chunks = nullptr;
   int n_chunks = 0;
   unsigned long long* chunk_q = nullptr;
   unsigned int* fsync = nullptr;
+  unsigned int* rq = nullptr;  // ready queue, 2 parities x 2 n_chunks entries
   int fused_grid = 1;
-  bool fused = true;  // PFARNA_FUSED=0 at pf_init: propagate and resample as two launches
+  bool fused = false;  // PFARNA_FUSED=1 at pf_init: the whole step as one persistent launch
   bool finish_pending = false;  // the last step's estimate / history not yet written (k_finish)
   int max_G = 1;
   uint32_t* parent = nullptr;
@@ -164,7 +164,7 @@ QuantCoeffs make_qc() {
 
 struct Layout {
   size_t trk, ts, gs, gd, tiles, frame_of, pv0, pv1, I0, I1, anc, lw, tp, ypad, hist, ghist, ring, ring_next, exo_next, keys_next,
-      tile_ctr, parent, ds, tasks, chunks, chunk_q, fsync,
+      tile_ctr, parent, ds, rq, chunks, chunk_q, fsync,
       tmap, total;
   size_t rp_pv, rp_I, ck_pv, ck_I, ca_pv0, ca_pv1, ca_I0, ca_I1, lam_hist, lbar_hist, dlam, Dacc, grad, logz, seed,
       replay_bad;
@@ -277,9 +277,9 @@ Layout plan(const pf_track_config* c, int n, int history) {
   L.exo_next = take(sizeof(uint32_t) * 2 * (size_t)L.G_total);
   L.keys_next = take(sizeof(uint4) * 2 * (size_t)L.G_total);
   L.tile_ctr = take(sizeof(int));
-  L.tasks = take(sizeof(int4) * (size_t)(L.n_tiles + 2 * L.n_chunks));
+  L.rq = take(sizeof(unsigned int) * 4 * (size_t)L.n_chunks);
   L.chunks = take(sizeof(int4) * (size_t)L.n_chunks);
-  L.chunk_q = take(3 * sizeof(unsigned long long) * (size_t)L.n_chunks);
+  L.chunk_q = take(4 * sizeof(unsigned long long) * (size_t)L.n_chunks);
   L.fsync = take(sizeof(unsigned int) * (size_t)FusedSync{L.G_total}.count());
   L.tiles = take(sizeof(int4) * L.n_tiles);
   L.frame_of = take(sizeof(int) * (size_t)n);
@@ -445,6 +445,7 @@ K1Args k1_args(const pf_handle* h) {
   a.tmaps = h->tmaps;
   a.ring_next = h->ring_next;
   a.ring_stride = h->G_total;
+  a.ring = h->ring;
   a.exo_next = h->exo_next;
   a.hist = h->hist;
   a.ghist = h->ghist;
@@ -458,12 +459,12 @@ K1Args k1_args(const pf_handle* h) {
   a.variants = h->variants ? 1 : 0;
   a.keys_next = h->keys_next;
   a.frame_of = h->frame_of;
-  a.tasks = h->tasks;
-  a.n_tasks = h->n_tasks;
+  a.n_chunks = h->n_chunks;
   a.chunks = h->chunks;
   a.gd = h->gd;
   a.chunk_q = h->chunk_q;
   a.sync = h->fsync;
+  a.rq = h->rq;
   a.qc = h->qc;
   return a;
 }
@@ -570,7 +571,7 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
   h->exo_next = (uint32_t*)(w + L.exo_next);
   h->keys_next = (uint4*)(w + L.keys_next);
   h->tile_ctr = (int*)(w + L.tile_ctr);
-  h->tasks = (int4*)(w + L.tasks);
+  h->rq = (unsigned int*)(w + L.rq);
   h->chunks = (int4*)(w + L.chunks);
   h->n_chunks = L.n_chunks;
   h->chunk_q = (unsigned long long*)(w + L.chunk_q);
@@ -615,8 +616,10 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
   std::vector<TrackParams> tp(n_tracks);
   std::vector<GroupDesc> gd;
   std::vector<int4> tiles;
+  std::vector<int4> chunks;  // fused step: (track, global group, first slot, items)
   gd.reserve(L.G_total);
   tiles.reserve(L.n_tiles);
+  chunks.reserve(L.n_chunks);
   long long part = 0, ypo = 0, paro = 0, gho = 0;
   int gro = 0, tio = 0, ho = 0;
   for (int t = 0; t < n_tracks; ++t) {
@@ -671,6 +674,10 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
       for (int j0 = 0; j0 < c.Np; j0 += K1_TILE)
         tiles.push_back(make_int4(t, g, j0, c.Np - j0 < K1_TILE ? c.Np - j0 : K1_TILE));
       D.tile_count = (int)tiles.size() - D.tile_begin;
+      D.chunk_begin = (int)chunks.size();
+      for (int j0 = 0; j0 < c.Np; j0 += RS_CHUNK)
+        chunks.push_back(make_int4(t, gro + g, j0, c.Np - j0 < RS_CHUNK ? c.Np - j0 : RS_CHUNK));
+      D.chunk_count = (int)chunks.size() - D.chunk_begin;
       gd.push_back(D);
     }
     const long long Nt = (long long)c.G * c.Np;
@@ -716,6 +723,7 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
   if ((e = cudaMemcpyAsync(h->trk, tp.data(), sizeof(TrackParams) * n_tracks, cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemcpyAsync(h->gd, gd.data(), sizeof(GroupDesc) * gd.size(), cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemcpyAsync(h->tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(h->chunks, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemcpyAsync(h->frame_of, ident.data(), sizeof(int) * ident.size(), cudaMemcpyHostToDevice, s)) ||
       (h->tmaps && (e = cudaMemcpyAsync(h->tmaps, maps.data(), sizeof(CUtensorMap) * n_tracks,
                                         cudaMemcpyHostToDevice, s)))) {
@@ -751,6 +759,19 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
   for (int t = 0; t < n_tracks; ++t) n_arna += (cfg[t].mode == PF_ARNA && cfg[t].G > 1 && cfg[t].G <= RING_SMEM_G);
   (void)n_arna;
   h->n_ring_blocks = n_tracks < 16 ? n_tracks : 16;
+  {
+    // PFARNA_FUSED=1: the one-launch (fused) step instead of propagate, then
+    // resample; measured slower on the tracking and batched workloads, so not
+    // the default
+    const char* fz = std::getenv("PFARNA_FUSED");
+    h->fused = fz && std::atoi(fz) == 1;
+    int focc = 1;
+    if ((e = fused_occupancy(h->R, &focc)) != cudaSuccess) { pf_destroy(h); return cuda_fail(nullptr, e, "occupancy"); }
+    if (focc < 1) focc = 1;
+    const int n_tasks = L.n_tiles + 2 * L.n_chunks;
+    const long long fw = (long long)sms * focc;
+    h->fused_grid = (int)(n_tasks < fw ? n_tasks : fw);
+  }
   for (int t = 0; t < n_tracks; ++t) {
     h->max_G = cfg[t].G > h->max_G ? cfg[t].G : h->max_G;
     if (cfg[t].resample_rule == PF_RESAMPLE_ESS) h->carry_any = true;
@@ -787,12 +808,24 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
   return PF_OK;
 }
 
-// The kernels of one step after frame preparation: propagate + weight, then
-// resample with the global step as its tail.
-static cudaError_t launch_step_kernels(pf_handle* h, cudaStream_t s) {
-  cudaError_t e = launch_propagate(k1_args(h), h->R, h->k1_grid + h->n_ring_blocks, h->pdl, s);
-  if (e != cudaSuccess) return e;
-  return launch_resample(resample_args(h, 1), h->G_total, h->rs_cluster, h->pdl, s, h->rs_threads);
+// The kernels of one step after frame preparation: the fused step, or
+// propagate + weight, then resample with the global step as its tail.
+// marks: record profiling events (not while a graph is being captured).
+static cudaError_t launch_step_kernels(pf_handle* h, cudaStream_t s, bool marks, const K1Args* k1p = nullptr) {
+  const K1Args k1 = k1p ? *k1p : k1_args(h);
+  cudaError_t e;
+  if (h->fused) {
+    if (marks && (e = mark(h, PF_KERNEL_FUSED_STEP, s)) != cudaSuccess) return e;
+    if ((e = launch_fused_step(k1, h->R, h->fused_grid + h->n_ring_blocks, h->pdl, s)) != cudaSuccess) return e;
+    return marks ? mark(h, PF_KERNEL_FUSED_STEP, s) : cudaSuccess;
+  }
+  if (marks && (e = mark(h, PF_KERNEL_PROPAGATE_WEIGHT, s)) != cudaSuccess) return e;
+  if ((e = launch_propagate(k1, h->R, h->k1_grid + h->n_ring_blocks, h->pdl, s)) != cudaSuccess) return e;
+  if (marks && (e = mark(h, PF_KERNEL_PROPAGATE_WEIGHT, s)) != cudaSuccess) return e;
+  if (marks && (e = mark(h, PF_KERNEL_RESAMPLE, s)) != cudaSuccess) return e;
+  if ((e = launch_resample(resample_args(h, 1), h->G_total, h->rs_cluster, h->pdl, s, h->rs_threads)) != cudaSuccess)
+    return e;
+  return marks ? mark(h, PF_KERNEL_RESAMPLE, s) : cudaSuccess;
 }
 
 pf_status pf_step(pf_handle* h, const float* const* frames, void* stream) {
@@ -810,14 +843,7 @@ pf_status pf_step(pf_handle* h, const float* const* frames, void* stream) {
     if ((e = prep_frames(h, frames, s)) != cudaSuccess) return cuda_fail(h, e, "k_frame_prep");
     if ((e = mark(h, PF_KERNEL_FRAME_PREP, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
   }
-  if ((e = mark(h, PF_KERNEL_PROPAGATE_WEIGHT, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
-  if ((e = launch_propagate(k1, h->R, h->k1_grid + h->n_ring_blocks, h->pdl, s)) != cudaSuccess)
-    return cuda_fail(h, e, "k_propagate_weight");
-  if ((e = mark(h, PF_KERNEL_PROPAGATE_WEIGHT, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
-  if ((e = mark(h, PF_KERNEL_RESAMPLE, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
-  if ((e = launch_resample(resample_args(h, 1), h->G_total, h->rs_cluster, h->pdl, s, h->rs_threads)) != cudaSuccess)
-    return cuda_fail(h, e, "k_resample");
-  if ((e = mark(h, PF_KERNEL_RESAMPLE, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
+  if ((e = launch_step_kernels(h, s, true, &k1)) != cudaSuccess) return cuda_fail(h, e, "step kernels");
   h->steps_run += 1;
   h->finish_pending = true;
   h->last_stream = s;
@@ -908,8 +934,10 @@ pf_status pf_step_table(pf_handle* h, const float* const* table_dev, int32_t T_t
   if (h->steps_run >= T_table) return fail(h, PF_ERR_STATE, "the frame table has no frame for this step");
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
+  if ((e = mark(h, PF_KERNEL_FRAME_PREP, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
   if ((e = launch_frames_table(h, table_dev, T_table, s)) != cudaSuccess) return cuda_fail(h, e, "k_frame_prep_table");
-  if ((e = launch_step_kernels(h, s)) != cudaSuccess) return cuda_fail(h, e, "step kernels");
+  if ((e = mark(h, PF_KERNEL_FRAME_PREP, s)) != cudaSuccess) return cuda_fail(h, e, "profile event");
+  if ((e = launch_step_kernels(h, s, true)) != cudaSuccess) return cuda_fail(h, e, "step kernels");
   h->steps_run += 1;
   h->finish_pending = true;
   h->last_stream = s;
@@ -939,7 +967,7 @@ pf_status pf_graph_step(pf_handle* h, const float* const* table_dev, int32_t T_t
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       cudaError_t e1 = launch_frames_table(h, table_dev, T_table, cs);
-      cudaError_t e2 = e1 == cudaSuccess ? launch_step_kernels(h, cs) : e1;
+      cudaError_t e2 = e1 == cudaSuccess ? launch_step_kernels(h, cs, false) : e1;
       e = cudaStreamEndCapture(cs, &g);
       if (e == cudaSuccess) e = e2;
     }
@@ -1054,7 +1082,7 @@ pf_status pf_autotune(pf_handle* h, const float* const* frames, int32_t* k1_grid
   // and weights, and the resampler candidates have replaced the ancestors
   // the propagate kernel reads, so only the resampler runs again, now with
   // the global step.
-  e = cached ? launch_step_kernels(h, s)
+  e = cached ? launch_step_kernels(h, s, false)
              : launch_resample(resample_args(h, 1), h->G_total, h->rs_cluster, false, s, h->rs_threads);
   if (e != cudaSuccess) return cuda_fail(h, e, "step kernels");
   h->steps_run += 1;
@@ -1319,7 +1347,9 @@ pf_status pf_reset(pf_handle* h, void* stream) {
   if ((e = cudaMemsetAsync(h->ds, 0, sizeof(DevState), s)) ||
       (e = cudaMemsetAsync(h->ts, 0, sizeof(TrackState) * h->n_tracks, s)) ||
       (e = cudaMemsetAsync(h->gs, 0, sizeof(GroupState) * h->G_total, s)) ||
-      (e = cudaMemsetAsync(h->tile_ctr, 0, sizeof(int), s)))
+      (e = cudaMemsetAsync(h->tile_ctr, 0, sizeof(int), s)) ||
+      (e = cudaMemsetAsync(h->fsync, 0, sizeof(unsigned int) * FusedSync{h->G_total}.count(), s)) ||
+      (e = cudaMemsetAsync(h->rq, 0, sizeof(unsigned int) * 4 * (size_t)h->n_chunks, s)))
     return cuda_fail(h, e, "pf_reset");
   InitArgs ia{h->trk, h->tiles, h->n_tiles, h->N_total, nullptr, h->pv[1], h->In[1]};
   for (int t = 0; t < h->n_tracks; ++t)

@@ -117,6 +117,9 @@ struct GroupState {
   unsigned long long Q; // group total weight code (step k)
   float xs[5];          // group estimate x^^m (step k)
   float ess;            // group ESS (step k)
+  // fused step: the resampling thresholds of step k (Thresholds below)
+  unsigned long long th_A, th_F1, th_M;
+  uint32_t th_B, th_F0, th_Np;
 };
 
 // Static description of a group.

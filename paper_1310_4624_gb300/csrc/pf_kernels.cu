@@ -791,6 +791,30 @@ __device__ __forceinline__ void prop_noise(uint32_t key0, uint32_t key1, uint32_
   box_muller_fast(w1.x, w1.y, e[4], e5);
 }
 
+// Ready-queue entries of the fused step: task kind << RQ_KIND_SHIFT | index.
+constexpr uint32_t RQ_KIND_SHIFT = 28;
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Fused step tasks and scheduling (defined with the resampler below).
+__device__ __noinline__ void fused_task_a(const K1Args& a, int k, int ci, unsigned char* smem);
+__device__ __noinline__ void fused_task_b(const K1Args& a, int k, int ci, unsigned char* smem);
+__device__ __noinline__ void fused_group_tiles_done(const K1Args& a, int k, int gi);
+__device__ __noinline__ int rq_try_claim(const K1Args& a, int par);
+__device__ __noinline__ int rq_entry(const K1Args& a, int par, unsigned pos);
+__device__ __noinline__ int rq_wait_claim(const K1Args& a, int par);
+__device__ __forceinline__ bool step_failed(const DevState* ds);
+
+// Shared memory of the fused step: the staged frame box of a P task, or the
+// prefixes and ancestor window of a B task, or the global step's scratch.
+constexpr size_t FUSED_SMEM = sizeof(unsigned long long) * pad8(RS_CHUNK) + sizeof(uint32_t) * pad8(2 * RS_CHUNK);
+constexpr size_t ROI_SMEM = sizeof(float) * 2 * (ROI_FLOATS + 4);
+static_assert(ROI_SMEM <= FUSED_SMEM && sizeof(GlobalScratch) <= FUSED_SMEM, "fused step shared memory");
+
 // Propagate + weight: tiles of K1_TILE = K1_PPT x K1_THREADS slots of one
 // group, K1_PPT particles per thread.  Each tile stages the bounding box of
 // its particles' patches (at most ROI_W x ROI_ROWS floats) in shared memory
@@ -799,15 +823,22 @@ __device__ __forceinline__ void prop_noise(uint32_t key0, uint32_t key1, uint32_
 // the previous step.
 // SINGLE: one track, whose parameters come from the kernel's constant
 // parameter block (a.p0) instead of global memory.
-template <int R, bool SINGLE, bool VARIANTS>
+// FUSED: the whole step in this launch -- the tiles are the P tasks, taken
+// between the resampling tasks A and B as those become ready (see "fused
+// step" below); the step index advances when the last CTA leaves.
+template <int R, bool SINGLE, bool VARIANTS, bool FUSED>
 __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(const __grid_constant__ K1Args a) {
   constexpr int D = 2 * R + 1;
   constexpr int PAD = 2 * R + 1;
   constexpr int NW = K1_THREADS / 32;
   // the staged box (TMA target) and a copy shifted left by one float, so that
   // any patch row starts on an 8-byte boundary in one of the two (pairwise
-  // loads); 4 spare floats cover the last pair of the last row
-  __shared__ __align__(128) float s_roi[2][ROI_FLOATS + 4];
+  // loads); 4 spare floats cover the last pair of the last row.  The fused
+  // step keeps it in dynamic shared memory, shared with the other tasks.
+  __shared__ __align__(128) float s_roi_static[FUSED ? 1 : 2][FUSED ? 4 : ROI_FLOATS + 4];
+  extern __shared__ __align__(128) unsigned char s_dyn[];
+  float (*s_roi)[ROI_FLOATS + 4] = FUSED ? reinterpret_cast<float (*)[ROI_FLOATS + 4]>(s_dyn)
+                                         : reinterpret_cast<float (*)[ROI_FLOATS + 4]>(&s_roi_static[0][0]);
   __shared__ int s_next[2];  // next tile, by iteration parity
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ float s_red[NW][8];
@@ -828,7 +859,7 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
     // exchange offsets o_g (Sec. III-C send sets) and ARNA ring order (they
     // depend only on the seed and the step index), then the previous step's
     // estimate, log c, log Z and history (finish_step).
-    static_assert(sizeof(GlobalScratch) <= sizeof(s_roi), "the leading blocks' scratch lives in s_roi");
+    static_assert(sizeof(GlobalScratch) <= ROI_SMEM, "the leading blocks' scratch lives in s_roi");
     // the fused step's counters of the next step (this launch uses parity
     // k & 1; the previous launch, which used the other parity, has ended)
     if (a.sync) {
@@ -838,10 +869,15 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
         a.sync[fs.pdone(par1, i)] = 0u;
         a.sync[fs.adone(par1, i)] = 0u;
       }
+      unsigned* q1 = a.rq + (size_t)par1 * 2 * a.n_chunks;
+      for (int i = blockIdx.x * K1_THREADS + threadIdx.x; i < 2 * a.n_chunks; i += a.n_ring_blocks * K1_THREADS)
+        q1[i] = 0u;
       if (blockIdx.x == 0 && threadIdx.x == 0) {
-        a.sync[fs.task_ctr(par1)] = 0u;
+        a.sync[fs.tile_ctr(par1)] = 0u;
         a.sync[fs.exit_ctr(par1)] = 0u;
         a.sync[fs.ring_done(par1)] = 0u;
+        a.sync[fs.rq_head(par1)] = 0u;
+        a.sync[fs.rq_tail(par1)] = 0u;
       }
     }
     const GlobalArgs ga{a.trk, a.ts, a.grp, nullptr, a.ring_next, a.ring_stride, a.exo_next, a.hist, a.ghist,
@@ -875,12 +911,21 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
       finish_step<K1_THREADS>(ga, t, *reinterpret_cast<GlobalScratch*>(&s_roi[0][0]));
       __syncthreads();
     }
-    return;
+    if constexpr (!FUSED) return;
+  }
+  __shared__ int s_last;
+  if (FUSED && (int)blockIdx.x < a.n_ring_blocks) {
+    // the group finalisations of this step wait for the leading blocks
+    // (they read the previous step's group state, which those overwrite)
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(&a.sync[FusedSync{a.ring_stride}.ring_done(k & 1)], 1u);
+    }
   }
   if (threadIdx.x == 0) {
     mbar_init(&s_bar, 1);
     fence_proxy_async();
-    if (tile < a.n_tiles) prefetch_tile(a, a.tiles[tile], k, pv_prev, I_prev);
+    if (!FUSED && tile < a.n_tiles) prefetch_tile(a, a.tiles[tile], k, pv_prev, I_prev);
   }
   __syncthreads();
   uint32_t phase = 0;
@@ -1146,6 +1191,110 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
     return true;
   };
 
+  if constexpr (FUSED) {
+    // Thread 0 schedules.  At the start of each task it claims, ahead of
+    // need, the CTA's next tile and -- when the queue showed published work
+    // and the CTA holds no position yet -- a queue position, so that both
+    // round trips overlap the task.  At the next task boundary it runs the
+    // held position's task if it is published, else the held tile; with no
+    // tile left it waits (bounded) for its position, or claims one and
+    // waits.  A held position depends only on earlier positions and on
+    // tiles, which are always runnable, so every wait ends.
+    __shared__ int s_code;
+    const FusedSync fs{a.ring_stride};
+    const int par = k & 1;
+    const unsigned total = 2u * (unsigned)a.n_chunks;
+    const bool worker = (int)blockIdx.x >= a.n_ring_blocks;
+    const unsigned* q = a.rq + (size_t)par * 2 * a.n_chunks;
+    unsigned* head = &a.sync[fs.rq_head(par)];
+    int pend = -1;                  // held queue position (thread 0)
+    unsigned ntile = 0u;            // held next tile (thread 0)
+    bool have_tile = false;
+    unsigned long long hint = 0ull; // (head, tail) as last read (thread 0)
+    if (worker && threadIdx.x == 0) {
+      ntile = atomicAdd(&a.sync[fs.tile_ctr(par)], 1u);
+      have_tile = true;
+    }
+    for (;;) {
+      if (threadIdx.x == 0) {
+        int code = -1;
+        if (worker) {
+          if (pend >= 0) {
+            const unsigned v = ld_acquire(q + pend);
+            if (v != 0u) {
+              code = (int)(v - 1u);
+              pend = -1;
+            }
+          }
+          if (code < 0 && have_tile && ntile < (unsigned)a.n_tiles) {
+            code = (int)ntile;  // kind TASK_P = 0
+            have_tile = false;
+          }
+          if (code < 0) {
+            // no tile left: the held position, or a new one
+            code = pend >= 0 ? rq_entry(a, par, (unsigned)pend) : rq_wait_claim(a, par);
+            pend = -1;
+          }
+          // claims for the next boundary, in flight during this task
+          if (code >= 0) {
+            if (!have_tile && ntile < (unsigned)a.n_tiles) {
+              ntile = atomicAdd(&a.sync[fs.tile_ctr(par)], 1u);
+              have_tile = true;
+            }
+            const unsigned h = (unsigned)hint, t = (unsigned)(hint >> 32);
+            if (pend < 0 && h < t && h < total && ntile < (unsigned)a.n_tiles) {
+              const unsigned p = atomicAdd(head, 1u);
+              pend = p < total ? (int)p : -1;
+            }
+            hint = *reinterpret_cast<volatile const unsigned long long*>(head);
+          }
+        }
+        s_code = code;
+      }
+      __syncthreads();
+      const int code = s_code;
+      if (code < 0) break;
+      const int kind = (int)((unsigned)code >> RQ_KIND_SHIFT), idx = code & ((1 << RQ_KIND_SHIFT) - 1);
+      if (kind == TASK_P) {
+        const int4 td = a.tiles[idx];
+        if (threadIdx.x == 0) prefetch_tile(a, td, k, pv_prev, I_prev);
+        if (!step_failed(a.ds)) {
+          tile = idx;
+          if constexpr (SINGLE)
+            run_tile(a.p0, td);
+          else
+            run_tile(a.trk[td.x], td);
+        }
+        __syncthreads();  // the tile's log-weights and partial sums are written
+        const int gi = (SINGLE ? a.p0.group_off : a.trk[td.x].group_off) + td.y;
+        if (threadIdx.x == 0) {
+          __threadfence();
+          const unsigned prev = atomicAdd(&a.sync[fs.pdone(par, gi)], 1u);
+          s_code = (prev + 1u == (unsigned)a.gd[gi].tile_count) ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_code) fused_group_tiles_done(a, k, gi);
+      } else if (kind == TASK_A) {
+        fused_task_a(a, k, idx, s_dyn);
+      } else {
+        fused_task_b(a, k, idx, s_dyn);
+      }
+      __syncthreads();  // the next task reuses the shared buffers and s_code
+    }
+    // the last CTA to leave advances the step index of every track
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned prev = atomicAdd(&a.sync[fs.exit_ctr(par)], 1u);
+      s_last = (prev + 1u == gridDim.x) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      for (int t = threadIdx.x; t < a.n_tracks; t += K1_THREADS) a.ts[t].k = k + 1;
+    }
+    return;
+  }
+
   // first tile by block index, the rest from a counter (reset by the
   // resampler), so CTAs finish together however many tiles each ran
   for (int it = 0; tile < a.n_tiles; ++it) {
@@ -1273,6 +1422,376 @@ __device__ __noinline__ void merge_windows(const unsigned long long* __restrict_
     ia0 = ia1;
     ib0 += mw;
   }
+}
+
+// ================================================================ fused step
+// One persistent launch per step.  Its CTAs take propagate + weight tiles
+// (P) from a counter, and resampling tasks from a ready queue as soon as
+// they can run: the tile that completes a group publishes the group maximum
+// and queues the group's chunk tasks A (quantise RS_CHUNK slots, sum their
+// weight codes); the A task that completes a group publishes the group
+// total, queues its chunk tasks B (scan and merge, Alg. 3 step 7), and
+// finishes the group's statistics (step 6); the track's last group runs
+// the global step (steps 8-10, and 1-2 of the next step).  A CTA takes a
+// ready task before a new tile, so no task ever waits for another; the only
+// wait is that of a CTA with no tiles left for the next ready task, and
+// every wait is bounded (0.2 s of %globaltimer: ERR_TIMEOUT, and the tasks
+// after it skip their work).  Counters and queue entries are per step
+// parity and cleared by the leading blocks of the step before.
+
+// An earlier kernel or task gave up (bounded wait) or met an out-of-range
+// ancestor: the weights mean nothing, later tasks skip their work.
+__device__ __forceinline__ bool step_failed(const DevState* ds) {
+  return (*reinterpret_cast<volatile const unsigned int*>(&ds->err) & (ERR_TIMEOUT | ERR_INDEX)) != 0u;
+}
+
+// Thread 0: the task published at queue position pos (waiting, bounded,
+// for its entry: the position was claimed after it was counted, or ahead of
+// it once no tiles were left), or -1.
+__device__ __noinline__ int rq_entry(const K1Args& a, int par, unsigned pos) {
+  const unsigned* q = a.rq + (size_t)par * 2 * a.n_chunks + pos;
+  unsigned v = ld_acquire(q);
+  if (v == 0u) {
+    const unsigned long long t0 = global_ns();
+    unsigned ns = 32;
+    while ((v = ld_acquire(q)) == 0u) {
+      if (step_failed(a.ds)) return -1;
+      if (global_ns() - t0 > 200000000ull) {
+        set_error(a.ds, ERR_TIMEOUT, 9u, pos, 0u);
+        return -1;
+      }
+      __nanosleep(ns);
+      if (ns < 1024) ns <<= 1;
+    }
+  }
+  return (int)(v - 1u);
+}
+
+// Thread 0, while tiles are left: one attempt at the next published ready
+// task; -1 if none is published or another CTA took it first.
+__device__ __noinline__ int rq_try_claim(const K1Args& a, int par) {
+  const FusedSync fs{a.ring_stride};
+  unsigned* head = &a.sync[fs.rq_head(par)];
+  const unsigned long long ht = *reinterpret_cast<volatile const unsigned long long*>(head);  // (head, tail)
+  const unsigned h = (unsigned)ht, t = (unsigned)(ht >> 32);
+  if (h >= t || atomicCAS(head, h, h + 1u) != h) return -1;
+  return rq_entry(a, par, h);
+}
+
+// Thread 0, once no tiles are left: the next queue position, whether its
+// task is published yet or not; -1 once every resampling task is taken (the
+// CTA then leaves).
+__device__ __noinline__ int rq_wait_claim(const K1Args& a, int par) {
+  const FusedSync fs{a.ring_stride};
+  const unsigned total = 2u * (unsigned)a.n_chunks;
+  if (*reinterpret_cast<volatile const unsigned*>(&a.sync[fs.rq_head(par)]) >= total) return -1;
+  const unsigned pos = atomicAdd(&a.sync[fs.rq_head(par)], 1u);
+  if (pos >= total) return -1;
+  return rq_entry(a, par, pos);
+}
+
+// Publish the chunk tasks of group d (kind TASK_A or TASK_B): the whole CTA
+// enters; the caller has written what the tasks read and fenced.
+__device__ __forceinline__ void rq_push_group(const K1Args& a, int par, const GroupDesc& d, int kind, int* s_pos) {
+  const FusedSync fs{a.ring_stride};
+  if (threadIdx.x == 0) *s_pos = (int)atomicAdd(&a.sync[fs.rq_tail(par)], (unsigned)d.chunk_count);
+  __syncthreads();
+  unsigned* q = a.rq + (size_t)par * 2 * a.n_chunks;
+  for (int c = threadIdx.x; c < d.chunk_count; c += K1_THREADS) {
+    __threadfence();
+    q[*s_pos + c] = (((unsigned)kind << RQ_KIND_SHIFT) | (unsigned)(d.chunk_begin + c)) + 1u;
+  }
+}
+
+// Thread 0: wait (bounded) until the leading blocks of this launch are done.
+__device__ __noinline__ int fused_wait_ring(const K1Args& a, int par, int gi) {
+  const FusedSync fs{a.ring_stride};
+  const unsigned* p = &a.sync[fs.ring_done(par)];
+  const unsigned target = (unsigned)a.n_ring_blocks;
+  if (ld_acquire(p) >= target) return 1;
+  const unsigned long long t0 = global_ns();
+  while (ld_acquire(p) < target) {
+    __nanosleep(128);
+    if (global_ns() - t0 > 200000000ull) {
+      set_error(a.ds, ERR_TIMEOUT, 7u, (uint32_t)gi, ld_acquire(p));
+      return 0;
+    }
+  }
+  return 1;
+}
+
+// The chunk's log-weights (items lo + threadIdx.x * RS_ITEMS .. + RS_ITEMS
+// of the group, -inf past its end), through L2: other CTAs of this launch
+// wrote them.
+__device__ __forceinline__ void fused_load_items(const float* __restrict__ lw, long long base, int i0, int hi,
+                                                 float (&v)[RS_ITEMS]) {
+  if (((base + i0) & 3) == 0 && i0 + RS_ITEMS <= hi) {
+    const float4 x0 = __ldcg(reinterpret_cast<const float4*>(lw + base + i0));
+    const float4 x1 = __ldcg(reinterpret_cast<const float4*>(lw + base + i0 + 4));
+    v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
+    v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+  } else {
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) v[r] = (i0 + r < hi) ? __ldcg(lw + base + i0 + r) : -INFINITY;
+  }
+}
+
+// The tile that completes group gi: the group maximum of its log-weights
+// from the tiles' maxima (NaN ignored), then the group's A tasks.
+__device__ __noinline__ void fused_group_tiles_done(const K1Args& a, int k, int gi) {
+  __shared__ float s_f[K1_THREADS / 32];
+  __shared__ int s_pos;
+  const GroupDesc d = a.gd[gi];
+  float m = -INFINITY;
+  for (int t = threadIdx.x; t < d.tile_count; t += K1_THREADS)
+    m = fmaxf(m, __ldcg(&a.tile_part[(long long)(d.tile_begin + t) * 8]));
+  const float M = block_max<K1_THREADS>(m, s_f);
+  if (threadIdx.x == 0) {
+    a.grp[gi].M = M;
+    __threadfence();
+  }
+  rq_push_group(a, k & 1, d, TASK_A, &s_pos);
+}
+
+// The A task that completes group gi: the group total of the weight codes
+// and Alg. 1's decision, the group's B tasks, then the group estimate and
+// ESS from the tile partial sums (Alg. 3 step 6) and the track's ticket;
+// the track's last group runs the global step.
+__device__ __noinline__ void fused_group_finalize(const K1Args& a, int k, int gi, float M, unsigned char* smem) {
+  __shared__ int s_flag, s_pos;
+  __shared__ unsigned long long s_w[K1_THREADS / 32];
+  __shared__ float s_stat[K1_THREADS / 32][8];
+  const FusedSync fs{a.ring_stride};
+  const int par = k & 1;
+  const GroupDesc d = a.gd[gi];
+  const TrackParams& P = a.trk[d.track];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool ess = P.resample_rule == 1;
+  unsigned long long q = 0, e1 = 0, e2 = 0;
+  for (int c = threadIdx.x; c < d.chunk_count; c += K1_THREADS) {
+    const long long cc = d.chunk_begin + c;
+    q += __ldcg(&a.chunk_q[4 * cc]);
+    if (ess) {
+      e1 += __ldcg(&a.chunk_q[4 * cc + 1]);
+      e2 += __ldcg(&a.chunk_q[4 * cc + 2]);
+    }
+  }
+  const unsigned long long Q = block_sum_u64<K1_THREADS>(q, s_w);
+  const unsigned long long E1 = ess ? block_sum_u64<K1_THREADS>(e1, s_w) : 0ull;
+  const unsigned long long E2 = ess ? block_sum_u64<K1_THREADS>(e2, s_w) : 0ull;
+  const bool resample = !ess || Q == 0 || ess_below(E1, E2, (uint32_t)P.Np, P.ess_t);
+  GroupState& G = a.grp[gi];
+  if (warp == 0) {
+    // each chunk's offset on the group's prefix-sum axis (exclusive sums of
+    // the chunk totals, in chunk order)
+    unsigned long long carry = 0;
+    for (int c0 = 0; c0 < d.chunk_count; c0 += 32) {
+      const int c = c0 + lane;
+      const unsigned long long x = c < d.chunk_count ? __ldcg(&a.chunk_q[4 * (long long)(d.chunk_begin + c)]) : 0ull;
+      unsigned long long y = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, y, o);
+        if (lane >= o) y += t;
+      }
+      if (c < d.chunk_count) a.chunk_q[4 * (long long)(d.chunk_begin + c) + 3] = carry + y - x;
+      carry += __shfl_sync(0xffffffffu, y, 31);
+    }
+    if (lane == 0) {
+      G.Q = Q;
+      G.carry_next = resample ? 0 : 1;
+      if (Q != 0) {
+        // the thresholds of the group's outputs (its resampling uniform word:
+        // Philox stream RESAMPLE, group, step)
+        const uint32_t u =
+            philox(P.key0, P.key1, make_uint4((uint32_t)d.g, 0u, (uint32_t)k, P.tag | (ST_RESAMPLE << 4))).x;
+        Thresholds th;
+        th.init_magic(Q, (uint32_t)P.Np, u, P.m_Np);
+        G.u = u;
+        G.th_A = th.A;
+        G.th_F1 = th.F1;
+        G.th_M = th.M;
+        G.th_B = th.B;
+        G.th_F0 = th.F0;
+        G.th_Np = th.Np;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) __threadfence();
+  rq_push_group(a, par, d, TASK_B, &s_pos);
+  // the leading blocks read the previous step's group estimates: they finish first
+  if (threadIdx.x == 0) s_flag = fused_wait_ring(a, par, gi);
+  float acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  if (Q != 0) {
+    for (int t = threadIdx.x; t < d.tile_count; t += K1_THREADS) {
+      const float* tp = a.tile_part + (long long)(d.tile_begin + t) * 8;
+      const float Mt = __ldcg(tp);
+      if (!(Mt - M >= -87.0f)) continue;
+      const float sc = __expf(Mt - M);
+#pragma unroll
+      for (int j = 0; j < 6; ++j) acc[j] = fmaf(sc, __ldcg(tp + 1 + j), acc[j]);
+      acc[6] = fmaf(sc * sc, __ldcg(tp + 7), acc[6]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 7; ++j) acc[j] = warp_sum(acc[j]);
+  if (lane == 0)
+#pragma unroll
+    for (int j = 0; j < 7; ++j) s_stat[warp][j] = acc[j];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t7[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int w = 0; w < K1_THREADS / 32; ++w)
+      for (int j = 0; j < 7; ++j) t7[j] += s_stat[w][j];
+    const bool okw = (Q != 0) && t7[0] > 0.0f;
+    for (int j = 0; j < 5; ++j) G.xs[j] = okw ? t7[1 + j] / t7[0] : 0.0f;
+    G.ess = okw ? t7[0] * t7[0] / t7[6] : 0.0f;
+    __threadfence();
+    const unsigned prev = atomicAdd(&a.ts[d.track].ticket, 1u);
+    s_flag = (prev + 1u == (unsigned)P.G) ? 1 : 0;
+    __threadfence();
+  }
+  __syncthreads();
+  if (s_flag) {
+    const GlobalArgs ga{a.trk, a.ts, a.grp, a.ring, a.ring_next, a.ring_stride, a.exo_next, a.hist, a.ghist,
+                        a.history, 1, a.ds, 1};
+    global_step<K1_THREADS>(ga, d.track, *reinterpret_cast<GlobalScratch*>(smem));
+    if (threadIdx.x == 0) a.ts[d.track].ticket = 0u;
+  }
+}
+
+// Task A of chunk ci: quantise the chunk's log-weights against the group
+// maximum (Alg. 3 step 7's fixed-point weights) and publish their sum; the
+// group's last chunk finalises the group.
+__device__ __noinline__ void fused_task_a(const K1Args& a, int k, int ci, unsigned char* smem) {
+  __shared__ int s_last;
+  __shared__ unsigned long long s_w[K1_THREADS / 32];
+  const FusedSync fs{a.ring_stride};
+  const int par = k & 1;
+  const int4 ch = a.chunks[ci];  // (track, group, first slot, items)
+  const GroupDesc d = a.gd[ch.y];
+  const TrackParams& P = a.trk[ch.x];
+  const bool ok = !step_failed(a.ds);
+  const bool ess = P.resample_rule == 1;
+  const float M = __ldcg(&a.grp[ch.y].M);
+  unsigned long long qs = 0, e1 = 0, e2 = 0;
+  if (ok) {
+    const float* __restrict__ lw = (k & 1) ? a.lw1 : a.lw;
+    float v[RS_ITEMS];
+    fused_load_items(lw, d.base, ch.z + (int)threadIdx.x * RS_ITEMS, ch.z + ch.w, v);
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+      const unsigned long long q = quantize(v[r], M, a.qc);
+      qs += q;
+      if (ess) {
+        const unsigned long long c = q >> 20;
+        e1 += c;
+        e2 += c * c;
+      }
+    }
+  }
+  qs = block_sum_u64<K1_THREADS>(qs, s_w);
+  if (ess) {
+    e1 = block_sum_u64<K1_THREADS>(e1, s_w);
+    e2 = block_sum_u64<K1_THREADS>(e2, s_w);
+  }
+  if (threadIdx.x == 0) {
+    a.chunk_q[4 * (long long)ci] = qs;
+    a.chunk_q[4 * (long long)ci + 1] = e1;
+    a.chunk_q[4 * (long long)ci + 2] = e2;
+    __threadfence();
+    const unsigned prev = atomicAdd(&a.sync[fs.adone(par, ch.y)], 1u);
+    s_last = (ok && prev + 1u == (unsigned)d.chunk_count) ? 1 : 0;
+  }
+  __syncthreads();
+  if (s_last) fused_group_finalize(a, k, ch.y, M, smem);
+}
+
+// Task B of chunk ci: the exact systematic resampling (Alg. 3 step 7) of the
+// outputs whose thresholds fall in this chunk: a block-wide scan of the
+// chunk's codes from the sum of the chunks before it, then the merge path
+// of the two-launch resampler.
+__device__ __noinline__ void fused_task_b(const K1Args& a, int k, int ci, unsigned char* smem) {
+  __shared__ int s_jlo, s_jhi;
+  __shared__ unsigned long long s_w[K1_THREADS / 32], s_sb;
+  __shared__ uint32_t s_u;
+  __shared__ Thresholds s_th;
+  const int4 ch = a.chunks[ci];
+  const GroupDesc d = a.gd[ch.y];
+  const TrackParams& P = a.trk[ch.x];
+  const int Np = d.Np, lo = ch.z, n = ch.w;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (step_failed(a.ds)) return;
+  const unsigned long long Q = __ldcg(&a.grp[ch.y].Q);
+  const bool keep = __ldcg(&a.grp[ch.y].carry_next) != 0;
+  const unsigned long long obase = (unsigned long long)d.g * (unsigned long long)Np;
+  uint32_t* __restrict__ anc = a.anc + (k & 1) * a.anc_stride + d.base;
+  if (Q == 0 || keep) {
+    // no finite weight, or Alg. 1's test keeps the particles: identity
+    for (int i = lo + threadIdx.x; i < lo + n; i += K1_THREADS) anc[i] = (uint32_t)(obase + i);
+    return;
+  }
+  const float M = __ldcg(&a.grp[ch.y].M);
+  if (threadIdx.x == 0) {
+    // the group's thresholds and this chunk's offset, from its finalisation
+    const GroupState& G = a.grp[ch.y];
+    s_sb = __ldcg(&a.chunk_q[4 * (long long)ci + 3]);
+    s_u = __ldcg(&G.u);
+    s_th.A = __ldcg(&G.th_A);
+    s_th.F1 = __ldcg(&G.th_F1);
+    s_th.M = __ldcg(&G.th_M);
+    s_th.B = __ldcg(&G.th_B);
+    s_th.F0 = __ldcg(&G.th_F0);
+    s_th.Np = __ldcg(&G.th_Np);
+  }
+  (void)P;
+  unsigned long long* s_incl = reinterpret_cast<unsigned long long*>(smem);
+  uint32_t* s_out = reinterpret_cast<uint32_t*>(smem + sizeof(unsigned long long) * pad8(RS_CHUNK));
+  const float* __restrict__ lw = (k & 1) ? a.lw1 : a.lw;
+  const int i0 = (int)threadIdx.x * RS_ITEMS;
+  float v[RS_ITEMS];
+  fused_load_items(lw, d.base, lo + i0, lo + n, v);
+  unsigned long long qv[RS_ITEMS];
+  unsigned long long tsum = 0;
+#pragma unroll
+  for (int r = 0; r < RS_ITEMS; ++r) {
+    qv[r] = quantize(v[r], M, a.qc);
+    tsum += qv[r];
+  }
+  // exclusive scan of the thread totals: warp shuffles, then warps
+  unsigned long long x = tsum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long t = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += t;
+  }
+  if (lane == 31) s_w[warp] = x;
+  __syncthreads();
+  unsigned long long wpre = 0, tot = 0;
+#pragma unroll
+  for (int w = 0; w < K1_THREADS / 32; ++w) {
+    const unsigned long long y = s_w[w];
+    if (w < warp) wpre += y;
+    tot += y;
+  }
+  const unsigned long long Sb = s_sb;
+  {
+    unsigned long long S = Sb + wpre + (x - tsum);
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+      S += qv[r];
+      s_incl[pad8(i0 + r)] = S;
+    }
+  }
+  if (threadIdx.x == 0) {
+    const Thresholds th = s_th;
+    const float inv_Q = 1.0f / u64_to_float_approx(Q);
+    s_jlo = count_below(th, Sb, inv_Q, Np, s_u, a.ds);
+    s_jhi = count_below(th, Sb + tot, inv_Q, Np, s_u, a.ds);
+  }
+  __syncthreads();
+  merge_windows<K1_THREADS>(s_incl, s_out, s_th, s_jlo, s_jhi, n, obase + lo, anc);
 }
 
 // Resampler: one thread-block cluster per group, each CTA a contiguous chunk
@@ -1615,7 +2134,7 @@ cudaError_t launch_frame_prep(const FrameArgs& a, int nt, int blocks_x, bool pdl
 
 template <int R>
 static const void* k1_ptr() {
-  return (const void*)k_propagate_weight<R, false, false>;
+  return (const void*)k_propagate_weight<R, false, false, false>;
 }
 
 const void* propagate_kernel(int R) {
@@ -1633,7 +2152,50 @@ const void* propagate_kernel(int R) {
 
 template <int R, bool SINGLE, bool VARIANTS>
 static cudaError_t launch_propagate_rs(const K1Args& a, dim3 g, bool pdl, cudaStream_t s) {
-  return launch_ex(k_propagate_weight<R, SINGLE, VARIANTS>, g, dim3(K1_THREADS), 0, pdl, s, a);
+  return launch_ex(k_propagate_weight<R, SINGLE, VARIANTS, false>, g, dim3(K1_THREADS), 0, pdl, s, a);
+}
+
+template <int R, bool SINGLE, bool VARIANTS>
+static cudaError_t launch_fused_rs(const K1Args& a, dim3 g, bool pdl, cudaStream_t s) {
+  return launch_ex(k_propagate_weight<R, SINGLE, VARIANTS, true>, g, dim3(K1_THREADS), 0, pdl, s, a, FUSED_SMEM);
+}
+
+template <int R>
+static cudaError_t launch_fused_r(const K1Args& a, dim3 g, bool pdl, cudaStream_t s) {
+  if (a.variants) return launch_fused_rs<R, false, true>(a, g, pdl, s);
+  if (a.n_tracks == 1) return launch_fused_rs<R, true, false>(a, g, pdl, s);
+  return launch_fused_rs<R, false, false>(a, g, pdl, s);
+}
+
+cudaError_t launch_fused_step(const K1Args& a, int R, int grid, bool pdl, cudaStream_t s) {
+  const dim3 g(grid);
+  switch (R) {
+    case 1: return launch_fused_r<1>(a, g, pdl, s);
+    case 2: return launch_fused_r<2>(a, g, pdl, s);
+    case 3: return launch_fused_r<3>(a, g, pdl, s);
+    case 4: return launch_fused_r<4>(a, g, pdl, s);
+    case 5: return launch_fused_r<5>(a, g, pdl, s);
+    case 6: return launch_fused_r<6>(a, g, pdl, s);
+    case 7: return launch_fused_r<7>(a, g, pdl, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Resident fused-step CTAs per SM (the single-track instance of radius R;
+// the instances differ little in registers).
+cudaError_t fused_occupancy(int R, int* blocks_per_sm) {
+  const void* f = nullptr;
+  switch (R) {
+    case 1: f = (const void*)k_propagate_weight<1, true, false, true>; break;
+    case 2: f = (const void*)k_propagate_weight<2, true, false, true>; break;
+    case 3: f = (const void*)k_propagate_weight<3, true, false, true>; break;
+    case 4: f = (const void*)k_propagate_weight<4, true, false, true>; break;
+    case 5: f = (const void*)k_propagate_weight<5, true, false, true>; break;
+    case 6: f = (const void*)k_propagate_weight<6, true, false, true>; break;
+    case 7: f = (const void*)k_propagate_weight<7, true, false, true>; break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, K1_THREADS, FUSED_SMEM);
 }
 
 // Instances: one track, several tracks, and tracks that use a method

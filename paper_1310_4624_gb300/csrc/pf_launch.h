@@ -69,6 +69,7 @@ struct K1Args {
   const CUtensorMap* tmaps;  // one per track over its padded frame, or nullptr
   int* ring_next;            // two buffers (by step parity) of G_total: ring order of step k+1 (ARNA)
   int ring_stride;           // G_total
+  int* ring;                 // ring order of each group's track (the global step's output)
   uint32_t* exo_next;        // two buffers (by step parity) of G_total: exchange offsets of step k+1
   HistRec* hist;
   GroupHist* ghist;
@@ -86,28 +87,36 @@ struct K1Args {
                              // uses keyed send sets: launches the variants instance (frames prepared)
   uint4* keys_next;          // two buffers (by step parity) of G_total: keyed send-permutation keys of step k+1
   const int* frame_of;       // per track: the track whose padded frame to read this step, or nullptr (its own)
-  // fused step (one persistent launch per step): the task list, the
-  // resampling chunks and the counters the tasks wait on
-  const int4* tasks;         // (kind, tile or chunk, global group, 0) in the order CTAs take them
-  int n_tasks;
+  // fused step (one persistent launch per step): the resampling chunks,
+  // their code sums, the counters and the ready queue of resampling tasks
+  int n_chunks;
   const int4* chunks;        // (track, global group, first slot in the group, items)
   const GroupDesc* gd;
-  unsigned long long* chunk_q;  // per chunk: sum of weight codes, and for Alg. 1's test sums of c and c^2
-  unsigned int* sync;        // [2][G_total] tiles done (per warp), [2][G_total] chunks done, then per
-                             // parity: task counter, CTAs exited, leading blocks done (see fused_sync)
+  unsigned long long* chunk_q;  // per chunk: sum of weight codes, for Alg. 1's test sums of c and c^2,
+                                // and the sum of the codes of the group's chunks before it
+  unsigned int* sync;        // counters by step parity (FusedSync)
+  unsigned int* rq;          // ready queue, two parities of 2 n_chunks entries: task + 1, 0 = not yet written
   QuantCoeffs qc;
   CUtensorMap zmap;
 };
 
-// Offsets of the fused step's counters in K1Args::sync (each by step parity).
+// Offsets of the fused step's counters in K1Args::sync, by step parity:
+// per global group the tiles done and the chunks quantised, then the tile
+// counter, CTAs that left, leading blocks done, and the ready queue's claim
+// and publish positions.
 struct FusedSync {
   int G_total;
   __host__ __device__ int pdone(int par, int gi) const { return par * G_total + gi; }
   __host__ __device__ int adone(int par, int gi) const { return 2 * G_total + par * G_total + gi; }
-  __host__ __device__ int task_ctr(int par) const { return 4 * G_total + par; }
+  __host__ __device__ int tile_ctr(int par) const { return 4 * G_total + par; }
   __host__ __device__ int exit_ctr(int par) const { return 4 * G_total + 2 + par; }
   __host__ __device__ int ring_done(int par) const { return 4 * G_total + 4 + par; }
-  __host__ __device__ int count() const { return 4 * G_total + 6; }
+  // claim position and publish position side by side (one 8-byte aligned
+  // load reads both: the counters start 256-byte aligned and 4 G_total + 6
+  // is even)
+  __host__ __device__ int rq_head(int par) const { return 4 * G_total + 6 + 2 * par; }
+  __host__ __device__ int rq_tail(int par) const { return 4 * G_total + 7 + 2 * par; }
+  __host__ __device__ int count() const { return 4 * G_total + 10; }
 };
 
 struct GlobalArgs {
@@ -219,7 +228,7 @@ cudaError_t launch_frame_prep(const FrameArgs& a, int nt, int blocks_x, bool pdl
 cudaError_t launch_frame_prep_table(const FrameTableArgs& a, int blocks_x, bool pdl, cudaStream_t s);
 cudaError_t launch_propagate(const K1Args& a, int R, int grid, bool pdl, cudaStream_t s);
 // The fused step: propagate + weight tiles, the per-group resampling and the
-// global step in one persistent launch (a.tasks).
+// global step in one persistent launch.
 cudaError_t launch_fused_step(const K1Args& a, int R, int grid, bool pdl, cudaStream_t s);
 cudaError_t fused_occupancy(int R, int* blocks_per_sm);
 // threads: RS_THREADS, or RS_THREADS_SMALL (eight CTAs per SM, for batches of small groups)
