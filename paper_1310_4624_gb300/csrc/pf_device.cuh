@@ -281,6 +281,12 @@ __device__ __forceinline__ float u64_to_float_approx(unsigned long long v) {
 struct Thresholds {
   unsigned long long A, F1, M;
   uint32_t B, F0, Np;
+  float Af, F1f;  // FP32 approximations of Q / Np and F / Np (comparison filter, le)
+
+  __device__ __forceinline__ void init_filter() {
+    Af = __fadd_rn((float)A, (float)B / (float)Np);
+    F1f = __fadd_rn((float)F1, (float)F0 / (float)Np);
+  }
 
   __device__ __forceinline__ void init(unsigned long long Q, uint32_t np, uint32_t u) {
     Np = np;
@@ -290,6 +296,7 @@ struct Thresholds {
     F1 = F / np;
     F0 = (uint32_t)(F - F1 * np);
     M = np > 1 ? (~0ull) / np + 1ull : 0ull;
+    init_filter();
   }
   // The same with the divisions by np done through m = ceil(2^64 / np)
   // (fastdiv_magic): q = floor(n m / 2^64) is floor(n / np) or one more
@@ -309,10 +316,25 @@ struct Thresholds {
     const unsigned long long F = (unsigned long long)u * (Q >> 32) + (((unsigned long long)u * (uint32_t)Q) >> 32);
     F1 = udiv(F, np, M);
     F0 = (uint32_t)(F - F1 * np);
+    init_filter();
   }
   __device__ __forceinline__ unsigned long long T(uint32_t j) const {
     const unsigned long long n = (unsigned long long)j * B + F0;
     return (unsigned long long)j * A + F1 + (Np > 1 ? __umul64hi(n, M) : n);
+  }
+  // S <= T_j, decided in FP32 when the two are far apart and exactly
+  // otherwise: T_j = j Q/Np + F/Np - frac in [0, 1) is approximated by
+  // fma(j, Af, F1f) within a relative 2^-21 (j < 2^24, a few FP32
+  // roundings) and S by its FP32 value within 2^-23, so a gap beyond
+  // 1e-6 of the larger plus 2 decides the comparison; the result is always
+  // that of the exact form.
+  __device__ __forceinline__ bool le(unsigned long long S, uint32_t j) const {
+    const float Tf = fmaf((float)j, Af, F1f);
+    const float Sf = __fmaf_rn((float)(uint32_t)(S >> 32), 4294967296.0f, (float)(uint32_t)S);
+    const float m = fmaf(fmaxf(Sf, Tf), 1.0e-6f, 2.0f);
+    if (Sf + m < Tf) return true;
+    if (Sf > Tf + m) return false;
+    return S <= T(j);
   }
 };
 

@@ -1330,19 +1330,40 @@ __device__ __forceinline__ int count_below(const Thresholds& th, unsigned long l
   return c;
 }
 
+// Shared-memory accesses through 32-bit shared-window addresses (the merge
+// helpers are not inlined, and a generic pointer would make every access a
+// generic one).
+__device__ __forceinline__ unsigned long long lds_u64(uint32_t addr) {
+  unsigned long long v;
+  asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ void sts_u32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+// X_i = s_incl[pad8(i)] at shared address base
+__device__ __forceinline__ unsigned long long incl_at(uint32_t base, int i) {
+  return lds_u64(base + 8u * (uint32_t)pad8(i));
+}
+
 // Block-wide split of a merge at diagonal p: the number of items among its
 // first p positions, for items i < n with boundaries X_i = s_incl[pad8(i)]
 // and outputs j0 + b, b < no, with thresholds T: the largest i in
 // [max(0, p - no), min(p, n)] with X_{i-1} <= T_{j0+p-i}.  A
 // NTR-ary search that every thread of the block (NTR threads) enters.
 template <int NTR>
-__device__ __noinline__ int merge_split(const unsigned long long* s_incl, const Thresholds& th, int j0, int n, int no, int p) {
+__device__ __noinline__ int merge_split(uint32_t s_incl, const Thresholds& th, int j0, int n, int no, int p) {
   int lo = max(0, p - no), hi = min(p, n);
   while (lo < hi) {
     const int m = hi - lo;
     const bool fine = m <= NTR;  // then candidates lo + 1 .. hi, else NTR evenly spaced
     const int c = fine ? lo + 1 + (int)threadIdx.x : lo + (int)(((long long)(threadIdx.x + 1) * m) / NTR);
-    const bool ok = (!fine || (int)threadIdx.x < m) && s_incl[pad8(c - 1)] <= th.T((uint32_t)(j0 + p - c));
+    const bool ok = (!fine || (int)threadIdx.x < m) && th.le(incl_at(s_incl, c - 1), (uint32_t)(j0 + p - c));
     const int cnt = __syncthreads_count(ok);  // the predicate holds for a prefix of the candidates
     if (fine) {
       lo += cnt;
@@ -1362,11 +1383,13 @@ __device__ __noinline__ int merge_split(const unsigned long long* s_incl, const 
 // obase_sub + item, stored to anc[j].  Every thread of the block enters.
 // (Not inlined: it runs with registers of its own.)
 template <int NTR>
-__device__ __noinline__ void merge_windows(const unsigned long long* __restrict__ s_incl, uint32_t* __restrict__ s_out,
+__device__ __noinline__ void merge_windows(const unsigned long long* __restrict__ s_incl_p, uint32_t* __restrict__ s_out_p,
                                            const Thresholds& th_s, int jlo, int jhi, int n,
                                            unsigned long long obase_sub, uint32_t* __restrict__ anc) {
   constexpr int WIN = 2 * NTR * RS_ITEMS;
   const Thresholds th = th_s;
+  const uint32_t s_incl = (uint32_t)__cvta_generic_to_shared(s_incl_p);
+  const uint32_t s_out = (uint32_t)__cvta_generic_to_shared(s_out_p);
   // Merge path over the item boundaries X_i = S_{i+1} (s_incl) and the
   // thresholds Y_j = T_j of this sub-chunk's outputs j in [jlo, jhi):
   // output j takes the first item i with T_j < S_{i+1}.  The merged
@@ -1390,20 +1413,23 @@ __device__ __noinline__ void merge_windows(const unsigned long long* __restrict_
     int lo2 = max(0, d0 - mw), hi2 = min(d0, nw);
     while (lo2 < hi2) {
       const int mid = (lo2 + hi2 + 1) >> 1;  // candidate number of items consumed
-      if (s_incl[pad8(ia0 + mid - 1)] <= th.T((uint32_t)(jw + d0 - mid))) lo2 = mid;
+      if (th.le(incl_at(s_incl, ia0 + mid - 1), (uint32_t)(jw + d0 - mid))) lo2 = mid;
       else hi2 = mid - 1;
     }
     int ia = lo2, ib = d0 - lo2;
     if (ib < mw) {
-      // T and its remainder at output jw + ib, then advance incrementally
+      // T and its remainder at output jw + ib, then advance incrementally;
+      // the current item's boundary stays in a register (past the window's
+      // last item it counts as unbounded)
       uint32_t jj = (uint32_t)(jw + ib);
       unsigned long long num = (unsigned long long)jj * th.B + th.F0;
       unsigned long long qd = th.Np > 1 ? __umul64hi(num, th.M) : num;
       uint32_t rem = (uint32_t)(num - qd * th.Np);
       unsigned long long Tj = (unsigned long long)jj * th.A + th.F1 + qd;
+      unsigned long long X = ia < nw ? incl_at(s_incl, ia0 + ia) : ~0ull;
       for (int dd = d0; dd < d1; ++dd) {
-        if (ib < mw && (ia >= nw || Tj < s_incl[pad8(ia0 + ia)])) {
-          s_out[pad8(ib)] = (uint32_t)(obase_sub + ia0 + ia);
+        if (ib < mw && Tj < X) {
+          sts_u32(s_out + 4u * (uint32_t)pad8(ib), (uint32_t)(obase_sub + ia0 + ia));
           ++ib;
           rem += th.B;
           Tj += th.A;
@@ -1413,11 +1439,12 @@ __device__ __noinline__ void merge_windows(const unsigned long long* __restrict_
           }
         } else {
           ++ia;
+          X = ia < nw ? incl_at(s_incl, ia0 + ia) : ~0ull;
         }
       }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < mw; e += NTR) anc[jw + e] = s_out[pad8(e)];
+    for (int e = threadIdx.x; e < mw; e += NTR) anc[jw + e] = lds_u32(s_out + 4u * (uint32_t)pad8(e));
     __syncthreads();
     ia0 = ia1;
     ib0 += mw;
@@ -1744,6 +1771,7 @@ __device__ __noinline__ void fused_task_b(const K1Args& a, int k, int ci, unsign
     s_th.B = __ldcg(&G.th_B);
     s_th.F0 = __ldcg(&G.th_F0);
     s_th.Np = __ldcg(&G.th_Np);
+    s_th.init_filter();
   }
   (void)P;
   unsigned long long* s_incl = reinterpret_cast<unsigned long long*>(smem);
