@@ -69,6 +69,7 @@ struct pf_handle {
   unsigned int* rq = nullptr;  // ready queue, 2 parities x 2 n_chunks entries
   int fused_grid = 1;
   bool fused = false;  // PFARNA_FUSED=1 at pf_init: the whole step as one persistent launch
+  bool global_cta = true;  // PFARNA_GLOBAL_CTA=0 at pf_init: the last group to report runs the global step
   bool finish_pending = false;  // the last step's estimate / history not yet written (k_finish)
   int max_G = 1;
   uint32_t* parent = nullptr;
@@ -503,7 +504,10 @@ GlobalArgs global_args(const pf_handle* h, int finalize) {
 ResampleArgs resample_args(const pf_handle* h, int fuse) {
   ResampleArgs ra{h->gd,  h->gs,  h->tile_part, h->lw, h->carry_any ? h->lw + lw_stride(h->N_total) : nullptr,
                   h->anc, h->N_total, nullptr, nullptr, 0, h->qc, h->ds};
-  ra.fuse_global = fuse;
+  // one track: the global step on an extra cluster of the launch, so that the
+  // group that reports last goes straight on to its own merge
+  ra.fuse_global = (fuse == 1 && h->n_tracks == 1 && h->global_cta) ? 2 : fuse;
+  ra.n_groups = h->G_total;
   ra.tile_ctr = h->tile_ctr;
   ra.glob = global_args(h, 1);
   return ra;
@@ -765,6 +769,8 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
     // the default
     const char* fz = std::getenv("PFARNA_FUSED");
     h->fused = fz && std::atoi(fz) == 1;
+    const char* gc = std::getenv("PFARNA_GLOBAL_CTA");
+    h->global_cta = !(gc && std::atoi(gc) == 0);
     int focc = 1;
     if ((e = fused_occupancy(h->R, &focc)) != cudaSuccess) { pf_destroy(h); return cuda_fail(nullptr, e, "occupancy"); }
     if (focc < 1) focc = 1;

@@ -1835,6 +1835,46 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(ResampleAr
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
   const int grp = blockIdx.x / C;
+  if (a.fuse_global == 2 && grp >= a.n_groups) {
+    // the extra cluster of a one-track step: its first CTA waits (bounded)
+    // until every group has reported its statistics, then runs the track's
+    // global step; nothing waits on it within the launch
+    extern __shared__ unsigned long long s_dyn_gs[];
+    __shared__ int s_ok;
+    grid_dep_wait();
+    if (rank == 0) {
+      if (threadIdx.x == 0) {
+        const unsigned* tk = &a.glob.ts[0].ticket;
+        const unsigned G = (unsigned)a.glob.trk[0].G;
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(tk) : "memory");
+        const unsigned long long t0 = global_ns();
+        int ok = 1;
+        while (v < G) {
+          // groups skip their work (and their ticket) after a failed propagate launch
+          if ((*reinterpret_cast<volatile const unsigned int*>(&a.ds->err) & (ERR_TIMEOUT | ERR_INDEX)) != 0u) {
+            ok = 0;
+            break;
+          }
+          __nanosleep(256);
+          asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(tk) : "memory");
+          if (global_ns() - t0 > 200000000ull) {
+            set_error(a.ds, ERR_TIMEOUT, 11u, v, G);
+            ok = 0;
+            break;
+          }
+        }
+        s_ok = ok;
+      }
+      __syncthreads();
+      if (s_ok) {
+        global_step<NTR>(a.glob, 0, *reinterpret_cast<GlobalScratch*>(s_dyn_gs));
+        if (threadIdx.x == 0) a.glob.ts[0].ticket = 0u;
+      }
+    }
+    grid_dep_launch();
+    return;
+  }
   const GroupDesc d = a.gd[grp];
   const int Np = d.Np;
   const int chunk = ((Np + C - 1) / C + 7) & ~7;
@@ -2016,7 +2056,7 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(ResampleAr
       __threadfence();
     }
     __syncthreads();
-    if (s_last) {
+    if (s_last && a.fuse_global == 1) {
       global_step<NTR>(a.glob, d.track, *reinterpret_cast<GlobalScratch*>(s_dyn_rs));
       if (threadIdx.x == 0) a.glob.ts[d.track].ticket = 0u;
       __syncthreads();  // the scratch is the prefix array below
@@ -2260,7 +2300,8 @@ static cudaError_t launch_resample_t(const ResampleArgs& a, int n_groups, int cl
     attr_err = cudaFuncSetAttribute(k_resample<NTR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
   if (attr_err != cudaSuccess) return attr_err;
-  return launch_ex(k_resample<NTR>, dim3((unsigned)(n_groups * cluster)), dim3(NTR), cluster, pdl, s, a, smem);
+  const int clusters = n_groups + (a.fuse_global == 2 ? 1 : 0);  // the global step's extra cluster
+  return launch_ex(k_resample<NTR>, dim3((unsigned)(clusters * cluster)), dim3(NTR), cluster, pdl, s, a, smem);
 }
 
 cudaError_t launch_resample(const ResampleArgs& a, int n_groups, int cluster, bool pdl, cudaStream_t s, int threads) {

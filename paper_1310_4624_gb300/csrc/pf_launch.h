@@ -148,7 +148,10 @@ struct ResampleArgs {
   int local_idx;               // 1: ancestors within the group
   QuantCoeffs qc;
   DevState* ds;
-  int fuse_global;             // 1: the last group of a track to finish runs its global step
+  int fuse_global;             // 1: the last group of a track to finish runs its global step;
+                               // 2 (one track): an extra cluster after the groups' runs it instead,
+                               // once every group has reported, so no group's merge waits behind it
+  int n_groups;                // groups of the launch (the extra cluster, if any, comes after them)
   int* tile_ctr;               // propagate kernel's tile counter to reset, or nullptr
   GlobalArgs glob;             // (fuse_global) arguments of that step, finalize = 1
 };
