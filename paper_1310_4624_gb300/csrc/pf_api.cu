@@ -508,6 +508,9 @@ ResampleArgs resample_args(const pf_handle* h, int fuse) {
   // group that reports last goes straight on to its own merge
   ra.fuse_global = (fuse == 1 && h->n_tracks == 1 && h->global_cta) ? 2 : fuse;
   ra.n_groups = h->G_total;
+  ra.lean = h->carry_any ? 0 : 1;  // no group resamples by Alg. 1's test
+  ra.max_np = 1;
+  for (int t = 0; t < h->n_tracks; ++t) ra.max_np = h->cfg[t].Np > ra.max_np ? h->cfg[t].Np : ra.max_np;
   ra.tile_ctr = h->tile_ctr;
   ra.glob = global_args(h, 1);
   return ra;

@@ -383,6 +383,13 @@ __device__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
   }
 }
 
+// global_step out of line, for the resampler (it runs on one CTA of the
+// launch, and inlined twice it would crowd the resampler's own registers).
+template <int NT>
+__device__ __noinline__ void global_step_call(const GlobalArgs& a, int t, GlobalScratch& sc) {
+  global_step<NT>(a, t, sc);
+}
+
 // The rest of the global step of the track's last finished step kd = k - 1
 // (Alg. 3 steps 9-10 and the history): global estimate from the group
 // estimates and carried weights, log c = the carried weights' LSE, log Z,
@@ -1826,7 +1833,12 @@ __device__ __noinline__ void fused_task_b(const K1Args& a, int k, int ci, unsign
 // of the group's slots (a multiple of 8), processed in sub-chunks of SUB
 // items; thread t owns the RS_ITEMS consecutive items [t*RS_ITEMS, ...).
 
-template <int NTR>
+// LEAN: the common filter step -- every CTA's chunk fits in its registers
+// (one sub-chunk), no group resamples by Alg. 1's test, no weight codes
+// are stored and the uniforms are the step's own -- with the other paths
+// compiled out (a smaller kernel: the resampler is latency-bound, and
+// instruction fetch leads its stalls).
+template <int NTR, bool LEAN>
 __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(ResampleArgs a) {
   constexpr int SUB = NTR * RS_ITEMS;  // items per sub-chunk
   constexpr int SUB_PAD = pad8(SUB);
@@ -1868,7 +1880,7 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(ResampleAr
       }
       __syncthreads();
       if (s_ok) {
-        global_step<NTR>(a.glob, 0, *reinterpret_cast<GlobalScratch*>(s_dyn_gs));
+        global_step_call<NTR>(a.glob, 0, *reinterpret_cast<GlobalScratch*>(s_dyn_gs));
         if (threadIdx.x == 0) a.glob.ts[0].ticket = 0u;
       }
     }
@@ -1879,15 +1891,15 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(ResampleAr
   const int Np = d.Np;
   const int chunk = ((Np + C - 1) / C + 7) & ~7;
   const int lo = min(rank * chunk, Np), hi = min(lo + chunk, Np);
-  const bool single = (hi - lo) <= SUB;  // the whole chunk stays in registers
+  const bool single = LEAN || (hi - lo) <= SUB;  // the whole chunk stays in registers
   // In a filter step: the track's step index (read before the cluster
   // barrier that precedes every ticket below, since the track's global step,
   // run by the last ticket holder, advances it), which picks the log-weight
   // buffer and the resampling uniform.
   const TrackParams* __restrict__ Pt = a.glob.trk ? a.glob.trk + d.track : nullptr;
-  const int kk = a.u_arr ? 0 : a.glob.ts[d.track].k;
+  const int kk = (!LEAN && a.u_arr) ? 0 : a.glob.ts[d.track].k;
   const float* __restrict__ lw = ((a.lw1 && (kk & 1)) ? a.lw1 : a.lw) + d.base;
-  const bool ess_rule = Pt && Pt->resample_rule == 1;
+  const bool ess_rule = !LEAN && Pt && Pt->resample_rule == 1;
   const bool vec = ((d.base & 3) == 0);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
@@ -1926,10 +1938,10 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(ResampleAr
   // (set by the previous step's global step, complete before the propagate
   // kernel ran), so it is drawn before waiting for the propagate kernel.
   uint32_t u = 0;
-  if (!a.u_arr)
+  if (LEAN || !a.u_arr)
     u = philox(Pt->key0, Pt->key1, make_uint4((uint32_t)d.g, 0u, (uint32_t)kk, Pt->tag | (ST_RESAMPLE << 4))).x;
   grid_dep_wait();
-  if (a.u_arr) u = a.u_arr[grp];
+  if (!LEAN && a.u_arr) u = a.u_arr[grp];
   if (a.tile_ctr && blockIdx.x == 0 && threadIdx.x == 0) *a.tile_ctr = 0;  // for the next propagate launch
   // A propagate launch that timed out or met an out-of-range ancestor left
   // weights that mean nothing: resample nothing.  Only the kernels before
@@ -2057,7 +2069,7 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(ResampleAr
     }
     __syncthreads();
     if (s_last && a.fuse_global == 1) {
-      global_step<NTR>(a.glob, d.track, *reinterpret_cast<GlobalScratch*>(s_dyn_rs));
+      global_step_call<NTR>(a.glob, d.track, *reinterpret_cast<GlobalScratch*>(s_dyn_rs));
       if (threadIdx.x == 0) a.glob.ts[d.track].ticket = 0u;
       __syncthreads();  // the scratch is the prefix array below
     }
@@ -2070,7 +2082,7 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(ResampleAr
     // no finite weight, or Alg. 1's test keeps the particles: identity
     for (int i = lo + threadIdx.x; i < hi; i += NTR) {
       anc[i] = (uint32_t)(obase + i);
-      if (a.q_out) a.q_out[d.base + i] = 0ull;
+      if (!LEAN && a.q_out) a.q_out[d.base + i] = 0ull;
     }
   } else {
     // the threshold constants: one thread computes them for the CTA, with
@@ -2093,7 +2105,7 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(ResampleAr
 #pragma unroll
         for (int r = 0; r < RS_ITEMS; ++r) qv[r] = quantize(v[r], M, a.qc);
       }
-      if (a.q_out)
+      if (!LEAN && a.q_out)
 #pragma unroll
         for (int r = 0; r < RS_ITEMS; ++r)
           if (i0 + r < n) a.q_out[d.base + sub + i0 + r] = qv[r];
@@ -2290,23 +2302,28 @@ cudaError_t launch_propagate(const K1Args& a, int R, int grid, bool pdl, cudaStr
   }
 }
 
-template <int NTR>
+template <int NTR, bool LEAN>
 static cudaError_t launch_resample_t(const ResampleArgs& a, int n_groups, int cluster, bool pdl, cudaStream_t s) {
   constexpr size_t smem = pad8(NTR * RS_ITEMS) * sizeof(unsigned long long) + pad8(2 * NTR * RS_ITEMS) * sizeof(uint32_t);
   static_assert(sizeof(GlobalScratch) <= smem, "the global step's scratch lives in the resampler's shared memory");
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_resample<NTR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_err = cudaFuncSetAttribute(k_resample<NTR, LEAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
   if (attr_err != cudaSuccess) return attr_err;
   const int clusters = n_groups + (a.fuse_global == 2 ? 1 : 0);  // the global step's extra cluster
-  return launch_ex(k_resample<NTR>, dim3((unsigned)(clusters * cluster)), dim3(NTR), cluster, pdl, s, a, smem);
+  return launch_ex(k_resample<NTR, LEAN>, dim3((unsigned)(clusters * cluster)), dim3(NTR), cluster, pdl, s, a, smem);
 }
 
 cudaError_t launch_resample(const ResampleArgs& a, int n_groups, int cluster, bool pdl, cudaStream_t s, int threads) {
-  if (threads == RS_THREADS_SMALL) return launch_resample_t<RS_THREADS_SMALL>(a, n_groups, cluster, pdl, s);
-  return launch_resample_t<RS_THREADS>(a, n_groups, cluster, pdl, s);
+  const long long chunk = (((long long)a.max_np + cluster - 1) / cluster + 7) / 8 * 8;  // as in k_resample
+  if (a.lean && !a.u_arr && !a.q_out && chunk <= (long long)threads * RS_ITEMS) {
+    if (threads == RS_THREADS_SMALL) return launch_resample_t<RS_THREADS_SMALL, true>(a, n_groups, cluster, pdl, s);
+    return launch_resample_t<RS_THREADS, true>(a, n_groups, cluster, pdl, s);
+  }
+  if (threads == RS_THREADS_SMALL) return launch_resample_t<RS_THREADS_SMALL, false>(a, n_groups, cluster, pdl, s);
+  return launch_resample_t<RS_THREADS, false>(a, n_groups, cluster, pdl, s);
 }
 
 cudaError_t launch_global(const GlobalArgs& a, int n_tracks, cudaStream_t s) {
