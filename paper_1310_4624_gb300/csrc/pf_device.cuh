@@ -329,12 +329,16 @@ struct Thresholds {
   // 1e-6 of the larger plus 2 decides the comparison; the result is always
   // that of the exact form.
   __device__ __forceinline__ bool le(unsigned long long S, uint32_t j) const {
-    const float Tf = fmaf((float)j, Af, F1f);
-    const float Sf = __fmaf_rn((float)(uint32_t)(S >> 32), 4294967296.0f, (float)(uint32_t)S);
+    return le(S, __fmaf_rn((float)(uint32_t)(S >> 32), 4294967296.0f, (float)(uint32_t)S), (float)j);
+  }
+  // The same with S's FP32 value Sf (as above) and j's, jf (exact: j < 2^24),
+  // given by the caller.
+  __device__ __forceinline__ bool le(unsigned long long S, float Sf, float jf) const {
+    const float Tf = fmaf(jf, Af, F1f);
     const float m = fmaf(fmaxf(Sf, Tf), 1.0e-6f, 2.0f);
     if (Sf + m < Tf) return true;
     if (Sf > Tf + m) return false;
-    return S <= T(j);
+    return S <= T((uint32_t)jf);
   }
 };
 

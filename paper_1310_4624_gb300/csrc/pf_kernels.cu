@@ -175,56 +175,89 @@ struct GlobalScratch {
   int ring[MAX_G];
 };
 
-// The global step of track t by one CTA of NT threads, each thread owning
-// groups m = threadIdx.x + i NT: what the next step needs (group weights
-// carried as offsets, Eq. 3 / Eq. 4 exchange count, ring order and
-// exchange offsets, step index) plus the history fields that it is about to
-// overwrite.  The estimate, log c, log Z and the rest of the history follow
-// in finish_step, off the critical path.  finalize = 0 prepares step 0.
-// Per-group inputs are read through L2 (written by other CTAs of the same
-// launch when this runs as the resampler's tail).
+// The global step's inputs that the groups of the step do not write: the
+// track's parameters and state, its ring, and the next step's ring and
+// exchange offsets (drawn by the propagate kernel).  They can be read
+// before the groups report.
 template <int NT>
-__device__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
-  constexpr int NW = NT / 32;
-  constexpr int GPT = (MAX_G + NT - 1) / NT;
-  // Every input first (the body then only computes and stores, so no load
-  // waits behind a store that might alias it).
+struct GlobalIn {
+  static constexpr int GPT = (MAX_G + NT - 1) / NT;
+  int G, Np, mode, topo, group_off, hist_off, k, nex_k;
+  long long ghist_off;
+  float cutoff, ex_ratio;
+  double pe_k;
+  int ring_m[GPT], rnext[GPT];
+  uint32_t exo[GPT];
+};
+
+template <int NT>
+__device__ __forceinline__ void global_load(const GlobalArgs& a, int t, GlobalIn<NT>& in) {
   const TrackParams* __restrict__ P = a.trk + t;
-  const int G = P->G, Np = P->Np, mode = P->mode, group_off = P->group_off, hist_off = P->hist_off;
-  const long long ghist_off = P->ghist_off;
-  const float cutoff = P->cutoff, ex_ratio = P->ex_ratio;
+  in.G = P->G;
+  in.Np = P->Np;
+  in.mode = P->mode;
+  in.topo = P->topology;
+  in.group_off = P->group_off;
+  in.hist_off = P->hist_off;
+  in.ghist_off = P->ghist_off;
+  in.cutoff = P->cutoff;
+  in.ex_ratio = P->ex_ratio;
+  const TrackState* __restrict__ T = a.ts + t;
+  in.k = __ldcg(&T->k);
+  in.nex_k = __ldcg(&T->n_ex);
+  in.pe_k = __ldcg(&T->pe_eff);
+  const int k1 = a.finalize ? in.k + 1 : 0;
+  const int* __restrict__ ring = a.ring + in.group_off;
+  const int* __restrict__ rnext_buf = a.ring_next + (size_t)(k1 & 1) * a.ring_stride + in.group_off;
+  const uint32_t* __restrict__ exo_buf = a.exo_next + (size_t)(k1 & 1) * a.ring_stride + in.group_off;
+#pragma unroll
+  for (int i = 0; i < GlobalIn<NT>::GPT; ++i) {
+    const int m = threadIdx.x + i * NT;
+    in.ring_m[i] = m;
+    in.rnext[i] = m;
+    in.exo[i] = 0;
+    if (m < in.G) {
+      in.ring_m[i] = __ldcg(&ring[m]);
+      in.rnext[i] = __ldcg(&rnext_buf[m]);
+      in.exo[i] = __ldcg(&exo_buf[m]);
+    }
+  }
+}
+
+template <int NT>
+__device__ __forceinline__ void global_step_core(const GlobalArgs& a, int t, GlobalScratch& sc,
+                                                 const GlobalIn<NT>& in) {
+  constexpr int NW = NT / 32;
+  constexpr int GPT = GlobalIn<NT>::GPT;
+  const int G = in.G, Np = in.Np, mode = in.mode, group_off = in.group_off, hist_off = in.hist_off;
+  const long long ghist_off = in.ghist_off;
+  const float cutoff = in.cutoff, ex_ratio = in.ex_ratio;
   TrackState* __restrict__ T = a.ts + t;
-  const int k = __ldcg(&T->k);
-  const int nex_k = __ldcg(&T->n_ex);
-  const double pe_k = __ldcg(&T->pe_eff);
+  const int k = in.k, nex_k = in.nex_k;
+  const double pe_k = in.pe_k;
   GroupState* __restrict__ gs = a.gs + group_off;
   int* __restrict__ ring = a.ring + group_off;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwa = G > NT ? NW : (G + 31) / 32;  // warps holding groups
   const int k1 = a.finalize ? k + 1 : 0;
-  const int* __restrict__ rnext_buf = a.ring_next + (size_t)(k1 & 1) * a.ring_stride + group_off;
-  const uint32_t* __restrict__ exo_buf = a.exo_next + (size_t)(k1 & 1) * a.ring_stride + group_off;
+  const int* ring_m = in.ring_m;
+  const int* rnext = in.rnext;
+  const uint32_t* exo = in.exo;
 
+  // the groups' results of the step
   unsigned long long Q[GPT];
   float Mg[GPT], lam[GPT];
-  int ring_m[GPT], rnext[GPT], cy[GPT];
-  uint32_t exo[GPT];
+  int cy[GPT];
 #pragma unroll
   for (int i = 0; i < GPT; ++i) {
     const int m = threadIdx.x + i * NT;
     Q[i] = 0;
     Mg[i] = 0.0f;
-    ring_m[i] = m;
-    rnext[i] = m;
-    exo[i] = 0;
     cy[i] = 0;
     if (m < G) {
       Q[i] = __ldcg(&gs[m].Q);
       Mg[i] = __ldcg(&gs[m].M);
       if (a.finalize) cy[i] = __ldcg(&gs[m].carry_next);
-      ring_m[i] = __ldcg(&ring[m]);
-      rnext[i] = __ldcg(&rnext_buf[m]);
-      exo[i] = __ldcg(&exo_buf[m]);
     }
   }
 
@@ -291,7 +324,7 @@ __device__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
   }
   // ring order of step k1 (Sec. IV-B), drawn one step ahead; for the
   // hypercube each group's partner
-  const int topo = P->topology;
+  const int topo = in.topo;
   const bool shuffled = k1 >= 1 && G > 1 && (mode == MODE_ARNA || topo == TOPO_HYPERCUBE);
 #pragma unroll
   for (int i = 0; i < GPT; ++i) {
@@ -381,6 +414,23 @@ __device__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
     if (!a.finalize) T->fin_k = -1;
     if (!a.keep_k) T->k = k1;
   }
+}
+
+// The global step of track t by one CTA of NT threads, each thread owning
+// groups m = threadIdx.x + i NT: what the next step needs (group weights
+// carried as offsets, Eq. 3 / Eq. 4 exchange count, ring order and
+// exchange offsets, step index) plus the history fields that it is about to
+// overwrite.  The estimate, log c, log Z and the rest of the history follow
+// in finish_step, off the critical path.  finalize = 0 prepares step 0.
+// Per-group inputs are read through L2 (written by other CTAs of the same
+// launch when this runs as the resampler's tail).  Every input is read
+// before the first store (so no load waits behind a store that might alias
+// it).
+template <int NT>
+__device__ __forceinline__ void global_step(const GlobalArgs& a, int t, GlobalScratch& sc) {
+  GlobalIn<NT> in;
+  global_load<NT>(a, t, in);
+  global_step_core<NT>(a, t, sc, in);
 }
 
 // global_step out of line, for the resampler (it runs on one CTA of the
@@ -1322,19 +1372,28 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
 }
 
 // ==================================================================== resample
-// Number of outputs j in [0, Np) with (j 2^32 + u) Q < S Np 2^32: an FP32
-// estimate, then exact 128-bit corrections (the estimate is within 1).
-// #{j in [0, Np) : T_j < S}: an FP32 estimate, then exact corrections.
+// #{j in [0, Np) : T_j < S}, the number of outputs that go to items whose
+// boundary is below S: an FP32 estimate (within one of the count), then
+// corrections by Thresholds::le, whose result is that of the exact form.
 __device__ __forceinline__ int count_below(const Thresholds& th, unsigned long long S, float inv_Q, int Np,
                                            uint32_t u, DevState* ds) {
   if (S == 0) return 0;
-  const float est = u64_to_float_approx(S) * inv_Q * (float)Np - (float)(u >> 8) * 5.9604645e-8f;
-  int c = (int)ceilf(fminf(fmaxf(est, 0.0f), (float)Np));
+  // Np <= 2^20: every candidate count is an integer held exactly in FP32
+  const float Sf = u64_to_float_approx(S);
+  const float Npf = (float)Np;
+  const float est = Sf * inv_Q * Npf - (float)(u >> 8) * 5.9604645e-8f;
+  float cf = ceilf(fminf(fmaxf(est, 0.0f), Npf));
   int it = 0;
-  while (c < Np && th.T((uint32_t)c) < S && it < 64) { ++c; ++it; }
-  while (c > 0 && th.T((uint32_t)(c - 1)) >= S && it < 64) { --c; ++it; }
-  if (it >= 64) set_error(ds, ERR_INVARIANT, 3u, (uint32_t)S, (uint32_t)c);
-  return c;
+  while (cf < Npf && !th.le(S, Sf, cf) && it < 64) {
+    cf += 1.0f;
+    ++it;
+  }
+  while (cf > 0.0f && th.le(S, Sf, cf - 1.0f) && it < 64) {
+    cf -= 1.0f;
+    ++it;
+  }
+  if (it >= 64) set_error(ds, ERR_INVARIANT, 3u, (uint32_t)S, (uint32_t)cf);
+  return (int)cf;
 }
 
 // Shared-memory accesses through 32-bit shared-window addresses (the merge
@@ -1353,6 +1412,17 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
 __device__ __forceinline__ void sts_u32(uint32_t addr, uint32_t v) {
   asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
+// A store to the shared memory of CTA `rank` of the cluster, at the
+// address `addr` has in this CTA's window.
+__device__ __forceinline__ void sts_cluster_u32(uint32_t addr, uint32_t rank, uint32_t v) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(addr), "r"(rank));
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(remote), "r"(v) : "memory");
+}
+// The two halves of a cluster barrier: stores before the arrival are
+// visible to every CTA of the cluster after its wait.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire;" ::: "memory"); }
 // X_i = s_incl[pad8(i)] at shared address base
 __device__ __forceinline__ unsigned long long incl_at(uint32_t base, int i) {
   return lds_u64(base + 8u * (uint32_t)pad8(i));
@@ -1829,6 +1899,47 @@ __device__ __noinline__ void fused_task_b(const K1Args& a, int k, int ci, unsign
   merge_windows<K1_THREADS>(s_incl, s_out, s_th, s_jlo, s_jhi, n, obase + lo, anc);
 }
 
+// Wait (bounded, 0.2 s) until the G groups of a track have taken their
+// tickets; 0 after a failed propagate launch (the groups skip their work and
+// their tickets) or a timeout.
+__device__ __forceinline__ int wait_tickets(const unsigned* tk, unsigned G, DevState* ds) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(tk) : "memory");
+  const unsigned long long t0 = global_ns();
+  while (v < G) {
+    if ((*reinterpret_cast<volatile const unsigned int*>(&ds->err) & (ERR_TIMEOUT | ERR_INDEX)) != 0u) return 0;
+    __nanosleep(64);
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(tk) : "memory");
+    if (global_ns() - t0 > 200000000ull) {
+      set_error(ds, ERR_TIMEOUT, 11u, v, G);
+      return 0;
+    }
+  }
+  return 1;
+}
+
+// The global step of a one-track resampling launch, by one CTA, once the
+// track's G groups have taken their tickets (a failed propagate launch or a
+// timeout ends the wait without a global step).  What the groups do not
+// write is read before the wait.
+template <int NT>
+__device__ __noinline__ void global_step_when_reported(const GlobalArgs& g, DevState* ds, GlobalScratch& sc) {
+  __shared__ int s_ok;
+  GlobalIn<NT> in;
+  global_load<NT>(g, 0, in);
+  if (threadIdx.x == 0) s_ok = wait_tickets(&g.ts[0].ticket, (unsigned)in.G, ds);
+  __syncthreads();
+  if (s_ok) {
+    global_step_core<NT>(g, 0, sc, in);
+    if (threadIdx.x == 0) g.ts[0].ticket = 0u;
+  }
+}
+
+// The lean resampler's mark array follows the global step's scratch in
+// dynamic shared memory (rank 0 may run the global step while the other
+// CTAs of its cluster mark its output positions).
+constexpr size_t RS_MARK_OFF = (sizeof(GlobalScratch) + 15) / 16 * 16;
+
 // Resampler: one thread-block cluster per group, each CTA a contiguous chunk
 // of the group's slots (a multiple of 8), processed in sub-chunks of SUB
 // items; thread t owns the RS_ITEMS consecutive items [t*RS_ITEMS, ...).
@@ -1839,7 +1950,7 @@ __device__ __noinline__ void fused_task_b(const K1Args& a, int k, int ci, unsign
 // compiled out (a smaller kernel: the resampler is latency-bound, and
 // instruction fetch leads its stalls).
 template <int NTR, bool LEAN>
-__global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(ResampleArgs a) {
+__global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(const __grid_constant__ ResampleArgs a) {
   constexpr int SUB = NTR * RS_ITEMS;  // items per sub-chunk
   constexpr int SUB_PAD = pad8(SUB);
   constexpr int WIN = 2 * SUB;         // merge window: items and outputs merged at once
@@ -1848,42 +1959,12 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(ResampleAr
   const int rank = (int)cl.block_rank();
   const int grp = blockIdx.x / C;
   if (a.fuse_global == 2 && grp >= a.n_groups) {
-    // the extra cluster of a one-track step: its first CTA waits (bounded)
-    // until every group has reported its statistics, then runs the track's
-    // global step; nothing waits on it within the launch
+    // the extra cluster of a one-track step: its first CTA runs the
+    // track's global step once every group has reported; nothing waits on
+    // it within the launch
     extern __shared__ unsigned long long s_dyn_gs[];
-    __shared__ int s_ok;
     grid_dep_wait();
-    if (rank == 0) {
-      if (threadIdx.x == 0) {
-        const unsigned* tk = &a.glob.ts[0].ticket;
-        const unsigned G = (unsigned)a.glob.trk[0].G;
-        unsigned v;
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(tk) : "memory");
-        const unsigned long long t0 = global_ns();
-        int ok = 1;
-        while (v < G) {
-          // groups skip their work (and their ticket) after a failed propagate launch
-          if ((*reinterpret_cast<volatile const unsigned int*>(&a.ds->err) & (ERR_TIMEOUT | ERR_INDEX)) != 0u) {
-            ok = 0;
-            break;
-          }
-          __nanosleep(256);
-          asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(tk) : "memory");
-          if (global_ns() - t0 > 200000000ull) {
-            set_error(a.ds, ERR_TIMEOUT, 11u, v, G);
-            ok = 0;
-            break;
-          }
-        }
-        s_ok = ok;
-      }
-      __syncthreads();
-      if (s_ok) {
-        global_step_call<NTR>(a.glob, 0, *reinterpret_cast<GlobalScratch*>(s_dyn_gs));
-        if (threadIdx.x == 0) a.glob.ts[0].ticket = 0u;
-      }
-    }
+    if (rank == 0) global_step_when_reported<NTR>(a.glob, a.ds, *reinterpret_cast<GlobalScratch*>(s_dyn_gs));
     grid_dep_launch();
     return;
   }
@@ -1915,9 +1996,12 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(ResampleAr
   // ancestors staged for coalesced stores.  Both are indexed through pad8
   // (one spare element per 8): a thread's 8 consecutive items then start 9
   // elements after its neighbour's, spreading a warp over the banks.
-  extern __shared__ unsigned long long s_dyn_rs[];
+  extern __shared__ __align__(16) unsigned long long s_dyn_rs[];
   unsigned long long* s_incl = s_dyn_rs;
   uint32_t* s_out = reinterpret_cast<uint32_t*>(s_dyn_rs + SUB_PAD);
+  // LEAN: one entry per output position of this CTA (NTR RS_ITEMS), 0 or
+  // the 1-based item whose outputs start there
+  uint32_t* s_mark = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(s_dyn_rs) + RS_MARK_OFF);
 
   float v[RS_ITEMS];
   auto load_sub = [&](int sub) {
@@ -1937,6 +2021,11 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(ResampleAr
   // step).  In a filter step it depends only on the seed and the step index
   // (set by the previous step's global step, complete before the propagate
   // kernel ran), so it is drawn before waiting for the propagate kernel.
+  if constexpr (LEAN) {
+    uint4* m4 = reinterpret_cast<uint4*>(s_mark) + 2 * threadIdx.x;
+    m4[0] = make_uint4(0u, 0u, 0u, 0u);  // before the cluster barrier that precedes any marking
+    m4[1] = make_uint4(0u, 0u, 0u, 0u);
+  }
   uint32_t u = 0;
   if (LEAN || !a.u_arr)
     u = philox(Pt->key0, Pt->key1, make_uint4((uint32_t)d.g, 0u, (uint32_t)kk, Pt->tag | (ST_RESAMPLE << 4))).x;
@@ -1973,7 +2062,7 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(ResampleAr
   // this CTA's total weight code, then the cluster prefix and group total;
   // under Alg. 1's test also the sums of c = q >> 20 and c^2
   unsigned long long qs = 0, e1 = 0, e2 = 0;
-  unsigned long long qv[RS_ITEMS];
+  unsigned long long qv[RS_ITEMS] = {0, 0, 0, 0, 0, 0, 0, 0};  // 0 on a CTA past the group's end
   for (int sub = lo; sub < hi; sub += SUB) {
     if (!single) load_sub(sub);
 #pragma unroll
@@ -2011,9 +2100,11 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(ResampleAr
   // Alg. 1: resample only when N_eff < N_thresh (every CTA of the cluster
   // decides alike from the same sums)
   const bool resample = !ess_rule || Q == 0 || ess_below(E1, E2, (uint32_t)Np, Pt->ess_t);
-  // no more reads of the other CTAs' shared memory: arrive now, wait (so
-  // that this CTA's shared memory outlives their reads) only at the end
-  auto cl_token = cl.barrier_arrive();
+  // No more reads of the other CTAs' shared memory: arrive now, wait (so
+  // that this CTA's shared memory outlives their reads) only at the end.
+  // LEAN: the CTAs write each other's mark arrays below, and a whole
+  // cluster barrier follows.
+  if constexpr (!LEAN) cluster_arrive();
 
   // group estimate and ESS from the propagate tiles' partial sums (rank 0),
   // each tile's sums rescaled from its own maximum to the group maximum
@@ -2096,6 +2187,49 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(ResampleAr
     __syncthreads();
     const Thresholds th = s_th;
     const float inv_Q = 1.0f / u64_to_float_approx(Q);
+    if constexpr (LEAN) {
+      // Alg. 3 step 7 by marking: item i takes the outputs O_i .. O_{i+1} - 1,
+      // O_i = #{j : T_j < S_i} with S_i the sum of the codes before it.  An
+      // item with outputs writes i + 1 at position O_i, and at the first
+      // position of every CTA whose range starts inside its own, into the
+      // mark array of the CTA that owns the position (outputs are split over
+      // the cluster like items).  A running maximum over each CTA's
+      // positions then gives every output its item, with the same work for
+      // every CTA however the weight is spread.
+      const int i0 = (int)threadIdx.x * RS_ITEMS;
+      unsigned long long tsum = 0;
+#pragma unroll
+      for (int r = 0; r < RS_ITEMS; ++r) tsum += qv[r];
+      unsigned long long x = tsum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+      }
+      if (lane == 31) s_w[warp] = x;
+      __syncthreads();
+      unsigned long long wpre = 0;
+#pragma unroll
+      for (int w = 0; w < NTR / 32; ++w)
+        if (w < warp) wpre += s_w[w];
+      unsigned long long S = Sb + wpre + (x - tsum);  // codes before the thread's first item
+      const uint32_t mark_addr = (uint32_t)__cvta_generic_to_shared(s_mark);
+      int c = count_below(th, S, inv_Q, Np, u, a.ds);
+#pragma unroll
+      for (int r = 0; r < RS_ITEMS; ++r) {
+        if (qv[r] == 0ull) continue;
+        S += qv[r];
+        const int c1 = count_below(th, S, inv_Q, Np, u, a.ds);
+        if (c1 > c) {
+          const uint32_t item = (uint32_t)(lo + i0 + r) + 1u;
+          int own = 0;  // c / chunk (C is at most 16)
+          for (int b = 1; b < C; ++b) own += c >= b * chunk ? 1 : 0;
+          sts_cluster_u32(mark_addr + 4u * (uint32_t)(c - own * chunk), (uint32_t)own, item);
+          for (int b = own + 1; b * chunk < c1; ++b) sts_cluster_u32(mark_addr, (uint32_t)b, item);
+        }
+        c = c1;
+      }
+    } else {
     unsigned long long carry = Sb;
     for (int sub = lo; sub < hi; sub += SUB) {
       const int n = min(SUB, hi - sub);
@@ -2146,11 +2280,53 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(ResampleAr
       carry += tot;
       __syncthreads();
     }
+    }
+  }
+
+  if constexpr (LEAN) {
+    cl.sync();  // every mark has landed, and the reads of s_pub_q are done
+    if (Q != 0 && resample) {
+      // running maximum over this CTA's positions p0 + 0 .. n_out - 1 (its
+      // first position always holds a mark)
+      const int p0 = rank * chunk, n_out = min(chunk, Np - p0);
+      const int i0 = (int)threadIdx.x * RS_ITEMS;
+      const uint4 m0 = reinterpret_cast<const uint4*>(s_mark)[2 * threadIdx.x];
+      const uint4 m1 = reinterpret_cast<const uint4*>(s_mark)[2 * threadIdx.x + 1];
+      uint32_t m[RS_ITEMS] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+      for (int r = 1; r < RS_ITEMS; ++r) m[r] = max(m[r], m[r - 1]);
+      uint32_t x = m[RS_ITEMS - 1];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x = max(x, t);
+      }
+      uint32_t pre = __shfl_up_sync(0xffffffffu, x, 1);
+      if (lane == 0) pre = 0u;
+      if (lane == 31) s_w[warp] = x;
+      __syncthreads();
+#pragma unroll
+      for (int w = 0; w < NTR / 32; ++w)
+        if (w < warp) pre = max(pre, (uint32_t)s_w[w]);
+      if (i0 < n_out && max(pre, m[0]) == 0u) set_error(a.ds, ERR_INVARIANT, 12u, (uint32_t)grp, (uint32_t)(p0 + i0));
+      uint32_t o[RS_ITEMS];
+#pragma unroll
+      for (int r = 0; r < RS_ITEMS; ++r) o[r] = (uint32_t)(obase + max(max(m[r], pre), 1u) - 1u);
+      uint32_t* out = anc + p0 + i0;
+      if (i0 + RS_ITEMS <= n_out && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+        reinterpret_cast<uint4*>(out)[0] = make_uint4(o[0], o[1], o[2], o[3]);
+        reinterpret_cast<uint4*>(out)[1] = make_uint4(o[4], o[5], o[6], o[7]);
+      } else {
+#pragma unroll
+        for (int r = 0; r < RS_ITEMS; ++r)
+          if (i0 + r < n_out) out[r] = o[r];
+      }
+    }
   }
 
   // The next kernel may start once every CTA is past its main work.
   grid_dep_launch();
-  cl.barrier_wait(std::move(cl_token));
+  if constexpr (!LEAN) cluster_wait();
 }
 
 
@@ -2304,7 +2480,9 @@ cudaError_t launch_propagate(const K1Args& a, int R, int grid, bool pdl, cudaStr
 
 template <int NTR, bool LEAN>
 static cudaError_t launch_resample_t(const ResampleArgs& a, int n_groups, int cluster, bool pdl, cudaStream_t s) {
-  constexpr size_t smem = pad8(NTR * RS_ITEMS) * sizeof(unsigned long long) + pad8(2 * NTR * RS_ITEMS) * sizeof(uint32_t);
+  constexpr size_t smem = LEAN ? RS_MARK_OFF + NTR * RS_ITEMS * sizeof(uint32_t)
+                              : pad8(NTR * RS_ITEMS) * sizeof(unsigned long long) +
+                                    pad8(2 * NTR * RS_ITEMS) * sizeof(uint32_t);
   static_assert(sizeof(GlobalScratch) <= smem, "the global step's scratch lives in the resampler's shared memory");
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
