@@ -117,6 +117,10 @@ struct GroupState {
   unsigned long long Q; // group total weight code (step k)
   float xs[5];          // group estimate x^^m (step k)
   float ess;            // group ESS (step k)
+  // group max log-weight of step k, by step parity: the largest tile
+  // maximum as an order-preserving key (float_key ^ 2^31, 0 = none yet),
+  // raised by the propagate tiles, cleared by the resampler one step ahead
+  uint32_t mkey[2];
   // fused step: the resampling thresholds of step k (Thresholds below)
   unsigned long long th_A, th_F1, th_M;
   uint32_t th_B, th_F0, th_Np;

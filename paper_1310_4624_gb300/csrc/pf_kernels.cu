@@ -1241,6 +1241,13 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
         }
       }
       a.tile_part[(long long)tile * 8 + threadIdx.x] = r;
+    } else if (!FUSED && threadIdx.x == 8) {
+      // raise the group maximum of the step (the resampler's quantisation scale)
+      int kt = INT_MIN;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) kt = max(kt, s_key[w]);
+      if (kt != INT_MIN)  // (the group reloaded: no register held across the tile for it)
+        atomicMax(&a.grp[P.group_off + __ldg(&a.tiles[tile].y)].mkey[k & 1], (uint32_t)kt ^ 0x80000000u);
     }
     // No barrier here: every shared buffer the next tile writes first (s_box,
     // then s_roi by TMA, s_red / s_key) is written only after that tile's
@@ -2042,10 +2049,11 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(const __gr
   float M = -INFINITY;
   if (single) load_sub(lo);  // the CTA's items, for the quantisation below
   if (a.tile_part != nullptr) {
-    float m = -INFINITY;
-    for (int t = threadIdx.x; t < d.tile_count; t += NTR)
-      m = fmaxf(m, a.tile_part[(long long)(d.tile_begin + t) * 8]);
-    M = block_max<NTR>(m, s_f);
+    // the largest tile maximum, raised by the propagate tiles (NaN and
+    // tiles with no finite weight never raise it)
+    const uint32_t mk = __ldcg(&a.gs[grp].mkey[kk & 1]);
+    M = mk == 0u ? -INFINITY : key_float((int)(mk ^ 0x80000000u));
+    if (rank == 0 && threadIdx.x == 0) a.gs[grp].mkey[(kk + 1) & 1] = 0u;  // for the next step's tiles
   } else {
     float m = -INFINITY;
     for (int sub = lo; sub < hi; sub += SUB) {
@@ -2106,10 +2114,43 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(const __gr
   // cluster barrier follows.
   if constexpr (!LEAN) cluster_arrive();
 
-  // group estimate and ESS from the propagate tiles' partial sums (rank 0),
-  // each tile's sums rescaled from its own maximum to the group maximum
+  // Rank 0 reports the group's weight (M, Q) and resampling decision, which
+  // is all the track's global step reads, and takes the group's ticket; the
+  // group estimate and ESS follow.  A ticket per track counts the groups
+  // that have reported: the track's global step runs once all G have, on
+  // the extra cluster of a one-track launch, else on the last taker (its
+  // rank-0 CTA, before its own ancestors, so that the global step overlaps
+  // the other groups' work).  The reporting thread fences before its
+  // ticket; the last taker fences before the reads.  The ancestors are not
+  // among the global step's inputs.
   if (rank == 0) {
     GroupState& G = a.gs[grp];
+    if (threadIdx.x == 0) {
+      G.M = M;
+      G.Q = Q;
+      G.carry_next = resample ? 0 : 1;
+      if (a.fuse_global == 2) {
+        __threadfence();
+        atomicAdd(&a.glob.ts[d.track].ticket, 1u);
+      }
+    }
+    if (a.fuse_global == 1) {
+      __shared__ int s_last;
+      if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&a.glob.ts[d.track].ticket, 1u);
+        s_last = (prev + 1u == (unsigned)a.glob.trk[d.track].G) ? 1 : 0;
+        __threadfence();
+      }
+      __syncthreads();
+      if (s_last) {
+        global_step_call<NTR>(a.glob, d.track, *reinterpret_cast<GlobalScratch*>(s_dyn_rs));
+        if (threadIdx.x == 0) a.glob.ts[d.track].ticket = 0u;
+        __syncthreads();  // the scratch is the prefix array below
+      }
+    }
+    // group estimate and ESS from the propagate tiles' partial sums, each
+    // tile's sums rescaled from its own maximum to the group maximum
     if (a.tile_part != nullptr) {
       float acc[7] = {0, 0, 0, 0, 0, 0, 0};
       if (Q != 0) {
@@ -2138,34 +2179,7 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(const __gr
         G.ess = ok ? t7[0] * t7[0] / t7[6] : 0.0f;
       }
     }
-    if (threadIdx.x == 0) {
-      G.M = M;
-      G.Q = Q;
-      G.carry_next = resample ? 0 : 1;
-    }
   }
-  // The last group of a track to report its statistics runs the track's
-  // global step (its rank-0 CTA), before its own ancestor search, so the
-  // global step overlaps the other groups' searches: a ticket per track
-  // counts groups.  The writer of the group's statistics (thread 0 of rank
-  // 0) fences before taking its ticket; the last taker fences before the
-  // reads.  The ancestors are not among the global step's inputs.
-  if (a.fuse_global && rank == 0) {
-    __shared__ int s_last;
-    if (threadIdx.x == 0) {
-      __threadfence();
-      const unsigned prev = atomicAdd(&a.glob.ts[d.track].ticket, 1u);
-      s_last = (prev + 1u == (unsigned)a.glob.trk[d.track].G) ? 1 : 0;
-      __threadfence();
-    }
-    __syncthreads();
-    if (s_last && a.fuse_global == 1) {
-      global_step_call<NTR>(a.glob, d.track, *reinterpret_cast<GlobalScratch*>(s_dyn_rs));
-      if (threadIdx.x == 0) a.glob.ts[d.track].ticket = 0u;
-      __syncthreads();  // the scratch is the prefix array below
-    }
-  }
-
 
   const unsigned long long obase = a.local_idx ? 0ull : (unsigned long long)(d.g) * (unsigned long long)Np;
   uint32_t* __restrict__ anc = a.anc + (kk & 1) * a.anc_stride + d.base;
