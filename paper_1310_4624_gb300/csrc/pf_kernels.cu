@@ -1930,7 +1930,7 @@ __device__ __forceinline__ int wait_tickets(const unsigned* tk, unsigned G, DevS
 // timeout ends the wait without a global step).  What the groups do not
 // write is read before the wait.
 template <int NT>
-__device__ __noinline__ void global_step_when_reported(const GlobalArgs& g, DevState* ds, GlobalScratch& sc) {
+__device__ __forceinline__ void global_step_when_reported(const GlobalArgs& g, DevState* ds, GlobalScratch& sc) {
   __shared__ int s_ok;
   GlobalIn<NT> in;
   global_load<NT>(g, 0, in);
