@@ -1380,27 +1380,25 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
 
 // ==================================================================== resample
 // #{j in [0, Np) : T_j < S}, the number of outputs that go to items whose
-// boundary is below S: an FP32 estimate (within one of the count), then
-// corrections by Thresholds::le, whose result is that of the exact form.
+// boundary is below S (0 <= S <= Q).  T_j < S exactly when j < x =
+// (S Np - F) / Q, so the count is ceil(x) clamped to [0, Np].  The FP32
+// estimate fma(S, Np / Q, -u 2^-32) is within Np 2^-21 < 1/2 of x (S and Q
+// each converted within 2^-23, the quotient and the product rounded, u
+// truncated to 24 bits, Np <= 2^20), so its ceiling is the count or one
+// off, and one comparison each way (Thresholds::le, whose result is that
+// of the exact form) settles it, without branches.  Both corrections at
+// once would break that bound: reported.
 __device__ __forceinline__ int count_below(const Thresholds& th, unsigned long long S, float inv_Q, int Np,
                                            uint32_t u, DevState* ds) {
-  if (S == 0) return 0;
-  // Np <= 2^20: every candidate count is an integer held exactly in FP32
   const float Sf = u64_to_float_approx(S);
   const float Npf = (float)Np;
-  const float est = Sf * inv_Q * Npf - (float)(u >> 8) * 5.9604645e-8f;
-  float cf = ceilf(fminf(fmaxf(est, 0.0f), Npf));
-  int it = 0;
-  while (cf < Npf && !th.le(S, Sf, cf) && it < 64) {
-    cf += 1.0f;
-    ++it;
-  }
-  while (cf > 0.0f && th.le(S, Sf, cf - 1.0f) && it < 64) {
-    cf -= 1.0f;
-    ++it;
-  }
-  if (it >= 64) set_error(ds, ERR_INVARIANT, 3u, (uint32_t)S, (uint32_t)cf);
-  return (int)cf;
+  const float est = fminf(fmaxf(fmaf(Sf, Npf * inv_Q, -(float)(u >> 8) * 5.9604645e-8f), 0.0f), Npf);
+  const float c0 = __fadd_ru(est, 8388608.0f) - 8388608.0f;  // ceil: est is in [0, 2^20]
+  const bool up = c0 < Npf && !th.le(S, Sf, c0);              // T_c0 < S
+  const bool dn = c0 > 0.0f && th.le(S, Sf, c0 - 1.0f);       // T_(c0-1) >= S
+  if (up && dn) set_error(ds, ERR_INVARIANT, 3u, (uint32_t)S, (uint32_t)c0);
+  const float c = c0 + (up ? 1.0f : 0.0f) - (dn ? 1.0f : 0.0f);
+  return S == 0 ? 0 : __float_as_int(c + 8388608.0f) - 0x4B000000;
 }
 
 // Shared-memory accesses through 32-bit shared-window addresses (the merge
@@ -2084,10 +2082,33 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(const __gr
       }
     }
   }
-  qs = block_sum_u64<NTR>(qs, s_w);
-  if (ess_rule) {
-    e1 = block_sum_u64<NTR>(e1, s_w);
-    e2 = block_sum_u64<NTR>(e2, s_w);
+  // LEAN: one scan of the thread totals gives both the CTA total and each
+  // thread's exclusive prefix within the CTA (kept for the marking below)
+  unsigned long long pre_cta = 0;
+  if constexpr (LEAN) {
+    unsigned long long x = qs;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long t = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += t;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    unsigned long long wpre = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < NTR / 32; ++w) {
+      const unsigned long long y = s_w[w];
+      if (w < warp) wpre += y;
+      tot += y;
+    }
+    pre_cta = wpre + (x - qs);
+    qs = tot;
+  } else {
+    qs = block_sum_u64<NTR>(qs, s_w);
+    if (ess_rule) {
+      e1 = block_sum_u64<NTR>(e1, s_w);
+      e2 = block_sum_u64<NTR>(e2, s_w);
+    }
   }
   if (threadIdx.x == 0) {
     s_pub_q = qs;
@@ -2190,16 +2211,22 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(const __gr
       if (!LEAN && a.q_out) a.q_out[d.base + i] = 0ull;
     }
   } else {
-    // the threshold constants: one thread computes them for the CTA, with
-    // the track's precomputed reciprocal of Np when it has one
-    if (threadIdx.x == 0) {
-      if (a.glob.trk)
-        s_th.init_magic(Q, (uint32_t)Np, u, a.glob.trk[d.track].m_Np);
-      else
-        s_th.init(Q, (uint32_t)Np, u);
+    // the threshold constants, with the track's precomputed reciprocal of Np
+    // when it has one: every thread's own (LEAN), else one thread's for the
+    // CTA
+    Thresholds th;
+    if constexpr (LEAN) {
+      th.init_magic(Q, (uint32_t)Np, u, Pt->m_Np);
+    } else {
+      if (threadIdx.x == 0) {
+        if (a.glob.trk)
+          s_th.init_magic(Q, (uint32_t)Np, u, a.glob.trk[d.track].m_Np);
+        else
+          s_th.init(Q, (uint32_t)Np, u);
+      }
+      __syncthreads();
+      th = s_th;
     }
-    __syncthreads();
-    const Thresholds th = s_th;
     const float inv_Q = 1.0f / u64_to_float_approx(Q);
     if constexpr (LEAN) {
       // Alg. 3 step 7 by marking: item i takes the outputs O_i .. O_{i+1} - 1,
@@ -2211,22 +2238,7 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(const __gr
       // positions then gives every output its item, with the same work for
       // every CTA however the weight is spread.
       const int i0 = (int)threadIdx.x * RS_ITEMS;
-      unsigned long long tsum = 0;
-#pragma unroll
-      for (int r = 0; r < RS_ITEMS; ++r) tsum += qv[r];
-      unsigned long long x = tsum;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long t = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += t;
-      }
-      if (lane == 31) s_w[warp] = x;
-      __syncthreads();
-      unsigned long long wpre = 0;
-#pragma unroll
-      for (int w = 0; w < NTR / 32; ++w)
-        if (w < warp) wpre += s_w[w];
-      unsigned long long S = Sb + wpre + (x - tsum);  // codes before the thread's first item
+      unsigned long long S = Sb + pre_cta;  // codes before the thread's first item
       const uint32_t mark_addr = (uint32_t)__cvta_generic_to_shared(s_mark);
       int c = count_below(th, S, inv_Q, Np, u, a.ds);
 #pragma unroll
