@@ -511,7 +511,7 @@ def adam_fit(pf, wl, fr, truth, iters: int = 200, lr: float = 0.02, fit=(0, 1, 2
         (-lz).backward()
         logt.grad.mul_(mask)
         opt.step()
-        v = float(lz)
+        v = float(lz.detach())
         first = v if first is None else first
         last = v
     dt = time.perf_counter() - t0
