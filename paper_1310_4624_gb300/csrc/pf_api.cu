@@ -643,6 +643,10 @@ pf_status pf_init(const pf_track_config* cfg, int32_t n_tracks, int32_t history,
     P.kappa = (float)std::exp2(-2.0 * (double)P.c_psf);
     P.key0 = (uint32_t)c.seed;
     P.key1 = (uint32_t)(c.seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+      P.rk[2 * r] = P.key0 + (uint32_t)r * 0x9E3779B9u;
+      P.rk[2 * r + 1] = P.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
     P.tag = c.track_id << 8;
     P.record = c.record_ancestors ? 1 : 0;
     P.obs_model = c.obs_model;

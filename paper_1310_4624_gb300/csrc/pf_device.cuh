@@ -63,6 +63,7 @@ struct TrackParams {
   float kappa;      // 2^(-2 c_psf): ratio of successive Gaussian ratios
   unsigned long long m_Np;  // fast-division reciprocal of Np
   uint32_t key0, key1, tag;   // Philox key; tag = track_id << 8
+  uint32_t rk[20];            // Philox round keys key0 + r W0, key1 + r W1 (r = 0..9), interleaved
   int record;
   int obs_model;              // 0: patch residual, 1: frame likelihood ratio
   int resample_rule;          // 0: every step, 1: Alg. 1's N_eff test per group
@@ -188,9 +189,10 @@ __device__ __forceinline__ uint4 philox(uint32_t k0, uint32_t k1, uint4 c) {
   return c;
 }
 
-// Uniform in (0,1): ((w >> 9) + 1/2) 2^-23, exact in FP32.
+// Uniform in (0,1): ((w >> 9) + 1/2) 2^-23 = (w >> 9) 2^-23 + 2^-24, exact
+// in FP32 (an odd multiple of 2^-24 below 1), so one fused multiply-add.
 __device__ __forceinline__ float u01(uint32_t w) {
-  return __fmul_rn(__fadd_rn((float)(w >> 9), 0.5f), 1.1920928955078125e-7f);
+  return __fmaf_rn((float)(w >> 9), 1.1920928955078125e-7f, 5.9604644775390625e-8f);
 }
 
 // Box-Muller pair from two words: rho (cos, sin) of 2 pi u_b.  The angle is

@@ -837,11 +837,15 @@ __device__ __forceinline__ void prefetch_tile(const K1Args& a, int4 td, int k, c
 
 // The five process-noise normals of slot j of group g at step k (Alg. 1
 // step P): Philox stream PROP, calls 0 and 1, Box-Muller on word pairs.
-__device__ __forceinline__ void prop_noise(uint32_t key0, uint32_t key1, uint32_t tag, int j, int g, int k,
-                                           float (&e)[5]) {
-  uint4 w0 = make_uint4(j, g, k, tag | (ST_PROP << 4) | 0u);
-  uint4 w1 = make_uint4(j, g, k, tag | (ST_PROP << 4) | 1u);
-  philox2(key0, key1, w0, w1);
+// RK: the track's precomputed round keys (parameters in the constant bank).
+template <bool RK>
+__device__ __forceinline__ void prop_noise(const TrackParams& P, int j, int g, int k, float (&e)[5]) {
+  uint4 w0 = make_uint4(j, g, k, P.tag | (ST_PROP << 4) | 0u);
+  uint4 w1 = make_uint4(j, g, k, P.tag | (ST_PROP << 4) | 1u);
+  if constexpr (RK)
+    philox2_rk(P.rk, w0, w1);
+  else
+    philox2(P.key0, P.key1, w0, w1);
   float e5;
   box_muller_fast(w0.x, w0.y, e[0], e[1]);
   box_muller_fast(w0.z, w0.w, e[2], e[3]);
@@ -1062,7 +1066,7 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
         if (k > 0) {
           // Alg. 1 step P: nearly constant velocity, unit frame interval
           float e[5];
-          prop_noise(P.key0, P.key1, P.tag, j, g, k, e);
+          prop_noise<SINGLE>(P, j, g, k, e);
           s[q].x = fmaf(P.spos, e[0], s[q].x + s[q].z);
           s[q].y = fmaf(P.spos, e[1], s[q].y + s[q].w);
           s[q].z = fmaf(P.sv, e[2], s[q].z);

@@ -310,6 +310,20 @@ __device__ __forceinline__ void box_muller_fast(uint32_t wa, uint32_t wb, float&
   e1 = -rho * s;
 }
 
+// Two Philox4x32-10 blocks with the round keys given (TrackParams::rk: in
+// the kernel's constant bank they are operands, not computed).
+__device__ __forceinline__ void philox2_rk(const uint32_t (&rk)[20], uint4& c, uint4& d) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x, p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    const unsigned long long q0 = (unsigned long long)0xD2511F53u * d.x, q1 = (unsigned long long)0xCD9E8D57u * d.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk[2 * r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ rk[2 * r + 1],
+                   (uint32_t)p0);
+    d = make_uint4((uint32_t)(q1 >> 32) ^ d.y ^ rk[2 * r], (uint32_t)q1, (uint32_t)(q0 >> 32) ^ d.w ^ rk[2 * r + 1],
+                   (uint32_t)q0);
+  }
+}
+
 // Two Philox4x32-10 blocks of the same key in lockstep (shared key schedule).
 __device__ __forceinline__ void philox2(uint32_t k0, uint32_t k1, uint4& c, uint4& d) {
 #pragma unroll
