@@ -34,7 +34,10 @@
  *   - Device faults detected by the kernels (bad index, bounded wait
  *     exhausted, internal invariant) set a device error word; it is read and
  *     reported (PF_ERR_DEVICE / PF_ERR_TIMEOUT) by the next call that
- *     synchronises.
+ *     synchronises.  A library built with PF_DEBUG also checks the indices
+ *     it takes from data (ring entries, exchange sources, mark positions,
+ *     patch reads) and reports a failed check the same way, with the site,
+ *     the index and the bound in the message.
  */
 #ifndef PFARNA_H
 #define PFARNA_H

@@ -69,7 +69,8 @@ _P = C.c_void_p
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """The library to load: the PF_DEBUG build when PFARNA_DEBUG=1."""
+    return _build.LIB_DEBUG if os.environ.get("PFARNA_DEBUG") == "1" else _build.LIB
 
 
 def load():

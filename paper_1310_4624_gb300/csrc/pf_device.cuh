@@ -47,6 +47,7 @@ constexpr int TOPO_RING = 0, TOPO_NODE_RING = 1, TOPO_HYPERCUBE = 2;
 
 // Device error word bits.
 constexpr uint32_t ERR_INDEX = 1u, ERR_TIMEOUT = 2u, ERR_INVARIANT = 4u, ERR_DRAW = 8u;
+constexpr uint32_t ERR_DEBUG = 16u;  // PF_DEBUG build: an index check failed (info: site, index, bound)
 
 enum : int { MODE_RNA = 0, MODE_ARNA = 1 };
 enum : int { INIT_POINT = 0, INIT_UNIFORM = 1, INIT_SHARING = 2, INIT_USER = 3 };
@@ -355,5 +356,22 @@ __device__ __forceinline__ void set_error(DevState* ds, uint32_t bit, uint32_t a
     ds->err_info[2] = c;
   }
 }
+
+// Index checks of the PF_DEBUG build (the stand-in for a memory checker):
+// an index outside [0, n) sets ERR_DEBUG with the site number, the index and
+// the bound, and is replaced by 0 so that the access stays in bounds.  Never
+// a trap or an assert.  In the normal build the index passes unchanged.
+#ifdef PF_DEBUG
+__device__ __forceinline__ long long dbg_index(DevState* ds, long long i, long long n, uint32_t site) {
+  if (i < 0 || i >= n) {
+    set_error(ds, ERR_DEBUG, site, (uint32_t)i, (uint32_t)n);
+    return 0;
+  }
+  return i;
+}
+#define PF_DBG_INDEX(ds, i, n, site) (::pf::dbg_index((ds), (long long)(i), (long long)(n), (site)))
+#else
+#define PF_DBG_INDEX(ds, i, n, site) (i)
+#endif
 
 }  // namespace pf

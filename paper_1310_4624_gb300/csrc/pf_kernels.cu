@@ -389,7 +389,10 @@ __device__ __forceinline__ void global_step_core(const GlobalArgs& a, int t, Glo
   for (int i = 0; i < GPT; ++i) {
     const int m = threadIdx.x + i * NT;
     if (m < G) {
-      const int rm = sc.ring[m];
+      int rm = sc.ring[m];
+#ifdef PF_DEBUG
+      rm = (int)PF_DBG_INDEX(a.ds, rm, G, 301u);
+#endif
       ring[m] = rm;
       if (topo == TOPO_HYPERCUBE)
         gs[m].pred = rm;  // mutual exchange with the partner
@@ -1009,6 +1012,9 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
     if (nex > 0) {
       o_r = gs[g].exo;
       sg = gs[g].pred;
+#ifdef PF_DEBUG
+      sg = (int)PF_DBG_INDEX(a.ds, sg, P.G, 105u);
+#endif
       o_s = gs[sg].exo;
       off_s = gs[sg].off;
     }
@@ -1050,7 +1056,11 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
         int sj;
         from_pred[q] = keyed ? exchange_keyed(j, Np, nex, P.perm_bits, key_r, key_s, sj)
                              : exchange_from_pred(j, Np, nex, o_r, o_s, P.m_Np, sj);
-        const uint32_t src = (uint32_t)((from_pred[q] ? sg : g) * Np + sj);
+        uint32_t src = (uint32_t)((from_pred[q] ? sg : g) * Np + sj);
+#ifdef PF_DEBUG
+        src = (uint32_t)PF_DBG_INDEX(a.ds, src, n_track, 101u);
+        PF_DBG_INDEX(a.ds, il, n_track, 102u);
+#endif
         const uint32_t par = (k == 0) ? src : anc_t[src];
         if (par >= n_track) {
           set_error(a.ds, ERR_INDEX, 1u, (uint32_t)tile, par);
@@ -1181,18 +1191,36 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
         const bool frame_model = P.obs_model == 1;
         if (staged) {
           const int c = pu[q] - u0, o = (pv[q] - vmin) * ROI_W;
-          const float* base = (c & 1) ? &s_roi[1][o + c - 1] : &s_roi[0][o + c];
-          ss = frame_model ? patch_ss_pairs<R, true>(base, gxI, dy, P.c_psf, P.kappa)
-                           : patch_ss_pairs<R, false>(base, gxI, dy, P.c_psf, P.kappa);
+#ifdef PF_DEBUG
+          // first and last floats the pairwise row loads touch
+          if (o + c - (c & 1) < 0 || o + c - (c & 1) + 2 * R * ROI_W + 2 * R + 1 >= ROI_FLOATS + 4) {
+            set_error(a.ds, ERR_DEBUG, 103u, (uint32_t)(o + c), (uint32_t)(ROI_FLOATS + 4));
+            ss = 0.0f;
+          } else
+#endif
+          {
+            const float* base = (c & 1) ? &s_roi[1][o + c - 1] : &s_roi[0][o + c];
+            ss = frame_model ? patch_ss_pairs<R, true>(base, gxI, dy, P.c_psf, P.kappa)
+                             : patch_ss_pairs<R, false>(base, gxI, dy, P.c_psf, P.kappa);
+          }
         } else if (raw) {
           ss = frame_model
                    ? patch_ss_raw<R, true>(a.zraw, P.W, P.H, P.bg, pu[q] - PAD, pv[q] - PAD, gxI, dy, P.c_psf, P.kappa)
                    : patch_ss_raw<R, false>(a.zraw, P.W, P.H, P.bg, pu[q] - PAD, pv[q] - PAD, gxI, dy, P.c_psf,
                                             P.kappa);
         } else {
-          const float* base = a.ypad + ypad_off + (long long)pv[q] * P.pitch + pu[q];
-          ss = frame_model ? patch_ss<R, true, false>(base, P.pitch, gxI, dy, P.c_psf, P.kappa)
-                           : patch_ss<R, false, false>(base, P.pitch, gxI, dy, P.c_psf, P.kappa);
+#ifdef PF_DEBUG
+          // the patch inside the padded frame (H + 2 PAD rows of P.pitch floats)
+          if (pu[q] < 0 || pu[q] + 2 * R >= P.pitch || pv[q] < 0 || pv[q] + 2 * R >= P.H + 2 * PAD) {
+            set_error(a.ds, ERR_DEBUG, 104u, (uint32_t)pu[q], (uint32_t)pv[q]);
+            ss = 0.0f;
+          } else
+#endif
+          {
+            const float* base = a.ypad + ypad_off + (long long)pv[q] * P.pitch + pu[q];
+            ss = frame_model ? patch_ss<R, true, false>(base, P.pitch, gxI, dy, P.c_psf, P.kappa)
+                             : patch_ss<R, false, false>(base, P.pitch, gxI, dy, P.c_psf, P.kappa);
+          }
         }
         const bool carried = VARIANTS && ((cmask >> (from_pred[q] ? 1 : 0)) & 1);
         lw[q] = fmaf(-ss, P.inv2so2, carried ? lw_t[g * Np + td.z + jj] : (from_pred[q] ? off_s : off_g));
@@ -2244,6 +2272,9 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(const __gr
       const int i0 = (int)threadIdx.x * RS_ITEMS;
       unsigned long long S = Sb + pre_cta;  // codes before the thread's first item
       const uint32_t mark_addr = (uint32_t)__cvta_generic_to_shared(s_mark);
+#ifdef PF_DEBUG
+      PF_DBG_INDEX(a.ds, chunk - 1, NTR * RS_ITEMS, 203u);  // the CTA's outputs fit its mark array
+#endif
       int c = count_below(th, S, inv_Q, Np, u, a.ds);
 #pragma unroll
       for (int r = 0; r < RS_ITEMS; ++r) {
@@ -2254,8 +2285,13 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(const __gr
           const uint32_t item = (uint32_t)(lo + i0 + r) + 1u;
           int own = 0;  // c / chunk (C is at most 16)
           for (int b = 1; b < C; ++b) own += c >= b * chunk ? 1 : 0;
-          sts_cluster_u32(mark_addr + 4u * (uint32_t)(c - own * chunk), (uint32_t)own, item);
-          for (int b = own + 1; b * chunk < c1; ++b) sts_cluster_u32(mark_addr, (uint32_t)b, item);
+          int pos = c - own * chunk;
+#ifdef PF_DEBUG
+          own = (int)PF_DBG_INDEX(a.ds, own, C, 201u);
+          pos = (int)PF_DBG_INDEX(a.ds, pos, chunk, 202u);
+#endif
+          sts_cluster_u32(mark_addr + 4u * (uint32_t)pos, (uint32_t)own, item);
+          for (int b = own + 1; b * chunk < c1 && b < C; ++b) sts_cluster_u32(mark_addr, (uint32_t)b, item);
         }
         c = c1;
       }
