@@ -1298,6 +1298,9 @@ pf_status pf_resample(const float* logw, const uint32_t* u, int32_t G, int32_t N
       (e = cudaMemcpyAsync(gd, h.data(), sizeof(GroupDesc) * G, cudaMemcpyHostToDevice, s)))
     return cuda_fail(nullptr, e, "pf_resample setup");
   ResampleArgs ra{gd, gs, nullptr, logw, nullptr, anc, 0, (unsigned long long*)q, u, 1, make_qc(), ds};
+  ra.n_groups = G;
+  ra.max_np = Np;
+  ra.lean = q ? 0 : 1;  // without codes to store, the lean instance when the chunks fit
   if ((e = launch_resample(ra, G, resample_cluster(Np, true), false, s)) != cudaSuccess)
     return cuda_fail(nullptr, e, "k_resample");
   return PF_OK;

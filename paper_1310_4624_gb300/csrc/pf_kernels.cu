@@ -1981,9 +1981,9 @@ constexpr size_t RS_MARK_OFF = (sizeof(GlobalScratch) + 15) / 16 * 16;
 // of the group's slots (a multiple of 8), processed in sub-chunks of SUB
 // items; thread t owns the RS_ITEMS consecutive items [t*RS_ITEMS, ...).
 
-// LEAN: the common filter step -- every CTA's chunk fits in its registers
-// (one sub-chunk), no group resamples by Alg. 1's test, no weight codes
-// are stored and the uniforms are the step's own -- with the other paths
+// LEAN: every CTA's chunk fits in its registers (one sub-chunk), no group
+// resamples by Alg. 1's test and no weight codes are stored (the common
+// filter step, and pf_resample without codes) -- with the other paths
 // compiled out (a smaller kernel: the resampler is latency-bound, and
 // instruction fetch leads its stalls).
 template <int NTR, bool LEAN>
@@ -2015,7 +2015,7 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(const __gr
   // run by the last ticket holder, advances it), which picks the log-weight
   // buffer and the resampling uniform.
   const TrackParams* __restrict__ Pt = a.glob.trk ? a.glob.trk + d.track : nullptr;
-  const int kk = (!LEAN && a.u_arr) ? 0 : a.glob.ts[d.track].k;
+  const int kk = a.u_arr ? 0 : a.glob.ts[d.track].k;
   const float* __restrict__ lw = ((a.lw1 && (kk & 1)) ? a.lw1 : a.lw) + d.base;
   const bool ess_rule = !LEAN && Pt && Pt->resample_rule == 1;
   const bool vec = ((d.base & 3) == 0);
@@ -2064,10 +2064,10 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(const __gr
     m4[1] = make_uint4(0u, 0u, 0u, 0u);
   }
   uint32_t u = 0;
-  if (LEAN || !a.u_arr)
+  if (!a.u_arr)
     u = philox(Pt->key0, Pt->key1, make_uint4((uint32_t)d.g, 0u, (uint32_t)kk, Pt->tag | (ST_RESAMPLE << 4))).x;
   grid_dep_wait();
-  if (!LEAN && a.u_arr) u = a.u_arr[grp];
+  if (a.u_arr) u = a.u_arr[grp];
   if (a.tile_ctr && blockIdx.x == 0 && threadIdx.x == 0) *a.tile_ctr = 0;  // for the next propagate launch
   // A propagate launch that timed out or met an out-of-range ancestor left
   // weights that mean nothing: resample nothing.  Only the kernels before
@@ -2248,7 +2248,10 @@ __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(const __gr
     // CTA
     Thresholds th;
     if constexpr (LEAN) {
-      th.init_magic(Q, (uint32_t)Np, u, Pt->m_Np);
+      if (Pt)
+        th.init_magic(Q, (uint32_t)Np, u, Pt->m_Np);
+      else
+        th.init(Q, (uint32_t)Np, u);
     } else {
       if (threadIdx.x == 0) {
         if (a.glob.trk)
@@ -2562,7 +2565,7 @@ static cudaError_t launch_resample_t(const ResampleArgs& a, int n_groups, int cl
 
 cudaError_t launch_resample(const ResampleArgs& a, int n_groups, int cluster, bool pdl, cudaStream_t s, int threads) {
   const long long chunk = (((long long)a.max_np + cluster - 1) / cluster + 7) / 8 * 8;  // as in k_resample
-  if (a.lean && !a.u_arr && !a.q_out && chunk <= (long long)threads * RS_ITEMS) {
+  if (a.lean && !a.q_out && chunk <= (long long)threads * RS_ITEMS) {
     if (threads == RS_THREADS_SMALL) return launch_resample_t<RS_THREADS_SMALL, true>(a, n_groups, cluster, pdl, s);
     return launch_resample_t<RS_THREADS, true>(a, n_groups, cluster, pdl, s);
   }

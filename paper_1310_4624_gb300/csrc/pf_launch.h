@@ -152,8 +152,9 @@ struct ResampleArgs {
                                // 2 (one track): an extra cluster after the groups' runs it instead,
                                // once every group has reported, so no group's merge waits behind it
   int n_groups;                // groups of the launch (the extra cluster, if any, comes after them)
-  int lean;                    // 1: a filter step with no group under Alg. 1's test and no codes stored:
-                               // the lean instance runs if every CTA's chunk also fits its registers
+  int lean;                    // 1: no group under Alg. 1's test and no codes stored (a filter step, or
+                               // pf_resample without codes): the lean instance runs if every CTA's chunk
+                               // also fits its registers
   int max_np;                  // the largest group of the launch (for that test)
   int* tile_ctr;               // propagate kernel's tile counter to reset, or nullptr
   GlobalArgs glob;             // (fuse_global) arguments of that step, finalize = 1

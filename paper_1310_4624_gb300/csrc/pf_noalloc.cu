@@ -151,6 +151,9 @@ extern "C" pf_status pf_resample_noalloc(const float* logw, const uint32_t* u, i
     return fail(PF_ERR_CUDA, std::string("k_noalloc_groups: ") + cudaGetErrorString(e));
   ResampleArgs ra{gd, gs, nullptr, logw, nullptr, anc, 0, reinterpret_cast<unsigned long long*>(q), u, 1,
                   resample_coeffs(), ds};
+  ra.n_groups = G;
+  ra.max_np = Np;
+  ra.lean = q ? 0 : 1;  // without codes to store, the lean instance when the chunks fit
   if ((e = launch_resample(ra, G, resample_cluster_size(Np), false, s)) != cudaSuccess)
     return fail(PF_ERR_CUDA, std::string("k_resample: ") + cudaGetErrorString(e));
   return PF_OK;

@@ -68,3 +68,21 @@ def test_resample_repeated_calls_are_deterministic(dev):
     a = resample(lw, u, 8, 20000)
     b = resample(lw, u, 8, 20000)
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("G,Np,kind", CASES)
+def test_resample_without_codes_matches_oracle_bit_exact(dev, G, Np, kind):
+    """Without codes to return, groups whose chunks fit a CTA's registers run
+    the lean instance (ancestors by marking each item's first output and a
+    running maximum); larger groups keep the merge path.  Either way the
+    ancestors equal the oracle's, on the same degenerate, tied and NaN inputs
+    (a single dominant particle's outputs span every CTA of its cluster)."""
+    from paper_1310_4624_gb300.filter import resample
+    rng = np.random.default_rng(G * 7919 + Np)
+    lw = _weights(kind, G, Np, rng)
+    u = rng.integers(0, 2 ** 32, size=G, dtype=np.uint64).astype(np.uint32)
+    anc = resample(torch.from_numpy(lw.ravel()).to(dev), torch.from_numpy(u.view(np.int32)).to(dev), G, Np)
+    anc = anc.cpu().numpy().reshape(G, Np)
+    for g in range(G):
+        ao = ora.resample(ora.quantize(lw[g]), int(u[g]))
+        assert np.array_equal(anc[g], ao), "group %d: %d ancestors differ" % (g, int((anc[g] != ao).sum()))
