@@ -1393,20 +1393,22 @@ __global__ void __launch_bounds__(K1_THREADS, K1_MIN_BLOCKS) k_propagate_weight(
 
   // first tile by block index, the rest from a counter (reset by the
   // resampler), so CTAs finish together however many tiles each ran
-  for (int it = 0; tile < a.n_tiles; ++it) {
-    const int4 td = a.tiles[tile];
-    if (threadIdx.x == 0) {
-      const int nt = stride + atomicAdd(a.tile_ctr, 1);
-      s_next[it & 1] = nt;
-      if (nt < a.n_tiles) prefetch_tile(a, a.tiles[nt], k, pv_prev, I_prev);
+  if constexpr (!FUSED) {  // (the one-launch step has returned above)
+    for (int it = 0; tile < a.n_tiles; ++it) {
+      const int4 td = a.tiles[tile];
+      if (threadIdx.x == 0) {
+        const int nt = stride + atomicAdd(a.tile_ctr, 1);
+        s_next[it & 1] = nt;
+        if (nt < a.n_tiles) prefetch_tile(a, a.tiles[nt], k, pv_prev, I_prev);
+      }
+      bool ok;
+      if constexpr (SINGLE)
+        ok = run_tile(a.p0, td);
+      else
+        ok = run_tile(a.trk[td.x], td);
+      if (!ok) return;
+      tile = s_next[it & 1];  // written before run_tile's barriers; rewritten two tiles later
     }
-    bool ok;
-    if constexpr (SINGLE)
-      ok = run_tile(a.p0, td);
-    else
-      ok = run_tile(a.trk[td.x], td);
-    if (!ok) return;
-    tile = s_next[it & 1];  // written before run_tile's barriers; rewritten two tiles later
   }
 }
 
@@ -1702,7 +1704,6 @@ __device__ __noinline__ void fused_group_finalize(const K1Args& a, int k, int gi
   __shared__ int s_flag, s_pos;
   __shared__ unsigned long long s_w[K1_THREADS / 32];
   __shared__ float s_stat[K1_THREADS / 32][8];
-  const FusedSync fs{a.ring_stride};
   const int par = k & 1;
   const GroupDesc d = a.gd[gi];
   const TrackParams& P = a.trk[d.track];
@@ -1990,7 +1991,6 @@ template <int NTR, bool LEAN>
 __global__ void __launch_bounds__(NTR, NTR >= 512 ? 2 : 8) k_resample(const __grid_constant__ ResampleArgs a) {
   constexpr int SUB = NTR * RS_ITEMS;  // items per sub-chunk
   constexpr int SUB_PAD = pad8(SUB);
-  constexpr int WIN = 2 * SUB;         // merge window: items and outputs merged at once
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
