@@ -3,22 +3,27 @@
 // Paper: Demirel et al., "An Adaptive Distributed Resampling Algorithm with
 // Non-Proportional Allocation" (arXiv:1310.4624).
 //
-// One step k of Alg. 3 (Alg. 2 for RNA) is four launches on one stream:
-//   k_frame_prep        y = z - b into a zero-padded frame (Sec. V model)
+// One step k of Alg. 3 (Alg. 2 for RNA) is two launches on one stream,
+// chained by programmatic dependent launch:
 //   k_propagate_weight  ring exchange composed with the previous resampling
 //                       (Alg. 3 steps 3-4), propagation (Alg. 1 step P),
-//                       likelihood (step U) and per-tile partial sums for
-//                       the group estimate (Alg. 3 step 6)
+//                       likelihood (step U) on frame boxes staged by TMA,
+//                       per-tile partial sums for the group estimate (Alg. 3
+//                       step 6) and the group maxima; its leading blocks
+//                       draw the next step's ring and exchange offsets and
+//                       finish the previous step's statistics
 //   k_resample          per-group exact systematic resampling on fixed-point
 //                       weight codes (Alg. 3 step 7), one thread-block
-//                       cluster per group, partial sums exchanged through
-//                       distributed shared memory
-//   k_global            per track: the master PE's reduction (steps 9-10),
-//                       S10 weight carry (step 8), and the ring order
-//                       (step 1) and exchange count (step 2, Eq. 3/4) of the
-//                       next step
-// The step index lives on the device, so the same launch sequence serves
-// every step.
+//                       cluster per group (code totals and the marks of the
+//                       ancestor search through distributed shared memory);
+//                       the track's global step -- the master PE's
+//                       reduction (steps 9-10), the weight carry (step 8),
+//                       the next ring order (step 1) and exchange count
+//                       (step 2, Eq. 3/4) -- once every group has reported
+// A batch of tracks given device frames first pads them (k_frame_prep);
+// k_global prepares step 0; k_finish / k_finish_out complete the last
+// step's statistics when the host reads them.  The step index lives on the
+// device, so the same launch sequence serves every step.
 #include <cooperative_groups.h>
 #include <mutex>
 #include <utility>
